@@ -1,0 +1,224 @@
+"""FP64 CPU oracle for one ORCA step -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  The GPU library never imports, links or calls it.
+
+The arithmetic lives in ``orca_oracle.c`` (plain C, FP64, neighbour decisions in FP32);
+this module compiles it with gcc and marshals numpy arrays through ctypes.  Every
+function cites the passage of "Fast Simulation of Crowd Collision Avoidance" (or of the
+ORCA method it defers to) that it follows; see the C file's header.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "orca_oracle.c")
+_LIB = os.path.join(_HERE, "liborca_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_F32P = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_F64P = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_I32P = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_U32P = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_I64P = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def compile_source(src: str, out: str) -> str:
+    """gcc -O2, FP contraction off (FP32 decisions must round once per operation)."""
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+            "-shared", src, "-o", out + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(out + ".tmp", out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP if available).  Returns the library path."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        return compile_source(_SRC, _LIB)
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    _lib = _bind(ctypes.CDLL(_LIB))
+    return _lib
+
+
+def _bind(lib):
+    c = ctypes
+    lib.oracle_grid.argtypes = [_F32P, c.c_int, c.c_float, c.c_longlong, _F32P, _I32P]
+    lib.oracle_grid.restype = c.c_int
+    lib.oracle_cells.argtypes = [_F32P, c.c_int, _F32P, _I32P, _U32P]
+    lib.oracle_cells.restype = None
+    lib.oracle_knn.argtypes = [_F32P, c.c_int, c.c_float, c.c_int, c.c_int, c.c_void_p,
+                               c.c_void_p, _I32P, _F32P]
+    lib.oracle_knn.restype = c.c_longlong
+    lib.oracle_orca_line.argtypes = [_F64P, _F64P, c.c_double, c.c_double, c.c_int, c.c_int,
+                                     _F64P, _F64P, _F64P]
+    lib.oracle_orca_line.restype = c.c_int
+    lib.oracle_lp2.argtypes = [_F64P, c.c_int, c.c_double, _F64P, c.c_int, _F64P]
+    lib.oracle_lp2.restype = c.c_int
+    lib.oracle_solve.argtypes = [_F64P, c.c_int, c.c_double, _F64P, _F64P]
+    lib.oracle_solve.restype = c.c_int
+    lib.oracle_step.argtypes = ([c.c_int] + [_F64P] * 7 + [c.c_double, c.c_int, c.c_double,
+                                c.c_int, c.c_int, c.c_void_p, c.c_void_p, c.c_int, _F64P,
+                                _F64P, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p])
+    lib.oracle_step.restype = c.c_int
+    lib.oracle_max_threads.argtypes = []
+    lib.oracle_max_threads.restype = c.c_int
+    return lib
+
+
+class use_library:
+    """Context manager: route this module's calls to another build of the oracle source
+    (the mutation tests compile deliberately broken copies and check that the pins fail)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self._saved = _load()
+        _lib = None
+        _lib = _bind(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def grid(pos, cell_size: float, max_cells: int):
+    """Spatial bins of Fig. 2 (FP32): returns (grid_f=[xmin, ymin, s, 1/s], grid_i=[gx, gy])."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1)
+    gf = np.zeros(4, np.float32)
+    gi = np.zeros(2, np.int32)
+    r = _load().oracle_grid(pos, pos.size // 2, float(cell_size), int(max_cells), gf, gi)
+    if r != 0:
+        raise ValueError(f"oracle_grid failed ({r})")
+    return gf, gi
+
+
+def cells(pos, gf, gi) -> np.ndarray:
+    pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1)
+    out = np.zeros(pos.size // 2, np.uint32)
+    _load().oracle_cells(pos, pos.size // 2, np.ascontiguousarray(gf, np.float32),
+                         np.ascontiguousarray(gi, np.int32), out)
+    return out
+
+
+def knn(pos, neighbor_dist: float, k: int, mode: int = 0, gf=None, gi=None):
+    """Neighbour sets (Fig. 2 filter + k nearest by (d^2, index)), FP32 decisions.
+
+    Returns (nbr int32[n, k] padded with -1, d2 float32[n, k], candidates scanned)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1)
+    n = pos.size // 2
+    nbr = np.zeros(n * k, np.int32)
+    d2 = np.zeros(n * k, np.float32)
+    if mode == 1:
+        gf = np.ascontiguousarray(gf, np.float32)
+        gi = np.ascontiguousarray(gi, np.int32)
+    scanned = _load().oracle_knn(pos, n, float(neighbor_dist), int(k), int(mode), _ptr(gf),
+                                 _ptr(gi), nbr, d2)
+    if scanned < 0:
+        raise ValueError("oracle_knn failed")
+    return nbr.reshape(n, k), d2.reshape(n, k), int(scanned)
+
+
+def orca_line(a, b, tau: float, dt: float, ia: int = 0, ib: int = 1):
+    """Half-plane ORCA_{a|b} (Fig. 1).  a, b = (px, py, vx, vy, r).
+
+    Returns (line [Px, Py, dx, dy], u [ux, uy], branch, margin); branch 0 cutoff circle,
+    1 left leg, 2 right leg, 3 overlapping agents."""
+    line = np.zeros(4)
+    u = np.zeros(2)
+    m = np.zeros(1)
+    br = _load().oracle_orca_line(np.asarray(a, np.float64), np.asarray(b, np.float64),
+                                  float(tau), float(dt), int(ia), int(ib), line, u, m)
+    return line, u, int(br), float(m[0])
+
+
+def lp2(lines, V: float, o, dir_opt: bool = False):
+    """Incremental 2-D LP (Section 3).  Returns (index of failing line or n, x)."""
+    lines = np.ascontiguousarray(lines, np.float64).reshape(-1)
+    x = np.zeros(2)
+    r = _load().oracle_lp2(lines, lines.size // 4, float(V), np.asarray(o, np.float64),
+                           int(bool(dir_opt)), x)
+    return int(r), x
+
+
+def solve(lines, V: float, o):
+    """LP2 then, if infeasible, the least-penetration LP3.  Returns (lp3_used, x)."""
+    lines = np.ascontiguousarray(lines, np.float64).reshape(-1)
+    x = np.zeros(2)
+    r = _load().oracle_solve(lines, lines.size // 4, float(V), np.asarray(o, np.float64), x)
+    return bool(r), x
+
+
+def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_dist: float,
+         max_neighbors: int, dt: float, knn_mode: int = 1, fp64_knn: bool = False,
+         gf=None, gi=None, nthreads: int | None = None):
+    """One synchronous ORCA step (Sections 2-3) in FP64.
+
+    Arrays are promoted to float64.  Returns a dict with pos, vel (float64[n, 2]),
+    nbr (int32[n, k]), lp3 (bool[n]), margin (float64[n]) and counters
+    {scanned, lines, lp1_calls, lp3_agents}."""
+    d = lambda a: np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1))
+    pos, vel, goal = d(pos), d(vel), d(goal)
+    radius, max_speed, pref_speed, time_horizon = d(radius), d(max_speed), d(pref_speed), d(time_horizon)
+    n = pos.size // 2
+    k = int(max_neighbors)
+    pos_out = np.zeros(2 * n)
+    vel_out = np.zeros(2 * n)
+    nbr = np.zeros(max(n * k, 1), np.int32)
+    status = np.zeros(max(n, 1), np.int32)
+    margin = np.zeros(max(n, 1))
+    counters = np.zeros(4, np.int64)
+    if gf is not None:
+        gf = np.ascontiguousarray(gf, np.float32)
+        gi = np.ascontiguousarray(gi, np.int32)
+    r = _load().oracle_step(n, pos, vel, goal, radius, max_speed, pref_speed, time_horizon,
+                            float(neighbor_dist), k, float(dt), int(knn_mode), int(bool(fp64_knn)),
+                            _ptr(gf), _ptr(gi), int(nthreads or max_threads()), pos_out, vel_out,
+                            _ptr(nbr), _ptr(status), _ptr(margin), _ptr(counters))
+    if r != 0:
+        raise ValueError(f"oracle_step failed ({r})")
+    return {
+        "pos": pos_out.reshape(n, 2), "vel": vel_out.reshape(n, 2),
+        "nbr": nbr[: n * k].reshape(n, k), "lp3": status[:n].astype(bool),
+        "margin": margin[:n],
+        "counters": dict(zip(("scanned", "lines", "lp1_calls", "lp3_agents"),
+                             (int(c) for c in counters))),
+    }
+
+
+def step_scene(scene, **kw):
+    """oracle step on a ``scenarios.Scene``'s current state."""
+    return step(scene.pos, scene.vel, scene.goal, scene.radius, scene.max_speed,
+                scene.pref_speed, scene.time_horizon, scene.neighbor_dist,
+                scene.max_neighbors, scene.dt, **kw)

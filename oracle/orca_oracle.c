@@ -1,0 +1,560 @@
+/*
+ * orca_oracle.c -- plain, slow, FP64 CPU oracle for one ORCA crowd-simulation step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library.  The GPU library never includes, links or
+ * calls anything from here, and this file includes nothing from the GPU library.
+ *
+ * What one step computes (Section 3 of "Fast Simulation of Crowd Collision Avoidance",
+ * which defers the ORCA mathematics to van den Berg et al., "Reciprocal n-body
+ * collision avoidance"):
+ *   1. preferred velocity towards the goal at the agent's preferred speed (Section 3,
+ *      first paragraph after Fig. 1; Section 4, test set-up);
+ *   2. spatial bins over the crowd and the observation filter r_obs (Fig. 2);
+ *   3. one ORCA half-plane per observed neighbour: the vector u from the relative
+ *      velocity to the nearest point of the boundary of the truncated velocity
+ *      obstacle VO^tau, and the half-plane through v + u/2 whose normal follows u
+ *      (Fig. 1 a-c);
+ *   4. the 2-D linear program: the velocity closest to the preferred one inside the
+ *      maximum-speed disc and every half-plane (Section 3, batch LP paragraphs),
+ *      solved by an incremental LP (Seidel's method, Section 2, in a fixed order);
+ *   5. when the half-planes have no common point, the velocity that least penetrates
+ *      them (Section 3, "least penetrates"), i.e. the minimum over the disc of the
+ *      largest violation, by the incremental 3-D LP;
+ *   6. all agents adopt their new velocity and move simultaneously (Section 2).
+ *
+ * Precision: every geometric quantity is FP64.  The two integer-valued decisions that
+ * must agree bit for bit with the GPU -- the grid cell of an agent and its neighbour
+ * set -- are taken in FP32 (float operands, one rounding per operation, no FMA: build
+ * with -ffp-contract=off), exactly as the GPU takes them.  In rollout mode (fp64_knn=1)
+ * the neighbour search runs in FP64 instead.
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   - neighbours: the max_neighbors nearest with squared distance strictly below r_obs^2,
+ *     ordered by (d^2, index); this order is also the LP's constraint order;
+ *   - the half-plane passes through v_a + u/2 (reciprocal share; the Fig. 1 caption's
+ *     "v + u" is the non-reciprocal form);
+ *   - overlapping agents (|p| <= R) use the time step dt in place of tau;
+ *   - |w| = 0 in the overlap case: n = -p/|p|, or (+1,0)/(-1,0) by index order when the
+ *     agents coincide;
+ *   - det(p, w) = 0 in the leg case selects the right leg;
+ *   - "clamped near the goal": if |goal - p| <= pref_speed*dt the preferred velocity is
+ *     (goal - p)/dt;
+ *   - parallel-line tolerance eps = 1e-5.
+ *
+ * Ill-conditioning: every branch decision whose outcome can move the result by more
+ * than rounding records its normalised distance to the threshold; the per-agent
+ * minimum ("margin") lets the parity tests set aside agents whose FP32 and FP64
+ * decisions may legitimately differ.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_EPS 1e-5
+#define OR_MAXK 64
+
+typedef struct { double x, y; } v2;
+typedef struct { v2 P, d; } line2;          /* point P, unit direction d; valid side: left of d */
+typedef struct { double m; } tags;            /* running minimum of normalised margins */
+
+static v2 mk(double x, double y) { v2 r; r.x = x; r.y = y; return r; }
+static v2 add(v2 a, v2 b) { return mk(a.x + b.x, a.y + b.y); }
+static v2 sub(v2 a, v2 b) { return mk(a.x - b.x, a.y - b.y); }
+static v2 scl(v2 a, double s) { return mk(a.x * s, a.y * s); }
+static double dot(v2 a, v2 b) { return a.x * b.x + a.y * b.y; }
+static double det2(v2 a, v2 b) { return a.x * b.y - a.y * b.x; }
+static double len(v2 a) { return sqrt(dot(a, a)); }
+
+static void note(tags* t, double value, double threshold, double scale) {
+    if (!t) return;
+    double s = fabs(scale) > 1e-300 ? fabs(scale) : 1e-300;
+    double m = fabs(value - threshold) / s;
+    if (m < t->m) t->m = m;
+}
+
+/* ----------------------------------------------------------------------------------
+ * Uniform grid of spatial bins (Fig. 2).  All arithmetic in FP32.
+ *   xmin/ymin: exact minimum over agents; s: cell edge; inv = fl(1/s);
+ *   gx = floor(fl(fl(xmax - xmin) * inv)) + 1 (same for gy);
+ *   capacity rule: while gx*gy > max_cells, s doubles (exact in FP32).
+ *   cell of (x, y): cx = floor(fl(fl(x - xmin) * inv)) clamped to [0, gx-1], likewise
+ *   cy; cell = cy*gx + cx.
+ * grid_f = {xmin, ymin, s, inv}, grid_i = {gx, gy}.
+ * -------------------------------------------------------------------------------- */
+int oracle_grid(const float* pos, int n, float cell_size, long long max_cells,
+                float* grid_f, int* grid_i) {
+    if (n <= 0 || !(cell_size > 0.0f) || max_cells < 1) return -1;
+    float xmin = pos[0], xmax = pos[0], ymin = pos[1], ymax = pos[1];
+    for (int i = 1; i < n; ++i) {
+        float x = pos[2 * i], y = pos[2 * i + 1];
+        if (x < xmin) xmin = x;
+        if (x > xmax) xmax = x;
+        if (y < ymin) ymin = y;
+        if (y > ymax) ymax = y;
+    }
+    float ex = xmax - xmin, ey = ymax - ymin;
+    float s = cell_size;
+    for (int it = 0; it < 200; ++it) {
+        float inv = 1.0f / s;
+        float fx = floorf(ex * inv), fy = floorf(ey * inv);
+        double cells = ((double)fx + 1.0) * ((double)fy + 1.0);
+        if (cells <= (double)max_cells) {
+            grid_f[0] = xmin; grid_f[1] = ymin; grid_f[2] = s; grid_f[3] = inv;
+            grid_i[0] = (int)fx + 1; grid_i[1] = (int)fy + 1;
+            return 0;
+        }
+        s = s * 2.0f;
+    }
+    return -2;
+}
+
+static int cell_coord(float v, float vmin, float inv, int g) {
+    float q = (v - vmin) * inv;
+    int c = (int)floorf(q);
+    if (c < 0) c = 0;
+    if (c > g - 1) c = g - 1;
+    return c;
+}
+
+void oracle_cells(const float* pos, int n, const float* grid_f, const int* grid_i,
+                  uint32_t* cell) {
+    for (int i = 0; i < n; ++i) {
+        int cx = cell_coord(pos[2 * i], grid_f[0], grid_f[3], grid_i[0]);
+        int cy = cell_coord(pos[2 * i + 1], grid_f[1], grid_f[3], grid_i[1]);
+        cell[i] = (uint32_t)cy * (uint32_t)grid_i[0] + (uint32_t)cx;
+    }
+}
+
+/* ----------------------------------------------------------------------------------
+ * Neighbour sets: for agent i, the k smallest (d^2, j) over j != i with d^2 < r_obs^2.
+ * FP32 mode: dx = fl(xj - xi), dy = fl(yj - yi), d^2 = fl(fl(dx*dx) + fl(dy*dy)),
+ * threshold fl(r_obs*r_obs).  FP64 mode: the same formula in double.
+ * -------------------------------------------------------------------------------- */
+typedef struct { double d2; int j; float d2f; } cand;
+
+static int cand_less(double d2a, int ja, double d2b, int jb) {
+    return d2a < d2b || (d2a == d2b && ja < jb);
+}
+
+static void cand_insert(cand* list, int* cnt, int k, double d2, float d2f, int j) {
+    if (*cnt == k && !cand_less(d2, j, list[k - 1].d2, list[k - 1].j)) return;
+    int p = (*cnt < k) ? (*cnt)++ : k - 1;
+    while (p > 0 && cand_less(d2, j, list[p - 1].d2, list[p - 1].j)) {
+        list[p] = list[p - 1];
+        --p;
+    }
+    list[p].d2 = d2; list[p].j = j; list[p].d2f = d2f;
+}
+
+static void consider(const float* pf, const double* pd, int fp64, int i, int j,
+                     float nd2f, double nd2d, cand* list, int* cnt, int k) {
+    if (j == i) return;
+    if (fp64) {
+        double dx = pd[2 * j] - pd[2 * i], dy = pd[2 * j + 1] - pd[2 * i + 1];
+        double d2 = dx * dx + dy * dy;
+        if (d2 < nd2d) cand_insert(list, cnt, k, d2, (float)d2, j);
+    } else {
+        float dx = pf[2 * j] - pf[2 * i];
+        float dy = pf[2 * j + 1] - pf[2 * i + 1];
+        float dxx = dx * dx;
+        float dyy = dy * dy;
+        float d2 = dxx + dyy;
+        if (d2 < nd2f) cand_insert(list, cnt, k, (double)d2, d2, j);
+    }
+}
+
+/* Cell lists for the grid mode: agents of each cell in ascending index order. */
+typedef struct { int gx, gy; float xmin, ymin, inv; int* start; int* items; } bins;
+
+static int bins_build(bins* b, const float* pf, int n, const float* grid_f, const int* grid_i) {
+    b->gx = grid_i[0]; b->gy = grid_i[1];
+    b->xmin = grid_f[0]; b->ymin = grid_f[1]; b->inv = grid_f[3];
+    long long nc = (long long)b->gx * b->gy;
+    b->start = (int*)calloc((size_t)nc + 1, sizeof(int));
+    b->items = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    uint32_t* cell = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    if (!b->start || !b->items || !cell) { free(cell); return -1; }
+    oracle_cells(pf, n, grid_f, grid_i, cell);
+    for (int i = 0; i < n; ++i) b->start[cell[i] + 1]++;
+    for (long long c = 0; c < nc; ++c) b->start[c + 1] += b->start[c];
+    int* fill = (int*)malloc(sizeof(int) * (size_t)nc);
+    if (!fill) { free(cell); return -1; }
+    memcpy(fill, b->start, sizeof(int) * (size_t)nc);
+    for (int i = 0; i < n; ++i) b->items[fill[cell[i]]++] = i;
+    free(fill);
+    free(cell);
+    return 0;
+}
+
+static void bins_free(bins* b) { free(b->start); free(b->items); }
+
+/* Grid-mode search: every cell overlapping [x - r_obs, x + r_obs] x [y - r_obs, y + r_obs],
+ * widened by one cell on each side to absorb the FP32 rounding of cell indices. */
+static long long knn_grid_one(const bins* b, const float* pf, const double* pd, int fp64,
+                              int i, float ndf, double ndd, cand* list, int* cnt, int k) {
+    float nd2f = ndf * ndf;
+    double nd2d = ndd * ndd;
+    double xi = fp64 ? pd[2 * i] : pf[2 * i], yi = fp64 ? pd[2 * i + 1] : pf[2 * i + 1];
+    double s = 1.0 / (double)b->inv;
+    double rx = (fp64 ? ndd : (double)ndf);
+    long long cx0 = (long long)floor((xi - rx - b->xmin) / s) - 1;
+    long long cx1 = (long long)floor((xi + rx - b->xmin) / s) + 1;
+    long long cy0 = (long long)floor((yi - rx - b->ymin) / s) - 1;
+    long long cy1 = (long long)floor((yi + rx - b->ymin) / s) + 1;
+    if (cx0 < 0) cx0 = 0;
+    if (cy0 < 0) cy0 = 0;
+    if (cx1 > b->gx - 1) cx1 = b->gx - 1;
+    if (cy1 > b->gy - 1) cy1 = b->gy - 1;
+    long long scanned = 0;
+    for (long long cy = cy0; cy <= cy1; ++cy)
+        for (long long cx = cx0; cx <= cx1; ++cx) {
+            long long c = cy * b->gx + cx;
+            for (int q = b->start[c]; q < b->start[c + 1]; ++q) {
+                consider(pf, pd, fp64, i, b->items[q], nd2f, nd2d, list, cnt, k);
+                ++scanned;
+            }
+        }
+    return scanned;
+}
+
+static void knn_brute_one(const float* pf, const double* pd, int fp64, int n, int i,
+                          float ndf, double ndd, cand* list, int* cnt, int k) {
+    float nd2f = ndf * ndf;
+    double nd2d = ndd * ndd;
+    for (int j = 0; j < n; ++j) consider(pf, pd, fp64, i, j, nd2f, nd2d, list, cnt, k);
+}
+
+/* Exported neighbour search (mode 0 brute force, 1 grid).  nbr: n*k, -1 padded;
+ * nbr_d2: the FP32 d^2 of each kept neighbour (0 for padding).  Returns candidates
+ * scanned. */
+long long oracle_knn(const float* pos, int n, float neighbor_dist, int k, int mode,
+                     const float* grid_f, const int* grid_i, int32_t* nbr, float* nbr_d2) {
+    if (k < 1 || k > OR_MAXK) return -1;
+    bins b;
+    long long scanned = 0;
+    if (mode == 1 && bins_build(&b, pos, n, grid_f, grid_i) != 0) return -1;
+    for (int i = 0; i < n; ++i) {
+        cand list[OR_MAXK];
+        int cnt = 0;
+        if (mode == 1) scanned += knn_grid_one(&b, pos, NULL, 0, i, neighbor_dist, 0, list, &cnt, k);
+        else { knn_brute_one(pos, NULL, 0, n, i, neighbor_dist, 0, list, &cnt, k); scanned += n - 1; }
+        for (int q = 0; q < k; ++q) {
+            nbr[(size_t)i * k + q] = q < cnt ? list[q].j : -1;
+            if (nbr_d2) nbr_d2[(size_t)i * k + q] = q < cnt ? list[q].d2f : 0.0f;
+        }
+    }
+    if (mode == 1) bins_free(&b);
+    return scanned;
+}
+
+/* ----------------------------------------------------------------------------------
+ * ORCA half-plane of agent a induced by neighbour b (Fig. 1).
+ *   p = p_b - p_a, v = v_a - v_b, R = r_a + r_b.
+ *   |p|^2 > R^2 (apart): w = v - p/tau.
+ *     cutoff circle when w.p < 0 and (w.p)^2 > R^2 |w|^2: n = w/|w|,
+ *       u = (R/tau - |w|) n, d = (n_y, -n_x);
+ *     otherwise a leg, l = sqrt(|p|^2 - R^2): left leg if det(p, w) > 0,
+ *       d = (p_x l - p_y R, p_x R + p_y l)/|p|^2; right leg otherwise,
+ *       d = -(p_x l + p_y R, -p_x R + p_y l)/|p|^2; u = (v.d) d - v.
+ *   |p|^2 <= R^2 (overlap): the same cutoff construction with dt in place of tau.
+ *   P = v_a + u/2.  Branch codes: 0 cutoff, 1 left leg, 2 right leg, 3 overlap.
+ * -------------------------------------------------------------------------------- */
+static line2 orca_line(v2 pa, v2 va, double ra, v2 pb, v2 vb, double rb, double tau,
+                       double dt, int ia, int ib, tags* tg, int* branch, v2* u_out) {
+    v2 p = sub(pb, pa), v = sub(va, vb);
+    double R = ra + rb, p2 = dot(p, p), R2 = R * R;
+    line2 L;
+    v2 u;
+    int br;
+    note(tg, p2, R2, R2);
+    if (p2 > R2) {
+        v2 w = sub(v, scl(p, 1.0 / tau));
+        double w2 = dot(w, w), wp = dot(w, p);
+        if (wp < 0.0 && wp * wp > R2 * w2) {
+            double wl = sqrt(w2);
+            v2 nrm = scl(w, 1.0 / wl);
+            L.d = mk(nrm.y, -nrm.x);
+            u = scl(nrm, R / tau - wl);
+            br = 0;
+        } else {
+            double leg = sqrt(p2 - R2);
+            double side = det2(p, w);
+            note(tg, side, 0.0, sqrt(p2 * w2));
+            if (side > 0.0) {
+                L.d = scl(mk(p.x * leg - p.y * R, p.x * R + p.y * leg), 1.0 / p2);
+                br = 1;
+            } else {
+                L.d = scl(mk(p.x * leg + p.y * R, -p.x * R + p.y * leg), -1.0 / p2);
+                br = 2;
+            }
+            u = sub(scl(L.d, dot(v, L.d)), v);
+        }
+    } else {
+        v2 w = sub(v, scl(p, 1.0 / dt));
+        double wl = len(w);
+        v2 nrm;
+        if (wl > 0.0) nrm = scl(w, 1.0 / wl);
+        else if (p2 > 0.0) nrm = scl(p, -1.0 / sqrt(p2));
+        else nrm = mk(ia < ib ? 1.0 : -1.0, 0.0);
+        L.d = mk(nrm.y, -nrm.x);
+        u = scl(nrm, R / dt - wl);
+        br = 3;
+    }
+    L.P = add(va, scl(u, 0.5));
+    if (branch) *branch = br;
+    if (u_out) *u_out = u;
+    return L;
+}
+
+/* ----------------------------------------------------------------------------------
+ * LP1: best point on line i inside the disc |x| <= V and the half-planes 0..i-1.
+ * Parametrise x(t) = P_i + t d_i.  The disc gives t in [-a - sqrt(D), -a + sqrt(D)],
+ * a = P_i.d_i, D = a^2 + V^2 - |P_i|^2.  Half-plane j bounds t by num/den with
+ * den = det(d_i, d_j), num = det(d_j, P_i - P_j): an upper bound when den > 0, a lower
+ * one when den < 0; a (nearly) parallel j (|den| <= eps) is infeasible iff num < 0.
+ * Objective: direction mode (maximise o.x) picks the end of the interval along o;
+ * otherwise the projection of o onto the line, clamped to the interval.
+ * Returns 1 and writes *x on success, 0 when the interval is empty.
+ * -------------------------------------------------------------------------------- */
+static int lp1(const line2* L, int i, double V, v2 o, int dir_opt, v2* x, tags* tg,
+               long long* work) {
+    double a = dot(L[i].P, L[i].d);
+    double D = a * a + V * V - dot(L[i].P, L[i].P);
+    note(tg, D, 0.0, V * V);
+    if (D < 0.0) return 0;
+    double sq = sqrt(D);
+    double tL = -a - sq, tR = -a + sq;
+    for (int j = 0; j < i; ++j) {
+        double den = det2(L[i].d, L[j].d);
+        double num = det2(L[j].d, sub(L[i].P, L[j].P));
+        if (work) ++*work;
+        note(tg, fabs(den), OR_EPS, OR_EPS);
+        if (fabs(den) <= OR_EPS) {
+            note(tg, num, 0.0, V);
+            if (num < 0.0) return 0;
+            continue;
+        }
+        double t = num / den;
+        if (den >= 0.0) { if (t < tR) tR = t; }
+        else { if (t > tL) tL = t; }
+        if (tL > tR) { note(tg, tL, tR, V); return 0; }
+    }
+    note(tg, tL, tR, V);
+    if (dir_opt) {
+        double od = dot(o, L[i].d);
+        note(tg, od, 0.0, 1.0);
+        *x = add(L[i].P, scl(L[i].d, od > 0.0 ? tR : tL));
+    } else {
+        double t = dot(L[i].d, sub(o, L[i].P));
+        if (t < tL) t = tL;
+        if (t > tR) t = tR;
+        *x = add(L[i].P, scl(L[i].d, t));
+    }
+    return 1;
+}
+
+/* LP2: incremental 2-D LP over lines 0..n-1 in order.  Start point: V*o in direction
+ * mode (o a unit vector), else o pulled onto the disc if outside it.  A line whose valid
+ * side does not contain x (det(d_i, P_i - x) > 0) moves x onto it by LP1.  Returns n on
+ * success, else the index of the line where LP1 found no point (x keeps its last
+ * feasible value). */
+static int lp2(const line2* L, int n, double V, v2 o, int dir_opt, v2* x, tags* tg,
+               long long* work) {
+    if (dir_opt) *x = scl(o, V);
+    else if (dot(o, o) > V * V) *x = scl(o, V / len(o));
+    else *x = o;
+    for (int i = 0; i < n; ++i) {
+        double viol = det2(L[i].d, sub(L[i].P, *x));
+        note(tg, viol, 0.0, V);
+        if (viol > 0.0) {
+            v2 keep = *x;
+            if (work) ++*work;
+            if (!lp1(L, i, V, o, dir_opt, x, tg, work)) { *x = keep; return i; }
+        }
+    }
+    return n;
+}
+
+/* LP3: least-penetration fallback (Section 3).  Minimises, over the disc, the largest
+ * violation max_i det(d_i, P_i - x), starting from line `begin` with penetration 0.
+ * When line i is violated by more than the current penetration, the optimum lies on
+ * the set where line i's violation equals the others'; each earlier line j gives the
+ * bisecting half-plane (through the intersection of lines i and j, direction
+ * normalise(d_j - d_i); parallel lines of opposite direction give the midline, parallel
+ * lines of the same direction give no constraint), and LP2 in direction mode maximises
+ * progress along the normal (-d_i.y, d_i.x).  A numerically failed LP2 keeps x. */
+static void lp3(const line2* L, int n, int begin, double V, v2* x, tags* tg,
+                long long* work) {
+    line2 proj[OR_MAXK];
+    double dist = 0.0;
+    for (int i = begin; i < n; ++i) {
+        double pen = det2(L[i].d, sub(L[i].P, *x));
+        note(tg, pen, dist, V);
+        if (pen > dist) {
+            int m = 0;
+            for (int j = 0; j < i; ++j) {
+                line2 q;
+                double den = det2(L[i].d, L[j].d);
+                note(tg, fabs(den), OR_EPS, OR_EPS);
+                if (fabs(den) <= OR_EPS) {
+                    if (dot(L[i].d, L[j].d) > 0.0) continue;
+                    q.P = scl(add(L[i].P, L[j].P), 0.5);
+                } else {
+                    q.P = add(L[i].P, scl(L[i].d, det2(L[j].d, sub(L[i].P, L[j].P)) / den));
+                }
+                v2 dd = sub(L[j].d, L[i].d);
+                q.d = scl(dd, 1.0 / len(dd));
+                proj[m++] = q;
+            }
+            v2 keep = *x;
+            if (work) ++*work;
+            if (lp2(proj, m, V, mk(-L[i].d.y, L[i].d.x), 1, x, tg, work) < m) *x = keep;
+            dist = det2(L[i].d, sub(L[i].P, *x));
+        }
+    }
+}
+
+/* ----------------------------------------------------------------------------------
+ * Exported building blocks (for pins).  lines: n*4 doubles {Px, Py, dx, dy}.
+ * -------------------------------------------------------------------------------- */
+int oracle_orca_line(const double* a /* px,py,vx,vy,r */, const double* b, double tau,
+                     double dt, int ia, int ib, double* line4, double* u2, double* margin) {
+    tags tg = {1e300};
+    int br;
+    v2 u;
+    line2 L = orca_line(mk(a[0], a[1]), mk(a[2], a[3]), a[4], mk(b[0], b[1]), mk(b[2], b[3]),
+                        b[4], tau, dt, ia, ib, &tg, &br, &u);
+    line4[0] = L.P.x; line4[1] = L.P.y; line4[2] = L.d.x; line4[3] = L.d.y;
+    if (u2) { u2[0] = u.x; u2[1] = u.y; }
+    if (margin) *margin = tg.m;
+    return br;
+}
+
+static void unpack(const double* lines, int n, line2* L) {
+    for (int i = 0; i < n; ++i) {
+        L[i].P = mk(lines[4 * i], lines[4 * i + 1]);
+        L[i].d = mk(lines[4 * i + 2], lines[4 * i + 3]);
+    }
+}
+
+int oracle_lp2(const double* lines, int n, double V, const double* o, int dir_opt,
+               double* x2) {
+    line2 L[OR_MAXK];
+    if (n < 0 || n > OR_MAXK) return -1;
+    unpack(lines, n, L);
+    v2 x;
+    int r = lp2(L, n, V, mk(o[0], o[1]), dir_opt, &x, NULL, NULL);
+    x2[0] = x.x; x2[1] = x.y;
+    return r;
+}
+
+/* Full velocity selection: LP2, then LP3 from the failing line.  Returns 1 if LP3 ran. */
+int oracle_solve(const double* lines, int n, double V, const double* o, double* x2) {
+    line2 L[OR_MAXK];
+    if (n < 0 || n > OR_MAXK) return -1;
+    unpack(lines, n, L);
+    v2 x;
+    int b = lp2(L, n, V, mk(o[0], o[1]), 0, &x, NULL, NULL);
+    if (b < n) lp3(L, n, b, V, &x, NULL, NULL);
+    x2[0] = x.x; x2[1] = x.y;
+    return b < n;
+}
+
+/* Preferred velocity: towards the goal at pref_speed; within one step of the goal,
+ * the velocity that reaches it in one step. */
+static v2 pref_velocity(v2 p, v2 goal, double pref_speed, double dt) {
+    v2 g = sub(goal, p);
+    double dist = len(g);
+    if (dist > pref_speed * dt) return scl(g, pref_speed / dist);
+    return scl(g, 1.0 / dt);
+}
+
+/* ----------------------------------------------------------------------------------
+ * One synchronous step for n agents.
+ * Inputs (length n or 2n, FP64; promote FP32 state for parity runs):
+ *   pos, vel, goal (x,y interleaved), radius, max_speed, pref_speed, time_horizon.
+ * Scene parameters: neighbor_dist (r_obs), k = max_neighbors, dt.
+ * knn_mode: 0 brute force, 1 grid (grid_f/grid_i from oracle_grid; NULL -> cell = r_obs).
+ * fp64_knn: 0 -> neighbour search in FP32 on (float)pos; 1 -> in FP64.
+ * Outputs: pos_out, vel_out (2n), nbr (n*k, -1 padded, may be NULL), status (n: bit0 LP3
+ * used, may be NULL), margin (n, may be NULL), counters[4] = {candidates scanned,
+ * lines built, LP1 calls (incl. inside LP3), agents needing LP3} (may be NULL).
+ * Returns 0, or a negative value on bad arguments / allocation failure.
+ * -------------------------------------------------------------------------------- */
+int oracle_step(int n, const double* pos, const double* vel, const double* goal,
+                const double* radius, const double* max_speed, const double* pref_speed,
+                const double* time_horizon, double neighbor_dist, int k, double dt,
+                int knn_mode, int fp64_knn, const float* grid_f_in, const int* grid_i_in,
+                int nthreads, double* pos_out, double* vel_out, int32_t* nbr,
+                int32_t* status, double* margin, long long* counters) {
+    if (n < 0 || k < 1 || k > OR_MAXK || !(dt > 0.0)) return -1;
+    if (counters) memset(counters, 0, 4 * sizeof(long long));
+    if (n == 0) return 0;
+    float* pf = (float*)malloc(sizeof(float) * 2 * (size_t)n);
+    if (!pf) return -2;
+    for (long long q = 0; q < 2LL * n; ++q) pf[q] = (float)pos[q];
+    float ndf = (float)neighbor_dist;
+    bins b;
+    int have_bins = 0;
+    if (knn_mode == 1) {
+        float gf[4];
+        int gi[2];
+        if (grid_f_in && grid_i_in) { memcpy(gf, grid_f_in, sizeof gf); memcpy(gi, grid_i_in, sizeof gi); }
+        else if (oracle_grid(pf, n, ndf, (long long)4 * n + 1024, gf, gi) != 0) { free(pf); return -3; }
+        if (bins_build(&b, pf, n, gf, gi) != 0) { free(pf); return -2; }
+        have_bins = 1;
+    }
+    long long c_scan = 0, c_lines = 0, c_work = 0, c_lp3 = 0;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads) reduction(+ : c_scan, c_lines, c_work, c_lp3)
+#endif
+    for (int i = 0; i < n; ++i) {
+        cand list[OR_MAXK];
+        line2 L[OR_MAXK];
+        int cnt = 0;
+        tags tg = {1e300};
+        if (have_bins) c_scan += knn_grid_one(&b, pf, pos, fp64_knn, i, ndf, neighbor_dist, list, &cnt, k);
+        else { knn_brute_one(pf, pos, fp64_knn, n, i, ndf, neighbor_dist, list, &cnt, k); c_scan += n - 1; }
+        v2 pa = mk(pos[2 * i], pos[2 * i + 1]), va = mk(vel[2 * i], vel[2 * i + 1]);
+        for (int q = 0; q < cnt; ++q) {
+            int j = list[q].j;
+            L[q] = orca_line(pa, va, radius[i], mk(pos[2 * j], pos[2 * j + 1]),
+                             mk(vel[2 * j], vel[2 * j + 1]), radius[j], time_horizon[i], dt,
+                             i, j, &tg, NULL, NULL);
+        }
+        c_lines += cnt;
+        v2 pv = pref_velocity(pa, mk(goal[2 * i], goal[2 * i + 1]), pref_speed[i], dt);
+        v2 x;
+        long long w = 0;
+        int bfail = lp2(L, cnt, max_speed[i], pv, 0, &x, &tg, &w);
+        int used3 = bfail < cnt;
+        if (used3) { lp3(L, cnt, bfail, max_speed[i], &x, &tg, &w); ++c_lp3; }
+        c_work += w;
+        vel_out[2 * i] = x.x;
+        vel_out[2 * i + 1] = x.y;
+        pos_out[2 * i] = pa.x + x.x * dt;
+        pos_out[2 * i + 1] = pa.y + x.y * dt;
+        if (nbr) for (int q = 0; q < k; ++q) nbr[(size_t)i * k + q] = q < cnt ? list[q].j : -1;
+        if (status) status[i] = used3;
+        if (margin) margin[i] = tg.m;
+    }
+    if (have_bins) bins_free(&b);
+    free(pf);
+    if (counters) { counters[0] = c_scan; counters[1] = c_lines; counters[2] = c_work; counters[3] = c_lp3; }
+    return 0;
+}
+
+/* Number of OpenMP threads the oracle would use by default (1 without OpenMP). */
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,157 @@
+"""Seeded synthetic crowd generators.
+
+This module only draws initial agent states and per-agent parameters; it holds none
+of the ORCA step's arithmetic (no preferred velocity, no cells, no half-planes, no
+LP).  The GPU path, the CPU oracle, the tests and the benchmark all start from the
+arrays produced here, so both sides of every parity check consume identical FP32
+values.
+
+The workloads stand in for the paper's test cases (Section 4): the two-way crossing
+(two crowds in opposite bands, each heading for the far side) and the N-way
+crossing, whose limit is the circle swap (every agent heads for its antipode).
+The paper uses no public dataset; all inputs here are synthetic.
+
+Every array is float32, length ``n`` (or ``2n`` for interleaved x/y pairs).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Scene:
+    """One crowd: FP32 agent state plus the scene-wide ORCA parameters.
+
+    pos, vel, goal: float32[n, 2] (x, y interleaved in memory).
+    radius, max_speed, pref_speed, time_horizon: float32[n].
+    neighbor_dist (r_obs of Fig. 2), max_neighbors, dt: scene-wide.
+    """
+
+    name: str
+    pos: np.ndarray
+    vel: np.ndarray
+    goal: np.ndarray
+    radius: np.ndarray
+    max_speed: np.ndarray
+    pref_speed: np.ndarray
+    time_horizon: np.ndarray
+    neighbor_dist: float
+    max_neighbors: int
+    dt: float
+    steps: int
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+    def arrays(self):
+        return (self.pos, self.vel, self.goal, self.radius, self.max_speed,
+                self.pref_speed, self.time_horizon)
+
+    def copy(self) -> "Scene":
+        return dataclasses.replace(self, **{f: getattr(self, f).copy() for f in
+                                            ("pos", "vel", "goal", "radius", "max_speed",
+                                             "pref_speed", "time_horizon")})
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _full(n, v) -> np.ndarray:
+    return np.full(n, v, dtype=np.float32)
+
+
+def circle_swap(n: int = 1024, circle_radius: float = 100.0, agent_radius: float = 0.5,
+                max_speed: float = 2.0, neighbor_dist: float = 15.0, max_neighbors: int = 10,
+                time_horizon: float = 10.0, dt: float = 0.25, steps: int = 100) -> Scene:
+    """Agents evenly spaced on a circle, each heading for the antipodal point.
+
+    Agent i sits at angle 2*pi*i/n; its goal is the point opposite.  With 1,024 agents
+    on a 100 m circle the arc spacing (0.614 m) is below the radius sum (1.0 m), so
+    neighbours start in contact.  Initial velocity is zero; preferred speed equals the
+    maximum speed.
+    """
+    ang = 2.0 * np.pi * np.arange(n, dtype=np.float64) / max(n, 1)
+    pos = np.stack([circle_radius * np.cos(ang), circle_radius * np.sin(ang)], axis=1)
+    pos = _f32(pos)
+    return Scene("circle_swap", pos, np.zeros_like(pos), _f32(-pos), _full(n, agent_radius),
+                 _full(n, max_speed), _full(n, max_speed), _full(n, time_horizon),
+                 neighbor_dist, max_neighbors, dt, steps)
+
+
+def bidirectional(n: int = 524288, seed: int = 1909, side: float | None = None,
+                  neighbor_dist: float = 10.0, max_neighbors: int = 10,
+                  time_horizon: float = 5.0, dt: float = 1.0 / 60.0, steps: int = 600,
+                  radius_range=(0.3, 0.5), speed_range=(1.2, 1.6)) -> Scene:
+    """Two-way crossing: two equal crowds in opposite bands of an open square.
+
+    Half the agents are uniform in the left quarter-width band, half in the right one;
+    each agent's goal is the same point shifted by three quarters of the side towards
+    the far side.  At 524,288 agents the square is 1 km (density ~1.05 agents/m^2 in
+    the bands).  For other counts the side scales with sqrt(n) so the density stays
+    the same.  radius ~ U[0.3, 0.5] m, max speed = preferred speed ~ U[1.2, 1.6] m/s.
+    Initial velocity is zero.
+    """
+    rng = np.random.default_rng(seed)
+    if side is None:
+        side = 1000.0 * math.sqrt(n / 524288.0)
+    band = 0.25 * side
+    h = n // 2
+    x = np.empty(n)
+    x[:h] = rng.uniform(0.0, band, h)
+    x[h:] = rng.uniform(side - band, side, n - h)
+    y = rng.uniform(0.0, side, n)
+    gx = np.where(np.arange(n) < h, x + 0.75 * side, x - 0.75 * side)
+    pos = _f32(np.stack([x, y], axis=1))
+    goal = _f32(np.stack([gx, y], axis=1))
+    radius = _f32(rng.uniform(radius_range[0], radius_range[1], n))
+    speed = _f32(rng.uniform(speed_range[0], speed_range[1], n))
+    return Scene("bidirectional", pos, np.zeros_like(pos), goal, radius, speed, speed.copy(),
+                 _full(n, time_horizon), neighbor_dist, max_neighbors, dt, steps)
+
+
+def dense(n: int = 2097152, seed: int = 1910, side: float | None = None,
+          neighbor_dist: float = 8.0, max_neighbors: int = 20, time_horizon: float = 4.0,
+          dt: float = 1.0 / 60.0, steps: int = 300, agent_radius: float = 0.4,
+          max_speed: float = 1.5) -> Scene:
+    """Dense stress: agents and goals uniform in a square (2 km at 2,097,152 agents).
+
+    For other counts the side scales with sqrt(n) (density ~0.52 agents/m^2).
+    """
+    rng = np.random.default_rng(seed)
+    if side is None:
+        side = 2000.0 * math.sqrt(n / 2097152.0)
+    pos = _f32(rng.uniform(0.0, side, (n, 2)))
+    goal = _f32(rng.uniform(0.0, side, (n, 2)))
+    return Scene("dense", pos, np.zeros_like(pos), goal, _full(n, agent_radius),
+                 _full(n, max_speed), _full(n, max_speed), _full(n, time_horizon),
+                 neighbor_dist, max_neighbors, dt, steps)
+
+
+def jitter_velocities(scene: Scene, seed: int, scale: float = 1.0) -> Scene:
+    """Return a copy whose velocities are random (|v| <= scale * max_speed).
+
+    Used by parity tests so that every half-plane branch (cutoff, both legs,
+    collision) occurs from the first step.
+    """
+    rng = np.random.default_rng(seed)
+    s = scene.copy()
+    ang = rng.uniform(0.0, 2.0 * np.pi, s.n)
+    mag = rng.uniform(0.0, scale, s.n) * s.max_speed.astype(np.float64)
+    s.vel = _f32(np.stack([mag * np.cos(ang), mag * np.sin(ang)], axis=1))
+    return s
+
+
+def scene_by_name(name: str, n: int | None = None, seed: int | None = None) -> Scene:
+    """The three single-scene workloads by name, optionally rescaled to ``n`` agents."""
+    if name == "circle_swap":
+        return circle_swap(n or 1024)
+    if name == "bidirectional":
+        return bidirectional(n or 524288, seed=1909 if seed is None else seed)
+    if name == "dense":
+        return dense(n or 2097152, seed=1910 if seed is None else seed)
+    raise ValueError(f"unknown scene {name!r}")
