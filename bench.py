@@ -1,0 +1,381 @@
+"""Benchmark: ORCA agent-steps/s on one GB300 (or N replicas, one per GPU).
+
+Workload: bidirectional flow, 524,288 agents (two crowds in opposite quarter-width bands of
+a 1 km square, radius U[0.3, 0.5] m, speed U[1.2, 1.6] m/s, r_obs 10 m, k = 10,
+tau 5 s, dt 1/60 s), seeded synthetic data.  A step is one full ORCA step (binning, sort,
+neighbour search, half-planes, LP, integrate) through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: W untimed steps, then K steps, each bracketed by CUDA events on the launching
+stream with a 256 MiB buffer write (larger than the 129 MB L2) between steps; the sum of
+the K step durations is the device time.  Barrier + synchronize on both sides, max over
+ranks.  Prints one JSON line on rank 0.
+
+--impl reference times the FP64 CPU oracle (the "reference arm") on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ORCA agent-steps/sec at 524,288 agents; ms/step; % of HBM roofline"
+UNIT = "agent-steps/s"
+WORKLOAD = ("bidirectional flow, 524,288 agents (two crowds in opposite 250 m bands of a 1 km "
+            "square), radius U[0.3,0.5] m, speed U[1.2,1.6] m/s, r_obs 10 m, k 10, tau 5 s, dt 1/60 s")
+# algorithmic HBM bytes per agent of the per-agent ORCA kernel: read pos, vel, goal (8 B
+# each), radius, max speed, pref speed, tau, id (4 B each); write pos, vel (8 B each).
+# Neighbour reads are re-reads of the cell-sorted copy and are not counted.
+ORCA_KERNEL_BYTES_PER_AGENT = 44 + 16
+
+
+def step_bytes_per_agent(passes: int) -> int:
+    """Algorithmic HBM bytes per agent of one whole step (see the design notes):
+    bbox 8, keys 12, radix passes (12 for pass 0, 20 after), cell table ~5, reorder 92,
+    ORCA kernel 60."""
+    return 8 + 12 + 12 + 20 * max(passes - 1, 0) + 5 + 92 + ORCA_KERNEL_BYTES_PER_AGENT
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash() -> str:
+    src = os.path.join(ROOT, "paper_1908_10107_gb300", "csrc", "orca_main.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the ORCA kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "orca_main_bidirectional_524288.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if h and t and h.group(1) == kernel_hash():
+        return float(t.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, out_path: str | None = None):
+        self.proc = None
+        self.lines = []
+        self.idx = device_index
+        self.out_path = out_path
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        self.lines = [l for l in out.splitlines() if l.strip()]
+        if self.out_path:
+            try:
+                with open(self.out_path, "w") as f:
+                    f.write(self.FIELDS + "\n" + "\n".join(self.lines) + "\n")
+            except Exception:
+                pass
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def device_smi_index(torch, dev: int) -> int:
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id,
+                                    props.pci_device_id)
+        out = subprocess.run(["nvidia-smi", "--query-gpu=index,pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=20).stdout
+        for line in out.splitlines():
+            i, b = [x.strip() for x in line.split(",")]
+            if b.lower().endswith(bus[-7:].lower()) and b.lower().split(":")[-2:] == bus.lower().split(":")[-2:]:
+                return int(i)
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis and vis.split(",")[0].strip().isdigit():
+        return int(vis.split(",")[dev].strip())
+    return dev
+
+
+def cpu_baseline(scene, budget_s: float = 12.0, max_steps: int = 4):
+    """The FP64 oracle (grid neighbour search, OpenMP over agents) on the host cores:
+    whole steps of the full crowd, repeated until the budget is used."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    st = scene.copy()
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < budget_s):
+        r = oracle.step_scene(st, knn_mode=1)
+        st.pos = r["pos"].astype(np.float32)
+        st.vel = r["vel"].astype(np.float32)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": scene.n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} whole steps of the {scene.n:,}-agent crowd (FP64, grid search, "
+                      f"OpenMP {cores} threads), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle timed on the host, same metric and workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1908_10107_gb300 import scenarios
+    oracle.build()
+    cores = oracle.max_threads()
+    sc = scenarios.bidirectional()
+    m = args.ref_sample
+    subset = np.sort(np.random.default_rng(7).choice(sc.n, m, replace=False))
+    for _ in range(args.warmup):
+        oracle.step_scene(sc, knn_mode=1, subset=subset)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step_scene(sc, knn_mode=1, subset=subset)
+    dt = time.perf_counter() - t0
+    value = m * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "n_agents": sc.n, "sample_agents_per_step": m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{m} sampled agents of the {sc.n:,}-agent crowd per step "
+                                   f"(neighbours searched among all agents), FP64, {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--agents", type=int, default=524288)
+    ap.add_argument("--cell-size", type=float, default=0.0)
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--clocks-out", default=None)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1908_10107_gb300 import abi, build, scenarios
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+
+    sc = scenarios.bidirectional(args.agents)
+    sim = abi.OrcaSim.for_scene(sc, cell_size=args.cell_size)
+    sim.set_scene(sc)
+    abi.orca_profile(sim.ctx, True)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phases = np.zeros((args.steps, 3))
+    sampler = ClockSampler(device_smi_index(torch, local), args.clocks_out)
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.15)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        ev_s[k].record(stream)
+        sim.step(1)
+        ev_e[k].record(stream)
+        phases[k] = abi.orca_profile_read(sim.ctx)
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = np.array([ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)])
+    total_ms = float(step_ms.sum())
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sim.sync()
+
+    n = sc.n
+    value = world * n * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+    main_ms = float(phases[:, 2].mean())
+    hbm_peak, peak_kind = peaks()
+    _, gf, gi = None, None, None
+    c_cells = int(sim.params.max_cells) or min(max(4 * n, 65536), 1 << 30)
+    achieved = ORCA_KERNEL_BYTES_PER_AGENT * n / (main_ms * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    counters = sim.counters()
+    launches = abi.orca_launches_per_step(sim.ctx) * args.steps
+
+    # passes actually needed this step (for the whole-step byte model)
+    grid_cells = None
+    try:
+        sim_rec = abi.OrcaSim.for_scene(sc, cell_size=args.cell_size, flags=abi.ORCA_FLAG_RECORD)
+        sim_rec.set_scene(sc)
+        sim_rec.step(1)
+        _, gf, gi = sim_rec.get_cells()
+        grid_cells = int(gi[0]) * int(gi[1])
+        sim_rec.close()
+    except Exception:
+        pass
+    passes = max(1, math.ceil(math.log2(max(grid_cells or c_cells, 2)) / 8))
+    step_bytes = step_bytes_per_agent(passes)
+
+    # end to end through the C ABI with pinned host buffers: upload, step, read back
+    pinned = [torch.from_numpy(a).pin_memory().numpy() for a in sc.arrays()]
+    out_pos = torch.empty((n, 2), dtype=torch.float32).pin_memory().numpy()
+    out_vel = torch.empty((n, 2), dtype=torch.float32).pin_memory().numpy()
+    abi.orca_profile(sim.ctx, False)
+    sim.set_agents(*pinned)
+    sim.step(1)
+    sim.get_state()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        abi.orca_set_agents(sim.ctx, n, *pinned, stream=stream)
+        sim.step(1)
+        abi.orca_get_state(sim.ctx, out_pos, out_vel, stream=stream)
+    e2e_dt = time.perf_counter() - t0
+    e2e_val = n * args.e2e_steps / e2e_dt
+    if dist:
+        t = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * n * args.e2e_steps / float(t.item())
+    h2d = sum(a.nbytes for a in pinned)
+    d2h = out_pos.nbytes + out_vel.nbytes
+    sim.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "n_agents": n, "replicas": world,
+                   "cell_size_m": float(gf[2]) if gf is not None else None,
+                   "grid": [int(gi[0]), int(gi[1])] if gi is not None else None,
+                   "l2": "flushed between steps (256 MiB write); per-step CUDA events summed",
+                   "graph": "one CUDA graph replay per step"},
+        "roofline": {"kernel": "orca_main (neighbours + half-planes + LP + integrate)",
+                     "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "alg_bytes_per_agent": ORCA_KERNEL_BYTES_PER_AGENT,
+                     "launch_ms": main_ms, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6800 GB/s"},
+        "step_roofline": {"bound": "hbm", "alg_bytes_per_agent": step_bytes,
+                          "achieved": step_bytes * n / (ms_per_step * 1e-3) / 1e9,
+                          "peak": hbm_peak, "unit": "GB/s",
+                          "frac": step_bytes * n / (ms_per_step * 1e-3) / 1e9 / hbm_peak},
+        "phases_ms": {"binning": float(phases[:, 0].mean()), "reorder": float(phases[:, 1].mean()),
+                      "orca_kernel": main_ms},
+        "lp3_fraction": counters["lp3_agent_steps"] / max(counters["agent_steps"], 1),
+        "candidates_per_agent": counters["candidates"] / max(counters["agent_steps"], 1),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "wall_s_timed_region": wall1 - wall0,
+        "kernel_source_sha256_16": kernel_hash(),
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * orca_gb300.h -- C ABI of the GB300 (sm_103a) ORCA crowd-simulation step.
+ *
+ * One call to orca_step advances every agent by one synchronous ORCA step
+ * ("Fast Simulation of Crowd Collision Avoidance", Section 3; all agents update
+ * simultaneously, Section 2):
+ *   1. preferred velocity towards the goal at the preferred speed (Section 3, first
+ *      paragraph after Fig. 1; Section 4 test set-up);
+ *   2. agents binned into a uniform grid of square cells (Fig. 2), sorted by cell;
+ *   3. each agent's neighbours: the max_neighbors nearest agents whose squared distance is
+ *      strictly below neighbor_dist^2 (the observation radius r_obs of Fig. 2), nearest
+ *      first, equal distances broken by lower agent index;
+ *   4. one ORCA half-plane per neighbour from the relative position, relative velocity,
+ *      radius sum and time horizon (Fig. 1 a-c);
+ *   5. the velocity closest to the preferred velocity inside the maximum-speed disc and
+ *      all half-planes, or, when they have no common point, the velocity that least
+ *      penetrates them (Section 3, LP paragraphs);
+ *   6. velocity and position update, pos += vel * dt.
+ *
+ * Conventions
+ *   - Every function returns an int status: ORCA_OK (0) or a negative ORCA_ERR_* code.
+ *     orca_last_error() gives a message for the last failure on a context.  No C++
+ *     exception crosses this ABI; the library never exits, aborts or traps the GPU.
+ *   - Arrays are FP32 structure-of-arrays indexed by agent (the order of
+ *     orca_set_agents).  "xy" arrays hold interleaved (x, y) pairs, 2*n floats.
+ *   - `where` says whether a pointer is host memory (ORCA_HOST) or device memory on the
+ *     context's GPU (ORCA_DEVICE).  Host pointers need not be pinned; with pinned memory
+ *     copies overlap better.  The caller keeps ownership of every pointer it passes.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is enqueued
+ *     asynchronously on it; calls that return data to the host synchronise it.  All calls
+ *     on one context must be ordered on the same stream (or ordered by the caller).
+ *   - Errors detected on the device (non-finite velocities, exhausted bounded waits) are
+ *     latched in a device word and reported by the next synchronising call
+ *     (orca_get_state / orca_sync).
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef ORCA_GB300_H
+#define ORCA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ORCA_API __attribute__((visibility("default")))
+#else
+#define ORCA_API
+#endif
+
+/* status codes */
+#define ORCA_OK 0
+#define ORCA_ERR_ARG (-1)      /* invalid argument */
+#define ORCA_ERR_NOMEM (-2)    /* workspace allocation failed or too small */
+#define ORCA_ERR_CUDA (-3)     /* a CUDA runtime call failed (message has the CUDA error) */
+#define ORCA_ERR_STATE (-4)    /* call not valid in the context's state (e.g. no agents) */
+#define ORCA_ERR_NUMERIC (-5)  /* a non-finite velocity or position was produced */
+#define ORCA_ERR_TIMEOUT (-6)  /* a bounded device-side wait gave up */
+#define ORCA_ERR_CAPACITY (-7) /* more agents / scenes / cells than the context was sized for */
+
+/* pointer location */
+#define ORCA_HOST 0
+#define ORCA_DEVICE 1
+
+/* orca_params.flags */
+#define ORCA_FLAG_RECORD 1u   /* keep each step's neighbour lists and cells for readout */
+#define ORCA_FLAG_NO_GRAPH 2u /* launch kernels directly instead of replaying a CUDA graph */
+
+typedef struct orca_ctx orca_ctx;
+
+/*
+ * Scene-wide parameters, fixed for the life of a context.
+ *   max_agents     capacity in agents (>= 1).
+ *   max_neighbors  k, the neighbours kept per agent (1..32).
+ *   max_cells      capacity of the cell table (0 -> max(4*max_agents, 65536)).  If the
+ *                  crowd's bounding box would need more cells, the cell edge doubles until
+ *                  it fits (the neighbour sets do not depend on the cell edge).
+ *   neighbor_dist  observation radius r_obs in metres (> 0).
+ *   dt             time step in seconds (> 0).
+ *   cell_size      grid cell edge in metres (0 -> neighbor_dist / 4).
+ *   flags          ORCA_FLAG_*.
+ */
+typedef struct orca_params {
+    int32_t max_agents;
+    int32_t max_neighbors;
+    int32_t max_cells;
+    float neighbor_dist;
+    float dt;
+    float cell_size;
+    uint32_t flags;
+    int32_t reserved;
+} orca_params;
+
+/* Bytes of device workspace orca_create needs for these parameters (256-byte aligned). */
+ORCA_API int orca_workspace_size(const orca_params* params, size_t* bytes);
+
+/*
+ * Create a context on the current CUDA device.
+ *   workspace       device buffer of at least orca_workspace_size() bytes, 256-byte
+ *                   aligned, owned by the caller and kept alive until orca_destroy; or
+ *                   NULL, in which case the library allocates (cudaMalloc) and frees it.
+ *   workspace_bytes size of `workspace` (ignored when it is NULL).
+ *   out             receives the context.  On failure *out is NULL.
+ */
+ORCA_API int orca_create(const orca_params* params, void* workspace, size_t workspace_bytes,
+                         orca_ctx** out);
+
+/* Destroy a context (waits for its work; frees what the library allocated). */
+ORCA_API int orca_destroy(orca_ctx* ctx);
+
+/*
+ * Load n agents (0 <= n <= max_agents), replacing the current crowd.
+ *   pos_xy, vel_xy, goal_xy  2*n floats each (metres, metres/second, metres).
+ *   radius                   n floats, agent radius (m, > 0).
+ *   max_speed                n floats, radius of the velocity disc (m/s, >= 0).
+ *   pref_speed               n floats, preferred walking speed (m/s, >= 0).
+ *   time_horizon             n floats, tau of Fig. 1 (s, > 0).
+ * Agent i of later readouts is agent i of these arrays.  Values are copied on `stream`;
+ * host arrays may be reused when the call returns.
+ */
+ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy,
+                             const float* vel_xy, const float* goal_xy, const float* radius,
+                             const float* max_speed, const float* pref_speed,
+                             const float* time_horizon, int where, void* stream);
+
+/*
+ * Advance nsteps (>= 0) synchronous ORCA steps on `stream`, asynchronously.
+ * The first call after orca_set_agents captures one step into a CUDA graph (unless
+ * ORCA_FLAG_NO_GRAPH); later calls replay it.  Capture happens on an internal stream, so
+ * `stream` may be the default stream.
+ */
+ORCA_API int orca_step(orca_ctx* ctx, int32_t nsteps, void* stream);
+
+/*
+ * Read the current state in agent order: pos_xy and vel_xy (2*n floats each; either may be
+ * NULL).  With ORCA_HOST the call synchronises `stream` and reports device-side errors.
+ */
+ORCA_API int orca_get_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int where,
+                            void* stream);
+
+/*
+ * Read the neighbour lists used by the last step (needs ORCA_FLAG_RECORD): n*k int32,
+ * row i = agent i's neighbours as agent indices, nearest first, -1 padded.
+ */
+ORCA_API int orca_get_neighbors(orca_ctx* ctx, int32_t* nbr, int where, void* stream);
+
+/*
+ * Read the grid cell of every agent in the last step (needs ORCA_FLAG_RECORD): n uint32,
+ * cell = cy * gx + cx.  grid_f (4 floats: xmin, ymin, cell edge, 1/edge) and grid_i
+ * (2 int32: gx, gy) receive the grid (host pointers; either may be NULL).  Synchronises.
+ */
+ORCA_API int orca_get_cells(orca_ctx* ctx, uint32_t* cell, float* grid_f, int32_t* grid_i,
+                            int where, void* stream);
+
+/*
+ * Counters accumulated since orca_set_agents (synchronises `stream`):
+ *   counters[0] agent-steps executed, [1] agent-steps that needed the least-penetration
+ *   fallback, [2] neighbour candidates examined, [3] half-planes built.
+ */
+ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
+
+/*
+ * Per-phase device timing.  With enable != 0 the step records CUDA events (event-record
+ * nodes inside the captured graph) between its three phases: binning (bounding box, cell
+ * keys, radix sort, cell table), reorder (gather into cell order) and the per-agent
+ * ORCA kernel.  Toggling rebuilds the graphs on the next orca_step.
+ */
+ORCA_API int orca_profile(orca_ctx* ctx, int enable);
+
+/*
+ * Durations in milliseconds of the three phases of the most recent profiled step:
+ * ms3[0] binning, ms3[1] reorder, ms3[2] ORCA kernel.  Waits for that step to finish.
+ */
+ORCA_API int orca_profile_read(orca_ctx* ctx, float* ms3);
+
+/* Number of kernels one orca_step enqueues per step (some exit at once when the radix
+ * sort needs fewer passes than the cell capacity allows). */
+ORCA_API int orca_launches_per_step(const orca_ctx* ctx, int32_t* count);
+
+/* Synchronise `stream` and report any latched device-side error. */
+ORCA_API int orca_sync(orca_ctx* ctx, void* stream);
+
+/* Agents currently loaded (0 if none). */
+ORCA_API int orca_num_agents(const orca_ctx* ctx, int32_t* n);
+
+/* Message of the last failure on ctx ("" if none); ctx may be NULL for creation errors. */
+ORCA_API const char* orca_last_error(const orca_ctx* ctx);
+
+/* Fixed text for a status code. */
+ORCA_API const char* orca_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ORCA_GB300_H */

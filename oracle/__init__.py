@@ -77,8 +77,9 @@ def _bind(lib):
     lib.oracle_solve.argtypes = [_F64P, c.c_int, c.c_double, _F64P, _F64P]
     lib.oracle_solve.restype = c.c_int
     lib.oracle_step.argtypes = ([c.c_int] + [_F64P] * 7 + [c.c_double, c.c_int, c.c_double,
-                                c.c_int, c.c_int, c.c_void_p, c.c_void_p, c.c_int, _F64P,
-                                _F64P, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p])
+                                c.c_int, c.c_int, c.c_void_p, c.c_void_p, c.c_void_p, c.c_int,
+                                c.c_int, _F64P, _F64P, c.c_void_p, c.c_void_p, c.c_void_p,
+                                c.c_void_p, c.c_int, c.c_void_p])
     lib.oracle_step.restype = c.c_int
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = c.c_int
@@ -182,36 +183,48 @@ def solve(lines, V: float, o):
 
 def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_dist: float,
          max_neighbors: int, dt: float, knn_mode: int = 1, fp64_knn: bool = False,
-         gf=None, gi=None, nthreads: int | None = None):
+         gf=None, gi=None, nthreads: int | None = None, subset=None,
+         sensitivity: bool = False):
     """One synchronous ORCA step (Sections 2-3) in FP64.
 
-    Arrays are promoted to float64.  Returns a dict with pos, vel (float64[n, 2]),
-    nbr (int32[n, k]), lp3 (bool[n]), margin (float64[n]) and counters
-    {scanned, lines, lp1_calls, lp3_agents}."""
+    Arrays are promoted to float64.  With ``subset`` (agent indices) only those agents are
+    stepped -- their neighbours are still searched among all agents -- and output row q
+    belongs to agent subset[q].  Returns a dict with pos, vel (float64[rows, 2]), nbr
+    (int32[rows, k]), lp3 (bool[rows]), margin (float64[rows]), sens (float64[rows], the
+    LP's sensitivity to FP32-sized perturbations of its half-planes, when
+    ``sensitivity``) and counters {scanned, lines, lp1_calls, lp3_agents}."""
     d = lambda a: np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1))
     pos, vel, goal = d(pos), d(vel), d(goal)
     radius, max_speed, pref_speed, time_horizon = d(radius), d(max_speed), d(pref_speed), d(time_horizon)
     n = pos.size // 2
     k = int(max_neighbors)
-    pos_out = np.zeros(2 * n)
-    vel_out = np.zeros(2 * n)
-    nbr = np.zeros(max(n * k, 1), np.int32)
-    status = np.zeros(max(n, 1), np.int32)
-    margin = np.zeros(max(n, 1))
+    if subset is not None:
+        subset = np.ascontiguousarray(subset, np.int32)
+        rows = subset.size
+    else:
+        rows = n
+    pos_out = np.zeros(max(2 * rows, 2))
+    vel_out = np.zeros(max(2 * rows, 2))
+    nbr = np.zeros(max(rows * k, 1), np.int32)
+    status = np.zeros(max(rows, 1), np.int32)
+    margin = np.zeros(max(rows, 1))
     counters = np.zeros(4, np.int64)
+    sens = np.zeros(max(rows, 1))
     if gf is not None:
         gf = np.ascontiguousarray(gf, np.float32)
         gi = np.ascontiguousarray(gi, np.int32)
     r = _load().oracle_step(n, pos, vel, goal, radius, max_speed, pref_speed, time_horizon,
                             float(neighbor_dist), k, float(dt), int(knn_mode), int(bool(fp64_knn)),
-                            _ptr(gf), _ptr(gi), int(nthreads or max_threads()), pos_out, vel_out,
-                            _ptr(nbr), _ptr(status), _ptr(margin), _ptr(counters))
+                            _ptr(gf), _ptr(gi), _ptr(subset), int(rows),
+                            int(nthreads or max_threads()), pos_out, vel_out,
+                            _ptr(nbr), _ptr(status), _ptr(margin), _ptr(counters),
+                            int(bool(sensitivity)), _ptr(sens))
     if r != 0:
         raise ValueError(f"oracle_step failed ({r})")
     return {
-        "pos": pos_out.reshape(n, 2), "vel": vel_out.reshape(n, 2),
-        "nbr": nbr[: n * k].reshape(n, k), "lp3": status[:n].astype(bool),
-        "margin": margin[:n],
+        "pos": pos_out[: 2 * rows].reshape(rows, 2), "vel": vel_out[: 2 * rows].reshape(rows, 2),
+        "nbr": nbr[: rows * k].reshape(rows, k), "lp3": status[:rows].astype(bool),
+        "margin": margin[:rows], "sens": sens[:rows],
         "counters": dict(zip(("scanned", "lines", "lp1_calls", "lp3_agents"),
                              (int(c) for c in counters))),
     }

@@ -42,10 +42,16 @@
  *     (goal - p)/dt;
  *   - parallel-line tolerance eps = 1e-5.
  *
- * Ill-conditioning: every branch decision whose outcome can move the result by more
- * than rounding records its normalised distance to the threshold; the per-agent
- * minimum ("margin") lets the parity tests set aside agents whose FP32 and FP64
- * decisions may legitimately differ.
+ * Ill-conditioning (for parity tests against an FP32 implementation):
+ *   - margin: the half-plane construction's discontinuous decisions (overlap or not,
+ *     left or right leg) record their normalised distance to the threshold; the
+ *     per-agent minimum is reported;
+ *   - sens (optional): the LP is re-solved with each half-plane shifted by +-4 FP32 ulps
+ *     of its offset and turned by +-2^-22 rad about its nearest point to the origin, one
+ *     at a time -- the rounding any FP32 construction of the half-planes carries -- and
+ *     the largest move of the chosen velocity is reported.  An agent whose velocity moves
+ *     by more than half the parity tolerance is not determined to that tolerance by FP32
+ *     half-planes.
  */
 #include <math.h>
 #include <stdint.h>
@@ -323,9 +329,9 @@ static line2 orca_line(v2 pa, v2 va, double ra, v2 pb, v2 vb, double rb, double 
  * -------------------------------------------------------------------------------- */
 static int lp1(const line2* L, int i, double V, v2 o, int dir_opt, v2* x, tags* tg,
                long long* work) {
+    (void)tg;
     double a = dot(L[i].P, L[i].d);
     double D = a * a + V * V - dot(L[i].P, L[i].P);
-    note(tg, D, 0.0, V * V);
     if (D < 0.0) return 0;
     double sq = sqrt(D);
     double tL = -a - sq, tR = -a + sq;
@@ -333,21 +339,17 @@ static int lp1(const line2* L, int i, double V, v2 o, int dir_opt, v2* x, tags* 
         double den = det2(L[i].d, L[j].d);
         double num = det2(L[j].d, sub(L[i].P, L[j].P));
         if (work) ++*work;
-        note(tg, fabs(den), OR_EPS, OR_EPS);
         if (fabs(den) <= OR_EPS) {
-            note(tg, num, 0.0, V);
             if (num < 0.0) return 0;
             continue;
         }
         double t = num / den;
         if (den >= 0.0) { if (t < tR) tR = t; }
         else { if (t > tL) tL = t; }
-        if (tL > tR) { note(tg, tL, tR, V); return 0; }
+        if (tL > tR) return 0;
     }
-    note(tg, tL, tR, V);
     if (dir_opt) {
         double od = dot(o, L[i].d);
-        note(tg, od, 0.0, 1.0);
         *x = add(L[i].P, scl(L[i].d, od > 0.0 ? tR : tL));
     } else {
         double t = dot(L[i].d, sub(o, L[i].P));
@@ -365,12 +367,12 @@ static int lp1(const line2* L, int i, double V, v2 o, int dir_opt, v2* x, tags* 
  * feasible value). */
 static int lp2(const line2* L, int n, double V, v2 o, int dir_opt, v2* x, tags* tg,
                long long* work) {
+    (void)tg;
     if (dir_opt) *x = scl(o, V);
     else if (dot(o, o) > V * V) *x = scl(o, V / len(o));
     else *x = o;
     for (int i = 0; i < n; ++i) {
         double viol = det2(L[i].d, sub(L[i].P, *x));
-        note(tg, viol, 0.0, V);
         if (viol > 0.0) {
             v2 keep = *x;
             if (work) ++*work;
@@ -390,17 +392,16 @@ static int lp2(const line2* L, int n, double V, v2 o, int dir_opt, v2* x, tags* 
  * progress along the normal (-d_i.y, d_i.x).  A numerically failed LP2 keeps x. */
 static void lp3(const line2* L, int n, int begin, double V, v2* x, tags* tg,
                 long long* work) {
+    (void)tg;
     line2 proj[OR_MAXK];
     double dist = 0.0;
     for (int i = begin; i < n; ++i) {
         double pen = det2(L[i].d, sub(L[i].P, *x));
-        note(tg, pen, dist, V);
         if (pen > dist) {
             int m = 0;
             for (int j = 0; j < i; ++j) {
                 line2 q;
                 double den = det2(L[i].d, L[j].d);
-                note(tg, fabs(den), OR_EPS, OR_EPS);
                 if (fabs(den) <= OR_EPS) {
                     if (dot(L[i].d, L[j].d) > 0.0) continue;
                     q.P = scl(add(L[i].P, L[j].P), 0.5);
@@ -481,70 +482,147 @@ static v2 pref_velocity(v2 p, v2 goal, double pref_speed, double dt) {
  * Scene parameters: neighbor_dist (r_obs), k = max_neighbors, dt.
  * knn_mode: 0 brute force, 1 grid (grid_f/grid_i from oracle_grid; NULL -> cell = r_obs).
  * fp64_knn: 0 -> neighbour search in FP32 on (float)pos; 1 -> in FP64.
- * Outputs: pos_out, vel_out (2n), nbr (n*k, -1 padded, may be NULL), status (n: bit0 LP3
- * used, may be NULL), margin (n, may be NULL), counters[4] = {candidates scanned,
- * lines built, LP1 calls (incl. inside LP3), agents needing LP3} (may be NULL).
- * Returns 0, or a negative value on bad arguments / allocation failure.
+ * subset/n_subset: if subset is non-NULL, only agents subset[0..n_subset-1] are stepped
+ *   (their neighbours are still searched among all n agents) and output row q belongs to
+ *   agent subset[q]; otherwise every agent is stepped and row i is agent i.
+ * Outputs: pos_out, vel_out (2 per row), nbr (k per row, -1 padded, may be NULL), status
+ * (1 per row: 1 if LP3 ran, may be NULL), margin (1 per row, may be NULL), counters[4] =
+ * {candidates scanned, lines built, LP1 calls (incl. inside LP3), agents needing LP3}
+ * (may be NULL), sens (1 per row, may be NULL; filled when cond_check != 0, see the
+ * header).  Returns 0, or a negative value on bad arguments / allocation failure.
  * -------------------------------------------------------------------------------- */
+/* Velocity selection (LP2, then LP3 if needed) on given lines. */
+static v2 select_velocity(const line2* L, int n, double V, v2 o) {
+    v2 x;
+    int b = lp2(L, n, V, o, 0, &x, NULL, NULL);
+    if (b < n) lp3(L, n, b, V, &x, NULL, NULL);
+    return x;
+}
+
+/* Largest move of the selected velocity when one half-plane at a time is shifted along
+ * its normal by +-eta_c (4 FP32 ulps of max(|offset|, V)) or turned by +-2^-22 rad about
+ * its point nearest the origin. */
+static double lp_sensitivity(const line2* L, int n, double V, v2 o, v2 x) {
+    line2 Q[OR_MAXK];
+    double worst = 0.0;
+    const double eta_r = ldexp(1.0, -22);
+    for (int q = 0; q < n; ++q) {
+        v2 nq = mk(-L[q].d.y, L[q].d.x);
+        double c = dot(nq, L[q].P);
+        double mag = fabs(c) > V ? fabs(c) : V;
+        int e2;
+        frexp(mag, &e2);
+        double eta_c = ldexp(1.0, e2 - 22); /* 4 ulps of a float in [2^(e2-1), 2^e2) */
+        for (int k = 0; k < 4; ++k) {
+            memcpy(Q, L, sizeof(line2) * (size_t)n);
+            v2 nn = nq;
+            double cc = c;
+            if (k == 0) cc = c + eta_c;
+            else if (k == 1) cc = c - eta_c;
+            else {
+                double a = k == 2 ? eta_r : -eta_r;
+                nn = mk(nq.x * cos(a) - nq.y * sin(a), nq.x * sin(a) + nq.y * cos(a));
+            }
+            Q[q].d = mk(nn.y, -nn.x);
+            Q[q].P = scl(nn, cc);
+            v2 y = select_velocity(Q, n, V, o);
+            double dv = fabs(y.x - x.x) > fabs(y.y - x.y) ? fabs(y.x - x.x) : fabs(y.y - x.y);
+            if (dv > worst) worst = dv;
+        }
+    }
+    return worst;
+}
+
+typedef struct {
+    int n, k, fp64, cond;
+    const double *pos, *vel, *goal, *radius, *max_speed, *pref_speed, *tau;
+    double nd, dt;
+    float ndf;
+    const float* pf;
+    const bins* b;
+} step_in;
+
+static void step_agent(const step_in* S, int i, double* pos_out, double* vel_out, int32_t* nbr,
+                       int32_t* status, double* margin, double* sens, long long* c_scan,
+                       long long* c_lines, long long* c_work, long long* c_lp3) {
+    cand list[OR_MAXK];
+    line2 L[OR_MAXK];
+    int cnt = 0;
+    tags tg = {1e300};
+    const double* pos = S->pos;
+    const double* vel = S->vel;
+    if (S->b) *c_scan += knn_grid_one(S->b, S->pf, pos, S->fp64, i, S->ndf, S->nd, list, &cnt, S->k);
+    else { knn_brute_one(S->pf, pos, S->fp64, S->n, i, S->ndf, S->nd, list, &cnt, S->k); *c_scan += S->n - 1; }
+    v2 pa = mk(pos[2 * i], pos[2 * i + 1]), va = mk(vel[2 * i], vel[2 * i + 1]);
+    for (int q = 0; q < cnt; ++q) {
+        int j = list[q].j;
+        L[q] = orca_line(pa, va, S->radius[i], mk(pos[2 * j], pos[2 * j + 1]),
+                         mk(vel[2 * j], vel[2 * j + 1]), S->radius[j], S->tau[i], S->dt, i, j,
+                         &tg, NULL, NULL);
+    }
+    *c_lines += cnt;
+    v2 pv = pref_velocity(pa, mk(S->goal[2 * i], S->goal[2 * i + 1]), S->pref_speed[i], S->dt);
+    v2 x;
+    long long w = 0;
+    int bfail = lp2(L, cnt, S->max_speed[i], pv, 0, &x, &tg, &w);
+    int used3 = bfail < cnt;
+    if (used3) { lp3(L, cnt, bfail, S->max_speed[i], &x, &tg, &w); ++*c_lp3; }
+    *c_work += w;
+    if (sens) *sens = S->cond ? lp_sensitivity(L, cnt, S->max_speed[i], pv, x) : 0.0;
+    vel_out[0] = x.x;
+    vel_out[1] = x.y;
+    pos_out[0] = pa.x + x.x * S->dt;
+    pos_out[1] = pa.y + x.y * S->dt;
+    if (nbr) for (int q = 0; q < S->k; ++q) nbr[q] = q < cnt ? list[q].j : -1;
+    if (status) *status = used3;
+    if (margin) *margin = tg.m;
+}
+
 int oracle_step(int n, const double* pos, const double* vel, const double* goal,
                 const double* radius, const double* max_speed, const double* pref_speed,
                 const double* time_horizon, double neighbor_dist, int k, double dt,
                 int knn_mode, int fp64_knn, const float* grid_f_in, const int* grid_i_in,
-                int nthreads, double* pos_out, double* vel_out, int32_t* nbr,
-                int32_t* status, double* margin, long long* counters) {
+                const int32_t* subset, int n_subset, int nthreads, double* pos_out,
+                double* vel_out, int32_t* nbr, int32_t* status, double* margin,
+                long long* counters, int cond_check, double* sens) {
     if (n < 0 || k < 1 || k > OR_MAXK || !(dt > 0.0)) return -1;
+    if (subset) {
+        if (n_subset < 0) return -1;
+        for (int q = 0; q < n_subset; ++q) if (subset[q] < 0 || subset[q] >= n) return -1;
+    }
     if (counters) memset(counters, 0, 4 * sizeof(long long));
-    if (n == 0) return 0;
+    int rows = subset ? n_subset : n;
+    if (n == 0 || rows == 0) return 0;
     float* pf = (float*)malloc(sizeof(float) * 2 * (size_t)n);
     if (!pf) return -2;
     for (long long q = 0; q < 2LL * n; ++q) pf[q] = (float)pos[q];
-    float ndf = (float)neighbor_dist;
+    step_in S;
+    S.n = n; S.k = k; S.fp64 = fp64_knn; S.cond = cond_check;
+    S.pos = pos; S.vel = vel; S.goal = goal; S.radius = radius; S.max_speed = max_speed;
+    S.pref_speed = pref_speed; S.tau = time_horizon;
+    S.nd = neighbor_dist; S.dt = dt; S.ndf = (float)neighbor_dist; S.pf = pf; S.b = NULL;
     bins b;
-    int have_bins = 0;
     if (knn_mode == 1) {
         float gf[4];
         int gi[2];
         if (grid_f_in && grid_i_in) { memcpy(gf, grid_f_in, sizeof gf); memcpy(gi, grid_i_in, sizeof gi); }
-        else if (oracle_grid(pf, n, ndf, (long long)4 * n + 1024, gf, gi) != 0) { free(pf); return -3; }
+        else if (oracle_grid(pf, n, S.ndf, (long long)4 * n + 1024, gf, gi) != 0) { free(pf); return -3; }
         if (bins_build(&b, pf, n, gf, gi) != 0) { free(pf); return -2; }
-        have_bins = 1;
+        S.b = &b;
     }
     long long c_scan = 0, c_lines = 0, c_work = 0, c_lp3 = 0;
 #ifdef _OPENMP
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads) reduction(+ : c_scan, c_lines, c_work, c_lp3)
 #endif
-    for (int i = 0; i < n; ++i) {
-        cand list[OR_MAXK];
-        line2 L[OR_MAXK];
-        int cnt = 0;
-        tags tg = {1e300};
-        if (have_bins) c_scan += knn_grid_one(&b, pf, pos, fp64_knn, i, ndf, neighbor_dist, list, &cnt, k);
-        else { knn_brute_one(pf, pos, fp64_knn, n, i, ndf, neighbor_dist, list, &cnt, k); c_scan += n - 1; }
-        v2 pa = mk(pos[2 * i], pos[2 * i + 1]), va = mk(vel[2 * i], vel[2 * i + 1]);
-        for (int q = 0; q < cnt; ++q) {
-            int j = list[q].j;
-            L[q] = orca_line(pa, va, radius[i], mk(pos[2 * j], pos[2 * j + 1]),
-                             mk(vel[2 * j], vel[2 * j + 1]), radius[j], time_horizon[i], dt,
-                             i, j, &tg, NULL, NULL);
-        }
-        c_lines += cnt;
-        v2 pv = pref_velocity(pa, mk(goal[2 * i], goal[2 * i + 1]), pref_speed[i], dt);
-        v2 x;
-        long long w = 0;
-        int bfail = lp2(L, cnt, max_speed[i], pv, 0, &x, &tg, &w);
-        int used3 = bfail < cnt;
-        if (used3) { lp3(L, cnt, bfail, max_speed[i], &x, &tg, &w); ++c_lp3; }
-        c_work += w;
-        vel_out[2 * i] = x.x;
-        vel_out[2 * i + 1] = x.y;
-        pos_out[2 * i] = pa.x + x.x * dt;
-        pos_out[2 * i + 1] = pa.y + x.y * dt;
-        if (nbr) for (int q = 0; q < k; ++q) nbr[(size_t)i * k + q] = q < cnt ? list[q].j : -1;
-        if (status) status[i] = used3;
-        if (margin) margin[i] = tg.m;
+    for (int q = 0; q < rows; ++q) {
+        int i = subset ? subset[q] : q;
+        step_agent(&S, i, pos_out + 2 * (size_t)q, vel_out + 2 * (size_t)q,
+                   nbr ? nbr + (size_t)q * k : NULL, status ? status + q : NULL,
+                   margin ? margin + q : NULL, sens ? sens + q : NULL, &c_scan, &c_lines,
+                   &c_work, &c_lp3);
     }
-    if (have_bins) bins_free(&b);
+    if (S.b) bins_free(&b);
     free(pf);
     if (counters) { counters[0] = c_scan; counters[1] = c_lines; counters[2] = c_work; counters[3] = c_lp3; }
     return 0;

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of include/orca_gb300.h.
+
+Each ``orca_*`` function here has the name and argument order of the C entry point and
+only marshals arguments: numpy arrays become host pointers (ORCA_HOST), CUDA torch
+tensors become device pointers (ORCA_DEVICE), and ``stream=None`` means torch's current
+stream.  All work runs in liborca_gb300.so; if the library is missing this module raises
+instead of falling back to anything.
+
+``OrcaSim`` bundles a context with a torch-owned device workspace.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ORCA_OK = 0
+ORCA_ERR_ARG = -1
+ORCA_ERR_NOMEM = -2
+ORCA_ERR_CUDA = -3
+ORCA_ERR_STATE = -4
+ORCA_ERR_NUMERIC = -5
+ORCA_ERR_TIMEOUT = -6
+ORCA_ERR_CAPACITY = -7
+ORCA_HOST = 0
+ORCA_DEVICE = 1
+ORCA_FLAG_RECORD = 1
+ORCA_FLAG_NO_GRAPH = 2
+
+LIB_PATH = _build.LIB
+HEADER = os.path.join(_build.ROOT, "include", "orca_gb300.h")
+
+
+class OrcaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class orca_params(ctypes.Structure):
+    _fields_ = [("max_agents", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
+                ("max_cells", ctypes.c_int32), ("neighbor_dist", ctypes.c_float),
+                ("dt", ctypes.c_float), ("cell_size", ctypes.c_float),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load liborca_gb300.so (built by ``build.build()``).  Raises if it is absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OrcaError(ORCA_ERR_STATE, f"{p} is missing: run paper_1908_10107_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    c = ctypes
+    vp, i32, sz = c.c_void_p, c.c_int32, c.c_size_t
+    P = c.POINTER(orca_params)
+    sigs = {
+        "orca_workspace_size": ([P, c.POINTER(sz)], c.c_int),
+        "orca_create": ([P, vp, sz, c.POINTER(vp)], c.c_int),
+        "orca_destroy": ([vp], c.c_int),
+        "orca_set_agents": ([vp, i32] + [vp] * 7 + [c.c_int, vp], c.c_int),
+        "orca_step": ([vp, i32, vp], c.c_int),
+        "orca_get_state": ([vp, vp, vp, c.c_int, vp], c.c_int),
+        "orca_get_neighbors": ([vp, vp, c.c_int, vp], c.c_int),
+        "orca_get_cells": ([vp, vp, vp, vp, c.c_int, vp], c.c_int),
+        "orca_get_counters": ([vp, vp, vp], c.c_int),
+        "orca_sync": ([vp, vp], c.c_int),
+        "orca_profile": ([vp, c.c_int], c.c_int),
+        "orca_profile_read": ([vp, vp], c.c_int),
+        "orca_launches_per_step": ([vp, c.POINTER(i32)], c.c_int),
+        "orca_num_agents": ([vp, c.POINTER(i32)], c.c_int),
+        "orca_last_error": ([vp], c.c_char_p),
+        "orca_status_string": ([c.c_int], c.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status != ORCA_OK:
+        lib = load_library()
+        msg = lib.orca_last_error(ctx).decode() or lib.orca_status_string(status).decode()
+        raise OrcaError(status, msg)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a, dtype):
+    """(pointer, where) for a numpy array or a CUDA torch tensor; None -> (None, None)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected C-contiguous {np.dtype(dtype)} array")
+        return ctypes.c_void_p(a.ctypes.data), ORCA_HOST
+    import torch
+    if isinstance(a, torch.Tensor):
+        tdt = {np.float32: torch.float32, np.int32: torch.int32, np.uint32: torch.int32}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError(f"expected contiguous {tdt} tensor")
+        return ctypes.c_void_p(a.data_ptr()), (ORCA_DEVICE if a.is_cuda else ORCA_HOST)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def make_params(max_agents: int, max_neighbors: int, neighbor_dist: float, dt: float,
+                cell_size: float = 0.0, max_cells: int = 0, flags: int = 0) -> orca_params:
+    return orca_params(int(max_agents), int(max_neighbors), int(max_cells), float(neighbor_dist),
+                       float(dt), float(cell_size), int(flags), 0)
+
+
+def orca_workspace_size(params: orca_params) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load_library().orca_workspace_size(ctypes.byref(params), ctypes.byref(n)))
+    return int(n.value)
+
+
+def orca_create(params: orca_params, workspace=None, workspace_bytes: int = 0):
+    """workspace: a CUDA torch tensor (caller-owned) or None (library-owned cudaMalloc)."""
+    ctx = ctypes.c_void_p()
+    wp = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else None
+    nbytes = workspace_bytes or (workspace.numel() * workspace.element_size() if workspace is not None else 0)
+    _check(load_library().orca_create(ctypes.byref(params), wp, nbytes, ctypes.byref(ctx)))
+    return ctx
+
+
+def orca_destroy(ctx):
+    _check(load_library().orca_destroy(ctx), ctx)
+
+
+def orca_set_agents(ctx, n, pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed,
+                    time_horizon, where=None, stream=None):
+    ptrs = [_ptr(a, np.float32) for a in (pos_xy, vel_xy, goal_xy, radius, max_speed,
+                                           pref_speed, time_horizon)]
+    w = where if where is not None else ptrs[0][1]
+    _check(load_library().orca_set_agents(ctx, int(n), *[p for p, _ in ptrs], int(w),
+                                          _stream(stream) if w == ORCA_DEVICE or stream is not None else None),
+           ctx)
+
+
+def orca_step(ctx, nsteps: int = 1, stream=None):
+    _check(load_library().orca_step(ctx, int(nsteps), _stream(stream)), ctx)
+
+
+def orca_get_state(ctx, pos_xy, vel_xy, where=None, stream=None):
+    pp, w1 = _ptr(pos_xy, np.float32)
+    vp, w2 = _ptr(vel_xy, np.float32)
+    w = where if where is not None else (w1 if w1 is not None else w2)
+    _check(load_library().orca_get_state(ctx, pp, vp, int(w), _stream(stream)), ctx)
+
+
+def orca_get_neighbors(ctx, nbr, where=None, stream=None):
+    p, w = _ptr(nbr, np.int32)
+    _check(load_library().orca_get_neighbors(ctx, p, int(where if where is not None else w),
+                                             _stream(stream)), ctx)
+
+
+def orca_get_cells(ctx, cell, grid_f=None, grid_i=None, where=None, stream=None):
+    p, w = _ptr(cell, np.uint32)
+    gf = ctypes.c_void_p(grid_f.ctypes.data) if grid_f is not None else None
+    gi = ctypes.c_void_p(grid_i.ctypes.data) if grid_i is not None else None
+    _check(load_library().orca_get_cells(ctx, p, gf, gi, int(where if where is not None else w),
+                                         _stream(stream)), ctx)
+
+
+def orca_get_counters(ctx, stream=None) -> np.ndarray:
+    out = np.zeros(4, np.int64)
+    _check(load_library().orca_get_counters(ctx, ctypes.c_void_p(out.ctypes.data),
+                                            _stream(stream)), ctx)
+    return out
+
+
+def orca_sync(ctx, stream=None):
+    _check(load_library().orca_sync(ctx, _stream(stream)), ctx)
+
+
+def orca_profile(ctx, enable: bool):
+    _check(load_library().orca_profile(ctx, int(bool(enable))), ctx)
+
+
+def orca_profile_read(ctx) -> np.ndarray:
+    out = np.zeros(3, np.float32)
+    _check(load_library().orca_profile_read(ctx, ctypes.c_void_p(out.ctypes.data)), ctx)
+    return out
+
+
+def orca_launches_per_step(ctx) -> int:
+    n = ctypes.c_int32(0)
+    _check(load_library().orca_launches_per_step(ctx, ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def orca_num_agents(ctx) -> int:
+    n = ctypes.c_int32(0)
+    _check(load_library().orca_num_agents(ctx, ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def orca_last_error(ctx) -> str:
+    return load_library().orca_last_error(ctx).decode()
+
+
+def orca_status_string(status: int) -> str:
+    return load_library().orca_status_string(int(status)).decode()
+
+
+class OrcaSim:
+    """A context plus its torch-owned device workspace.
+
+    >>> sim = OrcaSim(max_agents=n, max_neighbors=10, neighbor_dist=10.0, dt=1/60)
+    >>> sim.set_scene(scene); sim.step(100); pos, vel = sim.get_state()
+    """
+
+    def __init__(self, max_agents: int, max_neighbors: int, neighbor_dist: float, dt: float,
+                 cell_size: float = 0.0, max_cells: int = 0, flags: int = 0, device=None):
+        import torch
+        self.params = make_params(max_agents, max_neighbors, neighbor_dist, dt, cell_size,
+                                  max_cells, flags)
+        self.device = torch.device(device or "cuda")
+        nbytes = orca_workspace_size(self.params)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            off = (-self.workspace.data_ptr()) % 256
+            self._ws = self.workspace[off: off + nbytes]
+            self.ctx = orca_create(self.params, self._ws, nbytes)
+        self.k = int(max_neighbors)
+
+    @classmethod
+    def for_scene(cls, scene, **kw):
+        return cls(max_agents=max(scene.n, 1), max_neighbors=scene.max_neighbors,
+                   neighbor_dist=scene.neighbor_dist, dt=scene.dt, **kw)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            orca_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n(self) -> int:
+        return orca_num_agents(self.ctx)
+
+    def set_agents(self, pos, vel, goal, radius, max_speed, pref_speed, time_horizon, stream=None):
+        n = (pos.shape[0] if pos.ndim == 2 else pos.shape[0] // 2)
+        orca_set_agents(self.ctx, n, pos, vel, goal, radius, max_speed, pref_speed,
+                        time_horizon, stream=stream)
+
+    def set_scene(self, scene, stream=None):
+        self.set_agents(*scene.arrays(), stream=stream)
+
+    def step(self, nsteps: int = 1, stream=None):
+        orca_step(self.ctx, nsteps, stream)
+
+    def get_state(self, device: bool = False, stream=None):
+        n = self.n
+        if device:
+            import torch
+            pos = torch.empty((n, 2), dtype=torch.float32, device=self.device)
+            vel = torch.empty((n, 2), dtype=torch.float32, device=self.device)
+        else:
+            pos = np.empty((n, 2), np.float32)
+            vel = np.empty((n, 2), np.float32)
+        orca_get_state(self.ctx, pos, vel, stream=stream)
+        return pos, vel
+
+    def get_neighbors(self, stream=None) -> np.ndarray:
+        out = np.empty((self.n, self.k), np.int32)
+        orca_get_neighbors(self.ctx, out, stream=stream)
+        return out
+
+    def get_cells(self, stream=None):
+        cell = np.empty(self.n, np.uint32)
+        gf = np.zeros(4, np.float32)
+        gi = np.zeros(2, np.int32)
+        orca_get_cells(self.ctx, cell, gf, gi, stream=stream)
+        return cell, gf, gi
+
+    def counters(self, stream=None) -> dict:
+        c = orca_get_counters(self.ctx, stream)
+        return dict(zip(("agent_steps", "lp3_agent_steps", "candidates", "lines"), map(int, c)))
+
+    def sync(self, stream=None):
+        orca_sync(self.ctx, stream)

@@ -1,0 +1,482 @@
+// orca_api.cu -- the C ABI (include/orca_gb300.h): context, workspace layout, step
+// orchestration and CUDA-graph capture.  No C++ exception crosses the ABI.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/orca_gb300.h"
+#include "orca_common.cuh"
+
+namespace orca {
+
+// Sub-allocation plan of the workspace (256-byte aligned pieces).
+struct Layout {
+    size_t off[32];
+    int count = 0;
+    size_t total = 0;
+    size_t add(size_t bytes) {
+        size_t o = total;
+        off[count++] = o;
+        total += (bytes + 255) & ~size_t(255);
+        return o;
+    }
+};
+
+struct Plan {
+    int N, K, max_cells, max_passes, nsb, nmb;
+    size_t o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2];
+    size_t o_keys[2], o_vals[2], o_hist, o_cells, o_part, o_misc, o_blk, o_rnbr, o_rcell,
+        o_stage[2];
+    size_t total;
+};
+
+static int default_max_cells(int N) {
+    long long c = 4LL * N;
+    if (c < 65536) c = 65536;
+    if (c > (1LL << 30)) c = 1LL << 30;
+    return (int)c;
+}
+
+static bool make_plan(const orca_params& p, Plan& pl) {
+    if (p.max_agents < 1 || p.max_neighbors < 1 || p.max_neighbors > kMaxNeighbors) return false;
+    if (!(p.neighbor_dist > 0.0f) || !(p.dt > 0.0f) || p.cell_size < 0.0f) return false;
+    if (p.max_cells < 0) return false;
+    pl.N = p.max_agents;
+    pl.K = p.max_neighbors;
+    pl.max_cells = p.max_cells ? p.max_cells : default_max_cells(p.max_agents);
+    int bits = 0;
+    while (bits < 31 && (1LL << bits) < (long long)pl.max_cells) ++bits;
+    pl.max_passes = (bits + kRadixBits - 1) / kRadixBits;
+    if (pl.max_passes < 1) pl.max_passes = 1;
+    pl.nsb = sort_blocks(pl.N);
+    pl.nmb = main_blocks(pl.N);
+    Layout L;
+    size_t N = (size_t)pl.N;
+    for (int b = 0; b < 2; ++b) {
+        pl.o_pv[b][0] = L.add(N * sizeof(float2));
+        pl.o_pv[b][1] = L.add(N * sizeof(float2));
+        pl.o_goal[b] = L.add(N * sizeof(float2));
+        pl.o_rad[b] = L.add(N * 4);
+        pl.o_vmax[b] = L.add(N * 4);
+        pl.o_pref[b] = L.add(N * 4);
+        pl.o_tau[b] = L.add(N * 4);
+        pl.o_id[b] = L.add(N * 4);
+        pl.o_keys[b] = L.add(N * 4);
+        pl.o_vals[b] = L.add(N * 4);
+        pl.o_stage[b] = L.add(N * sizeof(float2));
+    }
+    pl.o_hist = L.add((size_t)kRadixBuckets * pl.nsb * 4);
+    pl.o_cells = L.add(((size_t)pl.max_cells + 1) * 4);
+    pl.o_part = L.add(kBboxBlocks * sizeof(float4));
+    pl.o_misc = L.add(sizeof(DeviceMisc));
+    pl.o_blk = L.add((size_t)pl.nmb * 4 * sizeof(unsigned long long));
+    if (p.flags & ORCA_FLAG_RECORD) {
+        pl.o_rnbr = L.add(N * pl.K * 4);
+        pl.o_rcell = L.add(N * 4);
+    } else {
+        pl.o_rnbr = pl.o_rcell = (size_t)-1;
+    }
+    pl.total = L.total;
+    return true;
+}
+
+}  // namespace orca
+
+using namespace orca;
+
+struct orca_ctx {
+    orca_params p;
+    Plan plan;
+    int device = 0;
+    char* ws = nullptr;
+    bool own_ws = false;
+    AgentState PV[2];
+    AgentParams PR[2];
+    BinBuffers bins;
+    unsigned long long* blk = nullptr;
+    int32_t* rec_nbr = nullptr;
+    uint32_t* rec_cell = nullptr;
+    float2* stage[2];
+    int n = 0;
+    int cur = 0;  // which PR buffer holds the current parameters
+    bool stepped = false;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    int graph_n = -1;
+    bool prof = false;
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::string err;
+};
+
+static std::string g_create_err;
+
+static int fail(orca_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+static int cuda_fail(orca_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, ORCA_ERR_CUDA, m);
+}
+
+#define CK(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+static void bind_buffers(orca_ctx* c) {
+    const Plan& pl = c->plan;
+    char* w = c->ws;
+    for (int b = 0; b < 2; ++b) {
+        c->PV[b].pos = (float2*)(w + pl.o_pv[b][0]);
+        c->PV[b].vel = (float2*)(w + pl.o_pv[b][1]);
+        c->PR[b].goal = (float2*)(w + pl.o_goal[b]);
+        c->PR[b].radius = (float*)(w + pl.o_rad[b]);
+        c->PR[b].max_speed = (float*)(w + pl.o_vmax[b]);
+        c->PR[b].pref_speed = (float*)(w + pl.o_pref[b]);
+        c->PR[b].tau = (float*)(w + pl.o_tau[b]);
+        c->PR[b].id = (uint32_t*)(w + pl.o_id[b]);
+        c->bins.keys[b] = (uint32_t*)(w + pl.o_keys[b]);
+        c->bins.vals[b] = (uint32_t*)(w + pl.o_vals[b]);
+        c->stage[b] = (float2*)(w + pl.o_stage[b]);
+    }
+    c->bins.hist = (uint32_t*)(w + pl.o_hist);
+    c->bins.cell_start = (uint32_t*)(w + pl.o_cells);
+    c->bins.bbox_partials = (float4*)(w + pl.o_part);
+    c->bins.misc = (DeviceMisc*)(w + pl.o_misc);
+    c->blk = (unsigned long long*)(w + pl.o_blk);
+    c->rec_nbr = pl.o_rnbr == (size_t)-1 ? nullptr : (int32_t*)(w + pl.o_rnbr);
+    c->rec_cell = pl.o_rcell == (size_t)-1 ? nullptr : (uint32_t*)(w + pl.o_rcell);
+}
+
+static void drop_graphs(orca_ctx* c) {
+    for (int b = 0; b < 2; ++b)
+        if (c->exec[b]) {
+            cudaGraphExecDestroy(c->exec[b]);
+            c->exec[b] = nullptr;
+        }
+    c->graph_n = -1;
+}
+
+// Enqueue one step whose current parameters live in PR[par].
+static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
+    const Plan& pl = c->plan;
+    float cs = c->p.cell_size > 0.0f ? c->p.cell_size : c->p.neighbor_dist * 0.25f;
+    cudaError_t e = cudaSuccess;
+    if (c->prof && (e = cudaEventRecordWithFlags(c->pev[0], st, cudaEventRecordExternal)) != cudaSuccess) return e;
+    e = launch_binning(c->n, cs, pl.max_cells, pl.max_passes, c->PV[0], c->bins, st);
+    if (e != cudaSuccess) return e;
+    if (c->prof && (e = cudaEventRecordWithFlags(c->pev[1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
+    e = launch_reorder(c->n, c->bins, c->PV[0], c->PV[1], c->PR[par], c->PR[par ^ 1], st);
+    if (e != cudaSuccess) return e;
+    if (c->prof && (e = cudaEventRecordWithFlags(c->pev[2], st, cudaEventRecordExternal)) != cudaSuccess) return e;
+    MainArgs a;
+    a.n = c->n;
+    a.k = pl.K;
+    a.nd = c->p.neighbor_dist;
+    a.dt = c->p.dt;
+    a.misc = c->bins.misc;
+    a.misc_rw = c->bins.misc;
+    a.cell_start = c->bins.cell_start;
+    a.in = c->PV[1];
+    a.prm = c->PR[par ^ 1];
+    a.out = c->PV[0];
+    a.block_counters = c->blk;
+    a.rec_nbr = c->rec_nbr;
+    a.rec_cell = c->rec_cell;
+    e = launch_main(a, st);
+    if (e != cudaSuccess) return e;
+    if (c->prof) e = cudaEventRecordWithFlags(c->pev[3], st, cudaEventRecordExternal);
+    return e;
+}
+
+// kernels per step: bbox, keys+histogram, per radix pass (upsweep except pass 0, scan,
+// downsweep), cell table, reorder, ORCA kernel
+static int launches_per_step(const orca_ctx* c) { return 2 + 3 * c->plan.max_passes - 1 + 3; }
+
+static int build_graphs(orca_ctx* ctx) {
+    drop_graphs(ctx);
+    for (int par = 0; par < 2; ++par) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        cudaError_t e = enqueue_step(ctx, par, ctx->cap);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(ctx, e, "kernel launch during capture");
+        }
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ctx->exec[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    ctx->graph_n = ctx->n;
+    return ORCA_OK;
+}
+
+static int check_device_error(orca_ctx* ctx, cudaStream_t st) {
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, &ctx->bins.misc->error, sizeof(int), cudaMemcpyDeviceToHost, st),
+       "cudaMemcpyAsync(error word)");
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (herr & kErrNumeric) return fail(ctx, ORCA_ERR_NUMERIC, "non-finite velocity or position produced");
+    if (herr & kErrTimeout) return fail(ctx, ORCA_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (herr & kErrCapacity)
+        return fail(ctx, ORCA_ERR_CAPACITY, "crowd extent does not fit the cell table (non-finite positions?)");
+    return ORCA_OK;
+}
+
+extern "C" {
+
+ORCA_API int orca_workspace_size(const orca_params* params, size_t* bytes) {
+    if (!params || !bytes) return fail(nullptr, ORCA_ERR_ARG, "null argument");
+    Plan pl;
+    if (!make_plan(*params, pl)) return fail(nullptr, ORCA_ERR_ARG, "invalid orca_params");
+    *bytes = pl.total;
+    return ORCA_OK;
+}
+
+ORCA_API int orca_create(const orca_params* params, void* workspace, size_t workspace_bytes,
+                         orca_ctx** out) {
+    if (!out) return fail(nullptr, ORCA_ERR_ARG, "null out");
+    *out = nullptr;
+    if (!params) return fail(nullptr, ORCA_ERR_ARG, "null params");
+    Plan pl;
+    if (!make_plan(*params, pl)) return fail(nullptr, ORCA_ERR_ARG, "invalid orca_params");
+    if (workspace && ((uintptr_t)workspace & 255))
+        return fail(nullptr, ORCA_ERR_ARG, "workspace must be 256-byte aligned");
+    if (workspace && workspace_bytes < pl.total)
+        return fail(nullptr, ORCA_ERR_NOMEM, "workspace smaller than orca_workspace_size()");
+    orca_ctx* ctx = new (std::nothrow) orca_ctx();
+    if (!ctx) return fail(nullptr, ORCA_ERR_NOMEM, "host allocation failed");
+    ctx->p = *params;
+    ctx->plan = pl;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess && workspace) {
+        ctx->ws = (char*)workspace;
+    } else if (e == cudaSuccess) {
+        e = cudaMalloc((void**)&ctx->ws, pl.total);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return fail(nullptr, ORCA_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        ctx->own_ws = true;
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        bind_buffers(ctx);
+        e = cudaMemset(ctx->bins.misc, 0, sizeof(DeviceMisc));
+    }
+    if (e != cudaSuccess) {
+        std::string m = std::string("context set-up: ") + cudaGetErrorString(e);
+        if (ctx->own_ws) cudaFree(ctx->ws);
+        if (ctx->cap) cudaStreamDestroy(ctx->cap);
+        delete ctx;
+        return fail(nullptr, ORCA_ERR_CUDA, m);
+    }
+    *out = ctx;
+    return ORCA_OK;
+}
+
+ORCA_API int orca_destroy(orca_ctx* ctx) {
+    if (!ctx) return ORCA_ERR_ARG;
+    cudaDeviceSynchronize();
+    drop_graphs(ctx);
+    for (int q = 0; q < 4; ++q)
+        if (ctx->pev[q]) cudaEventDestroy(ctx->pev[q]);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->own_ws) cudaFree(ctx->ws);
+    delete ctx;
+    return ORCA_OK;
+}
+
+ORCA_API int orca_profile(orca_ctx* ctx, int enable) {
+    if (!ctx) return ORCA_ERR_ARG;
+    bool on = enable != 0;
+    if (on && !ctx->pev[0])
+        for (int q = 0; q < 4; ++q) CK(cudaEventCreate(&ctx->pev[q]), "cudaEventCreate");
+    if (on != ctx->prof) drop_graphs(ctx);
+    ctx->prof = on;
+    return ORCA_OK;
+}
+
+ORCA_API int orca_profile_read(orca_ctx* ctx, float* ms3) {
+    if (!ctx || !ms3) return ORCA_ERR_ARG;
+    if (!ctx->prof || !ctx->stepped) return fail(ctx, ORCA_ERR_STATE, "no profiled step yet");
+    CK(cudaEventSynchronize(ctx->pev[3]), "cudaEventSynchronize");
+    for (int q = 0; q < 3; ++q) CK(cudaEventElapsedTime(&ms3[q], ctx->pev[q], ctx->pev[q + 1]), "cudaEventElapsedTime");
+    return ORCA_OK;
+}
+
+ORCA_API int orca_launches_per_step(const orca_ctx* ctx, int32_t* count) {
+    if (!ctx || !count) return ORCA_ERR_ARG;
+    *count = launches_per_step(ctx);
+    return ORCA_OK;
+}
+
+ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy, const float* vel_xy,
+                             const float* goal_xy, const float* radius, const float* max_speed,
+                             const float* pref_speed, const float* time_horizon, int where,
+                             void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (n < 0) return fail(ctx, ORCA_ERR_ARG, "n < 0");
+    if (n > ctx->plan.N) return fail(ctx, ORCA_ERR_CAPACITY, "n exceeds max_agents");
+    if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
+    if (n > 0 && (!pos_xy || !vel_xy || !goal_xy || !radius || !max_speed || !pref_speed || !time_horizon))
+        return fail(ctx, ORCA_ERR_ARG, "null array");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemcpyKind kind = where == ORCA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    size_t N = (size_t)n;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(ctx->PV[0].pos, pos_xy, N * 8, kind, st), "copy pos");
+        CK(cudaMemcpyAsync(ctx->PV[0].vel, vel_xy, N * 8, kind, st), "copy vel");
+        CK(cudaMemcpyAsync(ctx->PR[0].goal, goal_xy, N * 8, kind, st), "copy goal");
+        CK(cudaMemcpyAsync(ctx->PR[0].radius, radius, N * 4, kind, st), "copy radius");
+        CK(cudaMemcpyAsync(ctx->PR[0].max_speed, max_speed, N * 4, kind, st), "copy max_speed");
+        CK(cudaMemcpyAsync(ctx->PR[0].pref_speed, pref_speed, N * 4, kind, st), "copy pref_speed");
+        CK(cudaMemcpyAsync(ctx->PR[0].tau, time_horizon, N * 4, kind, st), "copy time_horizon");
+        CK(launch_iota(n, ctx->PR[0].id, st), "iota kernel");
+    }
+    CK(cudaMemsetAsync(ctx->bins.misc, 0, sizeof(DeviceMisc), st), "reset misc");
+    CK(cudaMemsetAsync(ctx->blk, 0, (size_t)ctx->plan.nmb * 4 * sizeof(unsigned long long), st),
+       "reset counters");
+    if (ctx->rec_nbr && n > 0) CK(cudaMemsetAsync(ctx->rec_nbr, 0xff, N * ctx->plan.K * 4, st), "reset record");
+    if (ctx->rec_cell && n > 0) CK(cudaMemsetAsync(ctx->rec_cell, 0, N * 4, st), "reset record");
+    if (where == ORCA_HOST) CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    ctx->n = n;
+    ctx->cur = 0;
+    ctx->stepped = false;
+    return ORCA_OK;
+}
+
+ORCA_API int orca_step(orca_ctx* ctx, int32_t nsteps, void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (nsteps < 0) return fail(ctx, ORCA_ERR_ARG, "nsteps < 0");
+    if (ctx->n == 0 || nsteps == 0) return ORCA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool graphs = !(ctx->p.flags & ORCA_FLAG_NO_GRAPH);
+    if (graphs && ctx->graph_n != ctx->n) {
+        int r = build_graphs(ctx);
+        if (r != ORCA_OK) return r;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        if (graphs) CK(cudaGraphLaunch(ctx->exec[ctx->cur], st), "cudaGraphLaunch");
+        else CK(enqueue_step(ctx, ctx->cur, st), "step launch");
+        ctx->cur ^= 1;
+    }
+    ctx->stepped = true;
+    return ORCA_OK;
+}
+
+ORCA_API int orca_get_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int where, void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t N = (size_t)ctx->n;
+    if (ctx->n > 0) {
+        if (where == ORCA_DEVICE) {
+            CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (float2*)pos_xy,
+                                (float2*)vel_xy, st), "unpermute kernel");
+        } else {
+            CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, ctx->stage[0],
+                                ctx->stage[1], st), "unpermute kernel");
+            if (pos_xy) CK(cudaMemcpyAsync(pos_xy, ctx->stage[0], N * 8, cudaMemcpyDeviceToHost, st), "copy pos");
+            if (vel_xy) CK(cudaMemcpyAsync(vel_xy, ctx->stage[1], N * 8, cudaMemcpyDeviceToHost, st), "copy vel");
+        }
+    }
+    if (where == ORCA_HOST) return check_device_error(ctx, st);
+    return ORCA_OK;
+}
+
+ORCA_API int orca_get_neighbors(orca_ctx* ctx, int32_t* nbr, int where, void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (!ctx->rec_nbr) return fail(ctx, ORCA_ERR_STATE, "context created without ORCA_FLAG_RECORD");
+    if (!nbr) return fail(ctx, ORCA_ERR_ARG, "null nbr");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = (size_t)ctx->n * ctx->plan.K * 4;
+    if (bytes)
+        CK(cudaMemcpyAsync(nbr, ctx->rec_nbr, bytes,
+                           where == ORCA_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st),
+           "copy neighbours");
+    if (where == ORCA_HOST) CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return ORCA_OK;
+}
+
+ORCA_API int orca_get_cells(orca_ctx* ctx, uint32_t* cell, float* grid_f, int32_t* grid_i, int where,
+                            void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (!ctx->rec_cell) return fail(ctx, ORCA_ERR_STATE, "context created without ORCA_FLAG_RECORD");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cell && ctx->n)
+        CK(cudaMemcpyAsync(cell, ctx->rec_cell, (size_t)ctx->n * 4,
+                           where == ORCA_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st),
+           "copy cells");
+    GridDev g;
+    CK(cudaMemcpyAsync(&g, &ctx->bins.misc->grid, sizeof g, cudaMemcpyDeviceToHost, st), "copy grid");
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (grid_f) {
+        grid_f[0] = g.xmin;
+        grid_f[1] = g.ymin;
+        grid_f[2] = g.s;
+        grid_f[3] = g.inv;
+    }
+    if (grid_i) {
+        grid_i[0] = g.gx;
+        grid_i[1] = g.gy;
+    }
+    return ORCA_OK;
+}
+
+ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream) {
+    if (!ctx || !counters4) return ORCA_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t cnt = (size_t)ctx->plan.nmb * 4;
+    unsigned long long* h = new (std::nothrow) unsigned long long[cnt];
+    if (!h) return fail(ctx, ORCA_ERR_NOMEM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(h, ctx->blk, cnt * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        delete[] h;
+        return cuda_fail(ctx, e, "copy counters");
+    }
+    for (int q = 0; q < 4; ++q) counters4[q] = 0;
+    for (size_t b = 0; b < (size_t)ctx->plan.nmb; ++b)
+        for (int q = 0; q < 4; ++q) counters4[q] += (int64_t)h[4 * b + q];
+    delete[] h;
+    return ORCA_OK;
+}
+
+ORCA_API int orca_sync(orca_ctx* ctx, void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    return check_device_error(ctx, (cudaStream_t)stream);
+}
+
+ORCA_API int orca_num_agents(const orca_ctx* ctx, int32_t* n) {
+    if (!ctx || !n) return ORCA_ERR_ARG;
+    *n = ctx->n;
+    return ORCA_OK;
+}
+
+ORCA_API const char* orca_last_error(const orca_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+ORCA_API const char* orca_status_string(int status) {
+    switch (status) {
+        case ORCA_OK: return "ok";
+        case ORCA_ERR_ARG: return "invalid argument";
+        case ORCA_ERR_NOMEM: return "out of memory";
+        case ORCA_ERR_CUDA: return "CUDA error";
+        case ORCA_ERR_STATE: return "invalid state";
+        case ORCA_ERR_NUMERIC: return "non-finite result";
+        case ORCA_ERR_TIMEOUT: return "device wait timed out";
+        case ORCA_ERR_CAPACITY: return "capacity exceeded";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

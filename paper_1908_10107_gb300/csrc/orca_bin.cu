@@ -1,0 +1,369 @@
+// orca_bin.cu -- spatial binning of the crowd (Fig. 2: "messages organised into bins").
+//
+// Per step, on one stream, with no host round trip:
+//   bbox_grid       exact min/max of positions -> grid descriptor (cell edge, gx, gy).
+//   keys_hist       cell key of every agent + digit histogram of radix pass 0.
+//   radix_upsweep / radix_scan / radix_downsweep   stable LSD radix sort of
+//                   (cell key, slot) with 8-bit digits; only ceil(bits(num_cells)/8)
+//                   passes do work, the rest return at once.
+//   cell_table      cell_start[c] = first sorted slot of cell c, for every c in
+//                   [0, num_cells] (empty cells included, no memset needed).
+//   reorder         gathers state and parameters into the new cell order.
+//
+// The sort is stable with respect to the previous step's cell order, so the layout is
+// deterministic; nothing downstream depends on the order inside a cell (neighbours are
+// ranked by (distance, agent index)).
+#include "orca_common.cuh"
+
+namespace orca {
+
+// ---------------------------------------------------------------------------------
+// Bounding box and grid.  Each block reduces a grid-stride share; the last block to
+// finish (ticket counter, no waiting) folds the partials and derives the grid in FP32:
+// inv = fl(1/s), g = floor(fl(fl(max - min) * inv)) + 1, doubling s while gx*gy exceeds
+// the table capacity.
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) bbox_grid_kernel(int n, const float2* __restrict__ pos,
+                                                        float cell_size, long long max_cells,
+                                                        int max_passes, float4* partials,
+                                                        DeviceMisc* misc) {
+    float xmin = INFINITY, ymin = INFINITY, xmax = -INFINITY, ymax = -INFINITY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float2 p = pos[i];
+        xmin = fminf(xmin, p.x);
+        xmax = fmaxf(xmax, p.x);
+        ymin = fminf(ymin, p.y);
+        ymax = fmaxf(ymax, p.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        xmin = fminf(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+        xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+        ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    }
+    __shared__ float4 s_part[8];
+    __shared__ bool s_last;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s_part[warp] = make_float4(xmin, ymin, xmax, ymax);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float4 r = s_part[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            r.x = fminf(r.x, s_part[w].x);
+            r.y = fminf(r.y, s_part[w].y);
+            r.z = fmaxf(r.z, s_part[w].z);
+            r.w = fmaxf(r.w, s_part[w].w);
+        }
+        partials[blockIdx.x] = r;
+        __threadfence();
+        unsigned int ticket = atomicAdd(&misc->bbox_ticket, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    float4 r = __ldcg(&partials[0]);
+    for (int b = 1; b < (int)gridDim.x; ++b) {
+        float4 q = __ldcg(&partials[b]);
+        r.x = fminf(r.x, q.x);
+        r.y = fminf(r.y, q.y);
+        r.z = fmaxf(r.z, q.z);
+        r.w = fmaxf(r.w, q.w);
+    }
+    misc->bbox_ticket = 0;
+    GridDev g;
+    g.xmin = r.x;
+    g.ymin = r.y;
+    float ex = __fsub_rn(r.z, r.x), ey = __fsub_rn(r.w, r.y);
+    float s = cell_size, inv = 1.0f, fx = 0.0f, fy = 0.0f;
+    bool fits = false;
+    for (int it = 0; it < 200 && !fits; ++it) {
+        inv = __fdiv_rn(1.0f, s);
+        fx = floorf(__fmul_rn(ex, inv));
+        fy = floorf(__fmul_rn(ey, inv));
+        double cells = ((double)fx + 1.0) * ((double)fy + 1.0);
+        if (cells <= (double)max_cells) fits = true;
+        else s = __fmul_rn(s, 2.0f);
+    }
+    if (!fits || !(ex >= 0.0f) || !(ey >= 0.0f)) {
+        // non-finite or absurd extent: everything in one cell, flag the error
+        atomicOr(&misc->error, kErrCapacity);
+        fx = fy = 0.0f;
+        s = 1.0f;
+        inv = 1.0f;
+        if (!(g.xmin == g.xmin) || isinf(g.xmin)) g.xmin = 0.0f;
+        if (!(g.ymin == g.ymin) || isinf(g.ymin)) g.ymin = 0.0f;
+    }
+    g.s = s;
+    g.inv = inv;
+    g.gx = (int)fx + 1;
+    g.gy = (int)fy + 1;
+    g.num_cells = g.gx * g.gy;
+    int bits = 0;
+    while (bits < 31 && (1u << bits) < (unsigned)g.num_cells) ++bits;
+    int passes = (bits + kRadixBits - 1) / kRadixBits;
+    g.passes = passes < 1 ? 1 : (passes > max_passes ? max_passes : passes);
+    // rounding of fl(fl(x - xmin) * inv) moves a cell boundary by at most a few ulps of
+    // the extent; 1e-5 relative is a wide margin
+    g.slop = 1e-5f * (fabsf(g.xmin) + fabsf(g.ymin) + ex + ey + 2.0f * s) + 1e-6f;
+    misc->grid = g;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Cell key of each agent and the digit-0 histogram of this block's tile.
+__global__ void __launch_bounds__(kSortThreads) keys_hist_kernel(int n, const float2* __restrict__ pos,
+                                                                 const DeviceMisc* __restrict__ misc,
+                                                                 uint32_t* __restrict__ keys,
+                                                                 uint32_t* __restrict__ hist) {
+    __shared__ uint32_t s_hist[kRadixBuckets];
+    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) s_hist[d] = 0;
+    __syncthreads();
+    const GridDev g = misc->grid;
+    int base = blockIdx.x * kSortTile;
+#pragma unroll
+    for (int c = 0; c < kSortItems; ++c) {
+        int i = base + c * kSortThreads + threadIdx.x;
+        if (i < n) {
+            float2 p = pos[i];
+            int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
+            int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
+            uint32_t key = (uint32_t)cy * (uint32_t)g.gx + (uint32_t)cx;
+            keys[i] = key;
+            atomicAdd(&s_hist[key & (kRadixBuckets - 1)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x)
+        hist[d * gridDim.x + blockIdx.x] = s_hist[d];
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(int n, int pass,
+                                                                     const DeviceMisc* __restrict__ misc,
+                                                                     const uint32_t* __restrict__ keys,
+                                                                     uint32_t* __restrict__ hist) {
+    if (pass >= misc->grid.passes) return;
+    __shared__ uint32_t s_hist[kRadixBuckets];
+    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) s_hist[d] = 0;
+    __syncthreads();
+    int shift = pass * kRadixBits;
+    int base = blockIdx.x * kSortTile;
+#pragma unroll
+    for (int c = 0; c < kSortItems; ++c) {
+        int i = base + c * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&s_hist[(keys[i] >> shift) & (kRadixBuckets - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x)
+        hist[d * gridDim.x + blockIdx.x] = s_hist[d];
+}
+
+// Exclusive scan, in place, of hist[d * nblocks + b] (digit-major), one CTA.
+// Warps scan digits (coalesced along blocks); digit totals are scanned in shared memory.
+__global__ void __launch_bounds__(1024) radix_scan_kernel(int nblocks, int pass,
+                                                          const DeviceMisc* __restrict__ misc,
+                                                          uint32_t* __restrict__ hist) {
+    if (pass >= misc->grid.passes) return;
+    __shared__ uint32_t s_tot[kRadixBuckets];
+    __shared__ uint32_t s_base[kRadixBuckets];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int d = warp; d < kRadixBuckets; d += nw) {
+        uint32_t run = 0;
+        uint32_t* row = hist + (size_t)d * nblocks;
+        for (int b0 = 0; b0 < nblocks; b0 += 32) {
+            int b = b0 + lane;
+            uint32_t v = b < nblocks ? row[b] : 0u;
+            uint32_t inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (b < nblocks) row[b] = run + inc - v;
+            run += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) s_tot[d] = run;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t run = 0;
+        for (int d0 = 0; d0 < kRadixBuckets; d0 += 32) {
+            uint32_t v = s_tot[d0 + lane];
+            uint32_t inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            s_base[d0 + lane] = run + inc - v;
+            run += __shfl_sync(0xffffffffu, inc, 31);
+        }
+    }
+    __syncthreads();
+    for (int d = warp; d < kRadixBuckets; d += nw) {
+        uint32_t add = s_base[d];
+        uint32_t* row = hist + (size_t)d * nblocks;
+        for (int b = lane; b < nblocks; b += 32) row[b] += add;
+    }
+}
+
+// Stable scatter of one radix pass.  The tile is walked in order in chunks of one item
+// per thread; inside a warp, lanes with equal digits rank themselves with match.any, and
+// per-warp digit counts in shared memory order the warps.  vals == nullptr means the
+// identity (slot index).
+__global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
+    int n, int pass, const DeviceMisc* __restrict__ misc, const uint32_t* __restrict__ keys_in,
+    const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ offsets) {
+    if (pass >= misc->grid.passes) return;
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t s_run[kRadixBuckets];
+    __shared__ uint32_t s_wcnt[kWarps][kRadixBuckets];
+    int warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) {
+        s_run[d] = offsets[d * gridDim.x + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s_wcnt[w][d] = 0;
+    }
+    __syncthreads();
+    int shift = pass * kRadixBits;
+    int base = blockIdx.x * kSortTile;
+    unsigned lt = lanemask_lt();
+    for (int c = 0; c < kSortItems; ++c) {
+        int i = base + c * kSortThreads + threadIdx.x;
+        bool valid = i < n;
+        uint32_t key = valid ? keys_in[i] : 0u;
+        uint32_t val = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
+        uint32_t d = (key >> shift) & (kRadixBuckets - 1);
+        unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        unsigned rank = 0;
+        if (valid) {
+            unsigned peers = __match_any_sync(vmask, d);
+            rank = __popc(peers & lt);
+            if ((peers & lt) == 0) s_wcnt[warp][d] = __popc(peers);
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t dst = s_run[d] + rank;
+            for (int w = 0; w < warp; ++w) dst += s_wcnt[w][d];
+            keys_out[dst] = key;
+            vals_out[dst] = val;
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < kRadixBuckets; dd += blockDim.x) {
+            uint32_t tot = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                tot += s_wcnt[w][dd];
+                s_wcnt[w][dd] = 0;
+            }
+            s_run[dd] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// cell_start[c] for c in [0, num_cells]: slot t writes every cell in (key[t-1], key[t]].
+__global__ void __launch_bounds__(256) cell_table_kernel(int n, const uint32_t* __restrict__ keys_a,
+                                                         const uint32_t* __restrict__ keys_b,
+                                                         const DeviceMisc* __restrict__ misc,
+                                                         uint32_t* __restrict__ cell_start) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > n) return;
+    const GridDev& g = misc->grid;
+    const uint32_t* keys = (g.passes & 1) ? keys_b : keys_a;
+    int prev = t == 0 ? -1 : (int)keys[t - 1];
+    int cur = t == n ? g.num_cells : (int)keys[t];
+    for (int c = prev + 1; c <= cur; ++c) cell_start[c] = (uint32_t)t;
+}
+
+// Gather state and parameters into the sorted order.
+__global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __restrict__ vals_a,
+                                                      const uint32_t* __restrict__ vals_b,
+                                                      const DeviceMisc* __restrict__ misc,
+                                                      AgentState src_s, AgentState dst_s,
+                                                      AgentParams src_p, AgentParams dst_p) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint32_t* vals = (misc->grid.passes & 1) ? vals_b : vals_a;
+    uint32_t s = vals[t];
+    dst_s.pos[t] = src_s.pos[s];
+    dst_s.vel[t] = src_s.vel[s];
+    dst_p.goal[t] = src_p.goal[s];
+    dst_p.radius[t] = src_p.radius[s];
+    dst_p.max_speed[t] = src_p.max_speed[s];
+    dst_p.pref_speed[t] = src_p.pref_speed[s];
+    dst_p.tau[t] = src_p.tau[s];
+    dst_p.id[t] = src_p.id[s];
+}
+
+// State back to agent order (readout).
+__global__ void __launch_bounds__(256) unpermute_kernel(int n, AgentState s, const uint32_t* __restrict__ id,
+                                                        float2* __restrict__ pos_out,
+                                                        float2* __restrict__ vel_out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    uint32_t i = id[t];
+    if (pos_out) pos_out[i] = s.pos[t];
+    if (vel_out) vel_out[i] = s.vel[t];
+}
+
+__global__ void __launch_bounds__(256) iota_kernel(int n, uint32_t* __restrict__ id) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) id[t] = (uint32_t)t;
+}
+
+// ---------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------
+int sort_blocks(int n) { return (n + kSortTile - 1) / kSortTile; }
+
+cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_passes,
+                           const AgentState& cur, const BinBuffers& b, cudaStream_t st) {
+    int nb_bbox = (n + 255) / 256;
+    if (nb_bbox > kBboxBlocks) nb_bbox = kBboxBlocks;
+    bbox_grid_kernel<<<nb_bbox, 256, 0, st>>>(n, cur.pos, cell_size, max_cells, max_passes,
+                                              b.bbox_partials, b.misc);
+    int nsb = sort_blocks(n);
+    keys_hist_kernel<<<nsb, kSortThreads, 0, st>>>(n, cur.pos, b.misc, b.keys[0], b.hist);
+    for (int pass = 0; pass < max_passes; ++pass) {
+        int src = pass & 1, dst = src ^ 1;
+        if (pass > 0)
+            radix_upsweep_kernel<<<nsb, kSortThreads, 0, st>>>(n, pass, b.misc, b.keys[src], b.hist);
+        radix_scan_kernel<<<1, 1024, 0, st>>>(nsb, pass, b.misc, b.hist);
+        radix_downsweep_kernel<<<nsb, kSortThreads, 0, st>>>(
+            n, pass, b.misc, b.keys[src], pass == 0 ? nullptr : b.vals[src], b.keys[dst],
+            b.vals[dst], b.hist);
+    }
+    cell_table_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, b.keys[0], b.keys[1], b.misc,
+                                                            b.cell_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
+                           const AgentState& dst_s, const AgentParams& src_p,
+                           const AgentParams& dst_p, cudaStream_t st) {
+    reorder_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, b.vals[0], b.vals[1], b.misc, src_s, dst_s,
+                                                    src_p, dst_p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, float2* pos_out,
+                             float2* vel_out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    unpermute_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s, id, pos_out, vel_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    iota_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, id);
+    return cudaGetLastError();
+}
+
+}  // namespace orca

@@ -1,0 +1,109 @@
+// orca_common.cuh -- shared device-side definitions of the GB300 ORCA step.
+//
+// Data layout in HBM (one context, n agents, k neighbours):
+//   PV[0], PV[1]: float2 pos[n], float2 vel[n].  PV[0] holds the state between steps in
+//                 the current cell order; PV[1] receives the cell-sorted copy each step
+//                 (the "messages" of Fig. 2: what neighbours read).
+//   PR[0], PR[1]: per-agent parameters float2 goal, float radius, max_speed, pref_speed,
+//                 time_horizon and uint32 id (agent index of orca_set_agents).  They are
+//                 permuted together with the state; the current copy alternates each step.
+//   sort keys/values (uint32, ping-pong), per-block digit histograms, the cell table
+//   cell_start[num_cells + 1], the grid descriptor and counters.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace orca {
+
+constexpr int kMaxNeighbors = 32;
+constexpr int kRadixBits = 8;
+constexpr int kRadixBuckets = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;  // items per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kBboxBlocks = 304;  // 2 x 152 SMs
+
+// device error bits (latched in DeviceMisc::error)
+constexpr int kErrNumeric = 1;
+constexpr int kErrTimeout = 2;
+constexpr int kErrCapacity = 4;
+
+// Grid of square cells over the crowd's bounding box, computed on the device each step.
+struct GridDev {
+    float xmin, ymin;  // exact minima over agents
+    float s, inv;      // cell edge and fl32(1/s)
+    int gx, gy;        // cells per row / column
+    int num_cells;     // gx * gy
+    int passes;        // radix passes needed for keys < num_cells
+    float slop;        // conservative bound on cell-assignment rounding, metres
+    int pad[3];
+};
+
+struct DeviceMisc {
+    GridDev grid;
+    unsigned int bbox_ticket;  // last-block-done counter of the bbox reduction
+    int error;                 // kErr* bits
+    unsigned long long counters[4];  // agent-steps, LP3 agent-steps, candidates, lines
+};
+
+struct AgentParams {  // one of PR[0] / PR[1]
+    float2* goal;
+    float* radius;
+    float* max_speed;
+    float* pref_speed;
+    float* tau;
+    uint32_t* id;
+};
+
+struct AgentState {  // one of PV[0] / PV[1]
+    float2* pos;
+    float2* vel;
+};
+
+struct BinBuffers {
+    uint32_t* keys[2];
+    uint32_t* vals[2];
+    uint32_t* hist;
+    uint32_t* cell_start;
+    float4* bbox_partials;
+    DeviceMisc* misc;
+};
+
+struct MainArgs {
+    int n, k;
+    float nd, dt;
+    const DeviceMisc* misc;
+    DeviceMisc* misc_rw;
+    const uint32_t* cell_start;
+    AgentState in;                       // sorted copy (read)
+    AgentParams prm;                     // sorted parameters (read)
+    AgentState out;                      // new state, same slots
+    unsigned long long* block_counters;  // 4 per block, accumulated
+    int32_t* rec_nbr;                    // n*k in agent order, or null
+    uint32_t* rec_cell;                  // n in agent order, or null
+};
+
+// host launchers (orca_bin.cu, orca_main.cu)
+int sort_blocks(int n);
+int main_blocks(int n);
+cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_passes,
+                           const AgentState& cur, const BinBuffers& b, cudaStream_t st);
+cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
+                           const AgentState& dst_s, const AgentParams& src_p,
+                           const AgentParams& dst_p, cudaStream_t st);
+cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, float2* pos_out,
+                             float2* vel_out, cudaStream_t st);
+cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st);
+cudaError_t launch_main(const MainArgs& a, cudaStream_t st);
+
+// Cell coordinate along one axis in FP32, one rounding per operation:
+// floor(fl(fl(v - vmin) * inv)) clamped to [0, g - 1].
+__device__ __forceinline__ int cell_coord(float v, float vmin, float inv, int g) {
+    float q = __fmul_rn(__fsub_rn(v, vmin), inv);
+    int c = __float2int_rd(q);
+    c = c < 0 ? 0 : c;
+    return c > g - 1 ? g - 1 : c;
+}
+
+}  // namespace orca

@@ -43,6 +43,12 @@ class Scene:
     dt: float
     steps: int
 
+    def __post_init__(self):
+        # scene parameters are FP32 values, the precision the GPU receives them in, so
+        # that both sides of a parity check start from identical numbers
+        self.neighbor_dist = float(np.float32(self.neighbor_dist))
+        self.dt = float(np.float32(self.dt))
+
     @property
     def n(self) -> int:
         return int(self.pos.shape[0])

@@ -1,0 +1,225 @@
+"""GPU step vs the FP64 oracle through the C ABI (parity tests proper).
+
+Sizes span many 128-agent tiles with ragged tails; the full-size workloads are checked on
+sampled agents (the oracle steps only those, searching neighbours among all agents).
+"""
+import numpy as np
+import pytest
+
+from paper_1908_10107_gb300 import abi
+from paper_1908_10107_gb300 import scenarios as S
+
+import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_10107_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("steps_before", [0, 10, 60])
+def test_circle_swap_1024(steps_before):
+    rep = parity.gpu_step_and_compare(S.circle_swap(), steps_before=steps_before)
+    assert rep["rows"] == 1024
+
+
+@pytest.mark.parametrize("n,seed", [(16381, 1), (4099, 2)])
+@pytest.mark.parametrize("jitter", [False, True])
+def test_bidirectional_small(n, seed, jitter):
+    sc = S.bidirectional(n, seed=seed)
+    if jitter:
+        sc = S.jitter_velocities(sc, seed)
+    parity.gpu_step_and_compare(sc)
+
+
+def test_bidirectional_after_steps():
+    sc = S.bidirectional(8190, seed=3)
+    parity.gpu_step_and_compare(sc, steps_before=40)
+
+
+@pytest.mark.parametrize("k", [10, 20])
+def test_dense_small(k):
+    sc = S.dense(20011, seed=4)
+    sc.max_neighbors = k
+    sc = S.jitter_velocities(sc, 5)
+    parity.gpu_step_and_compare(sc)
+
+
+@pytest.mark.parametrize("cell_size", [0.3, 1.0, 2.5, 10.0, 40.0])
+def test_cell_size_does_not_change_results(cell_size):
+    sc = S.jitter_velocities(S.bidirectional(6000, seed=6), 6)
+    parity.gpu_step_and_compare(sc, cell_size=cell_size)
+
+
+def test_cell_capacity_doubling():
+    sc = S.jitter_velocities(S.bidirectional(5000, seed=7), 7)
+    parity.gpu_step_and_compare(sc, cell_size=0.1, max_cells=1000)
+
+
+@pytest.mark.parametrize("k", [1, 3, 16, 32])
+def test_neighbour_counts(k):
+    sc = S.jitter_velocities(S.dense(3000, seed=8), 8)
+    sc.max_neighbors = k
+    parity.gpu_step_and_compare(sc)
+
+
+def test_full_size_bidirectional_sampled():
+    sc = S.bidirectional()  # 524,288 agents, the benchmark's workload
+    rng = np.random.default_rng(0)
+    subset = np.sort(rng.choice(sc.n, 4000, replace=False))
+    parity.gpu_step_and_compare(sc, steps_before=5, subset=subset)
+
+
+def test_full_size_dense_sampled():
+    sc = S.dense()  # 2,097,152 agents, k = 20
+    rng = np.random.default_rng(1)
+    subset = np.sort(rng.choice(sc.n, 2000, replace=False))
+    parity.gpu_step_and_compare(sc, subset=subset)
+
+
+# ----------------------------------------------------------------------------- edge cases
+def _tiny(pos, vel=None, goal=None, r=0.5, vmax=1.5, pref=1.0, tau=5.0, nd=10.0, k=10, dt=0.1):
+    pos = np.asarray(pos, np.float32).reshape(-1, 2)
+    n = pos.shape[0]
+    f = lambda v: np.full(n, v, np.float32)
+    return S.Scene("tiny", pos, np.zeros_like(pos) if vel is None else np.asarray(vel, np.float32).reshape(-1, 2),
+                   (pos + 5.0) if goal is None else np.asarray(goal, np.float32).reshape(-1, 2),
+                   f(r), f(vmax), f(pref), f(tau), nd, k, dt, 1)
+
+
+def test_empty_crowd():
+    sim = parity.make_sim(_tiny(np.zeros((1, 2))))
+    abi.orca_set_agents(sim.ctx, 0, *[np.zeros(0, np.float32)] * 7)
+    sim.step(3)
+    pos, vel = sim.get_state()
+    assert pos.shape == (0, 2)
+    sim.sync()
+
+
+def test_single_agent():
+    parity.gpu_step_and_compare(_tiny([[1.0, 2.0]], goal=[[4.0, 6.0]]))
+
+
+def test_head_on_pair():
+    sc = _tiny([[-2.0, 0.0], [2.0, 0.0]], vel=[[1.0, 0.0], [-1.0, 0.0]],
+               goal=[[1000.0, 0.0], [-1000.0, 0.0]], vmax=1.33, pref=1.0, tau=10.0, dt=0.25)
+    parity.gpu_step_and_compare(sc)
+
+
+def test_coincident_agents():
+    pos = np.array([[0, 0], [0, 0], [0, 0], [0.3, 0.0], [5, 5]], np.float32)
+    parity.gpu_step_and_compare(_tiny(pos))
+
+
+def test_all_agents_in_one_cell():
+    sc = S.jitter_velocities(S.bidirectional(1500, seed=9), 9)
+    parity.gpu_step_and_compare(sc, cell_size=1e4)
+
+
+def test_neighbour_radius_is_strict():
+    # lattice spacing 2.0 with r_obs 2.0: the axis neighbours at exactly r_obs are excluded
+    g = np.stack(np.meshgrid(np.arange(20.0), np.arange(20.0)), -1).reshape(-1, 2) * 2.0
+    sc = _tiny(g, nd=2.0, r=0.3)
+    parity.gpu_step_and_compare(sc)
+    sc = _tiny(g, nd=2.0001, r=0.3)
+    parity.gpu_step_and_compare(sc)
+
+
+def test_lattice_ties_break_by_index():
+    g = np.stack(np.meshgrid(np.arange(30.0), np.arange(30.0)), -1).reshape(-1, 2)
+    perm = np.random.default_rng(10).permutation(len(g))
+    sc = _tiny(g[perm], nd=3.0, r=0.2, k=12)
+    parity.gpu_step_and_compare(sc)
+
+
+# ------------------------------------------------------------------- determinism, readout
+def test_graph_and_direct_launch_agree_bitwise():
+    sc = S.jitter_velocities(S.bidirectional(10000, seed=11), 11)
+    out = []
+    for flags in (0, abi.ORCA_FLAG_NO_GRAPH):
+        sim = parity.make_sim(sc, flags=flags)
+        sim.set_scene(sc)
+        sim.step(25)
+        out.append(sim.get_state())
+        sim.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_state_round_trip_is_exact():
+    sc = S.jitter_velocities(S.dense(7000, seed=12), 12)
+    sim = parity.make_sim(sc)
+    sim.set_scene(sc)
+    pos, vel = sim.get_state()
+    np.testing.assert_array_equal(pos, sc.pos)
+    np.testing.assert_array_equal(vel, sc.vel)
+    sim.step(7)
+    pos, vel = sim.get_state()
+    # resume from a checkpoint: reload the read-out state, continue, compare with uninterrupted
+    st = sc.copy()
+    st.pos, st.vel = pos, vel
+    sim2 = parity.make_sim(sc)
+    sim2.set_scene(st)
+    sim.step(5)
+    sim2.step(5)
+    a, b = sim.get_state(), sim2.get_state()
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_device_pointers_match_host_pointers():
+    import torch
+    sc = S.jitter_velocities(S.bidirectional(5000, seed=13), 13)
+    sim = parity.make_sim(sc)
+    dev = [torch.from_numpy(a).cuda() for a in sc.arrays()]
+    sim.set_agents(*dev)
+    sim.step(3)
+    pd, vd = sim.get_state(device=True)
+    torch.cuda.synchronize()
+    sim.set_scene(sc)
+    sim.step(3)
+    ph, vh = sim.get_state()
+    np.testing.assert_array_equal(pd.cpu().numpy(), ph)
+    np.testing.assert_array_equal(vd.cpu().numpy(), vh)
+
+
+def test_counters():
+    sc = S.jitter_velocities(S.bidirectional(4000, seed=14), 14)
+    sim = parity.make_sim(sc)
+    sim.set_scene(sc)
+    sim.step(4)
+    c = sim.counters()
+    assert c["agent_steps"] == 4 * sc.n
+    assert 0 < c["lp3_agent_steps"] <= c["agent_steps"]
+    assert c["lines"] <= 4 * sc.n * sc.max_neighbors
+    assert c["candidates"] >= c["lines"]
+
+
+def test_non_finite_input_is_reported():
+    sc = _tiny(np.random.default_rng(15).uniform(0, 10, (64, 2)))
+    sc.pos[3] = np.nan
+    sim = parity.make_sim(sc)
+    sim.set_scene(sc)
+    sim.step(1)
+    with pytest.raises(abi.OrcaError) as e:
+        sim.sync()
+    assert e.value.status == abi.ORCA_ERR_NUMERIC
+
+
+def test_capacity_errors():
+    sc = _tiny(np.zeros((10, 2)))
+    sim = parity.make_sim(sc, max_agents=5)
+    with pytest.raises(abi.OrcaError) as e:
+        sim.set_scene(sc)
+    assert e.value.status == abi.ORCA_ERR_CAPACITY
+    sim2 = parity.make_sim(sc, flags=0)
+    sim2.set_scene(sc)
+    with pytest.raises(abi.OrcaError) as e:
+        sim2.get_neighbors()
+    assert e.value.status == abi.ORCA_ERR_STATE

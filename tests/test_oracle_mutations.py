@@ -42,7 +42,7 @@ MUTANTS = {
                                "return d2a < d2b || (d2a == d2b && ja > jb);"),
     "pref_velocity_no_clamp": ("if (dist > pref_speed * dt) return scl(g, pref_speed / dist);",
                                "if (dist > 0.0) return scl(g, pref_speed / dist);"),
-    "integrate_old_velocity": ("pos_out[2 * i] = pa.x + x.x * dt;", "pos_out[2 * i] = pa.x + va.x * dt;"),
+    "integrate_old_velocity": ("pos_out[0] = pa.x + x.x * S->dt;", "pos_out[0] = pa.x + va.x * S->dt;"),
     "knn_wrong_agent": ("float dx = pf[2 * j] - pf[2 * i];", "float dx = pf[2 * j] - pf[2 * j + 1];"),
 }
 
