@@ -25,7 +25,7 @@ struct Layout {
 
 struct Plan {
     int N, K, max_cells, max_passes, nsb, nmb;
-    size_t o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2];
+    size_t o_msg, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2];
     size_t o_keys[2], o_vals[2], o_hist, o_cells, o_part, o_misc, o_blk, o_rnbr, o_rcell,
         o_stage[2];
     size_t total;
@@ -53,6 +53,7 @@ static bool make_plan(const orca_params& p, Plan& pl) {
     pl.nmb = main_blocks(pl.N);
     Layout L;
     size_t N = (size_t)pl.N;
+    pl.o_msg = L.add(N * sizeof(float4));
     for (int b = 0; b < 2; ++b) {
         pl.o_pv[b][0] = L.add(N * sizeof(float2));
         pl.o_pv[b][1] = L.add(N * sizeof(float2));
@@ -91,7 +92,8 @@ struct orca_ctx {
     int device = 0;
     char* ws = nullptr;
     bool own_ws = false;
-    AgentState PV[2];
+    AgentState PV[2];  // PV[0]: state between steps; PV[1].vel: sorted velocities
+    Sorted sorted;     // sorted messages (+ PV[1].vel)
     AgentParams PR[2];
     BinBuffers bins;
     unsigned long long* blk = nullptr;
@@ -144,6 +146,8 @@ static void bind_buffers(orca_ctx* c) {
         c->bins.vals[b] = (uint32_t*)(w + pl.o_vals[b]);
         c->stage[b] = (float2*)(w + pl.o_stage[b]);
     }
+    c->sorted.msg = (float4*)(w + pl.o_msg);
+    c->sorted.vel = c->PV[1].vel;
     c->bins.hist = (uint32_t*)(w + pl.o_hist);
     c->bins.cell_start = (uint32_t*)(w + pl.o_cells);
     c->bins.bbox_partials = (float4*)(w + pl.o_part);
@@ -171,7 +175,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     e = launch_binning(c->n, cs, pl.max_cells, pl.max_passes, c->PV[0], c->bins, st);
     if (e != cudaSuccess) return e;
     if (c->prof && (e = cudaEventRecordWithFlags(c->pev[1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
-    e = launch_reorder(c->n, c->bins, c->PV[0], c->PV[1], c->PR[par], c->PR[par ^ 1], st);
+    e = launch_reorder(c->n, c->bins, c->PV[0], c->sorted, c->PR[par], c->PR[par ^ 1], st);
     if (e != cudaSuccess) return e;
     if (c->prof && (e = cudaEventRecordWithFlags(c->pev[2], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     MainArgs a;
@@ -182,7 +186,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     a.misc = c->bins.misc;
     a.misc_rw = c->bins.misc;
     a.cell_start = c->bins.cell_start;
-    a.in = c->PV[1];
+    a.in = c->sorted;
     a.prm = c->PR[par ^ 1];
     a.out = c->PV[0];
     a.block_counters = c->blk;

@@ -282,24 +282,27 @@ __global__ void __launch_bounds__(256) cell_table_kernel(int n, const uint32_t* 
     for (int c = prev + 1; c <= cur; ++c) cell_start[c] = (uint32_t)t;
 }
 
-// Gather state and parameters into the sorted order.
+// Gather state and parameters into the sorted order; build the message records.
 __global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __restrict__ vals_a,
                                                       const uint32_t* __restrict__ vals_b,
                                                       const DeviceMisc* __restrict__ misc,
-                                                      AgentState src_s, AgentState dst_s,
+                                                      AgentState src_s, Sorted dst_s,
                                                       AgentParams src_p, AgentParams dst_p) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const uint32_t* vals = (misc->grid.passes & 1) ? vals_b : vals_a;
     uint32_t s = vals[t];
-    dst_s.pos[t] = src_s.pos[s];
+    float2 p = src_s.pos[s];
+    float r = src_p.radius[s];
+    uint32_t id = src_p.id[s];
+    dst_s.msg[t] = make_float4(p.x, p.y, r, __uint_as_float(id));
     dst_s.vel[t] = src_s.vel[s];
     dst_p.goal[t] = src_p.goal[s];
-    dst_p.radius[t] = src_p.radius[s];
+    dst_p.radius[t] = r;
     dst_p.max_speed[t] = src_p.max_speed[s];
     dst_p.pref_speed[t] = src_p.pref_speed[s];
     dst_p.tau[t] = src_p.tau[s];
-    dst_p.id[t] = src_p.id[s];
+    dst_p.id[t] = id;
 }
 
 // State back to agent order (readout).
@@ -346,7 +349,7 @@ cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_
 }
 
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
-                           const AgentState& dst_s, const AgentParams& src_p,
+                           const Sorted& dst_s, const AgentParams& src_p,
                            const AgentParams& dst_p, cudaStream_t st) {
     reorder_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, b.vals[0], b.vals[1], b.misc, src_s, dst_s,
                                                     src_p, dst_p);

@@ -61,6 +61,14 @@ struct AgentState {  // one of PV[0] / PV[1]
     float2* vel;
 };
 
+// Cell-sorted message of one agent (Fig. 2: what neighbours observe): position, radius
+// and agent index (as bits) in one 16-byte record; velocity is kept apart because only
+// the k selected neighbours need it.
+struct Sorted {
+    float4* msg;  // (x, y, radius, id bits)
+    float2* vel;
+};
+
 struct BinBuffers {
     uint32_t* keys[2];
     uint32_t* vals[2];
@@ -76,7 +84,7 @@ struct MainArgs {
     const DeviceMisc* misc;
     DeviceMisc* misc_rw;
     const uint32_t* cell_start;
-    AgentState in;                       // sorted copy (read)
+    Sorted in;                           // sorted messages and velocities (read)
     AgentParams prm;                     // sorted parameters (read)
     AgentState out;                      // new state, same slots
     unsigned long long* block_counters;  // 4 per block, accumulated
@@ -90,7 +98,7 @@ int main_blocks(int n);
 cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_passes,
                            const AgentState& cur, const BinBuffers& b, cudaStream_t st);
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
-                           const AgentState& dst_s, const AgentParams& src_p,
+                           const Sorted& dst_s, const AgentParams& src_p,
                            const AgentParams& dst_p, cudaStream_t st);
 cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, float2* pos_out,
                              float2* vel_out, cudaStream_t st);
