@@ -179,6 +179,37 @@ ORCA_API int orca_profile_read(orca_ctx* ctx, float* ms3);
  * sort needs fewer passes than the cell capacity allows). */
 ORCA_API int orca_launches_per_step(const orca_ctx* ctx, int32_t* count);
 
+/*
+ * One ORCA step without any memory allocation, for callers that cannot allocate GPU
+ * memory: code inside a host framework that must route every device allocation through
+ * its own pool, or call sites where cudaMalloc's implicit device synchronisation is not
+ * allowed.  (The paper has no counterpart; this is a deployment convenience.)
+ *
+ * Inputs are device arrays in agent order, laid out as for orca_set_agents (pos_xy,
+ * vel_xy, goal_xy: 2*n floats; radius, max_speed, pref_speed, time_horizon: n floats);
+ * neighbor_dist, max_neighbors (1..32), dt and cell_size (0 -> neighbor_dist/4) as in
+ * orca_params.  Outputs pos_out_xy, vel_out_xy: device arrays of 2*n floats receiving the
+ * state after one step, in agent order; they must not overlap the inputs.  The result is
+ * the same as one orca_step of a context holding these agents.
+ *
+ * All scratch space lives in a fixed device array inside the library, sized for at most
+ * 65,536 agents and 262,144 grid cells (about 7 MiB, held on every GPU that loads the
+ * library until the process exits); n above 65,536 returns ORCA_ERR_CAPACITY.  More cells
+ * than that only coarsen the grid (results do not change).  The first call on a device
+ * looks up the array's device address; make that first call before any stream capture.
+ * The call is asynchronous on `stream`; non-finite inputs give non-finite outputs and
+ * are not reported here.  Every call shares the one array, so calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race and corrupt each other:
+ * order them.  Errors: ORCA_ERR_ARG, ORCA_ERR_CAPACITY, ORCA_ERR_CUDA, with a message in
+ * orca_last_error(NULL).
+ */
+ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const float* vel_xy,
+                              const float* goal_xy, const float* radius, const float* max_speed,
+                              const float* pref_speed, const float* time_horizon,
+                              float neighbor_dist, int32_t max_neighbors, float dt,
+                              float cell_size, float* pos_out_xy, float* vel_out_xy,
+                              void* stream);
+
 /* Synchronise `stream` and report any latched device-side error. */
 ORCA_API int orca_sync(orca_ctx* ctx, void* stream);
 

@@ -76,6 +76,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_profile": ([vp, c.c_int], c.c_int),
         "orca_profile_read": ([vp, vp], c.c_int),
         "orca_launches_per_step": ([vp, c.POINTER(i32)], c.c_int),
+        "orca_step_static": ([i32] + [vp] * 7 + [c.c_float, i32, c.c_float, c.c_float, vp, vp, vp],
+                             c.c_int),
         "orca_num_agents": ([vp, c.POINTER(i32)], c.c_int),
         "orca_last_error": ([vp], c.c_char_p),
         "orca_status_string": ([c.c_int], c.c_char_p),
@@ -207,6 +209,22 @@ def orca_launches_per_step(ctx) -> int:
     n = ctypes.c_int32(0)
     _check(load_library().orca_launches_per_step(ctx, ctypes.byref(n)), ctx)
     return int(n.value)
+
+
+def orca_step_static(n, pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed, time_horizon,
+                     neighbor_dist, max_neighbors, dt, cell_size, pos_out_xy, vel_out_xy,
+                     stream=None):
+    """One step with no allocation (library-internal fixed scratch); device tensors only."""
+    ptrs = []
+    for a in (pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed, time_horizon, pos_out_xy,
+              vel_out_xy):
+        p, w = _ptr(a, np.float32)
+        if w != ORCA_DEVICE:
+            raise TypeError("orca_step_static takes CUDA tensors")
+        ptrs.append(p)
+    _check(load_library().orca_step_static(int(n), *ptrs[:7], float(neighbor_dist),
+                                           int(max_neighbors), float(dt), float(cell_size),
+                                           ptrs[7], ptrs[8], _stream(stream)))
 
 
 def orca_num_agents(ctx) -> int:

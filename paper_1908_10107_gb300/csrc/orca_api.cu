@@ -119,6 +119,11 @@ static int fail(orca_ctx* c, int code, const std::string& msg) {
     return code;
 }
 
+namespace orca {
+// Message for orca_last_error(NULL), for entry points that have no context.
+void set_context_free_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace orca
+
 static int cuda_fail(orca_ctx* c, cudaError_t e, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return fail(c, ORCA_ERR_CUDA, m);
