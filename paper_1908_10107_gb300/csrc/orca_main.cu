@@ -43,6 +43,7 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
     if (D < 0.0f) return false;
     float sq = sqrtf(D);
     float tL = -sq, tR = sq;
+#pragma unroll 1
     for (int j = 0; j < i; ++j) {
         float4 lj;
         if (!line(j, lj)) continue;
@@ -52,7 +53,7 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
             if (rhs > 0.0f) return false;
             continue;
         }
-        float t = -rhs / den;
+        float t = __fdividef(-rhs, den);
         if (den >= 0.0f) tR = fminf(tR, t);
         else tL = fmaxf(tL, t);
         if (tL > tR) return false;
@@ -77,7 +78,7 @@ __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float
     } else {
         float o2 = ox * ox + oy * oy;
         if (o2 > V * V) {
-            float s = V / sqrtf(o2);
+            float s = V * rsqrtf(o2);
             xx = ox * s;
             xy = oy * s;
         } else {
@@ -85,6 +86,7 @@ __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float
             xy = oy;
         }
     }
+#pragma unroll 1
     for (int i = 0; i < n; ++i) {
         float4 li;
         if (!line(i, li)) continue;
@@ -132,6 +134,7 @@ struct Bisectors {
 __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, float V, float& xx,
                                         float& xy) {
     float dist = 0.0f;
+#pragma unroll 1
     for (int i = begin; i < n; ++i) {
         float4 li = row[i];
         if (li.z - (li.x * xx + li.y * xy) > dist) {
@@ -168,18 +171,20 @@ __device__ __forceinline__ float4 orca_line_dev(float2 p, float2 v, float r, flo
         float wx = vx - px * itau, wy = vy - py * itau;
         float w2 = wx * wx + wy * wy, wp = wx * px + wy * py;
         if (wp < 0.0f && wp * wp > R2 * w2) {
-            float wl = sqrtf(w2);
-            L.x = wx / wl;
-            L.y = wy / wl;
-            L.z = L.x * v.x + L.y * v.y + 0.5f * (R * itau - wl);
+            float iw = rsqrtf(w2);
+            L.x = wx * iw;
+            L.y = wy * iw;
+            L.z = L.x * v.x + L.y * v.y + 0.5f * (R * itau - w2 * iw);
         } else {
-            float leg = sqrtf(p2 - R2);
+            float l2 = p2 - R2;
+            float leg = l2 * rsqrtf(l2);
+            float ip2 = __fdividef(1.0f, p2);
             if (det2f(px, py, wx, wy) > 0.0f) {  // left leg
-                L.x = -(px * R + py * leg) / p2;
-                L.y = (px * leg - py * R) / p2;
+                L.x = -(px * R + py * leg) * ip2;
+                L.y = (px * leg - py * R) * ip2;
             } else {  // right leg
-                L.x = (py * leg - px * R) / p2;
-                L.y = -(px * leg + py * R) / p2;
+                L.x = (py * leg - px * R) * ip2;
+                L.y = -(px * leg + py * R) * ip2;
             }
             L.z = 0.5f * (L.x * (v.x + vj.x) + L.y * (v.y + vj.y));
         }
@@ -188,10 +193,11 @@ __device__ __forceinline__ float4 orca_line_dev(float2 p, float2 v, float r, flo
         float ql = sqrtf(qx * qx + qy * qy);
         float nx, ny;
         if (ql > 0.0f) {
-            nx = -qx / ql;
-            ny = -qy / ql;
+            float iq = __fdividef(1.0f, ql);
+            nx = -qx * iq;
+            ny = -qy * iq;
         } else if (p2 > 0.0f) {
-            float ip = 1.0f / sqrtf(p2);
+            float ip = rsqrtf(p2);
             nx = -px * ip;
             ny = -py * ip;
         } else {
@@ -337,16 +343,22 @@ __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_ma
         unsigned long long kk[KMAX];
         int ks[KMAX];
         cand = knn_dev<KMAX>(a, g, t, p, k, kk, ks);
-        float2 v = a.in.vel[t];
-        float itau = 1.0f / a.prm.tau[t];
-        float half_idt = 0.5f / a.dt;
+        // park the neighbours' slots in the row (one unrolled store each), then build the
+        // half-planes in a rolled loop: one copy of the line code keeps the kernel small
+        // enough for the instruction cache
 #pragma unroll
         for (int l = 0; l < KMAX; ++l) {
-            if (l >= KMAX - k && kk[l] != ~0ull) {
-                int q = ks[l];
-                row[cnt++] = orca_line_dev(p, v, me4.z, itau, a.dt, half_idt, me, a.in.msg[q],
-                                           a.in.vel[q]);
-            }
+            if (l >= KMAX - k && kk[l] != ~0ull) row[cnt++].w = __int_as_float(ks[l]);
+        }
+        float2 v = a.in.vel[t];
+        float itau = __fdividef(1.0f, a.prm.tau[t]);
+        float idt = __fdividef(1.0f, a.dt);
+        float half_idt = 0.5f * idt;
+#pragma unroll 1
+        for (int l = 0; l < cnt; ++l) {
+            int q = __float_as_int(row[l].w);
+            row[l] = orca_line_dev(p, v, me4.z, itau, a.dt, half_idt, me, a.in.msg[q],
+                                   a.in.vel[q]);
         }
         if (a.rec_nbr) {
             int w = 0;
@@ -366,14 +378,15 @@ __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_ma
         float2 goal = a.prm.goal[t];
         float pref = a.prm.pref_speed[t], V = a.prm.max_speed[t];
         float gx_ = goal.x - p.x, gy_ = goal.y - p.y;
-        float gd = sqrtf(gx_ * gx_ + gy_ * gy_);
+        float g2 = gx_ * gx_ + gy_ * gy_;
+        float ig = rsqrtf(g2);
         float ox, oy;
-        if (gd > pref * a.dt) {
-            ox = gx_ * (pref / gd);
-            oy = gy_ * (pref / gd);
+        if (g2 * ig > pref * a.dt) {
+            ox = gx_ * (pref * ig);
+            oy = gy_ * (pref * ig);
         } else {
-            ox = gx_ / a.dt;
-            oy = gy_ / a.dt;
+            ox = gx_ * idt;
+            oy = gy_ * idt;
         }
         RowLines rl{row};
         int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy);
