@@ -247,6 +247,11 @@ def main():
     sc = scenarios.bidirectional(args.agents)
     sim = abi.OrcaSim.for_scene(sc, cell_size=args.cell_size)
     sim.set_scene(sc)
+    tune = None
+    if args.cell_size <= 0:
+        from paper_1908_10107_gb300 import autotune
+        tune = autotune.tune_cell_size(sim, sc, use_cache=False, cache_path=None)
+        args.cell_size = tune["cell_size"]
     abi.orca_profile(sim.ctx, True)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -348,7 +353,9 @@ def main():
                    "cell_size_m": float(gf[2]) if gf is not None else None,
                    "grid": [int(gi[0]), int(gi[1])] if gi is not None else None,
                    "l2": "flushed between steps (256 MiB write); per-step CUDA events summed",
-                   "graph": "one CUDA graph replay per step"},
+                   "graph": "one CUDA graph replay per step",
+                   "cell_size_tuning_ms": ({f"{k:.4g}": round(v, 4) for k, v in tune["timings_ms"].items()}
+                                           if tune else "fixed by --cell-size")},
         "roofline": {"kernel": "orca_main (neighbours + half-planes + LP + integrate)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,

@@ -210,6 +210,13 @@ ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const float* vel_x
                               float cell_size, float* pos_out_xy, float* vel_out_xy,
                               void* stream);
 
+/*
+ * Change the grid cell edge (metres, > 0; 0 -> neighbor_dist / 4) used from the next
+ * orca_step on.  Results do not depend on it (the neighbour search is exact for any
+ * edge); speed does.  Rebuilds the step graphs.
+ */
+ORCA_API int orca_set_cell_size(orca_ctx* ctx, float cell_size);
+
 /* Synchronise `stream` and report any latched device-side error. */
 ORCA_API int orca_sync(orca_ctx* ctx, void* stream);
 

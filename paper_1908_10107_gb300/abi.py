@@ -76,6 +76,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_profile": ([vp, c.c_int], c.c_int),
         "orca_profile_read": ([vp, vp], c.c_int),
         "orca_launches_per_step": ([vp, c.POINTER(i32)], c.c_int),
+        "orca_set_cell_size": ([vp, c.c_float], c.c_int),
         "orca_step_static": ([i32] + [vp] * 7 + [c.c_float, i32, c.c_float, c.c_float, vp, vp, vp],
                              c.c_int),
         "orca_num_agents": ([vp, c.POINTER(i32)], c.c_int),
@@ -203,6 +204,10 @@ def orca_profile_read(ctx) -> np.ndarray:
     out = np.zeros(3, np.float32)
     _check(load_library().orca_profile_read(ctx, ctypes.c_void_p(out.ctypes.data)), ctx)
     return out
+
+
+def orca_set_cell_size(ctx, cell_size: float):
+    _check(load_library().orca_set_cell_size(ctx, float(cell_size)), ctx)
 
 
 def orca_launches_per_step(ctx) -> int:

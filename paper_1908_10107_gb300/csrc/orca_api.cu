@@ -321,6 +321,16 @@ ORCA_API int orca_profile_read(orca_ctx* ctx, float* ms3) {
     return ORCA_OK;
 }
 
+ORCA_API int orca_set_cell_size(orca_ctx* ctx, float cell_size) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (!(cell_size >= 0.0f) || !isfinite(cell_size)) return fail(ctx, ORCA_ERR_ARG, "cell_size must be >= 0");
+    if (cell_size != ctx->p.cell_size) {
+        ctx->p.cell_size = cell_size;
+        drop_graphs(ctx);
+    }
+    return ORCA_OK;
+}
+
 ORCA_API int orca_launches_per_step(const orca_ctx* ctx, int32_t* count) {
     if (!ctx || !count) return ORCA_ERR_ARG;
     *count = launches_per_step(ctx);

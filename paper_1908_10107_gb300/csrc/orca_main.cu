@@ -211,91 +211,117 @@ __device__ __forceinline__ float4 orca_line_dev(float2 p, float2 v, float r, flo
     return L;
 }
 
-// Exact k nearest neighbours of the agent at sorted slot t.  Keys (d2 bits << 32 | id)
-// are kept ascending in kk; the first KMAX-k entries are permanent zero sentinels so that
-// the live window is the last k entries.  Returns the number of candidates examined.
+// Candidates q0..q1-1 (sorted slots) offered to the top-k list of the agent at slot t.
+// lim is the largest d^2 that can still enter: the largest float below r_obs^2 until the
+// list is full, then the k-th key's d^2 (equal d^2 is settled by the 64-bit key).
+template <int KMAX>
+__device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint32_t q0, uint32_t q1,
+                                            int t, float2 p, unsigned long long (&kk)[KMAX],
+                                            int (&ks)[KMAX], float& lim) {
+#pragma unroll 1
+    for (uint32_t q = q0; q < q1; ++q) {
+        float4 mj = msg[q];
+        float ddx = __fsub_rn(mj.x, p.x), ddy = __fsub_rn(mj.y, p.y);
+        float d2 = __fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy));
+        if (!(d2 <= lim) || (int)q == t) continue;
+        unsigned long long key =
+            ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(mj.w);
+        if (key >= kk[KMAX - 1]) continue;
+        bool done = false;
+#pragma unroll
+        for (int l = KMAX - 1; l > 0; --l) {
+            if (!done) {
+                if (key < kk[l - 1]) {
+                    kk[l] = kk[l - 1];
+                    ks[l] = ks[l - 1];
+                } else {
+                    kk[l] = key;
+                    ks[l] = (int)q;
+                    done = true;
+                }
+            }
+        }
+        if (!done) {
+            kk[0] = key;
+            ks[0] = (int)q;
+        }
+        if (kk[KMAX - 1] != ~0ull) lim = __uint_as_float((unsigned)(kk[KMAX - 1] >> 32));
+    }
+}
+
+// Exact k nearest neighbours of the agent at sorted slot t: keys (d2 bits << 32 | id)
+// kept ascending in kk; the first KMAX-k entries are permanent zero sentinels so that
+// the live window is the last k entries.  Ring search from the agent's cell (ring 0),
+// one visit per cell through a single loop (one copy of the insertion code).  Ring 1 is
+// visited nearest cells first -- the two sides the agent is closest to, their corner,
+// then the rest -- so the list fills with near candidates and prunes the others; wider
+// rings go round the perimeter.  A cell is skipped when a conservative lower bound of its
+// agents' fl32 d^2 (cell box minus the cell-assignment slop, d^2 rounding 1e-5) exceeds
+// lim; the search stops when the next ring's bound does.
 template <int KMAX>
 __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g, int t, float2 p,
                                             int k, unsigned long long (&kk)[KMAX], int (&ks)[KMAX]) {
-    const float4* __restrict__ msg = a.in.msg;
+    // ring-1 visiting order as offsets (ax*sx, ay*sy), ax+1 and ay+1 packed 2 bits each
+    constexpr unsigned kAx = 2u | 1u << 2 | 2u << 4 | 0u << 6 | 1u << 8 | 0u << 10 | 2u << 12 | 0u << 14;
+    constexpr unsigned kAy = 1u | 2u << 2 | 2u << 4 | 1u << 6 | 0u << 8 | 2u << 10 | 0u << 12 | 0u << 14;
     int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
     int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
     float nd2 = __fmul_rn(a.nd, a.nd);
+    float lim = __int_as_float(__float_as_int(nd2) - 1);  // largest float below r_obs^2
 #pragma unroll
     for (int l = 0; l < KMAX; ++l) {
         kk[l] = (l < KMAX - k) ? 0ull : ~0ull;
         ks[l] = -1;
     }
+    float ox = p.x - (g.xmin + (float)cx * g.s), oy = p.y - (g.ymin + (float)cy * g.s);
+    int sx = ox > 0.5f * g.s ? 1 : -1, sy = oy > 0.5f * g.s ? 1 : -1;
+    int r = 0, e = 0;
     unsigned cand = 0;
-    const float s = g.s, slop = g.slop;
-    for (int r = 0;; ++r) {
-        for (int dyc = -r; dyc <= r; ++dyc) {
-            int yy = cy + dyc;
-            if (yy < 0 || yy >= g.gy) continue;
-            bool full_row = (dyc == -r || dyc == r);
-            for (int part = 0; part < (full_row ? 1 : 2); ++part) {
-                int x0, x1;
-                if (full_row) {
-                    x0 = cx - r;
-                    x1 = cx + r;
-                } else {
-                    x0 = x1 = part == 0 ? cx - r : cx + r;
-                }
-                x0 = max(x0, 0);
-                x1 = min(x1, g.gx - 1);
-                if (x0 > x1) continue;
-                // conservative lower bound of fl32 d^2 to any agent of these cells
-                float bx0 = g.xmin + (float)x0 * s, bx1 = g.xmin + (float)(x1 + 1) * s;
-                float by0 = g.ymin + (float)yy * s, by1 = by0 + s;
-                float ddx = fmaxf(0.0f, fmaxf(bx0 - p.x, p.x - bx1) - slop);
-                float ddy = fmaxf(0.0f, fmaxf(by0 - p.y, p.y - by1) - slop);
-                float lb2 = (ddx * ddx + ddy * ddy) * (1.0f - 1e-5f);
-                bool full = kk[KMAX - 1] != ~0ull;
-                float kth = full ? __uint_as_float((unsigned)(kk[KMAX - 1] >> 32)) : nd2;
-                if (full ? (lb2 > kth) : (lb2 >= nd2)) continue;
-                int c0 = yy * g.gx + x0;
-                uint32_t q0 = a.cell_start[c0], q1 = a.cell_start[c0 + (x1 - x0) + 1];
+#pragma unroll 1
+    for (;;) {
+        int dx, dy;
+        if (r == 0) {
+            dx = dy = 0;
+        } else if (r == 1) {
+            dx = ((int)((kAx >> (2 * e)) & 3u) - 1) * sx;
+            dy = ((int)((kAy >> (2 * e)) & 3u) - 1) * sy;
+        } else if (e < 2 * r + 1) {
+            dx = e - r;
+            dy = -r;
+        } else if (e < 4 * r + 2) {
+            dx = e - (3 * r + 1);
+            dy = r;
+        } else if (e < 6 * r + 1) {
+            dx = -r;
+            dy = e - (5 * r + 1);
+        } else {
+            dx = r;
+            dy = e - 7 * r;
+        }
+        int x = cx + dx, y = cy + dy;
+        if (x >= 0 && y >= 0 && x < g.gx && y < g.gy) {
+            float bx0 = g.xmin + (float)x * g.s, by0 = g.ymin + (float)y * g.s;
+            float ddx = fmaxf(0.0f, fmaxf(bx0 - p.x, p.x - (bx0 + g.s)) - g.slop);
+            float ddy = fmaxf(0.0f, fmaxf(by0 - p.y, p.y - (by0 + g.s)) - g.slop);
+            if ((ddx * ddx + ddy * ddy) * (1.0f - 1e-5f) <= lim) {
+                int c = y * g.gx + x;
+                uint32_t q0 = a.cell_start[c], q1 = a.cell_start[c + 1];
                 cand += q1 - q0;
-                for (uint32_t q = q0; q < q1; ++q) {
-                    float4 mj = msg[q];
-                    float ddx2 = __fsub_rn(mj.x, p.x), ddy2 = __fsub_rn(mj.y, p.y);
-                    float d2 = __fadd_rn(__fmul_rn(ddx2, ddx2), __fmul_rn(ddy2, ddy2));
-                    unsigned long long key =
-                        ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(mj.w);
-                    if (!(d2 < nd2) || (int)q == t || key >= kk[KMAX - 1]) continue;
-                    bool done = false;
-#pragma unroll
-                    for (int l = KMAX - 1; l > 0; --l) {
-                        if (!done) {
-                            if (key < kk[l - 1]) {
-                                kk[l] = kk[l - 1];
-                                ks[l] = ks[l - 1];
-                            } else {
-                                kk[l] = key;
-                                ks[l] = (int)q;
-                                done = true;
-                            }
-                        }
-                    }
-                    if (!done) {
-                        kk[0] = key;
-                        ks[0] = (int)q;
-                    }
-                }
+                offer_range<KMAX>(a.in.msg, q0, q1, t, p, kk, ks, lim);
             }
         }
-        // stop when ring r+1 cannot hold a better candidate (or does not exist)
+        if (++e < (r == 0 ? 1 : 8 * r)) continue;
+        // next ring: does any of its cells exist and possibly lie within reach?
+        ++r;
+        e = 0;
         float lb = INFINITY;
-        if (cx - r - 1 >= 0) lb = fminf(lb, p.x - (g.xmin + (float)(cx - r) * s));
-        if (cx + r + 1 <= g.gx - 1) lb = fminf(lb, (g.xmin + (float)(cx + r + 1) * s) - p.x);
-        if (cy - r - 1 >= 0) lb = fminf(lb, p.y - (g.ymin + (float)(cy - r) * s));
-        if (cy + r + 1 <= g.gy - 1) lb = fminf(lb, (g.ymin + (float)(cy + r + 1) * s) - p.y);
+        if (cx - r >= 0) lb = fminf(lb, p.x - (g.xmin + (float)(cx - r + 1) * g.s));
+        if (cx + r <= g.gx - 1) lb = fminf(lb, (g.xmin + (float)(cx + r) * g.s) - p.x);
+        if (cy - r >= 0) lb = fminf(lb, p.y - (g.ymin + (float)(cy - r + 1) * g.s));
+        if (cy + r <= g.gy - 1) lb = fminf(lb, (g.ymin + (float)(cy + r) * g.s) - p.y);
         if (lb == INFINITY) break;
-        lb = fmaxf(0.0f, lb - slop);
-        float lb2 = lb * lb * (1.0f - 1e-5f);
-        bool full = kk[KMAX - 1] != ~0ull;
-        float kth = full ? __uint_as_float((unsigned)(kk[KMAX - 1] >> 32)) : nd2;
-        if (full ? (lb2 > kth) : (lb2 >= nd2)) break;
+        lb = fmaxf(0.0f, lb - g.slop);
+        if (lb * lb * (1.0f - 1e-5f) > lim) break;
     }
     return cand;
 }
