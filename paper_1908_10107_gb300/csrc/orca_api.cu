@@ -26,7 +26,7 @@ struct Layout {
 struct Plan {
     int N, K, max_cells, max_passes, nsb, nmb;
     size_t o_msg, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2];
-    size_t o_keys[2], o_vals[2], o_hist, o_cells, o_part, o_misc, o_blk, o_rnbr, o_rcell,
+    size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_part, o_misc, o_blk, o_rnbr, o_rcell,
         o_stage[2];
     size_t total;
 };
@@ -68,6 +68,7 @@ static bool make_plan(const orca_params& p, Plan& pl) {
         pl.o_stage[b] = L.add(N * sizeof(float2));
     }
     pl.o_hist = L.add((size_t)kRadixBuckets * pl.nsb * 4);
+    pl.o_tot = L.add((size_t)kRadixBuckets * 4);
     pl.o_cells = L.add(((size_t)pl.max_cells + 1) * 4);
     pl.o_part = L.add(kBboxBlocks * sizeof(float4));
     pl.o_misc = L.add(sizeof(DeviceMisc));
@@ -154,6 +155,7 @@ static void bind_buffers(orca_ctx* c) {
     c->sorted.msg = (float4*)(w + pl.o_msg);
     c->sorted.vel = c->PV[1].vel;
     c->bins.hist = (uint32_t*)(w + pl.o_hist);
+    c->bins.digit_totals = (uint32_t*)(w + pl.o_tot);
     c->bins.cell_start = (uint32_t*)(w + pl.o_cells);
     c->bins.bbox_partials = (float4*)(w + pl.o_part);
     c->bins.misc = (DeviceMisc*)(w + pl.o_misc);

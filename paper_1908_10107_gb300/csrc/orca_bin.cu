@@ -61,15 +61,34 @@ __global__ void __launch_bounds__(256) bbox_grid_kernel(int n, const float2* __r
         s_last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
+    // last block: fold the partials with every thread, then one thread derives the grid
     __threadfence();
-    float4 r = __ldcg(&partials[0]);
-    for (int b = 1; b < (int)gridDim.x; ++b) {
+    float4 r = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
         float4 q = __ldcg(&partials[b]);
         r.x = fminf(r.x, q.x);
         r.y = fminf(r.y, q.y);
         r.z = fmaxf(r.z, q.z);
         r.w = fmaxf(r.w, q.w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        r.x = fminf(r.x, __shfl_xor_sync(0xffffffffu, r.x, o));
+        r.y = fminf(r.y, __shfl_xor_sync(0xffffffffu, r.y, o));
+        r.z = fmaxf(r.z, __shfl_xor_sync(0xffffffffu, r.z, o));
+        r.w = fmaxf(r.w, __shfl_xor_sync(0xffffffffu, r.w, o));
+    }
+    __syncthreads();
+    if (lane == 0) s_part[warp] = r;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    r = s_part[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        r.x = fminf(r.x, s_part[w].x);
+        r.y = fminf(r.y, s_part[w].y);
+        r.z = fmaxf(r.z, s_part[w].z);
+        r.w = fmaxf(r.w, s_part[w].w);
     }
     misc->bbox_ticket = 0;
     GridDev g;
@@ -163,53 +182,32 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(int n, int 
         hist[d * gridDim.x + blockIdx.x] = s_hist[d];
 }
 
-// Exclusive scan, in place, of hist[d * nblocks + b] (digit-major), one CTA.
-// Warps scan digits (coalesced along blocks); digit totals are scanned in shared memory.
-__global__ void __launch_bounds__(1024) radix_scan_kernel(int nblocks, int pass,
-                                                          const DeviceMisc* __restrict__ misc,
-                                                          uint32_t* __restrict__ hist) {
+// Exclusive scan, in place, of each digit's row hist[d * nblocks + 0..nblocks-1] (one
+// warp per digit, kScanWarps digits per CTA), and the digit's total into totals[d].  The
+// scan across digits is done by every downsweep block from the 256 totals.
+constexpr int kScanWarps = 8;
+__global__ void __launch_bounds__(kScanWarps * 32) radix_scan_kernel(int nblocks, int pass,
+                                                                     const DeviceMisc* __restrict__ misc,
+                                                                     uint32_t* __restrict__ hist,
+                                                                     uint32_t* __restrict__ totals) {
     if (pass >= misc->grid.passes) return;
-    __shared__ uint32_t s_tot[kRadixBuckets];
-    __shared__ uint32_t s_base[kRadixBuckets];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int d = warp; d < kRadixBuckets; d += nw) {
-        uint32_t run = 0;
-        uint32_t* row = hist + (size_t)d * nblocks;
-        for (int b0 = 0; b0 < nblocks; b0 += 32) {
-            int b = b0 + lane;
-            uint32_t v = b < nblocks ? row[b] : 0u;
-            uint32_t inc = v;
+    int lane = threadIdx.x & 31;
+    int d = blockIdx.x * kScanWarps + (threadIdx.x >> 5);
+    uint32_t run = 0;
+    uint32_t* row = hist + (size_t)d * nblocks;
+    for (int b0 = 0; b0 < nblocks; b0 += 32) {
+        int b = b0 + lane;
+        uint32_t v = b < nblocks ? row[b] : 0u;
+        uint32_t inc = v;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (b < nblocks) row[b] = run + inc - v;
-            run += __shfl_sync(0xffffffffu, inc, 31);
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
-        if (lane == 0) s_tot[d] = run;
+        if (b < nblocks) row[b] = run + inc - v;
+        run += __shfl_sync(0xffffffffu, inc, 31);
     }
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t run = 0;
-        for (int d0 = 0; d0 < kRadixBuckets; d0 += 32) {
-            uint32_t v = s_tot[d0 + lane];
-            uint32_t inc = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            s_base[d0 + lane] = run + inc - v;
-            run += __shfl_sync(0xffffffffu, inc, 31);
-        }
-    }
-    __syncthreads();
-    for (int d = warp; d < kRadixBuckets; d += nw) {
-        uint32_t add = s_base[d];
-        uint32_t* row = hist + (size_t)d * nblocks;
-        for (int b = lane; b < nblocks; b += 32) row[b] += add;
-    }
+    if (lane == 0) totals[d] = run;
 }
 
 // Stable scatter of one radix pass.  The tile is walked in order in chunks of one item
@@ -219,14 +217,30 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(int nblocks, int pass,
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     int n, int pass, const DeviceMisc* __restrict__ misc, const uint32_t* __restrict__ keys_in,
     const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ offsets) {
+    uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ offsets,
+    const uint32_t* __restrict__ totals) {
     if (pass >= misc->grid.passes) return;
     constexpr int kWarps = kSortThreads / 32;
+    static_assert(kSortThreads == kRadixBuckets, "one thread per digit below");
     __shared__ uint32_t s_run[kRadixBuckets];
     __shared__ uint32_t s_wcnt[kWarps][kRadixBuckets];
+    __shared__ uint32_t s_wsum[kWarps];
     int warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) {
-        s_run[d] = offsets[d * gridDim.x + blockIdx.x];
+    {
+        // base of each digit: exclusive scan of the digit totals (thread = digit)
+        int lane0 = threadIdx.x & 31;
+        uint32_t v = totals[threadIdx.x], inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane0 >= o) inc += y;
+        }
+        if (lane0 == 31) s_wsum[warp] = inc;
+        __syncthreads();
+        uint32_t base = inc - v;
+        for (int w = 0; w < warp; ++w) base += s_wsum[w];
+        int d = threadIdx.x;
+        s_run[d] = base + offsets[d * gridDim.x + blockIdx.x];
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) s_wcnt[w][d] = 0;
     }
@@ -338,10 +352,11 @@ cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_
         int src = pass & 1, dst = src ^ 1;
         if (pass > 0)
             radix_upsweep_kernel<<<nsb, kSortThreads, 0, st>>>(n, pass, b.misc, b.keys[src], b.hist);
-        radix_scan_kernel<<<1, 1024, 0, st>>>(nsb, pass, b.misc, b.hist);
+        radix_scan_kernel<<<kRadixBuckets / kScanWarps, kScanWarps * 32, 0, st>>>(
+            nsb, pass, b.misc, b.hist, b.digit_totals);
         radix_downsweep_kernel<<<nsb, kSortThreads, 0, st>>>(
             n, pass, b.misc, b.keys[src], pass == 0 ? nullptr : b.vals[src], b.keys[dst],
-            b.vals[dst], b.hist);
+            b.vals[dst], b.hist, b.digit_totals);
     }
     cell_table_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, b.keys[0], b.keys[1], b.misc,
                                                             b.cell_start);

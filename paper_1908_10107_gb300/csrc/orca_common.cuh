@@ -73,6 +73,7 @@ struct BinBuffers {
     uint32_t* keys[2];
     uint32_t* vals[2];
     uint32_t* hist;
+    uint32_t* digit_totals;  // kRadixBuckets per radix pass (reused)
     uint32_t* cell_start;
     float4* bbox_partials;
     DeviceMisc* misc;

@@ -27,7 +27,7 @@ constexpr int kStaticMaxDevices = 64;
 
 // Scratch layout (bytes), every piece 256-byte aligned.
 struct StaticLayout {
-    size_t id, keys0, keys1, vals0, vals1, hist, cells, part, misc, msg, svel, goal, radius,
+    size_t id, keys0, keys1, vals0, vals1, hist, tot, cells, part, misc, msg, svel, goal, radius,
         vmax, pref, tau, sid, opos, ovel, blk, total;
 };
 
@@ -44,6 +44,7 @@ constexpr StaticLayout static_layout() {
     L.vals0 = o; o += al256(N * 4);
     L.vals1 = o; o += al256(N * 4);
     L.hist = o; o += al256((size_t)kRadixBuckets * nsb * 4);
+    L.tot = o; o += al256((size_t)kRadixBuckets * 4);
     L.cells = o; o += al256(((size_t)kStaticMaxCells + 1) * 4);
     L.part = o; o += al256(kBboxBlocks * 16);
     L.misc = o; o += al256(sizeof(DeviceMisc));
@@ -136,6 +137,7 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
     bins.vals[0] = (uint32_t*)(base + L.vals0);
     bins.vals[1] = (uint32_t*)(base + L.vals1);
     bins.hist = (uint32_t*)(base + L.hist);
+    bins.digit_totals = (uint32_t*)(base + L.tot);
     bins.cell_start = (uint32_t*)(base + L.cells);
     bins.bbox_partials = (float4*)(base + L.part);
     bins.misc = (DeviceMisc*)(base + L.misc);
