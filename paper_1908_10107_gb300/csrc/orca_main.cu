@@ -8,8 +8,9 @@
 //      neighbour (Fig. 1) written to the agent's row of shared memory;
 //   2. (thread per agent) LP2 -- incremental 2-D LP over the disc and the half-planes in
 //      neighbour order; agents whose LP2 fails are appended to a per-CTA queue;
-//   3. (thread per queued agent) LP3 -- least penetration (Section 3).  The queue keeps
-//      whole warps on LP3 work instead of idling the lanes whose LP2 succeeded;
+//   3. LP3 -- least penetration (Section 3) -- for the queued agents, a group of G lanes
+//      per agent, so the whole CTA works on the queue instead of idling the lanes whose
+//      LP2 succeeded;
 //   4. vel <- x, pos <- pos + x*dt into the same sorted slot of the state buffer.
 // Half-planes never leave the SM (the paper stores them in global memory, Section 5).
 #include "orca_common.cuh"
@@ -127,25 +128,93 @@ struct Bisectors {
     }
 };
 
-// LP3: least penetration (Section 3).  Penetration of line i at x: c_i - n_i.x.  When
-// line i is violated by more than the current penetration, LP2 in direction mode
+// LP3: least penetration (Section 3), by a group of G lanes (G a power of two, lanes
+// aligned in the warp) on one queued agent.  Penetration of line i at x: c_i - n_i.x.
+// When line i is violated by more than the current penetration, LP2 in direction mode
 // maximises n_i.x over the bisectors of i with the earlier lines; a numerically failed
-// LP2 keeps x.
-__device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, float V, float& xx,
-                                        float& xy) {
+// LP2 keeps x.  The group takes the sequential algorithm's decisions in the same order:
+//   * LP2's scan for the first violated bisector checks G bisectors at a time and takes
+//     the lowest violated index of the first chunk that has one (a ballot);
+//   * LP1's bounds over the earlier bisectors are split over the lanes and combined with
+//     min / max shuffles (exact, order-free); the sequential early exits (tL > tR, an
+//     infeasible parallel bisector) become "any lane failed" / "final tL > tR", which
+//     fail exactly when some prefix fails because the bounds only tighten.
+template <int G>
+__device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begin, float V,
+                                              float& xx, float& xy) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane & (G - 1);
+    const int base = lane & ~(G - 1);
+    const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << base);
     float dist = 0.0f;
 #pragma unroll 1
     for (int i = begin; i < n; ++i) {
-        float4 li = row[i];
-        if (li.z - (li.x * xx + li.y * xy) > dist) {
-            Bisectors bis{row, li};
-            float sx = xx, sy = xy;
-            if (lp2_dev(bis, i, V, li.x, li.y, true, xx, xy) < i) {
-                xx = sx;
-                xy = sy;
+        const float4 li = row[i];
+        if (!(li.z - (li.x * xx + li.y * xy) > dist)) continue;
+        Bisectors bis{row, li};
+        float nx = li.x * V, ny = li.y * V;  // direction mode starts at V * n_i
+        bool ok = true;
+        int start = 0;
+#pragma unroll 1
+        for (;;) {
+            int f = -1;
+#pragma unroll 1
+            for (int c0 = start; c0 < i; c0 += G) {
+                int j = c0 + g;
+                bool viol = false;
+                float4 q;
+                if (j < i && bis(j, q)) viol = q.z - (q.x * nx + q.y * ny) > 0.0f;
+                unsigned bal = (__ballot_sync(mask, viol) >> base) & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
+                if (bal) {
+                    f = c0 + __ffs(bal) - 1;
+                    break;
+                }
             }
-            dist = li.z - (li.x * xx + li.y * xy);
+            if (f < 0) break;  // every bisector holds: LP2 succeeded
+            float4 qf;
+            bis(f, qf);
+            float D = V * V - qf.z * qf.z;
+            if (D < 0.0f) {
+                ok = false;
+                break;
+            }
+            float sq = sqrtf(D);
+            float tL = -sq, tR = sq;
+            bool fail = false;
+#pragma unroll 1
+            for (int j = g; j < f; j += G) {
+                float4 qj;
+                if (!bis(j, qj)) continue;
+                float den = det2f(qf.x, qf.y, qj.x, qj.y);
+                float rhs = qj.z - qf.z * (qf.x * qj.x + qf.y * qj.y);
+                if (fabsf(den) <= kEps) {
+                    fail |= rhs > 0.0f;
+                    continue;
+                }
+                float t = __fdividef(-rhs, den);
+                if (den >= 0.0f) tR = fminf(tR, t);
+                else tL = fmaxf(tL, t);
+            }
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                tR = fminf(tR, __shfl_xor_sync(mask, tR, o));
+                tL = fmaxf(tL, __shfl_xor_sync(mask, tL, o));
+            }
+            if (__any_sync(mask, fail) || tL > tR) {
+                ok = false;
+                break;
+            }
+            float dx = qf.y, dy = -qf.x;
+            float t = (li.x * dx + li.y * dy > 0.0f) ? tR : tL;
+            nx = qf.z * qf.x + t * dx;
+            ny = qf.z * qf.y + t * dy;
+            start = f + 1;
         }
+        if (ok) {
+            xx = nx;
+            xy = ny;
+        }
+        dist = li.z - (li.x * xx + li.y * xy);
     }
 }
 
@@ -329,6 +398,13 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
 template <int KMAX>
 constexpr int main_min_blocks() { return KMAX <= 10 ? 7 : (KMAX <= 16 ? 4 : (KMAX <= 20 ? 4 : 2)); }
 
+// Lanes per queued agent in LP3, by measurement on the 524,288-agent flow (k = 10) and
+// the 2,097,152-agent dense crowd (k = 20): with at most 16 half-planes the group's
+// ballots and shuffles cost more than they save, so each queued agent gets one thread;
+// with 20-32 half-planes groups of 4 are 17% faster than one thread.
+template <int KMAX>
+__host__ __device__ constexpr int lp3_group() { return KMAX <= 16 ? 1 : 4; }
+
 template <int KMAX>
 constexpr size_t main_smem_bytes() { return sizeof(float4) * kMainThreads * (KMAX + 1); }
 
@@ -427,13 +503,15 @@ __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_ma
         }
     }
     __syncthreads();
-    // ---- phase 3: least penetration for the queued agents, packed onto whole warps
+    // ---- phase 3: least penetration for the queued agents, one group of G lanes each,
+    // so every thread of the CTA works on the queue
+    constexpr int G = lp3_group<KMAX>();
     const int nq = s_qn;
-    for (int q = tid; q < nq; q += kMainThreads) {
+    for (int q = tid / G; q < nq; q += kMainThreads / G) {
         int ag = s_queue[q];
         float2 x = s_x[ag];
-        lp3_dev(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
-        s_x[ag] = x;
+        lp3_group_dev<G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
+        if ((tid & (G - 1)) == 0) s_x[ag] = x;
     }
     __syncthreads();
     // ---- phase 4: integrate
