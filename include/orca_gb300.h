@@ -81,6 +81,7 @@ typedef struct orca_ctx orca_ctx;
  *   dt             time step in seconds (> 0).
  *   cell_size      grid cell edge in metres (0 -> neighbor_dist / 4).
  *   flags          ORCA_FLAG_*.
+ *   max_scenes     scenes a batch may hold (orca_set_scenes); 0 or 1 for single scenes.
  */
 typedef struct orca_params {
     int32_t max_agents;
@@ -90,8 +91,24 @@ typedef struct orca_params {
     float dt;
     float cell_size;
     uint32_t flags;
-    int32_t reserved;
+    int32_t max_scenes;  /* capacity in scenes for orca_set_scenes (0 or 1: single scene) */
 } orca_params;
+
+/*
+ * One scene of a batch (orca_set_scenes): `count` consecutive agents that interact only
+ * with each other, with their own ORCA parameters.
+ *   count          agents in the scene (>= 0).
+ *   max_neighbors  k for this scene (1 .. the context's max_neighbors).
+ *   neighbor_dist  r_obs (> 0).  dt: time step (> 0).  cell_size: grid edge (0 -> r_obs/4).
+ */
+typedef struct orca_scene {
+    int32_t count;
+    int32_t max_neighbors;
+    float neighbor_dist;
+    float dt;
+    float cell_size;
+    int32_t reserved;
+} orca_scene;
 
 /* Bytes of device workspace orca_create needs for these parameters (256-byte aligned). */
 ORCA_API int orca_workspace_size(const orca_params* params, size_t* bytes);
@@ -126,6 +143,29 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy,
                              const float* time_horizon, int where, void* stream);
 
 /*
+ * Load a batch of n_scenes independent scenes (1 <= n_scenes <= max_scenes) that advance
+ * together: scene s owns the next scenes[s].count agents of the arrays (laid out as for
+ * orca_set_agents, scene after scene), and its agents see only each other.  Each scene has
+ * its own grid over its own bounding box; the cell table is shared, each scene's share
+ * of max_cells being proportional to its agents (at least one cell; a scene that would
+ * need more doubles its cell edge).  `scenes` is a host array.  orca_step then advances
+ * every scene with one persistent launch of the per-agent kernel per step, inside the
+ * captured graph.  orca_set_agents returns the context to a single scene.
+ */
+ORCA_API int orca_set_scenes(orca_ctx* ctx, int32_t n_scenes, const orca_scene* scenes,
+                             const float* pos_xy, const float* vel_xy, const float* goal_xy,
+                             const float* radius, const float* max_speed,
+                             const float* pref_speed, const float* time_horizon, int where,
+                             void* stream);
+
+/*
+ * Grids of the last step (needs a batch): for scene s, grid_f[4s..4s+3] = xmin, ymin, cell
+ * edge, 1/edge and grid_i[3s..3s+2] = gx, gy, first global cell id.  Host pointers;
+ * synchronises `stream`.  orca_get_cells reports global cell ids (first id + cy*gx + cx).
+ */
+ORCA_API int orca_get_scene_grids(orca_ctx* ctx, float* grid_f, int32_t* grid_i, void* stream);
+
+/*
  * Advance nsteps (>= 0) synchronous ORCA steps on `stream`, asynchronously.
  * The first call after orca_set_agents captures one step into a CUDA graph (unless
  * ORCA_FLAG_NO_GRAPH); later calls replay it.  Capture happens on an internal stream, so
@@ -141,8 +181,9 @@ ORCA_API int orca_get_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int whe
                             void* stream);
 
 /*
- * Read the neighbour lists used by the last step (needs ORCA_FLAG_RECORD): n*k int32,
- * row i = agent i's neighbours as agent indices, nearest first, -1 padded.
+ * Read the neighbour lists used by the last step (needs ORCA_FLAG_RECORD): n*k int32
+ * (k = the context's max_neighbors), row i = agent i's neighbours as agent indices,
+ * nearest first, -1 padded.
  */
 ORCA_API int orca_get_neighbors(orca_ctx* ctx, int32_t* nbr, int where, void* stream);
 

@@ -44,7 +44,13 @@ class orca_params(ctypes.Structure):
     _fields_ = [("max_agents", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
                 ("max_cells", ctypes.c_int32), ("neighbor_dist", ctypes.c_float),
                 ("dt", ctypes.c_float), ("cell_size", ctypes.c_float),
-                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("max_scenes", ctypes.c_int32)]
+
+
+class orca_scene(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
+                ("neighbor_dist", ctypes.c_float), ("dt", ctypes.c_float),
+                ("cell_size", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -67,6 +73,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_create": ([P, vp, sz, c.POINTER(vp)], c.c_int),
         "orca_destroy": ([vp], c.c_int),
         "orca_set_agents": ([vp, i32] + [vp] * 7 + [c.c_int, vp], c.c_int),
+        "orca_set_scenes": ([vp, i32, vp] + [vp] * 7 + [c.c_int, vp], c.c_int),
+        "orca_get_scene_grids": ([vp, vp, vp, vp], c.c_int),
         "orca_step": ([vp, i32, vp], c.c_int),
         "orca_get_state": ([vp, vp, vp, c.c_int, vp], c.c_int),
         "orca_get_neighbors": ([vp, vp, c.c_int, vp], c.c_int),
@@ -126,9 +134,10 @@ def _ptr(a, dtype):
 
 
 def make_params(max_agents: int, max_neighbors: int, neighbor_dist: float, dt: float,
-                cell_size: float = 0.0, max_cells: int = 0, flags: int = 0) -> orca_params:
+                cell_size: float = 0.0, max_cells: int = 0, flags: int = 0,
+                max_scenes: int = 0) -> orca_params:
     return orca_params(int(max_agents), int(max_neighbors), int(max_cells), float(neighbor_dist),
-                       float(dt), float(cell_size), int(flags), 0)
+                       float(dt), float(cell_size), int(flags), int(max_scenes))
 
 
 def orca_workspace_size(params: orca_params) -> int:
@@ -158,6 +167,28 @@ def orca_set_agents(ctx, n, pos_xy, vel_xy, goal_xy, radius, max_speed, pref_spe
     _check(load_library().orca_set_agents(ctx, int(n), *[p for p, _ in ptrs], int(w),
                                           _stream(stream) if w == ORCA_DEVICE or stream is not None else None),
            ctx)
+
+
+def orca_set_scenes(ctx, scenes, pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed,
+                    time_horizon, where=None, stream=None):
+    """scenes: sequence of (count, max_neighbors, neighbor_dist, dt, cell_size)."""
+    arr = (orca_scene * len(scenes))(*[orca_scene(int(c), int(k), float(nd), float(dt), float(cs), 0)
+                                       for c, k, nd, dt, cs in scenes])
+    ptrs = [_ptr(a, np.float32) for a in (pos_xy, vel_xy, goal_xy, radius, max_speed,
+                                           pref_speed, time_horizon)]
+    w = where if where is not None else ptrs[0][1]
+    _check(load_library().orca_set_scenes(ctx, len(scenes), ctypes.cast(arr, ctypes.c_void_p),
+                                          *[p for p, _ in ptrs], int(w),
+                                          _stream(stream) if w == ORCA_DEVICE or stream is not None else None),
+           ctx)
+
+
+def orca_get_scene_grids(ctx, n_scenes: int, stream=None):
+    gf = np.zeros(4 * n_scenes, np.float32)
+    gi = np.zeros(3 * n_scenes, np.int32)
+    _check(load_library().orca_get_scene_grids(ctx, ctypes.c_void_p(gf.ctypes.data),
+                                               ctypes.c_void_p(gi.ctypes.data), _stream(stream)), ctx)
+    return gf.reshape(n_scenes, 4), gi.reshape(n_scenes, 3)
 
 
 def orca_step(ctx, nsteps: int = 1, stream=None):
@@ -254,10 +285,12 @@ class OrcaSim:
     """
 
     def __init__(self, max_agents: int, max_neighbors: int, neighbor_dist: float, dt: float,
-                 cell_size: float = 0.0, max_cells: int = 0, flags: int = 0, device=None):
+                 cell_size: float = 0.0, max_cells: int = 0, flags: int = 0, device=None,
+                 max_scenes: int = 0):
         import torch
         self.params = make_params(max_agents, max_neighbors, neighbor_dist, dt, cell_size,
-                                  max_cells, flags)
+                                  max_cells, flags, max_scenes)
+        self.n_scenes = 0
         self.device = torch.device(device or "cuda")
         nbytes = orca_workspace_size(self.params)
         with torch.cuda.device(self.device):
@@ -266,6 +299,12 @@ class OrcaSim:
             self._ws = self.workspace[off: off + nbytes]
             self.ctx = orca_create(self.params, self._ws, nbytes)
         self.k = int(max_neighbors)
+
+    @classmethod
+    def for_batch(cls, batch, **kw):
+        return cls(max_agents=max(batch.n, 1), max_neighbors=batch.max_neighbors,
+                   neighbor_dist=batch.scenes[0].neighbor_dist, dt=batch.scenes[0].dt,
+                   max_scenes=len(batch.scenes), **kw)
 
     @classmethod
     def for_scene(cls, scene, **kw):
@@ -294,6 +333,14 @@ class OrcaSim:
 
     def set_scene(self, scene, stream=None):
         self.set_agents(*scene.arrays(), stream=stream)
+
+    def set_batch(self, batch, cell_size: float = 0.0, stream=None):
+        """Load a ``scenarios.Batch`` (needs max_scenes >= its scene count)."""
+        self.n_scenes = len(batch.scenes)
+        orca_set_scenes(self.ctx, batch.scene_params(cell_size), *batch.arrays(), stream=stream)
+
+    def get_scene_grids(self, stream=None):
+        return orca_get_scene_grids(self.ctx, self.n_scenes, stream)
 
     def step(self, nsteps: int = 1, stream=None):
         orca_step(self.ctx, nsteps, stream)

@@ -24,9 +24,9 @@ struct Layout {
 };
 
 struct Plan {
-    int N, K, max_cells, max_passes, nsb, nmb;
+    int N, K, S, max_cells, max_passes, nsb, nmb;
     size_t o_msg, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2];
-    size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_part, o_misc, o_blk, o_rnbr, o_rcell,
+    size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_scenes, o_slot, o_part, o_misc, o_blk, o_rnbr, o_rcell,
         o_stage[2];
     size_t total;
 };
@@ -41,9 +41,10 @@ static int default_max_cells(int N) {
 static bool make_plan(const orca_params& p, Plan& pl) {
     if (p.max_agents < 1 || p.max_neighbors < 1 || p.max_neighbors > kMaxNeighbors) return false;
     if (!(p.neighbor_dist > 0.0f) || !(p.dt > 0.0f) || p.cell_size < 0.0f) return false;
-    if (p.max_cells < 0) return false;
+    if (p.max_cells < 0 || p.max_scenes < 0) return false;
     pl.N = p.max_agents;
     pl.K = p.max_neighbors;
+    pl.S = p.max_scenes > 1 ? p.max_scenes : 1;
     pl.max_cells = p.max_cells ? p.max_cells : default_max_cells(p.max_agents);
     int bits = 0;
     while (bits < 31 && (1LL << bits) < (long long)pl.max_cells) ++bits;
@@ -69,7 +70,10 @@ static bool make_plan(const orca_params& p, Plan& pl) {
     }
     pl.o_hist = L.add((size_t)kRadixBuckets * pl.nsb * 4);
     pl.o_tot = L.add((size_t)kRadixBuckets * 4);
-    pl.o_cells = L.add(((size_t)pl.max_cells + 1) * 4);
+    // a batch gives every scene at least one cell beyond its proportional share
+    pl.o_cells = L.add(((size_t)pl.max_cells + pl.S + 1) * 4);
+    pl.o_scenes = L.add((size_t)pl.S * sizeof(SceneDev));
+    pl.o_slot = p.max_scenes > 1 ? L.add(N * 4) : (size_t)-1;
     pl.o_part = L.add(kBboxBlocks * sizeof(float4));
     pl.o_misc = L.add(sizeof(DeviceMisc));
     pl.o_blk = L.add((size_t)pl.nmb * 4 * sizeof(unsigned long long));
@@ -108,6 +112,10 @@ struct orca_ctx {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int graph_n = -1;
     bool prof = false;
+    int n_scenes = 0;  // 0: single scene (orca_set_agents); else a batch
+    SceneDev* scenes = nullptr;
+    int* slot_scene = nullptr;
+    int resident = 0;  // CTAs of the ORCA kernel resident at once (persistent launch)
     cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::string err;
 };
@@ -160,6 +168,8 @@ static void bind_buffers(orca_ctx* c) {
     c->bins.bbox_partials = (float4*)(w + pl.o_part);
     c->bins.misc = (DeviceMisc*)(w + pl.o_misc);
     c->blk = (unsigned long long*)(w + pl.o_blk);
+    c->scenes = (SceneDev*)(w + pl.o_scenes);
+    c->slot_scene = pl.o_slot == (size_t)-1 ? nullptr : (int*)(w + pl.o_slot);
     c->rec_nbr = pl.o_rnbr == (size_t)-1 ? nullptr : (int32_t*)(w + pl.o_rnbr);
     c->rec_cell = pl.o_rcell == (size_t)-1 ? nullptr : (uint32_t*)(w + pl.o_rcell);
 }
@@ -179,7 +189,11 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     float cs = c->p.cell_size > 0.0f ? c->p.cell_size : c->p.neighbor_dist * 0.25f;
     cudaError_t e = cudaSuccess;
     if (c->prof && (e = cudaEventRecordWithFlags(c->pev[0], st, cudaEventRecordExternal)) != cudaSuccess) return e;
-    e = launch_binning(c->n, cs, pl.max_cells, pl.max_passes, c->PV[0], c->bins, st);
+    if (c->n_scenes > 0)
+        e = launch_binning_batch(c->n, c->n_scenes, c->scenes, c->slot_scene, pl.max_passes, c->PV[0],
+                                 c->bins, st);
+    else
+        e = launch_binning(c->n, cs, pl.max_cells, pl.max_passes, c->PV[0], c->bins, st);
     if (e != cudaSuccess) return e;
     if (c->prof && (e = cudaEventRecordWithFlags(c->pev[1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     e = launch_reorder(c->n, c->bins, c->PV[0], c->sorted, c->PR[par], c->PR[par ^ 1], st);
@@ -199,7 +213,10 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     a.block_counters = c->blk;
     a.rec_nbr = c->rec_nbr;
     a.rec_cell = c->rec_cell;
-    e = launch_main(a, st);
+    a.scenes = c->n_scenes > 0 ? c->scenes : nullptr;
+    a.slot_scene = c->n_scenes > 0 ? c->slot_scene : nullptr;
+    a.rec_stride = pl.K;
+    e = launch_main(a, pl.K, c->n_scenes > 0 ? c->resident : 0, st);
     if (e != cudaSuccess) return e;
     if (c->prof) e = cudaEventRecordWithFlags(c->pev[3], st, cudaEventRecordExternal);
     return e;
@@ -371,6 +388,89 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy, cons
     ctx->n = n;
     ctx->cur = 0;
     ctx->stepped = false;
+    if (ctx->n_scenes != 0) {
+        ctx->n_scenes = 0;
+        drop_graphs(ctx);
+    }
+    return ORCA_OK;
+}
+
+ORCA_API int orca_set_scenes(orca_ctx* ctx, int32_t n_scenes, const orca_scene* scenes,
+                             const float* pos_xy, const float* vel_xy, const float* goal_xy,
+                             const float* radius, const float* max_speed, const float* pref_speed,
+                             const float* time_horizon, int where, void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (!ctx->slot_scene) return fail(ctx, ORCA_ERR_STATE, "context created with max_scenes <= 1");
+    if (n_scenes < 1 || !scenes) return fail(ctx, ORCA_ERR_ARG, "need at least one scene");
+    if (n_scenes > ctx->plan.S) return fail(ctx, ORCA_ERR_CAPACITY, "n_scenes exceeds max_scenes");
+    long long total = 0;
+    for (int q = 0; q < n_scenes; ++q) {
+        const orca_scene& sc = scenes[q];
+        if (sc.count < 0 || sc.max_neighbors < 1 || sc.max_neighbors > ctx->plan.K ||
+            !(sc.neighbor_dist > 0.0f) || !(sc.dt > 0.0f) || !(sc.cell_size >= 0.0f))
+            return fail(ctx, ORCA_ERR_ARG, "invalid orca_scene " + std::to_string(q));
+        total += sc.count;
+    }
+    if (total > ctx->plan.N) return fail(ctx, ORCA_ERR_CAPACITY, "agents exceed max_agents");
+    int n = (int)total;
+    int r = orca_set_agents(ctx, n, pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed,
+                            time_horizon, where, stream);
+    if (r != ORCA_OK) return r;
+    SceneDev* h = new (std::nothrow) SceneDev[n_scenes];
+    if (!h) return fail(ctx, ORCA_ERR_NOMEM, "host allocation failed");
+    long long off = 0;
+    for (int q = 0; q < n_scenes; ++q) {
+        SceneDev d;
+        memset(&d, 0, sizeof d);
+        d.off = (int)off;
+        d.cnt = scenes[q].count;
+        d.k = scenes[q].max_neighbors;
+        d.nd = scenes[q].neighbor_dist;
+        d.dt = scenes[q].dt;
+        d.cell_size = scenes[q].cell_size;
+        long long share = n > 0 ? (long long)ctx->plan.max_cells * scenes[q].count / n : 0;
+        d.cell_budget = share < 1 ? 1 : share;
+        h[q] = d;
+        off += scenes[q].count;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ctx->scenes, h, sizeof(SceneDev) * n_scenes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_slot_scene(n, n_scenes, ctx->scenes, ctx->slot_scene, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    delete[] h;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set scenes");
+    if (!ctx->resident) ctx->resident = main_resident_blocks(ctx->plan.K);
+    ctx->n_scenes = n_scenes;
+    drop_graphs(ctx);
+    return ORCA_OK;
+}
+
+ORCA_API int orca_get_scene_grids(orca_ctx* ctx, float* grid_f, int32_t* grid_i, void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (ctx->n_scenes < 1) return fail(ctx, ORCA_ERR_STATE, "no batch loaded");
+    cudaStream_t st = (cudaStream_t)stream;
+    SceneDev* h = new (std::nothrow) SceneDev[ctx->n_scenes];
+    if (!h) return fail(ctx, ORCA_ERR_NOMEM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(h, ctx->scenes, sizeof(SceneDev) * ctx->n_scenes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        delete[] h;
+        return cuda_fail(ctx, e, "copy scene grids");
+    }
+    for (int q = 0; q < ctx->n_scenes; ++q) {
+        if (grid_f) {
+            grid_f[4 * q] = h[q].grid.xmin;
+            grid_f[4 * q + 1] = h[q].grid.ymin;
+            grid_f[4 * q + 2] = h[q].grid.s;
+            grid_f[4 * q + 3] = h[q].grid.inv;
+        }
+        if (grid_i) {
+            grid_i[3 * q] = h[q].grid.gx;
+            grid_i[3 * q + 1] = h[q].grid.gy;
+            grid_i[3 * q + 2] = h[q].cell_off;
+        }
+    }
+    delete[] h;
     return ORCA_OK;
 }
 

@@ -17,6 +17,48 @@
 
 namespace orca {
 
+// Grid over a bounding box r = (xmin, ymin, xmax, ymax), all in FP32:
+// inv = fl(1/s), g = floor(fl(fl(max - min) * inv)) + 1, doubling s while gx*gy exceeds
+// max_cells.  A non-finite or absurd extent puts everything in one cell and sets *err.
+__device__ GridDev derive_grid(float4 r, float cell_size, long long max_cells, int max_passes,
+                               int* err) {
+    GridDev g;
+    g.xmin = r.x;
+    g.ymin = r.y;
+    float ex = __fsub_rn(r.z, r.x), ey = __fsub_rn(r.w, r.y);
+    float s = cell_size, inv = 1.0f, fx = 0.0f, fy = 0.0f;
+    bool fits = false;
+    for (int it = 0; it < 200 && !fits; ++it) {
+        inv = __fdiv_rn(1.0f, s);
+        fx = floorf(__fmul_rn(ex, inv));
+        fy = floorf(__fmul_rn(ey, inv));
+        double cells = ((double)fx + 1.0) * ((double)fy + 1.0);
+        if (cells <= (double)max_cells) fits = true;
+        else s = __fmul_rn(s, 2.0f);
+    }
+    if (!fits || !(ex >= 0.0f) || !(ey >= 0.0f)) {
+        *err |= kErrCapacity;
+        fx = fy = 0.0f;
+        s = 1.0f;
+        inv = 1.0f;
+        if (!(g.xmin == g.xmin) || isinf(g.xmin)) g.xmin = 0.0f;
+        if (!(g.ymin == g.ymin) || isinf(g.ymin)) g.ymin = 0.0f;
+    }
+    g.s = s;
+    g.inv = inv;
+    g.gx = (int)fx + 1;
+    g.gy = (int)fy + 1;
+    g.num_cells = g.gx * g.gy;
+    int bits = 0;
+    while (bits < 31 && (1u << bits) < (unsigned)g.num_cells) ++bits;
+    int passes = (bits + kRadixBits - 1) / kRadixBits;
+    g.passes = passes < 1 ? 1 : (passes > max_passes ? max_passes : passes);
+    // rounding of fl(fl(x - xmin) * inv) moves a cell boundary by at most a few ulps of
+    // the extent; 1e-5 relative is a wide margin
+    g.slop = 1e-5f * (fabsf(g.xmin) + fabsf(g.ymin) + ex + ey + 2.0f * s) + 1e-6f;
+    return g;
+}
+
 // ---------------------------------------------------------------------------------
 // Bounding box and grid.  Each block reduces a grid-stride share; the last block to
 // finish (ticket counter, no waiting) folds the partials and derives the grid in FP32:
@@ -91,42 +133,10 @@ __global__ void __launch_bounds__(256) bbox_grid_kernel(int n, const float2* __r
         r.w = fmaxf(r.w, s_part[w].w);
     }
     misc->bbox_ticket = 0;
-    GridDev g;
-    g.xmin = r.x;
-    g.ymin = r.y;
-    float ex = __fsub_rn(r.z, r.x), ey = __fsub_rn(r.w, r.y);
-    float s = cell_size, inv = 1.0f, fx = 0.0f, fy = 0.0f;
-    bool fits = false;
-    for (int it = 0; it < 200 && !fits; ++it) {
-        inv = __fdiv_rn(1.0f, s);
-        fx = floorf(__fmul_rn(ex, inv));
-        fy = floorf(__fmul_rn(ey, inv));
-        double cells = ((double)fx + 1.0) * ((double)fy + 1.0);
-        if (cells <= (double)max_cells) fits = true;
-        else s = __fmul_rn(s, 2.0f);
-    }
-    if (!fits || !(ex >= 0.0f) || !(ey >= 0.0f)) {
-        // non-finite or absurd extent: everything in one cell, flag the error
-        atomicOr(&misc->error, kErrCapacity);
-        fx = fy = 0.0f;
-        s = 1.0f;
-        inv = 1.0f;
-        if (!(g.xmin == g.xmin) || isinf(g.xmin)) g.xmin = 0.0f;
-        if (!(g.ymin == g.ymin) || isinf(g.ymin)) g.ymin = 0.0f;
-    }
-    g.s = s;
-    g.inv = inv;
-    g.gx = (int)fx + 1;
-    g.gy = (int)fy + 1;
-    g.num_cells = g.gx * g.gy;
-    int bits = 0;
-    while (bits < 31 && (1u << bits) < (unsigned)g.num_cells) ++bits;
-    int passes = (bits + kRadixBits - 1) / kRadixBits;
-    g.passes = passes < 1 ? 1 : (passes > max_passes ? max_passes : passes);
-    // rounding of fl(fl(x - xmin) * inv) moves a cell boundary by at most a few ulps of
-    // the extent; 1e-5 relative is a wide margin
-    g.slop = 1e-5f * (fabsf(g.xmin) + fabsf(g.ymin) + ex + ey + 2.0f * s) + 1e-6f;
-    misc->grid = g;
+    misc->tile_counter = 0;
+    int err = 0;
+    misc->grid = derive_grid(r, cell_size, max_cells, max_passes, &err);
+    if (err) atomicOr(&misc->error, err);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -136,23 +146,33 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Cell key of each agent and the digit-0 histogram of this block's tile.
+// Batch mode (scenes != null): the key is the scene's cell offset plus its local cell.
 __global__ void __launch_bounds__(kSortThreads) keys_hist_kernel(int n, const float2* __restrict__ pos,
                                                                  const DeviceMisc* __restrict__ misc,
+                                                                 const SceneDev* __restrict__ scenes,
+                                                                 const int* __restrict__ slot_scene,
                                                                  uint32_t* __restrict__ keys,
                                                                  uint32_t* __restrict__ hist) {
     __shared__ uint32_t s_hist[kRadixBuckets];
     for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) s_hist[d] = 0;
     __syncthreads();
-    const GridDev g = misc->grid;
     int base = blockIdx.x * kSortTile;
 #pragma unroll
     for (int c = 0; c < kSortItems; ++c) {
         int i = base + c * kSortThreads + threadIdx.x;
         if (i < n) {
             float2 p = pos[i];
+            uint32_t off = 0;
+            const GridDev* gp = &misc->grid;
+            if (scenes) {
+                const SceneDev* sc = scenes + slot_scene[i];
+                gp = &sc->grid;
+                off = (uint32_t)sc->cell_off;
+            }
+            const GridDev g = *gp;
             int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
             int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
-            uint32_t key = (uint32_t)cy * (uint32_t)g.gx + (uint32_t)cx;
+            uint32_t key = off + (uint32_t)cy * (uint32_t)g.gx + (uint32_t)cx;
             keys[i] = key;
             atomicAdd(&s_hist[key & (kRadixBuckets - 1)], 1u);
         }
@@ -340,6 +360,8 @@ __global__ void __launch_bounds__(256) iota_kernel(int n, uint32_t* __restrict__
 // ---------------------------------------------------------------------------------
 int sort_blocks(int n) { return (n + kSortTile - 1) / kSortTile; }
 
+void launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cudaStream_t st);
+
 cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_passes,
                            const AgentState& cur, const BinBuffers& b, cudaStream_t st) {
     int nb_bbox = (n + 255) / 256;
@@ -347,7 +369,14 @@ cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_
     bbox_grid_kernel<<<nb_bbox, 256, 0, st>>>(n, cur.pos, cell_size, max_cells, max_passes,
                                               b.bbox_partials, b.misc);
     int nsb = sort_blocks(n);
-    keys_hist_kernel<<<nsb, kSortThreads, 0, st>>>(n, cur.pos, b.misc, b.keys[0], b.hist);
+    keys_hist_kernel<<<nsb, kSortThreads, 0, st>>>(n, cur.pos, b.misc, nullptr, nullptr, b.keys[0],
+                                                   b.hist);
+    launch_radix_passes(n, nsb, max_passes, b, st);
+    return cudaGetLastError();
+}
+
+// Radix passes over the keys written by keys_hist, then the cell table.
+void launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cudaStream_t st) {
     for (int pass = 0; pass < max_passes; ++pass) {
         int src = pass & 1, dst = src ^ 1;
         if (pass > 0)
@@ -360,7 +389,6 @@ cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_
     }
     cell_table_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, b.keys[0], b.keys[1], b.misc,
                                                             b.cell_start);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
@@ -381,6 +409,117 @@ cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, flo
 cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     iota_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, id);
+    return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------------
+// Batch of independent scenes
+// ---------------------------------------------------------------------------------
+// Bounding box and grid of each scene: one CTA per scene over its slot range.
+__global__ void __launch_bounds__(1024) scene_bbox_grid_kernel(const float2* __restrict__ pos,
+                                                               SceneDev* scenes, int max_passes,
+                                                               DeviceMisc* misc) {
+    SceneDev* sc = scenes + blockIdx.x;
+    const int off = sc->off, cnt = sc->cnt;
+    float4 r = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        float2 p = pos[off + i];
+        r.x = fminf(r.x, p.x);
+        r.y = fminf(r.y, p.y);
+        r.z = fmaxf(r.z, p.x);
+        r.w = fmaxf(r.w, p.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        r.x = fminf(r.x, __shfl_xor_sync(0xffffffffu, r.x, o));
+        r.y = fminf(r.y, __shfl_xor_sync(0xffffffffu, r.y, o));
+        r.z = fmaxf(r.z, __shfl_xor_sync(0xffffffffu, r.z, o));
+        r.w = fmaxf(r.w, __shfl_xor_sync(0xffffffffu, r.w, o));
+    }
+    __shared__ float4 s_part[32];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s_part[warp] = r;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        r.x = fminf(r.x, s_part[w].x);
+        r.y = fminf(r.y, s_part[w].y);
+        r.z = fmaxf(r.z, s_part[w].z);
+        r.w = fmaxf(r.w, s_part[w].w);
+    }
+    if (cnt == 0) r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float cs = sc->cell_size > 0.0f ? sc->cell_size : sc->nd * 0.25f;
+    int err = 0;
+    sc->grid = derive_grid(r, cs, sc->cell_budget, max_passes, &err);
+    if (err) atomicOr(&misc->error, err);
+}
+
+// Cell offsets of the scenes (exclusive scan of their cell counts), the total and the
+// radix passes it needs; resets the persistent kernel's tile counter.
+__global__ void __launch_bounds__(1024) scene_prefix_kernel(int n_scenes, SceneDev* scenes,
+                                                            int max_passes, DeviceMisc* misc) {
+    __shared__ long long s_sum[1024];
+    int per = (n_scenes + blockDim.x - 1) / blockDim.x;
+    int s0 = threadIdx.x * per, s1 = min(s0 + per, n_scenes);
+    long long sum = 0;
+    for (int q = s0; q < s1; ++q) sum += scenes[q].grid.num_cells;
+    s_sum[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            long long v = s_sum[t];
+            s_sum[t] = run;
+            run += v;
+        }
+        int bits = 0;
+        while (bits < 31 && (1LL << bits) < run) ++bits;
+        int passes = (bits + kRadixBits - 1) / kRadixBits;
+        misc->grid.num_cells = (int)run;
+        misc->grid.passes = passes < 1 ? 1 : (passes > max_passes ? max_passes : passes);
+        misc->tile_counter = 0;
+    }
+    __syncthreads();
+    long long run = s_sum[threadIdx.x];
+    for (int q = s0; q < s1; ++q) {
+        scenes[q].cell_off = (int)run;
+        run += scenes[q].grid.num_cells;
+    }
+}
+
+// Scene of every slot: the first scene whose slot range ends after it (binary search;
+// the ends are non-decreasing, and empty scenes own no slot).
+__global__ void __launch_bounds__(256) slot_scene_kernel(int n, int n_scenes,
+                                                         const SceneDev* __restrict__ scenes,
+                                                         int* __restrict__ slot_scene) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int lo = 0, hi = n_scenes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (scenes[mid].off + scenes[mid].cnt > t) hi = mid;
+        else lo = mid + 1;
+    }
+    slot_scene[t] = lo;
+}
+
+cudaError_t launch_slot_scene(int n, int n_scenes, const SceneDev* scenes, int* slot_scene,
+                              cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    slot_scene_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, n_scenes, scenes, slot_scene);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_binning_batch(int n, int n_scenes, SceneDev* scenes, const int* slot_scene,
+                                 int max_passes, const AgentState& cur, const BinBuffers& b,
+                                 cudaStream_t st) {
+    scene_bbox_grid_kernel<<<n_scenes, 1024, 0, st>>>(cur.pos, scenes, max_passes, b.misc);
+    scene_prefix_kernel<<<1, 1024, 0, st>>>(n_scenes, scenes, max_passes, b.misc);
+    int nsb = sort_blocks(n);
+    keys_hist_kernel<<<nsb, kSortThreads, 0, st>>>(n, cur.pos, b.misc, scenes, slot_scene,
+                                                   b.keys[0], b.hist);
+    launch_radix_passes(n, nsb, max_passes, b, st);
     return cudaGetLastError();
 }
 

@@ -41,10 +41,26 @@ struct GridDev {
 };
 
 struct DeviceMisc {
-    GridDev grid;
+    GridDev grid;              // single scene: the grid; batch: num_cells / passes of all scenes
     unsigned int bbox_ticket;  // last-block-done counter of the bbox reduction
     int error;                 // kErr* bits
+    unsigned int tile_counter; // next tile of the persistent ORCA kernel (reset every step)
+    int pad_;
     unsigned long long counters[4];  // agent-steps, LP3 agent-steps, candidates, lines
+};
+
+// One scene of a batch: its slot range (fixed: the sort keeps scenes contiguous), its
+// parameters and, recomputed every step, its grid and the offset of its cells in the
+// global cell table (composite cell id = cell_off + cy * gx + cx).
+struct SceneDev {
+    GridDev grid;
+    int off, cnt;        // agent slots [off, off + cnt)
+    int cell_off;        // first global cell id
+    int k;               // neighbours kept (<= the context's max_neighbors)
+    float nd, dt;        // r_obs, time step
+    float cell_size;     // requested cell edge
+    int pad_;
+    long long cell_budget;  // cells this scene may use (capacity rule)
 };
 
 struct AgentParams {  // one of PR[0] / PR[1]
@@ -80,8 +96,11 @@ struct BinBuffers {
 };
 
 struct MainArgs {
-    int n, k;
-    float nd, dt;
+    int n, k;                            // agents; neighbours (single scene)
+    float nd, dt;                        // r_obs, time step (single scene)
+    const SceneDev* scenes;              // batch: per-scene parameters and grids, else null
+    const int* slot_scene;               // batch: scene of each slot, else null
+    int rec_stride;                      // row length of rec_nbr (the context's max k)
     const DeviceMisc* misc;
     DeviceMisc* misc_rw;
     const uint32_t* cell_start;
@@ -98,13 +117,20 @@ int sort_blocks(int n);
 int main_blocks(int n);
 cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_passes,
                            const AgentState& cur, const BinBuffers& b, cudaStream_t st);
+cudaError_t launch_binning_batch(int n, int n_scenes, SceneDev* scenes, const int* slot_scene,
+                                 int max_passes, const AgentState& cur, const BinBuffers& b,
+                                 cudaStream_t st);
+cudaError_t launch_slot_scene(int n, int n_scenes, const SceneDev* scenes, int* slot_scene,
+                              cudaStream_t st);
+int main_resident_blocks(int k);
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
                            const Sorted& dst_s, const AgentParams& src_p,
                            const AgentParams& dst_p, cudaStream_t st);
 cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, float2* pos_out,
                              float2* vel_out, cudaStream_t st);
 cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st);
-cudaError_t launch_main(const MainArgs& a, cudaStream_t st);
+// kmax: template bound (>= every scene's k); grid_blocks > 0: persistent launch
+cudaError_t launch_main(const MainArgs& a, int kmax, int grid_blocks, cudaStream_t st);
 
 // Cell coordinate along one axis in FP32, one rounding per operation:
 // floor(fl(fl(v - vmin) * inv)) clamped to [0, g - 1].

@@ -328,14 +328,15 @@ __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint
 // agents' fl32 d^2 (cell box minus the cell-assignment slop, d^2 rounding 1e-5) exceeds
 // lim; the search stops when the next ring's bound does.
 template <int KMAX>
-__device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g, int t, float2 p,
-                                            int k, unsigned long long (&kk)[KMAX], int (&ks)[KMAX]) {
+__device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g, int cell_off,
+                                            float nd, int t, float2 p, int k,
+                                            unsigned long long (&kk)[KMAX], int (&ks)[KMAX]) {
     // ring-1 visiting order as offsets (ax*sx, ay*sy), ax+1 and ay+1 packed 2 bits each
     constexpr unsigned kAx = 2u | 1u << 2 | 2u << 4 | 0u << 6 | 1u << 8 | 0u << 10 | 2u << 12 | 0u << 14;
     constexpr unsigned kAy = 1u | 2u << 2 | 2u << 4 | 1u << 6 | 0u << 8 | 2u << 10 | 0u << 12 | 0u << 14;
     int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
     int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
-    float nd2 = __fmul_rn(a.nd, a.nd);
+    float nd2 = __fmul_rn(nd, nd);
     float lim = __int_as_float(__float_as_int(nd2) - 1);  // largest float below r_obs^2
 #pragma unroll
     for (int l = 0; l < KMAX; ++l) {
@@ -373,7 +374,7 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
             float ddx = fmaxf(0.0f, fmaxf(bx0 - p.x, p.x - (bx0 + g.s)) - g.slop);
             float ddy = fmaxf(0.0f, fmaxf(by0 - p.y, p.y - (by0 + g.s)) - g.slop);
             if ((ddx * ddx + ddy * ddy) * (1.0f - 1e-5f) <= lim) {
-                int c = y * g.gx + x;
+                int c = cell_off + y * g.gx + x;
                 uint32_t q0 = a.cell_start[c], q1 = a.cell_start[c + 1];
                 cand += q1 - q0;
                 offer_range<KMAX>(a.in.msg, q0, q1, t, p, kk, ks, lim);
@@ -408,6 +409,32 @@ __host__ __device__ constexpr int lp3_group() { return KMAX <= 16 ? 1 : 4; }
 template <int KMAX>
 constexpr size_t main_smem_bytes() { return sizeof(float4) * kMainThreads * (KMAX + 1); }
 
+// Parameters of the scene an agent belongs to (the one scene, or its scene of a batch).
+struct SceneView {
+    GridDev g;
+    int cell_off, k;
+    float nd, dt;
+};
+
+__device__ __forceinline__ void scene_view(const MainArgs& a, int t, SceneView& v) {
+    if (a.scenes) {
+        const SceneDev& sc = a.scenes[a.slot_scene[t]];
+        v.g = sc.grid;
+        v.cell_off = sc.cell_off;
+        v.k = sc.k;
+        v.nd = sc.nd;
+        v.dt = sc.dt;
+    } else {
+        v.g = a.misc->grid;
+        v.cell_off = 0;
+        v.k = a.k;
+        v.nd = a.nd;
+        v.dt = a.dt;
+    }
+}
+
+// Persistent over tiles of kMainThreads consecutive agents: tile blockIdx.x first, then
+// tiles taken from a per-step counter (with one CTA per tile this loop runs once).
 template <int KMAX>
 __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_main_kernel(MainArgs a) {
     constexpr int KP = KMAX + 1;  // padded rows: conflict-free float4 accesses
@@ -418,127 +445,140 @@ __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_ma
     __shared__ unsigned char s_cnt[kMainThreads];
     __shared__ unsigned char s_queued[kMainThreads];
     __shared__ unsigned char s_queue[kMainThreads];
-    __shared__ int s_qn;
-    __shared__ unsigned long long s_cand, s_lines_n;
+    __shared__ int s_qn, s_tile;
+    __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        s_qn = 0;
         s_cand = 0;
         s_lines_n = 0;
+        s_act = 0;
+        s_lp3 = 0;
     }
-    s_queued[tid] = 0;
-    __syncthreads();
-    const int t = blockIdx.x * kMainThreads + tid;
-    const bool active = t < a.n;
-    const int k = a.k;
+    const int ntiles = (a.n + kMainThreads - 1) / kMainThreads;
     float4* row = s_lines + tid * KP;
-    float2 p = make_float2(0.0f, 0.0f);
-    float xx = 0.0f, xy = 0.0f;
-    int cnt = 0;
-    unsigned cand = 0;
-    if (active) {
-        const GridDev g = a.misc->grid;
-        // ---- phase 1: neighbours and half-planes
-        float4 me4 = a.in.msg[t];
-        p = make_float2(me4.x, me4.y);
-        uint32_t me = __float_as_uint(me4.w);
-        unsigned long long kk[KMAX];
-        int ks[KMAX];
-        cand = knn_dev<KMAX>(a, g, t, p, k, kk, ks);
-        // park the neighbours' slots in the row (one unrolled store each), then build the
-        // half-planes in a rolled loop: one copy of the line code keeps the kernel small
-        // enough for the instruction cache
-#pragma unroll
-        for (int l = 0; l < KMAX; ++l) {
-            if (l >= KMAX - k && kk[l] != ~0ull) row[cnt++].w = __int_as_float(ks[l]);
-        }
-        float2 v = a.in.vel[t];
-        float itau = __fdividef(1.0f, a.prm.tau[t]);
-        float idt = __fdividef(1.0f, a.dt);
-        float half_idt = 0.5f * idt;
 #pragma unroll 1
-        for (int l = 0; l < cnt; ++l) {
-            int q = __float_as_int(row[l].w);
-            row[l] = orca_line_dev(p, v, me4.z, itau, a.dt, half_idt, me, a.in.msg[q],
-                                   a.in.vel[q]);
-        }
-        if (a.rec_nbr) {
-            int w = 0;
+    for (int tile = blockIdx.x; tile < ntiles;) {
+        if (tid == 0) s_qn = 0;
+        s_queued[tid] = 0;
+        __syncthreads();
+        const int t = tile * kMainThreads + tid;
+        const bool active = t < a.n;
+        float2 p = make_float2(0.0f, 0.0f);
+        float xx = 0.0f, xy = 0.0f, dt = 1.0f;
+        int cnt = 0;
+        unsigned cand = 0;
+        if (active) {
+            SceneView sv;
+            scene_view(a, t, sv);
+            dt = sv.dt;
+            // ---- phase 1: neighbours and half-planes
+            float4 me4 = a.in.msg[t];
+            p = make_float2(me4.x, me4.y);
+            uint32_t me = __float_as_uint(me4.w);
+            unsigned long long kk[KMAX];
+            int ks[KMAX];
+            cand = knn_dev<KMAX>(a, sv.g, sv.cell_off, sv.nd, t, p, sv.k, kk, ks);
+            // park the neighbours' slots in the row (one unrolled store each), then build
+            // the half-planes in a rolled loop: one copy of the line code keeps the kernel
+            // small enough for the instruction cache
 #pragma unroll
-            for (int l = 0; l < KMAX; ++l)
-                if (l >= KMAX - k)
-                    a.rec_nbr[(size_t)me * k + (w++)] =
-                        kk[l] != ~0ull ? (int32_t)(kk[l] & 0xffffffffu) : -1;
+            for (int l = 0; l < KMAX; ++l) {
+                if (l >= KMAX - sv.k && kk[l] != ~0ull) row[cnt++].w = __int_as_float(ks[l]);
+            }
+            float2 v = a.in.vel[t];
+            float itau = __fdividef(1.0f, a.prm.tau[t]);
+            float idt = __fdividef(1.0f, dt);
+            float half_idt = 0.5f * idt;
+#pragma unroll 1
+            for (int l = 0; l < cnt; ++l) {
+                int q = __float_as_int(row[l].w);
+                row[l] = orca_line_dev(p, v, me4.z, itau, dt, half_idt, me, a.in.msg[q], a.in.vel[q]);
+            }
+            if (a.rec_nbr) {
+                int w = 0;
+#pragma unroll
+                for (int l = 0; l < KMAX; ++l)
+                    if (l >= KMAX - sv.k)
+                        a.rec_nbr[(size_t)me * a.rec_stride + (w++)] =
+                            kk[l] != ~0ull ? (int32_t)(kk[l] & 0xffffffffu) : -1;
+                for (; w < a.rec_stride; ++w) a.rec_nbr[(size_t)me * a.rec_stride + w] = -1;
+            }
+            if (a.rec_cell) {
+                int cx = cell_coord(p.x, sv.g.xmin, sv.g.inv, sv.g.gx);
+                int cy = cell_coord(p.y, sv.g.ymin, sv.g.inv, sv.g.gy);
+                a.rec_cell[me] = (uint32_t)sv.cell_off + (uint32_t)cy * (uint32_t)sv.g.gx + (uint32_t)cx;
+            }
+            // ---- phase 2: preferred velocity (towards the goal at the preferred speed, or
+            // onto the goal within one step) and LP2
+            float2 goal = a.prm.goal[t];
+            float pref = a.prm.pref_speed[t], V = a.prm.max_speed[t];
+            float gx_ = goal.x - p.x, gy_ = goal.y - p.y;
+            float g2 = gx_ * gx_ + gy_ * gy_;
+            float ig = rsqrtf(g2);
+            float ox, oy;
+            if (g2 * ig > pref * dt) {
+                ox = gx_ * (pref * ig);
+                oy = gy_ * (pref * ig);
+            } else {
+                ox = gx_ * idt;
+                oy = gy_ * idt;
+            }
+            RowLines rl{row};
+            int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy);
+            if (b < cnt) {
+                int slot = atomicAdd(&s_qn, 1);
+                s_queue[slot] = (unsigned char)tid;
+                s_queued[tid] = 1;
+                s_x[tid] = make_float2(xx, xy);
+                s_b[tid] = (unsigned char)b;
+                s_cnt[tid] = (unsigned char)cnt;
+                s_V[tid] = V;
+            }
         }
-        if (a.rec_cell) {
-            int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
-            int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
-            a.rec_cell[me] = (uint32_t)cy * (uint32_t)g.gx + (uint32_t)cx;
+        __syncthreads();
+        // ---- phase 3: least penetration for the queued agents, G lanes each
+        constexpr int G = lp3_group<KMAX>();
+        const int nq = s_qn;
+        for (int q = tid / G; q < nq; q += kMainThreads / G) {
+            int ag = s_queue[q];
+            float2 x = s_x[ag];
+            lp3_group_dev<G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
+            if ((tid & (G - 1)) == 0) s_x[ag] = x;
         }
-        // ---- phase 2: preferred velocity (towards the goal at the preferred speed, or
-        // onto the goal within one step) and LP2
-        float2 goal = a.prm.goal[t];
-        float pref = a.prm.pref_speed[t], V = a.prm.max_speed[t];
-        float gx_ = goal.x - p.x, gy_ = goal.y - p.y;
-        float g2 = gx_ * gx_ + gy_ * gy_;
-        float ig = rsqrtf(g2);
-        float ox, oy;
-        if (g2 * ig > pref * a.dt) {
-            ox = gx_ * (pref * ig);
-            oy = gy_ * (pref * ig);
-        } else {
-            ox = gx_ * idt;
-            oy = gy_ * idt;
+        __syncthreads();
+        // ---- phase 4: integrate
+        if (active) {
+            if (s_queued[tid]) {
+                float2 x = s_x[tid];
+                xx = x.x;
+                xy = x.y;
+            }
+            float nx = p.x + xx * dt, ny = p.y + xy * dt;
+            if (!isfinite(xx) || !isfinite(xy) || !isfinite(nx) || !isfinite(ny))
+                atomicOr(&a.misc_rw->error, kErrNumeric);
+            a.out.vel[t] = make_float2(xx, xy);
+            a.out.pos[t] = make_float2(nx, ny);
         }
-        RowLines rl{row};
-        int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy);
-        if (b < cnt) {
-            int slot = atomicAdd(&s_qn, 1);
-            s_queue[slot] = (unsigned char)tid;
-            s_queued[tid] = 1;
-            s_x[tid] = make_float2(xx, xy);
-            s_b[tid] = (unsigned char)b;
-            s_cnt[tid] = (unsigned char)cnt;
-            s_V[tid] = V;
+        // ---- counters: one shared-memory atomic per warp
+        unsigned wc = __reduce_add_sync(0xffffffffu, cand);
+        unsigned wl = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+        unsigned wa = __reduce_add_sync(0xffffffffu, active ? 1u : 0u);
+        if ((tid & 31) == 0) {
+            atomicAdd(&s_cand, (unsigned long long)wc);
+            atomicAdd(&s_lines_n, (unsigned long long)wl);
+            atomicAdd(&s_act, (unsigned long long)wa);
         }
+        if (tid == 0) {
+            s_lp3 += (unsigned long long)nq;
+            s_tile = (int)atomicAdd(&a.misc_rw->tile_counter, 1u) + (int)gridDim.x;
+        }
+        __syncthreads();
+        tile = s_tile;
     }
-    __syncthreads();
-    // ---- phase 3: least penetration for the queued agents, one group of G lanes each,
-    // so every thread of the CTA works on the queue
-    constexpr int G = lp3_group<KMAX>();
-    const int nq = s_qn;
-    for (int q = tid / G; q < nq; q += kMainThreads / G) {
-        int ag = s_queue[q];
-        float2 x = s_x[ag];
-        lp3_group_dev<G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
-        if ((tid & (G - 1)) == 0) s_x[ag] = x;
-    }
-    __syncthreads();
-    // ---- phase 4: integrate
-    if (active) {
-        if (s_queued[tid]) {
-            float2 x = s_x[tid];
-            xx = x.x;
-            xy = x.y;
-        }
-        float nx = p.x + xx * a.dt, ny = p.y + xy * a.dt;
-        if (!isfinite(xx) || !isfinite(xy) || !isfinite(nx) || !isfinite(ny))
-            atomicOr(&a.misc_rw->error, kErrNumeric);
-        a.out.vel[t] = make_float2(xx, xy);
-        a.out.pos[t] = make_float2(nx, ny);
-    }
-    // ---- counters: one shared-memory atomic per warp
-    unsigned wc = __reduce_add_sync(0xffffffffu, cand);
-    unsigned wl = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
-    if ((tid & 31) == 0) {
-        atomicAdd(&s_cand, (unsigned long long)wc);
-        atomicAdd(&s_lines_n, (unsigned long long)wl);
-    }
-    int n_act = __syncthreads_count(active);
     if (tid == 0) {
         unsigned long long* c = a.block_counters + 4 * (size_t)blockIdx.x;
-        c[0] += (unsigned long long)n_act;
-        c[1] += (unsigned long long)nq;
+        c[0] += s_act;
+        c[1] += s_lp3;
         c[2] += s_cand;
         c[3] += s_lines_n;
     }
@@ -546,21 +586,47 @@ __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_ma
 
 int main_blocks(int n) { return (n + kMainThreads - 1) / kMainThreads; }
 
+// CTAs of the ORCA kernel that fit on the GPU at once (for the persistent launch).
 template <int KMAX>
-static cudaError_t launch_main_k(const MainArgs& a, cudaStream_t st) {
+static int resident_blocks_k() {
+    constexpr size_t smem = main_smem_bytes<KMAX>();
+    if (cudaFuncSetAttribute(orca_main_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, orca_main_kernel<KMAX>, kMainThreads,
+                                                      smem) != cudaSuccess)
+        return 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm * sms;
+}
+
+int main_resident_blocks(int k) {
+    if (k <= 10) return resident_blocks_k<10>();
+    if (k <= 16) return resident_blocks_k<16>();
+    if (k <= 20) return resident_blocks_k<20>();
+    return resident_blocks_k<32>();
+}
+
+// grid_blocks > 0: persistent launch with that many CTAs (capped at one per tile).
+template <int KMAX>
+static cudaError_t launch_main_k(const MainArgs& a, int grid_blocks, cudaStream_t st) {
     constexpr size_t smem = main_smem_bytes<KMAX>();
     cudaError_t e = cudaFuncSetAttribute(orca_main_kernel<KMAX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    orca_main_kernel<KMAX><<<main_blocks(a.n), kMainThreads, smem, st>>>(a);
+    int nb = main_blocks(a.n);
+    if (grid_blocks > 0 && grid_blocks < nb) nb = grid_blocks;
+    orca_main_kernel<KMAX><<<nb, kMainThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_main(const MainArgs& a, cudaStream_t st) {
-    if (a.k <= 10) return launch_main_k<10>(a, st);
-    if (a.k <= 16) return launch_main_k<16>(a, st);
-    if (a.k <= 20) return launch_main_k<20>(a, st);
-    return launch_main_k<32>(a, st);
+cudaError_t launch_main(const MainArgs& a, int kmax, int grid_blocks, cudaStream_t st) {
+    if (kmax <= 10) return launch_main_k<10>(a, grid_blocks, st);
+    if (kmax <= 16) return launch_main_k<16>(a, grid_blocks, st);
+    if (kmax <= 20) return launch_main_k<20>(a, grid_blocks, st);
+    return launch_main_k<32>(a, grid_blocks, st);
 }
 
 }  // namespace orca

@@ -167,7 +167,10 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
         a.block_counters = (unsigned long long*)(base + L.blk);
         a.rec_nbr = nullptr;
         a.rec_cell = nullptr;
-        e = launch_main(a, st);
+        a.scenes = nullptr;
+        a.slot_scene = nullptr;
+        a.rec_stride = max_neighbors;
+        e = launch_main(a, max_neighbors, 0, st);
     }
     if (e == cudaSuccess) e = launch_unpermute(n, out, dst_p.id, (float2*)pos_out_xy, (float2*)vel_out_xy, st);
     if (e != cudaSuccess)

@@ -161,3 +161,48 @@ def scene_by_name(name: str, n: int | None = None, seed: int | None = None) -> S
     if name == "dense":
         return dense(n or 2097152, seed=1910 if seed is None else seed)
     raise ValueError(f"unknown scene {name!r}")
+
+
+@dataclasses.dataclass
+class Batch:
+    """Independent scenes advanced together.  Agent arrays are the scenes' arrays
+    concatenated scene after scene; ``offsets[s]:offsets[s+1]`` are scene s's agents."""
+
+    scenes: list
+
+    @property
+    def n(self) -> int:
+        return int(sum(s.n for s in self.scenes))
+
+    @property
+    def offsets(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum([s.n for s in self.scenes])]).astype(np.int64)
+
+    def arrays(self):
+        cols = list(zip(*[s.arrays() for s in self.scenes]))
+        return tuple(np.ascontiguousarray(np.concatenate(c, axis=0)) for c in cols)
+
+    def scene_params(self, cell_size: float = 0.0):
+        """(count, max_neighbors, neighbor_dist, dt, cell_size) per scene."""
+        return [(s.n, s.max_neighbors, s.neighbor_dist, s.dt, cell_size) for s in self.scenes]
+
+    @property
+    def max_neighbors(self) -> int:
+        return max(s.max_neighbors for s in self.scenes)
+
+
+def batched(n_scenes: int = 256, seed: int = 1912, lo: int = 500, hi: int = 50000) -> Batch:
+    """Scenes of uneven size: counts round(exp(U[ln lo, ln hi])); each scene is, with equal
+    probability, a circle swap (the 1,024-agent circle's parameters, radius scaled so the
+    spacing on the circle is unchanged) or a bidirectional flow (the 524,288-agent flow's
+    parameters, side scaled with sqrt(count)).  Scene s's flow uses seed + s."""
+    rng = np.random.default_rng(seed)
+    counts = np.round(np.exp(rng.uniform(math.log(lo), math.log(hi), n_scenes))).astype(int)
+    kinds = rng.integers(0, 2, n_scenes)
+    scenes = []
+    for s, (c, kind) in enumerate(zip(counts, kinds)):
+        if kind == 0:
+            scenes.append(circle_swap(int(c), circle_radius=100.0 * c / 1024.0))
+        else:
+            scenes.append(bidirectional(int(c), seed=seed + 1 + s))
+    return Batch(scenes)
