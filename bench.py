@@ -209,6 +209,79 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(torch, step_fn, steps, warmup, flush, stream):
+    """Device time (ms) of `steps` calls of step_fn, L2 flushed before each, CUDA events on
+    the launching stream."""
+    for _ in range(warmup):
+        step_fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        step_fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return float(sum(a.elapsed_time(b) for a, b in ev))
+
+
+def run_batched(args):
+    """256 independent scenes (counts log-uniform in [500, 50,000], circle swaps and
+    bidirectional flows) advanced by one persistent launch per step in a CUDA graph:
+    untuned, autotuned (cell-edge factor and launch shape), and one context per scene."""
+    import torch
+    from paper_1908_10107_gb300 import abi, autotune, scenarios
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    batch = scenarios.batched()
+    n = batch.n
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sim = abi.OrcaSim.for_batch(batch)
+    sim.set_batch(batch)
+    untuned = timed_steps(torch, lambda: sim.step(1), args.steps, args.warmup, flush, stream)
+    tune = autotune.tune_batch(sim, batch)
+    tuned = timed_steps(torch, lambda: sim.step(1), args.steps, args.warmup, flush, stream)
+    launches = abi.orca_launches_per_step(sim.ctx)
+    sim.close()
+    per_scene = None
+    if not args.no_per_scene:
+        sims = []
+        for sc, cs in zip(batch.scenes, tune["cell_sizes"]):
+            s1 = abi.OrcaSim.for_scene(sc, cell_size=cs)
+            s1.set_scene(sc)
+            sims.append(s1)
+
+        def step_all():
+            for s1 in sims:
+                s1.step(1)
+        per_scene = timed_steps(torch, step_all, max(args.steps // 4, 3), args.warmup, flush, stream)
+        per_scene_steps = max(args.steps // 4, 3)
+        for s1 in sims:
+            s1.close()
+    line = {
+        "metric": "batched ORCA agent-steps/sec (256 scenes, one persistent launch per step)",
+        "value": n * args.steps / (tuned * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tuned / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": f"256 scenes, {n:,} agents, counts log-uniform in [500, 50000], "
+                               "circle swaps and bidirectional flows", "n_agents": n,
+                   "l2": "flushed between steps (256 MiB write)"},
+        "untuned": {"value": n * args.steps / (untuned * 1e-3), "ms_per_step": untuned / args.steps,
+                    "setting": "cell edge r_obs/4 per scene, 128 threads, default LP3 lanes"},
+        "tuned": {"value": n * args.steps / (tuned * 1e-3), "ms_per_step": tuned / args.steps,
+                  "cell_factor": tune["factor"], "shape": list(tune["shape"]),
+                  "factor_timings_ms": {str(k): round(v, 4) for k, v in tune["factor_timings_ms"].items()},
+                  "shape_timings_ms": {k: round(v, 4) for k, v in tune["timings_ms"].items()}},
+        "gpu_launches": launches * args.steps,
+    }
+    if per_scene is not None:
+        line["one_context_per_scene"] = {"value": n * per_scene_steps / (per_scene * 1e-3),
+                                         "ms_per_step": per_scene / per_scene_steps,
+                                         "setting": "256 contexts, 256 graph launches per step, tuned cells"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,8 +294,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--clocks-out", default=None)
+    ap.add_argument("--workload", choices=["plain", "batched"], default="plain")
+    ap.add_argument("--no-per-scene", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "batched" and args.impl == "ours":
+        run_batched(args)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -247,11 +325,12 @@ def main():
     sc = scenarios.bidirectional(args.agents)
     sim = abi.OrcaSim.for_scene(sc, cell_size=args.cell_size)
     sim.set_scene(sc)
-    tune = None
+    tune = shape = None
     if args.cell_size <= 0:
         from paper_1908_10107_gb300 import autotune
         tune = autotune.tune_cell_size(sim, sc, use_cache=False, cache_path=None)
         args.cell_size = tune["cell_size"]
+        shape = autotune.tune_launch(sim, lambda: sim.set_scene(sc))
     abi.orca_profile(sim.ctx, True)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -355,7 +434,10 @@ def main():
                    "l2": "flushed between steps (256 MiB write); per-step CUDA events summed",
                    "graph": "one CUDA graph replay per step",
                    "cell_size_tuning_ms": ({f"{k:.4g}": round(v, 4) for k, v in tune["timings_ms"].items()}
-                                           if tune else "fixed by --cell-size")},
+                                           if tune else "fixed by --cell-size"),
+                   "launch_shape": list(shape["shape"]) if shape else [128, 1],
+                   "launch_shape_tuning_ms": ({k: round(v, 4) for k, v in shape["timings_ms"].items()}
+                                              if shape else None)},
         "roofline": {"kernel": "orca_main (neighbours + half-planes + LP + integrate)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,

@@ -258,6 +258,14 @@ ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const float* vel_x
  */
 ORCA_API int orca_set_cell_size(orca_ctx* ctx, float cell_size);
 
+/*
+ * Launch shape of the per-agent ORCA kernel: threads per CTA (64, 128 or 256; default 128)
+ * and lanes that share one agent's least-penetration solve (1 or 4; 0 -> default: 1 for
+ * max_neighbors <= 16, else 4).  Results do not depend on it; speed does.  Rebuilds the
+ * step graphs.
+ */
+ORCA_API int orca_set_launch(orca_ctx* ctx, int32_t threads_per_block, int32_t lp3_lanes);
+
 /* Synchronise `stream` and report any latched device-side error. */
 ORCA_API int orca_sync(orca_ctx* ctx, void* stream);
 

@@ -85,6 +85,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_profile_read": ([vp, vp], c.c_int),
         "orca_launches_per_step": ([vp, c.POINTER(i32)], c.c_int),
         "orca_set_cell_size": ([vp, c.c_float], c.c_int),
+        "orca_set_launch": ([vp, i32, i32], c.c_int),
         "orca_step_static": ([i32] + [vp] * 7 + [c.c_float, i32, c.c_float, c.c_float, vp, vp, vp],
                              c.c_int),
         "orca_num_agents": ([vp, c.POINTER(i32)], c.c_int),
@@ -239,6 +240,10 @@ def orca_profile_read(ctx) -> np.ndarray:
 
 def orca_set_cell_size(ctx, cell_size: float):
     _check(load_library().orca_set_cell_size(ctx, float(cell_size)), ctx)
+
+
+def orca_set_launch(ctx, threads_per_block: int = 128, lp3_lanes: int = 0):
+    _check(load_library().orca_set_launch(ctx, int(threads_per_block), int(lp3_lanes)), ctx)
 
 
 def orca_launches_per_step(ctx) -> int:

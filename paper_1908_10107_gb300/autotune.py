@@ -1,4 +1,4 @@
-"""Cell-size autotuner for the ORCA step.
+"""Autotuner for the ORCA step: grid cell edge and launch shape.
 
 The neighbour search is exact for any grid cell edge, so the edge is a pure speed knob:
 too coarse and each agent scans many candidates, too fine and it visits many empty
@@ -7,6 +7,11 @@ per-phase profiling events (on the context's current state; the state is restore
 afterwards) for a set of edges expressed in units of the expected k-th neighbour
 distance, and returns the fastest.  Results are cached in a JSON file keyed by
 (agent-count bucket, density bucket, k).
+
+``tune_launch`` then tries the per-agent kernel's launch shapes (threads per CTA 64 / 128 /
+256, and 1 or 4 lanes per least-penetration solve); ``tune_batch`` does both for a batch of
+scenes, where each scene's edge is a common factor times its own expected k-th neighbour
+distance.
 """
 from __future__ import annotations
 
@@ -84,3 +89,57 @@ def tune_cell_size(sim: "abi.OrcaSim", scene, steps: int = 6, factors=FACTORS,
         except OSError:
             pass
     return {"cell_size": best, "timings_ms": timings, "kth_distance": rk, "cached": False}
+
+
+SHAPES = ((64, 1), (128, 1), (256, 1), (64, 4), (128, 4), (256, 4))
+
+
+def _time_steps(sim, reload, steps):
+    reload()
+    sim.step(2)
+    ms = []
+    for _ in range(steps):
+        sim.step(1)
+        ms.append(float(abi.orca_profile_read(sim.ctx).sum()))
+    return float(np.median(ms))
+
+
+def tune_launch(sim: "abi.OrcaSim", reload, steps: int = 6, shapes=SHAPES) -> dict:
+    """Fastest (threads per CTA, LP3 lanes) for the crowd that ``reload()`` loads into
+    ``sim``; leaves ``sim`` set to it and reloaded."""
+    abi.orca_profile(sim.ctx, True)
+    timings = {}
+    for tpb, lanes in shapes:
+        abi.orca_set_launch(sim.ctx, tpb, lanes)
+        timings[(tpb, lanes)] = _time_steps(sim, reload, steps)
+    abi.orca_profile(sim.ctx, False)
+    best = min(timings, key=timings.get)
+    abi.orca_set_launch(sim.ctx, *best)
+    reload()
+    return {"shape": best, "timings_ms": {f"{a}x{b}": v for (a, b), v in timings.items()}}
+
+
+def batch_cell_sizes(batch, factor: float):
+    return [float(np.float32(factor * expected_kth_distance(sc.pos, sc.max_neighbors)))
+            if sc.n > 1 else 0.0 for sc in batch.scenes]
+
+
+def set_batch_cells(sim, batch, cells):
+    params = [(sc.n, sc.max_neighbors, sc.neighbor_dist, sc.dt, cs)
+              for sc, cs in zip(batch.scenes, cells)]
+    sim.n_scenes = len(batch.scenes)
+    abi.orca_set_scenes(sim.ctx, params, *batch.arrays())
+
+
+def tune_batch(sim: "abi.OrcaSim", batch, steps: int = 5, factors=FACTORS, shapes=SHAPES) -> dict:
+    """Cell-edge factor (common to all scenes, times each scene's expected k-th neighbour
+    distance) and launch shape for a batch; leaves ``sim`` tuned with the batch loaded."""
+    abi.orca_profile(sim.ctx, True)
+    ftimes = {}
+    for f in factors:
+        cells = batch_cell_sizes(batch, f)
+        ftimes[f] = _time_steps(sim, lambda: set_batch_cells(sim, batch, cells), steps)
+    best_f = min(ftimes, key=ftimes.get)
+    cells = batch_cell_sizes(batch, best_f)
+    shape = tune_launch(sim, lambda: set_batch_cells(sim, batch, cells), steps, shapes)
+    return {"factor": best_f, "factor_timings_ms": ftimes, "cell_sizes": cells, **shape}

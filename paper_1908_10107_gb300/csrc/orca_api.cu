@@ -116,6 +116,7 @@ struct orca_ctx {
     SceneDev* scenes = nullptr;
     int* slot_scene = nullptr;
     int resident = 0;  // CTAs of the ORCA kernel resident at once (persistent launch)
+    LaunchShape shape{128, 1};
     cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::string err;
 };
@@ -216,7 +217,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     a.scenes = c->n_scenes > 0 ? c->scenes : nullptr;
     a.slot_scene = c->n_scenes > 0 ? c->slot_scene : nullptr;
     a.rec_stride = pl.K;
-    e = launch_main(a, pl.K, c->n_scenes > 0 ? c->resident : 0, st);
+    e = launch_main(a, pl.K, c->shape, c->n_scenes > 0 ? c->resident : 0, st);
     if (e != cudaSuccess) return e;
     if (c->prof) e = cudaEventRecordWithFlags(c->pev[3], st, cudaEventRecordExternal);
     return e;
@@ -283,6 +284,7 @@ ORCA_API int orca_create(const orca_params* params, void* workspace, size_t work
     if (!ctx) return fail(nullptr, ORCA_ERR_NOMEM, "host allocation failed");
     ctx->p = *params;
     ctx->plan = pl;
+    ctx->shape.lp3_group = default_lp3_group(pl.K);
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess && workspace) {
         ctx->ws = (char*)workspace;
@@ -345,6 +347,22 @@ ORCA_API int orca_set_cell_size(orca_ctx* ctx, float cell_size) {
     if (!(cell_size >= 0.0f) || !isfinite(cell_size)) return fail(ctx, ORCA_ERR_ARG, "cell_size must be >= 0");
     if (cell_size != ctx->p.cell_size) {
         ctx->p.cell_size = cell_size;
+        drop_graphs(ctx);
+    }
+    return ORCA_OK;
+}
+
+ORCA_API int orca_set_launch(orca_ctx* ctx, int32_t threads_per_block, int32_t lp3_lanes) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256)
+        return fail(ctx, ORCA_ERR_ARG, "threads_per_block must be 64, 128 or 256");
+    if (lp3_lanes != 0 && lp3_lanes != 1 && lp3_lanes != 4)
+        return fail(ctx, ORCA_ERR_ARG, "lp3_lanes must be 0 (default), 1 or 4");
+    LaunchShape sh{threads_per_block, lp3_lanes ? lp3_lanes : default_lp3_group(ctx->plan.K)};
+    if (sh.tpb != ctx->shape.tpb || sh.lp3_group != ctx->shape.lp3_group) {
+        ctx->shape = sh;
+        ctx->resident = 0;
+        if (ctx->n_scenes > 0) ctx->resident = main_resident_blocks(ctx->plan.K, ctx->shape);
         drop_graphs(ctx);
     }
     return ORCA_OK;
@@ -439,7 +457,7 @@ ORCA_API int orca_set_scenes(orca_ctx* ctx, int32_t n_scenes, const orca_scene* 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     delete[] h;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set scenes");
-    if (!ctx->resident) ctx->resident = main_resident_blocks(ctx->plan.K);
+    if (!ctx->resident) ctx->resident = main_resident_blocks(ctx->plan.K, ctx->shape);
     ctx->n_scenes = n_scenes;
     drop_graphs(ctx);
     return ORCA_OK;

@@ -122,15 +122,23 @@ cudaError_t launch_binning_batch(int n, int n_scenes, SceneDev* scenes, const in
                                  cudaStream_t st);
 cudaError_t launch_slot_scene(int n, int n_scenes, const SceneDev* scenes, int* slot_scene,
                               cudaStream_t st);
-int main_resident_blocks(int k);
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
                            const Sorted& dst_s, const AgentParams& src_p,
                            const AgentParams& dst_p, cudaStream_t st);
 cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, float2* pos_out,
                              float2* vel_out, cudaStream_t st);
 cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st);
+// Launch shape of the ORCA kernel: threads per CTA (64, 128 or 256) and lanes per queued
+// agent in the least-penetration phase (1 or 4).
+struct LaunchShape {
+    int tpb;
+    int lp3_group;
+};
+int default_lp3_group(int kmax);
 // kmax: template bound (>= every scene's k); grid_blocks > 0: persistent launch
-cudaError_t launch_main(const MainArgs& a, int kmax, int grid_blocks, cudaStream_t st);
+cudaError_t launch_main(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
+                        cudaStream_t st);
+int main_resident_blocks(int kmax, const LaunchShape& sh);
 
 // Cell coordinate along one axis in FP32, one rounding per operation:
 // floor(fl(fl(v - vmin) * inv)) clamped to [0, g - 1].

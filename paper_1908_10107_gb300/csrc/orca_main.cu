@@ -26,7 +26,6 @@ namespace orca {
 // Stored as float4 (nx, ny, c, unused).
 
 constexpr float kEps = 1e-5f;
-constexpr int kMainThreads = 128;
 
 __device__ __forceinline__ float det2f(float ax, float ay, float bx, float by) {
     return ax * by - ay * bx;
@@ -127,6 +126,28 @@ struct Bisectors {
         return true;
     }
 };
+
+// LP3: least penetration (Section 3), one thread per queued agent.  Penetration of line
+// i at x: c_i - n_i.x.  When line i is violated by more than the current penetration, LP2
+// in direction mode maximises n_i.x over the bisectors of i with the earlier lines; a
+// numerically failed LP2 keeps x.
+__device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, float V, float& xx,
+                                        float& xy) {
+    float dist = 0.0f;
+#pragma unroll 1
+    for (int i = begin; i < n; ++i) {
+        float4 li = row[i];
+        if (li.z - (li.x * xx + li.y * xy) > dist) {
+            Bisectors bis{row, li};
+            float sx = xx, sy = xy;
+            if (lp2_dev(bis, i, V, li.x, li.y, true, xx, xy) < i) {
+                xx = sx;
+                xy = sy;
+            }
+            dist = li.z - (li.x * xx + li.y * xy);
+        }
+    }
+}
 
 // LP3: least penetration (Section 3), by a group of G lanes (G a power of two, lanes
 // aligned in the warp) on one queued agent.  Penetration of line i at x: c_i - n_i.x.
@@ -396,18 +417,21 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
     return cand;
 }
 
-template <int KMAX>
-constexpr int main_min_blocks() { return KMAX <= 10 ? 7 : (KMAX <= 16 ? 4 : (KMAX <= 20 ? 4 : 2)); }
+// Minimum resident CTAs for __launch_bounds__: a register budget per thread that keeps
+// 28 warps per SM at k <= 10, 16 at k <= 20 and 8 at k = 32 without heavy spilling.
+template <int KMAX, int TPB>
+constexpr int main_min_blocks() {
+    return ((KMAX <= 10 ? 28 : (KMAX <= 20 ? 16 : 8)) * 32 + TPB - 1) / TPB;
+}
 
-// Lanes per queued agent in LP3, by measurement on the 524,288-agent flow (k = 10) and
-// the 2,097,152-agent dense crowd (k = 20): with at most 16 half-planes the group's
-// ballots and shuffles cost more than they save, so each queued agent gets one thread;
-// with 20-32 half-planes groups of 4 are 17% faster than one thread.
-template <int KMAX>
-__host__ __device__ constexpr int lp3_group() { return KMAX <= 16 ? 1 : 4; }
+// Default lanes per queued agent in LP3 (one thread, or a group of four sharing the
+// bisector scans and LP1 bounds).  Measured on the 524,288-agent flow (k = 10): one thread
+// 0.289 ms against 0.353 ms for the group code; with 20-32 half-planes per agent the
+// group's longer scans pay for its ballots and shuffles (the autotuner checks both).
+int default_lp3_group(int kmax) { return kmax <= 16 ? 1 : 4; }
 
-template <int KMAX>
-constexpr size_t main_smem_bytes() { return sizeof(float4) * kMainThreads * (KMAX + 1); }
+template <int KMAX, int TPB>
+constexpr size_t main_smem_bytes() { return sizeof(float4) * TPB * (KMAX + 1); }
 
 // Parameters of the scene an agent belongs to (the one scene, or its scene of a batch).
 struct SceneView {
@@ -433,18 +457,18 @@ __device__ __forceinline__ void scene_view(const MainArgs& a, int t, SceneView& 
     }
 }
 
-// Persistent over tiles of kMainThreads consecutive agents: tile blockIdx.x first, then
+// Persistent over tiles of TPB consecutive agents: tile blockIdx.x first, then
 // tiles taken from a per-step counter (with one CTA per tile this loop runs once).
-template <int KMAX>
-__global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_main_kernel(MainArgs a) {
+template <int KMAX, int TPB, int G>
+__global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_kernel(MainArgs a) {
     constexpr int KP = KMAX + 1;  // padded rows: conflict-free float4 accesses
-    extern __shared__ float4 s_lines[];  // kMainThreads * KP half-planes
-    __shared__ float2 s_x[kMainThreads];
-    __shared__ float s_V[kMainThreads];
-    __shared__ unsigned char s_b[kMainThreads];
-    __shared__ unsigned char s_cnt[kMainThreads];
-    __shared__ unsigned char s_queued[kMainThreads];
-    __shared__ unsigned char s_queue[kMainThreads];
+    extern __shared__ float4 s_lines[];  // TPB * KP half-planes
+    __shared__ float2 s_x[TPB];
+    __shared__ float s_V[TPB];
+    __shared__ unsigned char s_b[TPB];
+    __shared__ unsigned char s_cnt[TPB];
+    __shared__ unsigned char s_queued[TPB];
+    __shared__ unsigned char s_queue[TPB];
     __shared__ int s_qn, s_tile;
     __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3;
     const int tid = threadIdx.x;
@@ -454,14 +478,14 @@ __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_ma
         s_act = 0;
         s_lp3 = 0;
     }
-    const int ntiles = (a.n + kMainThreads - 1) / kMainThreads;
+    const int ntiles = (a.n + TPB - 1) / TPB;
     float4* row = s_lines + tid * KP;
 #pragma unroll 1
     for (int tile = blockIdx.x; tile < ntiles;) {
         if (tid == 0) s_qn = 0;
         s_queued[tid] = 0;
         __syncthreads();
-        const int t = tile * kMainThreads + tid;
+        const int t = tile * TPB + tid;
         const bool active = t < a.n;
         float2 p = make_float2(0.0f, 0.0f);
         float xx = 0.0f, xy = 0.0f, dt = 1.0f;
@@ -537,12 +561,12 @@ __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_ma
         }
         __syncthreads();
         // ---- phase 3: least penetration for the queued agents, G lanes each
-        constexpr int G = lp3_group<KMAX>();
         const int nq = s_qn;
-        for (int q = tid / G; q < nq; q += kMainThreads / G) {
+        for (int q = tid / G; q < nq; q += TPB / G) {
             int ag = s_queue[q];
             float2 x = s_x[ag];
-            lp3_group_dev<G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
+            if (G == 1) lp3_dev(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
+            else lp3_group_dev<G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
             if ((tid & (G - 1)) == 0) s_x[ag] = x;
         }
         __syncthreads();
@@ -568,13 +592,13 @@ __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_ma
             atomicAdd(&s_lines_n, (unsigned long long)wl);
             atomicAdd(&s_act, (unsigned long long)wa);
         }
-        if (tid == 0) {
-            s_lp3 += (unsigned long long)nq;
-            s_tile = (int)atomicAdd(&a.misc_rw->tile_counter, 1u) + (int)gridDim.x;
-        }
+        if (tid == 0) s_lp3 += (unsigned long long)nq;
+        if ((int)gridDim.x >= ntiles) break;  // one CTA per tile: no work queue
+        if (tid == 0) s_tile = (int)atomicAdd(&a.misc_rw->tile_counter, 1u) + (int)gridDim.x;
         __syncthreads();
         tile = s_tile;
     }
+    __syncthreads();
     if (tid == 0) {
         unsigned long long* c = a.block_counters + 4 * (size_t)blockIdx.x;
         c[0] += s_act;
@@ -584,49 +608,75 @@ __global__ void __launch_bounds__(kMainThreads, main_min_blocks<KMAX>()) orca_ma
     }
 }
 
-int main_blocks(int n) { return (n + kMainThreads - 1) / kMainThreads; }
+// at most one CTA per 64 agents (the smallest CTA)
+int main_blocks(int n) { return (n + 63) / 64; }
 
 // CTAs of the ORCA kernel that fit on the GPU at once (for the persistent launch).
-template <int KMAX>
+template <int KMAX, int TPB, int G>
 static int resident_blocks_k() {
-    constexpr size_t smem = main_smem_bytes<KMAX>();
-    if (cudaFuncSetAttribute(orca_main_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    constexpr size_t smem = main_smem_bytes<KMAX, TPB>();
+    if (cudaFuncSetAttribute(orca_main_kernel<KMAX, TPB, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
     int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, orca_main_kernel<KMAX>, kMainThreads,
-                                                      smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, orca_main_kernel<KMAX, TPB, G>, TPB, smem) !=
+        cudaSuccess)
         return 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return per_sm * sms;
 }
 
-int main_resident_blocks(int k) {
-    if (k <= 10) return resident_blocks_k<10>();
-    if (k <= 16) return resident_blocks_k<16>();
-    if (k <= 20) return resident_blocks_k<20>();
-    return resident_blocks_k<32>();
-}
-
-// grid_blocks > 0: persistent launch with that many CTAs (capped at one per tile).
-template <int KMAX>
+template <int KMAX, int TPB, int G>
 static cudaError_t launch_main_k(const MainArgs& a, int grid_blocks, cudaStream_t st) {
-    constexpr size_t smem = main_smem_bytes<KMAX>();
-    cudaError_t e = cudaFuncSetAttribute(orca_main_kernel<KMAX>,
+    constexpr size_t smem = main_smem_bytes<KMAX, TPB>();
+    cudaError_t e = cudaFuncSetAttribute(orca_main_kernel<KMAX, TPB, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int nb = main_blocks(a.n);
+    int nb = (a.n + TPB - 1) / TPB;
     if (grid_blocks > 0 && grid_blocks < nb) nb = grid_blocks;
-    orca_main_kernel<KMAX><<<nb, kMainThreads, smem, st>>>(a);
+    orca_main_kernel<KMAX, TPB, G><<<nb, TPB, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_main(const MainArgs& a, int kmax, int grid_blocks, cudaStream_t st) {
-    if (kmax <= 10) return launch_main_k<10>(a, grid_blocks, st);
-    if (kmax <= 16) return launch_main_k<16>(a, grid_blocks, st);
-    if (kmax <= 20) return launch_main_k<20>(a, grid_blocks, st);
-    return launch_main_k<32>(a, grid_blocks, st);
+// Dispatch over (k bound, threads per CTA, LP3 lanes per agent).  resident != null:
+// return the resident CTA count instead of launching.
+template <int KMAX, int TPB>
+static cudaError_t dispatch_g(const MainArgs& a, int g, int grid_blocks, cudaStream_t st, int* resident) {
+    if (g == 4) {
+        if (resident) { *resident = resident_blocks_k<KMAX, TPB, 4>(); return cudaSuccess; }
+        return launch_main_k<KMAX, TPB, 4>(a, grid_blocks, st);
+    }
+    if (resident) { *resident = resident_blocks_k<KMAX, TPB, 1>(); return cudaSuccess; }
+    return launch_main_k<KMAX, TPB, 1>(a, grid_blocks, st);
+}
+
+template <int KMAX>
+static cudaError_t dispatch_tpb(const MainArgs& a, const LaunchShape& sh, int grid_blocks, cudaStream_t st,
+                                int* resident) {
+    if (sh.tpb == 64) return dispatch_g<KMAX, 64>(a, sh.lp3_group, grid_blocks, st, resident);
+    if (sh.tpb == 256) return dispatch_g<KMAX, 256>(a, sh.lp3_group, grid_blocks, st, resident);
+    return dispatch_g<KMAX, 128>(a, sh.lp3_group, grid_blocks, st, resident);
+}
+
+static cudaError_t dispatch(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
+                            cudaStream_t st, int* resident) {
+    if (kmax <= 10) return dispatch_tpb<10>(a, sh, grid_blocks, st, resident);
+    if (kmax <= 16) return dispatch_tpb<16>(a, sh, grid_blocks, st, resident);
+    if (kmax <= 20) return dispatch_tpb<20>(a, sh, grid_blocks, st, resident);
+    return dispatch_tpb<32>(a, sh, grid_blocks, st, resident);
+}
+
+int main_resident_blocks(int kmax, const LaunchShape& sh) {
+    int r = 0;
+    MainArgs dummy{};
+    dispatch(dummy, kmax, sh, 0, nullptr, &r);
+    return r;
+}
+
+cudaError_t launch_main(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
+                        cudaStream_t st) {
+    return dispatch(a, kmax, sh, grid_blocks, st, nullptr);
 }
 
 }  // namespace orca

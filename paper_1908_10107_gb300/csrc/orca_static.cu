@@ -37,7 +37,7 @@ constexpr StaticLayout static_layout() {
     StaticLayout L{};
     size_t N = kStaticMaxAgents, o = 0;
     int nsb = (kStaticMaxAgents + kSortTile - 1) / kSortTile;
-    int nmb = (kStaticMaxAgents + 127) / 128;
+    int nmb = (kStaticMaxAgents + 63) / 64;
     L.id = o; o += al256(N * 4);
     L.keys0 = o; o += al256(N * 4);
     L.keys1 = o; o += al256(N * 4);
@@ -170,7 +170,8 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
         a.scenes = nullptr;
         a.slot_scene = nullptr;
         a.rec_stride = max_neighbors;
-        e = launch_main(a, max_neighbors, 0, st);
+        LaunchShape sh{128, default_lp3_group(max_neighbors)};
+        e = launch_main(a, max_neighbors, sh, 0, st);
     }
     if (e == cudaSuccess) e = launch_unpermute(n, out, dst_p.id, (float2*)pos_out_xy, (float2*)vel_out_xy, st);
     if (e != cudaSuccess)
