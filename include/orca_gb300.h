@@ -266,6 +266,42 @@ ORCA_API int orca_set_cell_size(orca_ctx* ctx, float cell_size);
  */
 ORCA_API int orca_set_launch(orca_ctx* ctx, int32_t threads_per_block, int32_t lp3_lanes);
 
+/*
+ * Differentiable rollouts (single scene).  A rollout of T steps from the loaded state
+ * records the positions p(1..T); its adjoint returns the gradient of a loss L(p(1..T))
+ * with respect to every agent's preferred speed, radius and time horizon (and initial
+ * position and velocity).  The adjoint is hand-written: it differentiates each step
+ * through the constraints that fixed the selected velocity, with neighbour sets and every
+ * branch held fixed (the step is piecewise smooth).  The forward pass keeps a checkpoint
+ * of the state every ckpt_every steps; the backward pass re-runs each segment from its
+ * checkpoint, recording, and sweeps it in reverse.
+ *
+ * orca_rollout_workspace_size: device bytes for (T, ckpt_every) on this context.
+ */
+ORCA_API int orca_rollout_workspace_size(const orca_ctx* ctx, int32_t T, int32_t ckpt_every,
+                                         size_t* bytes);
+
+/*
+ * Run T >= 1 steps from the loaded state, checkpointing every ckpt_every >= 1 steps.
+ *   traj_pos  device, T*n*2 floats: p(t) for t = 1..T in agent order (may be NULL).
+ *   workspace device buffer of orca_rollout_workspace_size bytes, 256-byte aligned, kept by
+ *             the caller until orca_rollout_backward.
+ * The context's state ends at step T.
+ */
+ORCA_API int orca_rollout_forward(orca_ctx* ctx, int32_t T, int32_t ckpt_every, float* traj_pos,
+                                  void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Gradients of L from dL/dp(t) (device, T*n*2 floats, t = 1..T) for the last
+ * orca_rollout_forward with this workspace.  Outputs (device, n floats each; overwritten;
+ * any may be NULL): g_pref_speed, g_radius, g_time_horizon; g_pos0, g_vel0 (2n floats):
+ * dL/dp(0), dL/dv(0).  The context's state is left undefined (reload it).
+ */
+ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g_pref_speed,
+                                   float* g_radius, float* g_time_horizon, float* g_pos0,
+                                   float* g_vel0, void* workspace, size_t workspace_bytes,
+                                   void* stream);
+
 /* Synchronise `stream` and report any latched device-side error. */
 ORCA_API int orca_sync(orca_ctx* ctx, void* stream);
 

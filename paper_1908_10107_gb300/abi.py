@@ -85,6 +85,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_profile_read": ([vp, vp], c.c_int),
         "orca_launches_per_step": ([vp, c.POINTER(i32)], c.c_int),
         "orca_set_cell_size": ([vp, c.c_float], c.c_int),
+        "orca_rollout_workspace_size": ([vp, i32, i32, c.POINTER(sz)], c.c_int),
+        "orca_rollout_forward": ([vp, i32, i32, vp, vp, sz, vp], c.c_int),
+        "orca_rollout_backward": ([vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], c.c_int),
         "orca_set_launch": ([vp, i32, i32], c.c_int),
         "orca_step_static": ([i32] + [vp] * 7 + [c.c_float, i32, c.c_float, c.c_float, vp, vp, vp],
                              c.c_int),
@@ -236,6 +239,30 @@ def orca_profile_read(ctx) -> np.ndarray:
     out = np.zeros(3, np.float32)
     _check(load_library().orca_profile_read(ctx, ctypes.c_void_p(out.ctypes.data)), ctx)
     return out
+
+
+def orca_rollout_workspace_size(ctx, T: int, ckpt_every: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load_library().orca_rollout_workspace_size(ctx, int(T), int(ckpt_every), ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def orca_rollout_forward(ctx, T, ckpt_every, traj_pos, workspace, stream=None):
+    """traj_pos: CUDA tensor [T, n, 2] or None; workspace: CUDA uint8 tensor (256-B aligned)."""
+    _check(load_library().orca_rollout_forward(ctx, int(T), int(ckpt_every), _dptr(traj_pos),
+                                               _dptr(workspace), workspace.numel(), _stream(stream)), ctx)
+
+
+def orca_rollout_backward(ctx, dL_dpos, g_pref_speed, g_radius, g_time_horizon, g_pos0, g_vel0,
+                          workspace, stream=None):
+    _check(load_library().orca_rollout_backward(ctx, _dptr(dL_dpos), _dptr(g_pref_speed),
+                                                _dptr(g_radius), _dptr(g_time_horizon),
+                                                _dptr(g_pos0), _dptr(g_vel0), _dptr(workspace),
+                                                workspace.numel(), _stream(stream)), ctx)
 
 
 def orca_set_cell_size(ctx, cell_size: float):

@@ -117,6 +117,8 @@ struct orca_ctx {
     int* slot_scene = nullptr;
     int resident = 0;  // CTAs of the ORCA kernel resident at once (persistent launch)
     LaunchShape shape{128, 1};
+    int roll_T = 0, roll_C = 0;  // last orca_rollout_forward
+    void* roll_ws = nullptr;
     cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::string err;
 };
@@ -217,6 +219,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     a.scenes = c->n_scenes > 0 ? c->scenes : nullptr;
     a.slot_scene = c->n_scenes > 0 ? c->slot_scene : nullptr;
     a.rec_stride = pl.K;
+    a.tape = nullptr;
     e = launch_main(a, pl.K, c->shape, c->n_scenes > 0 ? c->resident : 0, st);
     if (e != cudaSuccess) return e;
     if (c->prof) e = cudaEventRecordWithFlags(c->pev[3], st, cudaEventRecordExternal);
@@ -226,6 +229,37 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
 // kernels per step: bbox, keys+histogram, per radix pass (upsweep except pass 0, scan,
 // downsweep), cell table, reorder, ORCA kernel
 static int launches_per_step(const orca_ctx* c) { return 2 + 3 * c->plan.max_passes - 1 + 3; }
+
+// One step launched directly with the neighbour lists and LP records written in agent
+// order (recomputation inside orca_rollout_backward).
+static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, uint32_t* tape,
+                                          cudaStream_t st) {
+    const Plan& pl = c->plan;
+    float cs = c->p.cell_size > 0.0f ? c->p.cell_size : c->p.neighbor_dist * 0.25f;
+    cudaError_t e = launch_binning(c->n, cs, pl.max_cells, pl.max_passes, c->PV[0], c->bins, st);
+    if (e != cudaSuccess) return e;
+    e = launch_reorder(c->n, c->bins, c->PV[0], c->sorted, c->PR[par], c->PR[par ^ 1], st);
+    if (e != cudaSuccess) return e;
+    MainArgs a;
+    a.n = c->n;
+    a.k = pl.K;
+    a.nd = c->p.neighbor_dist;
+    a.dt = c->p.dt;
+    a.misc = c->bins.misc;
+    a.misc_rw = c->bins.misc;
+    a.cell_start = c->bins.cell_start;
+    a.in = c->sorted;
+    a.prm = c->PR[par ^ 1];
+    a.out = c->PV[0];
+    a.block_counters = c->blk;
+    a.rec_nbr = nbr;
+    a.rec_cell = nullptr;
+    a.scenes = nullptr;
+    a.slot_scene = nullptr;
+    a.rec_stride = pl.K;
+    a.tape = tape;
+    return launch_main(a, pl.K, c->shape, 0, st);
+}
 
 static int build_graphs(orca_ctx* ctx) {
     drop_graphs(ctx);
@@ -586,6 +620,163 @@ ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream) 
     for (size_t b = 0; b < (size_t)ctx->plan.nmb; ++b)
         for (int q = 0; q < 4; ++q) counters4[q] += (int64_t)h[4 * b + q];
     delete[] h;
+    return ORCA_OK;
+}
+
+// Rollout workspace: checkpoints, parameters in agent order, one segment's recomputed
+// states / neighbour lists / LP records, and two pairs of adjoint buffers.
+struct RolloutPlan {
+    int T, C, nseg;
+    size_t ckpt, goal, radius, vmax, pref, tau, seg_state, seg_nbr, seg_tape, adj, gscratch, total;
+};
+
+static RolloutPlan rollout_plan(const orca_ctx* c, int T, int C) {
+    RolloutPlan r;
+    r.T = T;
+    r.C = C;
+    r.nseg = (T + C - 1) / C;
+    size_t N = (size_t)(c->n > 0 ? c->n : 1), K = (size_t)c->plan.K;
+    Layout L;
+    r.ckpt = L.add((size_t)(r.nseg + 1) * N * 16);
+    r.goal = L.add(N * 8);
+    r.radius = L.add(N * 4);
+    r.vmax = L.add(N * 4);
+    r.pref = L.add(N * 4);
+    r.tau = L.add(N * 4);
+    r.seg_state = L.add((size_t)(C + 1) * N * 16);
+    r.seg_nbr = L.add((size_t)C * N * K * 4);
+    r.seg_tape = L.add((size_t)C * N * 4);
+    r.adj = L.add(4 * N * 8);
+    r.gscratch = L.add(3 * N * 4);
+    r.total = L.total;
+    return r;
+}
+
+ORCA_API int orca_rollout_workspace_size(const orca_ctx* ctx, int32_t T, int32_t ckpt_every,
+                                         size_t* bytes) {
+    if (!ctx || !bytes || T < 1 || ckpt_every < 1) return ORCA_ERR_ARG;
+    *bytes = rollout_plan(ctx, T, ckpt_every).total;
+    return ORCA_OK;
+}
+
+ORCA_API int orca_rollout_forward(orca_ctx* ctx, int32_t T, int32_t ckpt_every, float* traj_pos,
+                                  void* workspace, size_t workspace_bytes, void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (T < 1 || ckpt_every < 1) return fail(ctx, ORCA_ERR_ARG, "T and ckpt_every must be >= 1");
+    if (ctx->n_scenes > 0) return fail(ctx, ORCA_ERR_STATE, "rollouts need a single scene");
+    if (ctx->n < 1) return fail(ctx, ORCA_ERR_STATE, "no agents loaded");
+    RolloutPlan r = rollout_plan(ctx, T, ckpt_every);
+    if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < r.total)
+        return fail(ctx, ORCA_ERR_NOMEM, "rollout workspace missing, misaligned or too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    char* w = (char*)workspace;
+    size_t N = (size_t)ctx->n;
+    auto ck = [&](int s) { return (float2*)(w + r.ckpt + (size_t)s * N * 16); };
+    CK(launch_unpermute_params(ctx->n, ctx->PR[ctx->cur], (float2*)(w + r.goal), (float*)(w + r.radius),
+                               (float*)(w + r.vmax), (float*)(w + r.pref), (float*)(w + r.tau), st),
+       "unpermute parameters");
+    CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, ck(0), ck(0) + N, st), "checkpoint");
+    for (int t = 0; t < T; ++t) {
+        int rr = orca_step(ctx, 1, stream);
+        if (rr != ORCA_OK) return rr;
+        if (traj_pos)
+            CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (float2*)traj_pos + (size_t)t * N,
+                                nullptr, st), "trajectory");
+        if ((t + 1) % ckpt_every == 0 && t + 1 < T) {
+            float2* c = ck((t + 1) / ckpt_every);
+            CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, c, c + N, st), "checkpoint");
+        }
+    }
+    ctx->roll_T = T;
+    ctx->roll_C = ckpt_every;
+    ctx->roll_ws = workspace;
+    return ORCA_OK;
+}
+
+ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g_pref_speed,
+                                   float* g_radius, float* g_time_horizon, float* g_pos0,
+                                   float* g_vel0, void* workspace, size_t workspace_bytes,
+                                   void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (!dL_dpos) return fail(ctx, ORCA_ERR_ARG, "dL_dpos is required");
+    if (workspace != ctx->roll_ws || ctx->roll_T < 1)
+        return fail(ctx, ORCA_ERR_STATE, "no orca_rollout_forward with this workspace");
+    RolloutPlan r = rollout_plan(ctx, ctx->roll_T, ctx->roll_C);
+    if (workspace_bytes < r.total) return fail(ctx, ORCA_ERR_NOMEM, "rollout workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    char* w = (char*)workspace;
+    const int n = ctx->n, T = r.T, C = r.C;
+    const size_t N = (size_t)n, K = (size_t)ctx->plan.K;
+    auto ck = [&](int s) { return (float2*)(w + r.ckpt + (size_t)s * N * 16); };
+    auto sstate = [&](int q) { return (float2*)(w + r.seg_state + (size_t)q * N * 16); };
+    float2* adj = (float2*)(w + r.adj);
+    float2* pnext = adj;
+    float2* vnext = adj + N;
+    float2* pcur = adj + 2 * N;
+    float2* vcur = adj + 3 * N;
+    const float2* dLdp = (const float2*)dL_dpos;
+    // parameter gradients accumulate into the caller's arrays, or into scratch
+    float* gs = (float*)(w + r.gscratch);
+    float* gp = g_pref_speed ? g_pref_speed : gs;
+    float* gr = g_radius ? g_radius : gs + N;
+    float* gt = g_time_horizon ? g_time_horizon : gs + 2 * N;
+    CK(cudaMemsetAsync(gp, 0, N * 4, st), "zero");
+    CK(cudaMemsetAsync(gr, 0, N * 4, st), "zero");
+    CK(cudaMemsetAsync(gt, 0, N * 4, st), "zero");
+    CK(cudaMemcpyAsync(pnext, dLdp + (size_t)(T - 1) * N, N * 8, cudaMemcpyDeviceToDevice, st), "seed");
+    CK(cudaMemsetAsync(vnext, 0, N * 8, st), "zero");
+    for (int seg = r.nseg - 1; seg >= 0; --seg) {
+        int t0 = seg * C, t1 = t0 + C < T ? t0 + C : T;
+        int rr = orca_set_agents(ctx, n, (const float*)ck(seg), (const float*)(ck(seg) + N),
+                                 (const float*)(w + r.goal), (const float*)(w + r.radius),
+                                 (const float*)(w + r.vmax), (const float*)(w + r.pref),
+                                 (const float*)(w + r.tau), ORCA_DEVICE, stream);
+        if (rr != ORCA_OK) return rr;
+        for (int t = t0; t < t1; ++t) {
+            float2* sp = sstate(t - t0);
+            CK(launch_unpermute(n, ctx->PV[0], ctx->PR[ctx->cur].id, sp, sp + N, st), "segment state");
+            CK(enqueue_recording_step(ctx, ctx->cur, (int32_t*)(w + r.seg_nbr) + (size_t)(t - t0) * N * K,
+                                      (uint32_t*)(w + r.seg_tape) + (size_t)(t - t0) * N, st),
+               "recording step");
+            ctx->cur ^= 1;
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            const float2* sp = sstate(t - t0);
+            CK(cudaMemsetAsync(pcur, 0, N * 8, st), "zero");
+            CK(cudaMemsetAsync(vcur, 0, N * 8, st), "zero");
+            AdjointArgs A;
+            A.n = n;
+            A.kstride = (int)K;
+            A.dt = ctx->p.dt;
+            A.pos = sp;
+            A.vel = sp + N;
+            A.goal = (const float2*)(w + r.goal);
+            A.radius = (const float*)(w + r.radius);
+            A.max_speed = (const float*)(w + r.vmax);
+            A.pref_speed = (const float*)(w + r.pref);
+            A.tau = (const float*)(w + r.tau);
+            A.nbr = (const int32_t*)(w + r.seg_nbr) + (size_t)(t - t0) * N * K;
+            A.tape = (const uint32_t*)(w + r.seg_tape) + (size_t)(t - t0) * N;
+            A.pbar_next = pnext;
+            A.vbar_next = vnext;
+            A.pbar = pcur;
+            A.vbar = vcur;
+            A.g_pref = gp;
+            A.g_radius = gr;
+            A.g_tau = gt;
+            CK(launch_adjoint(A, (int)K, st), "adjoint kernel");
+            if (t >= 1) CK(launch_axpy2(n, pcur, dLdp + (size_t)(t - 1) * N, st), "loss gradient");
+            float2* tmp = pnext;
+            pnext = pcur;
+            pcur = tmp;
+            tmp = vnext;
+            vnext = vcur;
+            vcur = tmp;
+        }
+    }
+    if (g_pos0) CK(cudaMemcpyAsync(g_pos0, pnext, N * 8, cudaMemcpyDeviceToDevice, st), "copy");
+    if (g_vel0) CK(cudaMemcpyAsync(g_vel0, vnext, N * 8, cudaMemcpyDeviceToDevice, st), "copy");
+    ctx->roll_T = 0;
     return ORCA_OK;
 }
 

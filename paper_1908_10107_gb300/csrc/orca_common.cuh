@@ -101,6 +101,7 @@ struct MainArgs {
     const SceneDev* scenes;              // batch: per-scene parameters and grids, else null
     const int* slot_scene;               // batch: scene of each slot, else null
     int rec_stride;                      // row length of rec_nbr (the context's max k)
+    uint32_t* tape;                      // rollouts: per-agent LP record (agent order), or null
     const DeviceMisc* misc;
     DeviceMisc* misc_rw;
     const uint32_t* cell_start;
@@ -139,6 +140,32 @@ int default_lp3_group(int kmax);
 cudaError_t launch_main(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
                         cudaStream_t st);
 int main_resident_blocks(int kmax, const LaunchShape& sh);
+
+// Reverse step of a rollout (orca_adjoint.cu); everything in agent order.
+struct AdjointArgs {
+    int n, kstride;
+    float dt;
+    const float2* pos;        // state at step t
+    const float2* vel;
+    const float2* goal;       // parameters
+    const float* radius;
+    const float* max_speed;
+    const float* pref_speed;
+    const float* tau;
+    const int32_t* nbr;       // n * kstride, -1 padded
+    const uint32_t* tape;     // n LP records
+    const float2* pbar_next;  // dL/dp(t+1), dL/dv(t+1)
+    const float2* vbar_next;
+    float2* pbar;             // dL/dp(t), dL/dv(t) (accumulated)
+    float2* vbar;
+    float* g_pref;            // parameter gradients (accumulated)
+    float* g_radius;
+    float* g_tau;
+};
+cudaError_t launch_adjoint(const AdjointArgs& A, int kmax, cudaStream_t st);
+cudaError_t launch_unpermute_params(int n, const AgentParams& src, float2* goal, float* radius,
+                                    float* vmax, float* pref, float* tau, cudaStream_t st);
+cudaError_t launch_axpy2(int n, float2* y, const float2* x, cudaStream_t st);
 
 // Cell coordinate along one axis in FP32, one rounding per operation:
 // floor(fl(fl(v - vmin) * inv)) clamped to [0, g - 1].

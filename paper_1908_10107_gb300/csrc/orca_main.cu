@@ -13,7 +13,7 @@
 //      LP2 succeeded;
 //   4. vel <- x, pos <- pos + x*dt into the same sorted slot of the state buffer.
 // Half-planes never leave the SM (the paper stores them in global memory, Section 5).
-#include "orca_common.cuh"
+#include "orca_geom.cuh"
 
 namespace orca {
 
@@ -25,24 +25,40 @@ namespace orca {
 // least-penetration bisectors need no intersection points (which can lie far away).
 // Stored as float4 (nx, ny, c, unused).
 
-constexpr float kEps = 1e-5f;
 
-__device__ __forceinline__ float det2f(float ax, float ay, float bx, float by) {
-    return ax * by - ay * bx;
-}
+// What fixes an agent's final velocity, recorded for the adjoint (rollouts only):
+//   kTapePref      x = preferred velocity o;          kTapePrefClip  x = V o / |o|;
+//   kTapeLine      x from LP1 on line i (LP2 phase);
+//   kTapeLp3Dir    x = V n_i (LP3, no bisector was violated);
+//   kTapeLp3Line   x from LP1 on the bisector of lines i and f (LP3).
+// For the LP1 cases: t was free (projection of o), or the disc's or line / bisector j's
+// bound on the tL (side 0) or tR (side 1) end.
+constexpr int kTapePref = 0, kTapePrefClip = 1, kTapeLine = 2, kTapeLp3Dir = 3, kTapeLp3Line = 4;
+constexpr int kBoundFree = 0, kBoundDisc = 1, kBoundLine = 2;
+
+struct LpTape {
+    int mode, i, f, bound, j, side;
+    __device__ __forceinline__ unsigned pack() const {
+        return (unsigned)mode | (unsigned)i << 3 | (unsigned)f << 9 | (unsigned)bound << 15 |
+               (unsigned)j << 17 | (unsigned)side << 23;
+    }
+};
 
 // LP1: best point on the boundary of line i inside the disc |x| <= V and the half-planes
 // 0..i-1.  x(t) = c_i n_i + t d_i with d_i = (n_i.y, -n_i.x).  The disc gives
 // |t| <= sqrt(V^2 - c_i^2); half-plane j gives -det(n_i, n_j) t >= c_j - c_i (n_i.n_j),
 // an upper bound on t when det(n_i, n_j) > 0, a lower one when < 0; a (nearly) parallel
 // j (|det| <= eps) is infeasible iff its right-hand side is positive.
+// rec (may be null) receives which bound fixed t.
 template <class LineAt>
 __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, float V, float ox,
-                                        float oy, bool dir_opt, float& xx, float& xy) {
+                                        float oy, bool dir_opt, float& xx, float& xy,
+                                        LpTape* rec = nullptr) {
     float D = V * V - li.z * li.z;
     if (D < 0.0f) return false;
     float sq = sqrtf(D);
     float tL = -sq, tR = sq;
+    int srcL = -1, srcR = -1;  // -1: the disc, else the bounding line
 #pragma unroll 1
     for (int j = 0; j < i; ++j) {
         float4 lj;
@@ -54,12 +70,27 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
             continue;
         }
         float t = __fdividef(-rhs, den);
-        if (den >= 0.0f) tR = fminf(tR, t);
-        else tL = fmaxf(tL, t);
+        if (den >= 0.0f) {
+            if (rec && t < tR) srcR = j;
+            tR = fminf(tR, t);
+        } else {
+            if (rec && t > tL) srcL = j;
+            tL = fmaxf(tL, t);
+        }
         if (tL > tR) return false;
     }
     float dx = li.y, dy = -li.x;
     float t = ox * dx + oy * dy;
+    if (rec) {
+        int side = -1;
+        if (dir_opt) side = t > 0.0f ? 1 : 0;
+        else if (t < tL) side = 0;
+        else if (t > tR) side = 1;
+        rec->side = side < 0 ? 0 : side;
+        int src = side == 0 ? srcL : srcR;
+        rec->bound = side < 0 ? kBoundFree : (src < 0 ? kBoundDisc : kBoundLine);
+        rec->j = src < 0 ? 0 : src;
+    }
     if (dir_opt) t = t > 0.0f ? tR : tL;
     else t = fminf(fmaxf(t, tL), tR);
     xx = li.z * li.x + t * dx;
@@ -69,21 +100,26 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
 
 // LP2: incremental 2-D LP over lines 0..n-1 in order (Section 3).  Returns n on success,
 // else the index of the line where LP1 failed (x keeps its last value).
+// rec (may be null) receives what fixed the returned x: the start point (mode kTapePref,
+// kTapePrefClip, or kTapeLp3Dir in direction mode) or the last LP1 (kTapeLine, line i).
 template <class LineAt>
 __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float ox, float oy,
-                                       bool dir_opt, float& xx, float& xy) {
+                                       bool dir_opt, float& xx, float& xy, LpTape* rec = nullptr) {
     if (dir_opt) {
         xx = ox * V;
         xy = oy * V;
+        if (rec) rec->mode = kTapeLp3Dir;
     } else {
         float o2 = ox * ox + oy * oy;
         if (o2 > V * V) {
             float s = V * rsqrtf(o2);
             xx = ox * s;
             xy = oy * s;
+            if (rec) rec->mode = kTapePrefClip;
         } else {
             xx = ox;
             xy = oy;
+            if (rec) rec->mode = kTapePref;
         }
     }
 #pragma unroll 1
@@ -92,10 +128,17 @@ __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float
         if (!line(i, li)) continue;
         if (li.z - (li.x * xx + li.y * xy) > 0.0f) {
             float sx = xx, sy = xy;
-            if (!lp1_dev(line, i, li, V, ox, oy, dir_opt, xx, xy)) {
+            LpTape r1;
+            if (!lp1_dev(line, i, li, V, ox, oy, dir_opt, xx, xy, rec ? &r1 : nullptr)) {
                 xx = sx;
                 xy = sy;
                 return i;
+            }
+            if (rec) {
+                r1.mode = kTapeLine;
+                r1.i = i;
+                r1.f = 0;
+                *rec = r1;
             }
         }
     }
@@ -131,8 +174,9 @@ struct Bisectors {
 // i at x: c_i - n_i.x.  When line i is violated by more than the current penetration, LP2
 // in direction mode maximises n_i.x over the bisectors of i with the earlier lines; a
 // numerically failed LP2 keeps x.
+// rec (may be null) keeps the record of the LP2 phase until an LP3 solve succeeds.
 __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, float V, float& xx,
-                                        float& xy) {
+                                        float& xy, LpTape* rec = nullptr) {
     float dist = 0.0f;
 #pragma unroll 1
     for (int i = begin; i < n; ++i) {
@@ -140,9 +184,22 @@ __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, flo
         if (li.z - (li.x * xx + li.y * xy) > dist) {
             Bisectors bis{row, li};
             float sx = xx, sy = xy;
-            if (lp2_dev(bis, i, V, li.x, li.y, true, xx, xy) < i) {
+            LpTape r2;
+            if (lp2_dev(bis, i, V, li.x, li.y, true, xx, xy, rec ? &r2 : nullptr) < i) {
                 xx = sx;
                 xy = sy;
+            } else if (rec) {
+                if (r2.mode == kTapeLine) {  // LP1 on the bisector of lines i and r2.i
+                    r2.f = r2.i;
+                    r2.mode = kTapeLp3Line;
+                } else {
+                    r2.f = 0;
+                    r2.bound = kBoundFree;
+                    r2.j = 0;
+                    r2.side = 0;
+                }
+                r2.i = i;
+                *rec = r2;
             }
             dist = li.z - (li.x * xx + li.y * xy);
         }
@@ -237,68 +294,6 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
         }
         dist = li.z - (li.x * xx + li.y * xy);
     }
-}
-
-// Half-plane of agent (p, v, r, 1/tau) induced by neighbour message mj = (x, y, r, id)
-// with velocity vj -- Fig. 1.  u runs from the relative velocity to the nearest
-// boundary point of VO^tau; the boundary passes through v + u/2 with the valid side
-// along the VO's outward normal.
-//   cut-off circle / overlap: n = w/|w| (w = v_rel - p/tau, or p/dt when overlapping),
-//     c = n.v + (R/tau - |w|)/2;
-//   legs: n is the leg's outward normal and c = n.(v + v_j)/2.
-// When overlapping, R/dt - |w| is formed as (R - |q|)/dt with q = p - v_rel dt (both
-// O(1) metres), which keeps more of the offset's FP32 precision.
-__device__ __forceinline__ float4 orca_line_dev(float2 p, float2 v, float r, float itau,
-                                                float dt, float half_idt, uint32_t me,
-                                                float4 mj, float2 vj) {
-    float px = mj.x - p.x, py = mj.y - p.y;
-    float vx = v.x - vj.x, vy = v.y - vj.y;
-    float R = r + mj.z;
-    float p2 = px * px + py * py, R2 = R * R;
-    float4 L;
-    L.w = 0.0f;
-    if (p2 > R2) {
-        float wx = vx - px * itau, wy = vy - py * itau;
-        float w2 = wx * wx + wy * wy, wp = wx * px + wy * py;
-        if (wp < 0.0f && wp * wp > R2 * w2) {
-            float iw = rsqrtf(w2);
-            L.x = wx * iw;
-            L.y = wy * iw;
-            L.z = L.x * v.x + L.y * v.y + 0.5f * (R * itau - w2 * iw);
-        } else {
-            float l2 = p2 - R2;
-            float leg = l2 * rsqrtf(l2);
-            float ip2 = __fdividef(1.0f, p2);
-            if (det2f(px, py, wx, wy) > 0.0f) {  // left leg
-                L.x = -(px * R + py * leg) * ip2;
-                L.y = (px * leg - py * R) * ip2;
-            } else {  // right leg
-                L.x = (py * leg - px * R) * ip2;
-                L.y = -(px * leg + py * R) * ip2;
-            }
-            L.z = 0.5f * (L.x * (v.x + vj.x) + L.y * (v.y + vj.y));
-        }
-    } else {
-        float qx = px - vx * dt, qy = py - vy * dt;  // = -w dt
-        float ql = sqrtf(qx * qx + qy * qy);
-        float nx, ny;
-        if (ql > 0.0f) {
-            float iq = __fdividef(1.0f, ql);
-            nx = -qx * iq;
-            ny = -qy * iq;
-        } else if (p2 > 0.0f) {
-            float ip = rsqrtf(p2);
-            nx = -px * ip;
-            ny = -py * ip;
-        } else {
-            nx = me < __float_as_uint(mj.w) ? 1.0f : -1.0f;
-            ny = 0.0f;
-        }
-        L.x = nx;
-        L.y = ny;
-        L.z = nx * v.x + ny * v.y + (R - ql) * half_idt;
-    }
-    return L;
 }
 
 // Candidates q0..q1-1 (sorted slots) offered to the top-k list of the agent at slot t.
@@ -459,7 +454,7 @@ __device__ __forceinline__ void scene_view(const MainArgs& a, int t, SceneView& 
 
 // Persistent over tiles of TPB consecutive agents: tile blockIdx.x first, then
 // tiles taken from a per-step counter (with one CTA per tile this loop runs once).
-template <int KMAX, int TPB, int G>
+template <int KMAX, int TPB, int G, bool TAPE = false>
 __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_kernel(MainArgs a) {
     constexpr int KP = KMAX + 1;  // padded rows: conflict-free float4 accesses
     extern __shared__ float4 s_lines[];  // TPB * KP half-planes
@@ -469,6 +464,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     __shared__ unsigned char s_cnt[TPB];
     __shared__ unsigned char s_queued[TPB];
     __shared__ unsigned char s_queue[TPB];
+    __shared__ LpTape s_tape[TAPE ? TPB : 1];
     __shared__ int s_qn, s_tile;
     __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3;
     const int tid = threadIdx.x;
@@ -489,6 +485,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         const bool active = t < a.n;
         float2 p = make_float2(0.0f, 0.0f);
         float xx = 0.0f, xy = 0.0f, dt = 1.0f;
+        uint32_t me = 0;
         int cnt = 0;
         unsigned cand = 0;
         if (active) {
@@ -498,7 +495,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             // ---- phase 1: neighbours and half-planes
             float4 me4 = a.in.msg[t];
             p = make_float2(me4.x, me4.y);
-            uint32_t me = __float_as_uint(me4.w);
+            me = __float_as_uint(me4.w);
             unsigned long long kk[KMAX];
             int ks[KMAX];
             cand = knn_dev<KMAX>(a, sv.g, sv.cell_off, sv.nd, t, p, sv.k, kk, ks);
@@ -534,21 +531,14 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             }
             // ---- phase 2: preferred velocity (towards the goal at the preferred speed, or
             // onto the goal within one step) and LP2
-            float2 goal = a.prm.goal[t];
-            float pref = a.prm.pref_speed[t], V = a.prm.max_speed[t];
-            float gx_ = goal.x - p.x, gy_ = goal.y - p.y;
-            float g2 = gx_ * gx_ + gy_ * gy_;
-            float ig = rsqrtf(g2);
-            float ox, oy;
-            if (g2 * ig > pref * dt) {
-                ox = gx_ * (pref * ig);
-                oy = gy_ * (pref * ig);
-            } else {
-                ox = gx_ * idt;
-                oy = gy_ * idt;
-            }
+            float V = a.prm.max_speed[t];
+            float2 o = pref_velocity_dev(p, a.prm.goal[t], a.prm.pref_speed[t], dt, idt);
+            float ox = o.x, oy = o.y;
             RowLines rl{row};
-            int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy);
+            LpTape tape;
+            tape.i = tape.f = tape.bound = tape.j = tape.side = 0;
+            int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy, TAPE ? &tape : nullptr);
+            if (TAPE) s_tape[tid] = tape;
             if (b < cnt) {
                 int slot = atomicAdd(&s_qn, 1);
                 s_queue[slot] = (unsigned char)tid;
@@ -565,7 +555,8 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         for (int q = tid / G; q < nq; q += TPB / G) {
             int ag = s_queue[q];
             float2 x = s_x[ag];
-            if (G == 1) lp3_dev(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
+            if (G == 1) lp3_dev(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y,
+                                TAPE ? &s_tape[TAPE ? ag : 0] : nullptr);
             else lp3_group_dev<G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
             if ((tid & (G - 1)) == 0) s_x[ag] = x;
         }
@@ -582,6 +573,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 atomicOr(&a.misc_rw->error, kErrNumeric);
             a.out.vel[t] = make_float2(xx, xy);
             a.out.pos[t] = make_float2(nx, ny);
+            if (TAPE) a.tape[me] = s_tape[TAPE ? tid : 0].pack();
         }
         // ---- counters: one shared-memory atomic per warp
         unsigned wc = __reduce_add_sync(0xffffffffu, cand);
@@ -659,8 +651,24 @@ static cudaError_t dispatch_tpb(const MainArgs& a, const LaunchShape& sh, int gr
     return dispatch_g<KMAX, 128>(a, sh.lp3_group, grid_blocks, st, resident);
 }
 
+template <int KMAX>
+static cudaError_t launch_tape_k(const MainArgs& a, cudaStream_t st) {
+    constexpr size_t smem = main_smem_bytes<KMAX, 128>();
+    cudaError_t e = cudaFuncSetAttribute(orca_main_kernel<KMAX, 128, 1, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    orca_main_kernel<KMAX, 128, 1, true><<<(a.n + 127) / 128, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 static cudaError_t dispatch(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
                             cudaStream_t st, int* resident) {
+    if (a.tape && !resident) {  // recording step of a rollout: 128 threads, serial LP3
+        if (kmax <= 10) return launch_tape_k<10>(a, st);
+        if (kmax <= 16) return launch_tape_k<16>(a, st);
+        if (kmax <= 20) return launch_tape_k<20>(a, st);
+        return launch_tape_k<32>(a, st);
+    }
     if (kmax <= 10) return dispatch_tpb<10>(a, sh, grid_blocks, st, resident);
     if (kmax <= 16) return dispatch_tpb<16>(a, sh, grid_blocks, st, resident);
     if (kmax <= 20) return dispatch_tpb<20>(a, sh, grid_blocks, st, resident);

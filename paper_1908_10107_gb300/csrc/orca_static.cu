@@ -170,6 +170,7 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
         a.scenes = nullptr;
         a.slot_scene = nullptr;
         a.rec_stride = max_neighbors;
+        a.tape = nullptr;
         LaunchShape sh{128, default_lp3_group(max_neighbors)};
         e = launch_main(a, max_neighbors, sh, 0, st);
     }
