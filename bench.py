@@ -282,6 +282,158 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def fd_check_patch(sc, T, C, rel=1e-3, m=64, seed=0):
+    """GPU adjoint of the mean squared position error against FP64 central differences of
+    the oracle on an m-agent patch of the crowd (full horizon).  Returns a summary."""
+    import torch
+    import oracle
+    from paper_1908_10107_gb300 import abi, adjoint, scenarios
+    oracle.build()
+    pt = scenarios.patch(sc, m, seed)
+    # the patch's own target rollout: perturbed parameters of its agents, in FP64
+    rng = np.random.default_rng(seed + 1)
+    tp = (pt.pref_speed * rng.uniform(0.9, 1.1, m)).astype(np.float32)
+    tr = (pt.radius * rng.uniform(0.9, 1.1, m)).astype(np.float32)
+    tt = (pt.time_horizon * rng.uniform(0.8, 1.2, m)).astype(np.float32)
+
+    def oracle_traj(pref, rad, tau):
+        pos, vel = pt.pos.astype(np.float64), pt.vel.astype(np.float64)
+        out = []
+        for _ in range(T):
+            r = oracle.step(pos, vel, pt.goal, rad, pt.max_speed, pref, tau, pt.neighbor_dist,
+                            pt.max_neighbors, pt.dt, knn_mode=0, fp64_knn=True, nthreads=1)
+            pos, vel = r["pos"], r["vel"]
+            out.append(pos)
+        return np.stack(out)
+
+    target_traj = oracle_traj(tp.astype(np.float64), tr.astype(np.float64), tt.astype(np.float64))
+    base = dict(pref=pt.pref_speed.astype(np.float64), rad=pt.radius.astype(np.float64),
+                tau=pt.time_horizon.astype(np.float64))
+
+    def loss(**kw):
+        a = dict(base)
+        a.update(kw)
+        tr_ = oracle_traj(a["pref"], a["rad"], a["tau"])
+        return float(((tr_ - target_traj) ** 2).sum() / (T * m))
+
+    sim = abi.OrcaSim.for_scene(pt)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in pt.arrays()]
+    pos0, vel0, goal, radius, vmax, pref, tau = dev
+    for t in (radius, pref, tau):
+        t.requires_grad_(True)
+    traj = adjoint.rollout(sim, pos0, vel0, goal, radius, vmax, pref, tau, T, C)
+    # how far the FP32 trajectory and the FP64 oracle trajectory drift apart
+    drift = np.abs(traj.detach().cpu().numpy().astype(np.float64) -
+                   oracle_traj(base_pref := pt.pref_speed.astype(np.float64),
+                               pt.radius.astype(np.float64), pt.time_horizon.astype(np.float64)))
+    drift_by_step = drift.max(axis=(1, 2))
+    tgt = torch.from_numpy(target_traj.astype(np.float32)).cuda()
+    adjoint.mse_trajectory_loss(traj, tgt).backward()
+    g = {"pref": pref.grad.cpu().numpy(), "rad": radius.grad.cpu().numpy(), "tau": tau.grad.cpu().numpy()}
+    sim.close()
+    ok = bad = excluded = 0
+    worst = 0.0
+    L0 = loss()
+    for key in ("pref", "rad", "tau"):
+        scale = np.abs(g[key]).max() + 1e-30
+        for a in range(m):
+            x0 = base[key][a]
+            h = 1e-6 * max(abs(x0), 1.0)
+            vals = {}
+            for dx in (h, -h, h / 2, -h / 2):
+                arr = base[key].copy()
+                arr[a] = x0 + dx
+                vals[dx] = loss(**{key: arr})
+            central = (vals[h] - vals[-h]) / (2 * h)
+            central2 = (vals[h / 2] - vals[-h / 2]) / h
+            fwd, bwd = (vals[h] - L0) / h, (L0 - vals[-h]) / h
+            if (abs(fwd - bwd) > 1e-2 * max(abs(fwd), abs(bwd)) + 1e-9 or
+                    abs(central - central2) > 1e-4 * max(abs(central), 1e-6)):
+                excluded += 1
+                continue
+            err = abs(g[key][a] - central)
+            worst = max(worst, float(err / max(abs(central), 1e-3 * scale)))
+            if err <= rel * abs(central) + 1e-3 * scale:
+                ok += 1
+            else:
+                bad += 1
+    del base_pref
+    return {"agents": m, "steps": T, "parameters_checked": ok + bad, "within_1e-3": ok,
+            "outside": bad, "excluded_non_differentiable": excluded,
+            "worst_relative_error": float(worst),
+            "fp32_fp64_trajectory_drift_m": {"step_1": float(drift_by_step[0]),
+                                             "final": float(drift_by_step[-1]),
+                                             "max": float(drift_by_step.max())}}
+
+
+def run_adjoint(args):
+    """Forward + adjoint rollout of the differentiable workload (16,384-agent flow, 64 steps
+    at dt 0.1 s, checkpoints every 8 steps, loss = mean squared position error against a
+    rollout with perturbed parameters) against the plain step on the same crowd."""
+    import torch
+    from paper_1908_10107_gb300 import abi, adjoint, scenarios
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    T, C = 64, 8
+    sc = scenarios.differentiable()
+    n = sc.n
+    target = scenarios.perturbed_parameters(sc, 7)
+    sim = abi.OrcaSim.for_scene(sc)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in sc.arrays()]
+    pos0, vel0, goal, radius, vmax, pref, tau = dev
+    tp, tr, tt = [torch.from_numpy(a).cuda() for a in target]
+    with torch.no_grad():
+        tgt = adjoint.rollout(sim, pos0, vel0, goal, tr, vmax, tp, tt, T, C)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    fwd_ms, bwd_ms = [], []
+    for rep in range(args.warmup + max(args.steps // 100, 5)):
+        for t in (radius, pref, tau):
+            t.grad = None
+            t.requires_grad_(True)
+        flush.fill_(rep & 0xff)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        traj = adjoint.rollout(sim, pos0, vel0, goal, radius, vmax, pref, tau, T, C)
+        loss = adjoint.mse_trajectory_loss(traj, tgt)
+        e1.record(stream)
+        loss.backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            fwd_ms.append(e0.elapsed_time(e1))
+            bwd_ms.append(e1.elapsed_time(e2))
+    # the plain step on the same crowd: T steps through the graph
+    sim.set_scene(sc)
+    plain = []
+    for rep in range(args.warmup + 5):
+        sim.set_scene(sc)
+        flush.fill_(rep & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(T)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            plain.append(e0.elapsed_time(e1))
+    sim.close()
+    f, b, pl = float(np.median(fwd_ms)), float(np.median(bwd_ms)), float(np.median(plain))
+    check = {f"T{h}": fd_check_patch(sc, h, C) for h in (8, 16, T)}
+    line = {
+        "metric": "forward+adjoint ORCA rollout agent-steps/sec (16,384 agents, 64 steps)",
+        "value": n * T / ((f + b) * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": T,
+        "warmup": args.warmup, "ms_per_step": (f + b) / T, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": "bidirectional flow, 16,384 agents, dt 0.1 s, 64 steps, checkpoint "
+                               "every 8; loss = mean squared position error against a rollout with "
+                               "perturbed pref speed / radius / tau", "n_agents": n},
+        "forward_ms": f, "backward_ms": b, "plain_ms_for_T_steps": pl,
+        "plain_value": n * T / (pl * 1e-3),
+        "forward_adjoint_over_plain": (f + b) / pl,
+        "fd_check_64_agent_patch_by_horizon": check,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,12 +446,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--clocks-out", default=None)
-    ap.add_argument("--workload", choices=["plain", "batched"], default="plain")
+    ap.add_argument("--workload", choices=["plain", "batched", "adjoint"], default="plain")
     ap.add_argument("--no-per-scene", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "batched" and args.impl == "ours":
         run_batched(args)
+        return
+    if args.workload == "adjoint" and args.impl == "ours":
+        run_adjoint(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

@@ -206,3 +206,34 @@ def batched(n_scenes: int = 256, seed: int = 1912, lo: int = 500, hi: int = 5000
         else:
             scenes.append(bidirectional(int(c), seed=seed + 1 + s))
     return Batch(scenes)
+
+
+def differentiable(n: int = 16384, seed: int = 1913, dt: float = 0.1, steps: int = 64) -> Scene:
+    """Bidirectional flow for differentiable rollouts: the 524,288-agent flow's parameters
+    (r_obs 10 m, k 10, tau 5 s, radius U[0.3, 0.5] m, speed U[1.2, 1.6] m/s) at ``n`` agents
+    with dt = 0.1 s, 64 steps.  The preferred speed is 90% of the maximum so that the
+    preferred velocity lies inside the speed disc."""
+    sc = bidirectional(n, seed=seed, dt=dt, steps=steps)
+    sc.pref_speed = _f32(sc.max_speed * np.float32(0.9))
+    return sc
+
+
+def perturbed_parameters(scene: Scene, seed: int):
+    """Target parameters: preferred speed x U[0.9, 1.1], radius x U[0.9, 1.1], time horizon
+    x U[0.8, 1.2], per agent.  Returns (pref_speed, radius, time_horizon), float32."""
+    rng = np.random.default_rng(seed)
+    n = scene.n
+    return (_f32(scene.pref_speed * rng.uniform(0.9, 1.1, n)),
+            _f32(scene.radius * rng.uniform(0.9, 1.1, n)),
+            _f32(scene.time_horizon * rng.uniform(0.8, 1.2, n)))
+
+
+def patch(scene: Scene, m: int, seed: int = 0) -> Scene:
+    """The m agents nearest a random agent of ``scene``, as a scene of their own."""
+    rng = np.random.default_rng(seed)
+    c = scene.pos[rng.integers(scene.n)].astype(np.float64)
+    idx = np.sort(np.argsort(((scene.pos - c) ** 2).sum(1))[:m])
+    s = scene.copy()
+    for f in ("pos", "vel", "goal", "radius", "max_speed", "pref_speed", "time_horizon"):
+        setattr(s, f, np.ascontiguousarray(getattr(scene, f)[idx]))
+    return s
