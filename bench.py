@@ -448,6 +448,8 @@ def main():
     ap.add_argument("--clocks-out", default=None)
     ap.add_argument("--workload", choices=["plain", "batched", "adjoint"], default="plain")
     ap.add_argument("--no-per-scene", action="store_true")
+    ap.add_argument("--tpb", type=int, default=0, help="fix threads per CTA (skips shape tuning)")
+    ap.add_argument("--lanes", type=int, default=0, help="fix LP3 lanes per agent (with --tpb)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "batched" and args.impl == "ours":
@@ -481,10 +483,14 @@ def main():
     sim = abi.OrcaSim.for_scene(sc, cell_size=args.cell_size)
     sim.set_scene(sc)
     tune = shape = None
+    from paper_1908_10107_gb300 import autotune
     if args.cell_size <= 0:
-        from paper_1908_10107_gb300 import autotune
         tune = autotune.tune_cell_size(sim, sc, use_cache=False, cache_path=None)
         args.cell_size = tune["cell_size"]
+    if args.tpb:
+        abi.orca_set_launch(sim.ctx, args.tpb, args.lanes)
+        shape = {"shape": (args.tpb, args.lanes), "timings_ms": None}
+    else:
         shape = autotune.tune_launch(sim, lambda: sim.set_scene(sc))
     abi.orca_profile(sim.ctx, True)
     stream = torch.cuda.current_stream()
@@ -592,7 +598,7 @@ def main():
                                            if tune else "fixed by --cell-size"),
                    "launch_shape": list(shape["shape"]) if shape else [128, 1],
                    "launch_shape_tuning_ms": ({k: round(v, 4) for k, v in shape["timings_ms"].items()}
-                                              if shape else None)},
+                                              if shape and shape["timings_ms"] else "fixed by --tpb")},
         "roofline": {"kernel": "orca_main (neighbours + half-planes + LP + integrate)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
