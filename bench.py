@@ -158,7 +158,7 @@ def device_smi_index(torch, dev: int) -> int:
     return dev
 
 
-def cpu_baseline(scene, budget_s: float = 12.0, max_steps: int = 4):
+def cpu_baseline(scene, budget_s: float = 12.0, max_steps: int = 30):
     """The FP64 oracle (grid neighbour search, OpenMP over agents) on the host cores:
     whole steps of the full crowd, repeated until the budget is used."""
     import oracle
