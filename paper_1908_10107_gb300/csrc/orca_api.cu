@@ -25,7 +25,7 @@ struct Layout {
 
 struct Plan {
     int N, K, S, max_cells, max_passes, nsb, nmb;
-    size_t o_msg, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2];
+    size_t o_msg, o_sslot, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2];
     size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_scenes, o_slot, o_part, o_misc, o_blk, o_rnbr, o_rcell,
         o_stage[2];
     size_t total;
@@ -55,6 +55,7 @@ static bool make_plan(const orca_params& p, Plan& pl) {
     Layout L;
     size_t N = (size_t)pl.N;
     pl.o_msg = L.add(N * sizeof(float4));
+    pl.o_sslot = L.add(N * 4);
     for (int b = 0; b < 2; ++b) {
         pl.o_pv[b][0] = L.add(N * sizeof(float2));
         pl.o_pv[b][1] = L.add(N * sizeof(float2));
@@ -164,6 +165,7 @@ static void bind_buffers(orca_ctx* c) {
         c->stage[b] = (float2*)(w + pl.o_stage[b]);
     }
     c->sorted.msg = (float4*)(w + pl.o_msg);
+    c->sorted.slot = (uint32_t*)(w + pl.o_sslot);
     c->sorted.vel = c->PV[1].vel;
     c->bins.hist = (uint32_t*)(w + pl.o_hist);
     c->bins.digit_totals = (uint32_t*)(w + pl.o_tot);

@@ -241,15 +241,23 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const uint32_t* __restrict__ totals) {
     if (pass >= misc->grid.passes) return;
     constexpr int kWarps = kSortThreads / 32;
-    static_assert(kSortThreads == kRadixBuckets, "one thread per digit below");
+    constexpr int kPer = kRadixBuckets / kSortThreads;  // digits per thread below
+    static_assert(kRadixBuckets % kSortThreads == 0, "whole digits per thread");
     __shared__ uint32_t s_run[kRadixBuckets];
     __shared__ uint32_t s_wcnt[kWarps][kRadixBuckets];
     __shared__ uint32_t s_wsum[kWarps];
     int warp = threadIdx.x >> 5;
     {
-        // base of each digit: exclusive scan of the digit totals (thread = digit)
+        // base of each digit: exclusive scan of the digit totals (kPer consecutive digits
+        // per thread)
         int lane0 = threadIdx.x & 31;
-        uint32_t v = totals[threadIdx.x], inc = v;
+        uint32_t v[kPer], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            v[q] = totals[threadIdx.x * kPer + q];
+            sum += v[q];
+        }
+        uint32_t inc = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -257,12 +265,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
         }
         if (lane0 == 31) s_wsum[warp] = inc;
         __syncthreads();
-        uint32_t base = inc - v;
+        uint32_t base = inc - sum;
         for (int w = 0; w < warp; ++w) base += s_wsum[w];
-        int d = threadIdx.x;
-        s_run[d] = base + offsets[d * gridDim.x + blockIdx.x];
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) s_wcnt[w][d] = 0;
+        for (int q = 0; q < kPer; ++q) {
+            int d = threadIdx.x * kPer + q;
+            s_run[d] = base + offsets[d * gridDim.x + blockIdx.x];
+            base += v[q];
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) s_wcnt[w][d] = 0;
+        }
     }
     __syncthreads();
     int shift = pass * kRadixBits;
@@ -330,6 +342,7 @@ __global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __r
     float r = src_p.radius[s];
     uint32_t id = src_p.id[s];
     dst_s.msg[t] = make_float4(p.x, p.y, r, __uint_as_float(id));
+    dst_s.slot[id] = (uint32_t)t;
     dst_s.vel[t] = src_s.vel[s];
     dst_p.goal[t] = src_p.goal[s];
     dst_p.radius[t] = r;

@@ -17,7 +17,7 @@
 namespace orca {
 
 constexpr int kMaxNeighbors = 32;
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 9;
 constexpr int kRadixBuckets = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;  // items per thread per tile
@@ -81,8 +81,9 @@ struct AgentState {  // one of PV[0] / PV[1]
 // and agent index (as bits) in one 16-byte record; velocity is kept apart because only
 // the k selected neighbours need it.
 struct Sorted {
-    float4* msg;  // (x, y, radius, id bits)
+    float4* msg;    // (x, y, radius, id bits)
     float2* vel;
+    uint32_t* slot;  // slot of each agent id (the inverse of msg[].w)
 };
 
 struct BinBuffers {

@@ -298,11 +298,12 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
 
 // Candidates q0..q1-1 (sorted slots) offered to the top-k list of the agent at slot t.
 // lim is the largest d^2 that can still enter: the largest float below r_obs^2 until the
-// list is full, then the k-th key's d^2 (equal d^2 is settled by the 64-bit key).
+// list is full, then the k-th key's d^2 (equal d^2 is settled by the 64-bit key).  The
+// list holds keys only; a neighbour's slot is looked up from its id afterwards.
 template <int KMAX>
 __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint32_t q0, uint32_t q1,
                                             int t, float2 p, unsigned long long (&kk)[KMAX],
-                                            int (&ks)[KMAX], float& lim) {
+                                            float& lim) {
 #pragma unroll 1
     for (uint32_t q = q0; q < q1; ++q) {
         float4 mj = msg[q];
@@ -318,18 +319,13 @@ __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint
             if (!done) {
                 if (key < kk[l - 1]) {
                     kk[l] = kk[l - 1];
-                    ks[l] = ks[l - 1];
                 } else {
                     kk[l] = key;
-                    ks[l] = (int)q;
                     done = true;
                 }
             }
         }
-        if (!done) {
-            kk[0] = key;
-            ks[0] = (int)q;
-        }
+        if (!done) kk[0] = key;
         if (kk[KMAX - 1] != ~0ull) lim = __uint_as_float((unsigned)(kk[KMAX - 1] >> 32));
     }
 }
@@ -346,7 +342,7 @@ __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint
 template <int KMAX>
 __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g, int cell_off,
                                             float nd, int t, float2 p, int k,
-                                            unsigned long long (&kk)[KMAX], int (&ks)[KMAX]) {
+                                            unsigned long long (&kk)[KMAX]) {
     // ring-1 visiting order as offsets (ax*sx, ay*sy), ax+1 and ay+1 packed 2 bits each
     constexpr unsigned kAx = 2u | 1u << 2 | 2u << 4 | 0u << 6 | 1u << 8 | 0u << 10 | 2u << 12 | 0u << 14;
     constexpr unsigned kAy = 1u | 2u << 2 | 2u << 4 | 1u << 6 | 0u << 8 | 2u << 10 | 0u << 12 | 0u << 14;
@@ -355,10 +351,7 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
     float nd2 = __fmul_rn(nd, nd);
     float lim = __int_as_float(__float_as_int(nd2) - 1);  // largest float below r_obs^2
 #pragma unroll
-    for (int l = 0; l < KMAX; ++l) {
-        kk[l] = (l < KMAX - k) ? 0ull : ~0ull;
-        ks[l] = -1;
-    }
+    for (int l = 0; l < KMAX; ++l) kk[l] = (l < KMAX - k) ? 0ull : ~0ull;
     float ox = p.x - (g.xmin + (float)cx * g.s), oy = p.y - (g.ymin + (float)cy * g.s);
     int sx = ox > 0.5f * g.s ? 1 : -1, sy = oy > 0.5f * g.s ? 1 : -1;
     int r = 0, e = 0;
@@ -393,7 +386,7 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
                 int c = cell_off + y * g.gx + x;
                 uint32_t q0 = a.cell_start[c], q1 = a.cell_start[c + 1];
                 cand += q1 - q0;
-                offer_range<KMAX>(a.in.msg, q0, q1, t, p, kk, ks, lim);
+                offer_range<KMAX>(a.in.msg, q0, q1, t, p, kk, lim);
             }
         }
         if (++e < (r == 0 ? 1 : 8 * r)) continue;
@@ -497,14 +490,14 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             p = make_float2(me4.x, me4.y);
             me = __float_as_uint(me4.w);
             unsigned long long kk[KMAX];
-            int ks[KMAX];
-            cand = knn_dev<KMAX>(a, sv.g, sv.cell_off, sv.nd, t, p, sv.k, kk, ks);
+            cand = knn_dev<KMAX>(a, sv.g, sv.cell_off, sv.nd, t, p, sv.k, kk);
             // park the neighbours' slots in the row (one unrolled store each), then build
             // the half-planes in a rolled loop: one copy of the line code keeps the kernel
             // small enough for the instruction cache
 #pragma unroll
             for (int l = 0; l < KMAX; ++l) {
-                if (l >= KMAX - sv.k && kk[l] != ~0ull) row[cnt++].w = __int_as_float(ks[l]);
+                if (l >= KMAX - sv.k && kk[l] != ~0ull)
+                    row[cnt++].w = __uint_as_float(a.in.slot[(uint32_t)kk[l]]);
             }
             float2 v = a.in.vel[t];
             float itau = __fdividef(1.0f, a.prm.tau[t]);

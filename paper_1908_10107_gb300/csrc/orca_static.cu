@@ -27,7 +27,7 @@ constexpr int kStaticMaxDevices = 64;
 
 // Scratch layout (bytes), every piece 256-byte aligned.
 struct StaticLayout {
-    size_t id, keys0, keys1, vals0, vals1, hist, tot, cells, part, misc, msg, svel, goal, radius,
+    size_t id, keys0, keys1, vals0, vals1, hist, tot, cells, part, misc, msg, sslot, svel, goal, radius,
         vmax, pref, tau, sid, opos, ovel, blk, total;
 };
 
@@ -49,6 +49,7 @@ constexpr StaticLayout static_layout() {
     L.part = o; o += al256(kBboxBlocks * 16);
     L.misc = o; o += al256(sizeof(DeviceMisc));
     L.msg = o; o += al256(N * 16);
+    L.sslot = o; o += al256(N * 4);
     L.svel = o; o += al256(N * 8);
     L.goal = o; o += al256(N * 8);
     L.radius = o; o += al256(N * 4);
@@ -127,7 +128,7 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
     AgentState src{(float2*)pos_xy, (float2*)vel_xy};
     AgentParams src_p{(float2*)goal_xy, (float*)radius, (float*)max_speed, (float*)pref_speed,
                       (float*)time_horizon, (uint32_t*)(base + L.id)};
-    Sorted sorted{(float4*)(base + L.msg), (float2*)(base + L.svel)};
+    Sorted sorted{(float4*)(base + L.msg), (float2*)(base + L.svel), (uint32_t*)(base + L.sslot)};
     AgentParams dst_p{(float2*)(base + L.goal), (float*)(base + L.radius), (float*)(base + L.vmax),
                       (float*)(base + L.pref), (float*)(base + L.tau), (uint32_t*)(base + L.sid)};
     AgentState out{(float2*)(base + L.opos), (float2*)(base + L.ovel)};
