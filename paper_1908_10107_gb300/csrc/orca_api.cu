@@ -25,7 +25,7 @@ struct Layout {
 
 struct Plan {
     int N, K, S, max_cells, max_passes, nsb, nmb;
-    size_t o_msg, o_sslot, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2];
+    size_t o_msg, o_sslot, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2], o_hint[2];
     size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_scenes, o_slot, o_part, o_misc, o_blk, o_rnbr, o_rcell,
         o_stage[2];
     size_t total;
@@ -65,6 +65,7 @@ static bool make_plan(const orca_params& p, Plan& pl) {
         pl.o_pref[b] = L.add(N * 4);
         pl.o_tau[b] = L.add(N * 4);
         pl.o_id[b] = L.add(N * 4);
+        pl.o_hint[b] = L.add(N * 4);
         pl.o_keys[b] = L.add(N * 4);
         pl.o_vals[b] = L.add(N * 4);
         pl.o_stage[b] = L.add(N * sizeof(float2));
@@ -160,6 +161,7 @@ static void bind_buffers(orca_ctx* c) {
         c->PR[b].pref_speed = (float*)(w + pl.o_pref[b]);
         c->PR[b].tau = (float*)(w + pl.o_tau[b]);
         c->PR[b].id = (uint32_t*)(w + pl.o_id[b]);
+        c->PR[b].hint = (float*)(w + pl.o_hint[b]);
         c->bins.keys[b] = (uint32_t*)(w + pl.o_keys[b]);
         c->bins.vals[b] = (uint32_t*)(w + pl.o_vals[b]);
         c->stage[b] = (float2*)(w + pl.o_stage[b]);
@@ -432,6 +434,8 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy, cons
         CK(cudaMemcpyAsync(ctx->PR[0].pref_speed, pref_speed, N * 4, kind, st), "copy pref_speed");
         CK(cudaMemcpyAsync(ctx->PR[0].tau, time_horizon, N * 4, kind, st), "copy time_horizon");
         CK(launch_iota(n, ctx->PR[0].id, st), "iota kernel");
+        // no neighbour-radius hint yet (NaN bits); it only steers the search's pruning
+        CK(cudaMemsetAsync(ctx->PR[0].hint, 0xff, N * 4, st), "reset hint");
     }
     CK(cudaMemsetAsync(ctx->bins.misc, 0, sizeof(DeviceMisc), st), "reset misc");
     CK(cudaMemsetAsync(ctx->blk, 0, (size_t)ctx->plan.nmb * 4 * sizeof(unsigned long long), st),

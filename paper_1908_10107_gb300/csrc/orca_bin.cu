@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __r
     dst_p.pref_speed[t] = src_p.pref_speed[s];
     dst_p.tau[t] = src_p.tau[s];
     dst_p.id[t] = id;
+    if (dst_p.hint) dst_p.hint[t] = src_p.hint[s];
 }
 
 // State back to agent order (readout).

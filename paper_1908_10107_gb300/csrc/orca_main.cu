@@ -296,14 +296,34 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
     }
 }
 
-// Candidates q0..q1-1 (sorted slots) offered to the top-k list of the agent at slot t.
-// lim is the largest d^2 that can still enter: the largest float below r_obs^2 until the
-// list is full, then the k-th key's d^2 (equal d^2 is settled by the 64-bit key).  The
-// list holds keys only; a neighbour's slot is looked up from its id afterwards.
+// Insert key into the ascending list kk (its largest entry drops out); the caller has
+// checked key < kk[KMAX-1].
 template <int KMAX>
+__device__ __forceinline__ void insert_key(unsigned long long key, unsigned long long (&kk)[KMAX]) {
+    bool done = false;
+#pragma unroll
+    for (int l = KMAX - 1; l > 0; --l) {
+        if (!done) {
+            if (key < kk[l - 1]) {
+                kk[l] = kk[l - 1];
+            } else {
+                kk[l] = key;
+                done = true;
+            }
+        }
+    }
+    if (!done) kk[0] = key;
+}
+
+// Candidates q0..q1-1 (sorted slots) offered to the top-k list of the agent at slot t.
+// A candidate enters when its fl32 d^2 <= lim; the first CAP entrants are parked in buf
+// (shared memory) and inserted after the search, later ones are inserted at once and
+// tighten lim to the k-th key's d^2 once the list is full (equal d^2 is settled by the
+// 64-bit key).  Parking keeps the divergent insertion out of the candidate loop.
+template <int KMAX, int CAP>
 __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint32_t q0, uint32_t q1,
                                             int t, float2 p, unsigned long long (&kk)[KMAX],
-                                            float& lim) {
+                                            unsigned long long* buf, int& nb, float& lim) {
 #pragma unroll 1
     for (uint32_t q = q0; q < q1; ++q) {
         float4 mj = msg[q];
@@ -312,20 +332,12 @@ __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint
         if (!(d2 <= lim) || (int)q == t) continue;
         unsigned long long key =
             ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(mj.w);
-        if (key >= kk[KMAX - 1]) continue;
-        bool done = false;
-#pragma unroll
-        for (int l = KMAX - 1; l > 0; --l) {
-            if (!done) {
-                if (key < kk[l - 1]) {
-                    kk[l] = kk[l - 1];
-                } else {
-                    kk[l] = key;
-                    done = true;
-                }
-            }
+        if (nb < CAP) {
+            buf[nb++] = key;
+            continue;
         }
-        if (!done) kk[0] = key;
+        if (key >= kk[KMAX - 1]) continue;
+        insert_key<KMAX>(key, kk);
         if (kk[KMAX - 1] != ~0ull) lim = __uint_as_float((unsigned)(kk[KMAX - 1] >> 32));
     }
 }
@@ -333,15 +345,21 @@ __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint
 // Exact k nearest neighbours of the agent at sorted slot t: keys (d2 bits << 32 | id)
 // kept ascending in kk; the first KMAX-k entries are permanent zero sentinels so that
 // the live window is the last k entries.  Ring search from the agent's cell (ring 0),
-// one visit per cell through a single loop (one copy of the insertion code).  Ring 1 is
+// one visit per cell through a single loop (one copy of the candidate code).  Ring 1 is
 // visited nearest cells first -- the two sides the agent is closest to, their corner,
-// then the rest -- so the list fills with near candidates and prunes the others; wider
-// rings go round the perimeter.  A cell is skipped when a conservative lower bound of its
-// agents' fl32 d^2 (cell box minus the cell-assignment slop, d^2 rounding 1e-5) exceeds
-// lim; the search stops when the next ring's bound does.
-template <int KMAX>
+// then the rest; wider rings go round the perimeter.  A cell is skipped when a
+// conservative lower bound of its agents' fl32 d^2 (cell box minus the cell-assignment
+// slop, d^2 rounding 1e-5) exceeds lim; the search stops when the next ring's bound does.
+//
+// lim starts at lim0 <= the largest float below r_obs^2 (a radius predicted from the
+// agent's previous step).  Every candidate with d^2 <= lim0 is offered, and all others
+// have larger d^2, so when at least k candidates were offered the list is exact; when
+// fewer were and lim0 was below the r_obs bound, the search is repeated with that bound.
+// buf holds CAP parked keys.
+template <int KMAX, int CAP>
 __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g, int cell_off,
-                                            float nd, int t, float2 p, int k,
+                                            float nd, int t, float2 p, int k, float lim0,
+                                            unsigned long long* buf,
                                             unsigned long long (&kk)[KMAX]) {
     // ring-1 visiting order as offsets (ax*sx, ay*sy), ax+1 and ay+1 packed 2 bits each
     constexpr unsigned kAx = 2u | 1u << 2 | 2u << 4 | 0u << 6 | 1u << 8 | 0u << 10 | 2u << 12 | 0u << 14;
@@ -349,58 +367,71 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
     int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
     int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
     float nd2 = __fmul_rn(nd, nd);
-    float lim = __int_as_float(__float_as_int(nd2) - 1);  // largest float below r_obs^2
-#pragma unroll
-    for (int l = 0; l < KMAX; ++l) kk[l] = (l < KMAX - k) ? 0ull : ~0ull;
+    const float lim_max = __int_as_float(__float_as_int(nd2) - 1);  // largest float below r_obs^2
+    lim0 = fminf(lim0, lim_max);  // a NaN prediction gives lim_max
     float ox = p.x - (g.xmin + (float)cx * g.s), oy = p.y - (g.ymin + (float)cy * g.s);
     int sx = ox > 0.5f * g.s ? 1 : -1, sy = oy > 0.5f * g.s ? 1 : -1;
-    int r = 0, e = 0;
     unsigned cand = 0;
 #pragma unroll 1
     for (;;) {
-        int dx, dy;
-        if (r == 0) {
-            dx = dy = 0;
-        } else if (r == 1) {
-            dx = ((int)((kAx >> (2 * e)) & 3u) - 1) * sx;
-            dy = ((int)((kAy >> (2 * e)) & 3u) - 1) * sy;
-        } else if (e < 2 * r + 1) {
-            dx = e - r;
-            dy = -r;
-        } else if (e < 4 * r + 2) {
-            dx = e - (3 * r + 1);
-            dy = r;
-        } else if (e < 6 * r + 1) {
-            dx = -r;
-            dy = e - (5 * r + 1);
-        } else {
-            dx = r;
-            dy = e - 7 * r;
-        }
-        int x = cx + dx, y = cy + dy;
-        if (x >= 0 && y >= 0 && x < g.gx && y < g.gy) {
-            float bx0 = g.xmin + (float)x * g.s, by0 = g.ymin + (float)y * g.s;
-            float ddx = fmaxf(0.0f, fmaxf(bx0 - p.x, p.x - (bx0 + g.s)) - g.slop);
-            float ddy = fmaxf(0.0f, fmaxf(by0 - p.y, p.y - (by0 + g.s)) - g.slop);
-            if ((ddx * ddx + ddy * ddy) * (1.0f - 1e-5f) <= lim) {
-                int c = cell_off + y * g.gx + x;
-                uint32_t q0 = a.cell_start[c], q1 = a.cell_start[c + 1];
-                cand += q1 - q0;
-                offer_range<KMAX>(a.in.msg, q0, q1, t, p, kk, lim);
+#pragma unroll
+        for (int l = 0; l < KMAX; ++l) kk[l] = (l < KMAX - k) ? 0ull : ~0ull;
+        float lim = lim0;
+        int nb = 0, r = 0, e = 0;
+#pragma unroll 1
+        for (;;) {
+            int dx, dy;
+            if (r == 0) {
+                dx = dy = 0;
+            } else if (r == 1) {
+                dx = ((int)((kAx >> (2 * e)) & 3u) - 1) * sx;
+                dy = ((int)((kAy >> (2 * e)) & 3u) - 1) * sy;
+            } else if (e < 2 * r + 1) {
+                dx = e - r;
+                dy = -r;
+            } else if (e < 4 * r + 2) {
+                dx = e - (3 * r + 1);
+                dy = r;
+            } else if (e < 6 * r + 1) {
+                dx = -r;
+                dy = e - (5 * r + 1);
+            } else {
+                dx = r;
+                dy = e - 7 * r;
             }
+            int x = cx + dx, y = cy + dy;
+            if (x >= 0 && y >= 0 && x < g.gx && y < g.gy) {
+                float bx0 = g.xmin + (float)x * g.s, by0 = g.ymin + (float)y * g.s;
+                float ddx = fmaxf(0.0f, fmaxf(bx0 - p.x, p.x - (bx0 + g.s)) - g.slop);
+                float ddy = fmaxf(0.0f, fmaxf(by0 - p.y, p.y - (by0 + g.s)) - g.slop);
+                if ((ddx * ddx + ddy * ddy) * (1.0f - 1e-5f) <= lim) {
+                    int c = cell_off + y * g.gx + x;
+                    uint32_t q0 = a.cell_start[c], q1 = a.cell_start[c + 1];
+                    cand += q1 - q0;
+                    offer_range<KMAX, CAP>(a.in.msg, q0, q1, t, p, kk, buf, nb, lim);
+                }
+            }
+            if (++e < (r == 0 ? 1 : 8 * r)) continue;
+            // next ring: does any of its cells exist and possibly lie within reach?
+            ++r;
+            e = 0;
+            float lb = INFINITY;
+            if (cx - r >= 0) lb = fminf(lb, p.x - (g.xmin + (float)(cx - r + 1) * g.s));
+            if (cx + r <= g.gx - 1) lb = fminf(lb, (g.xmin + (float)(cx + r) * g.s) - p.x);
+            if (cy - r >= 0) lb = fminf(lb, p.y - (g.ymin + (float)(cy - r + 1) * g.s));
+            if (cy + r <= g.gy - 1) lb = fminf(lb, (g.ymin + (float)(cy + r) * g.s) - p.y);
+            if (lb == INFINITY) break;
+            lb = fmaxf(0.0f, lb - g.slop);
+            if (lb * lb * (1.0f - 1e-5f) > lim) break;
         }
-        if (++e < (r == 0 ? 1 : 8 * r)) continue;
-        // next ring: does any of its cells exist and possibly lie within reach?
-        ++r;
-        e = 0;
-        float lb = INFINITY;
-        if (cx - r >= 0) lb = fminf(lb, p.x - (g.xmin + (float)(cx - r + 1) * g.s));
-        if (cx + r <= g.gx - 1) lb = fminf(lb, (g.xmin + (float)(cx + r) * g.s) - p.x);
-        if (cy - r >= 0) lb = fminf(lb, p.y - (g.ymin + (float)(cy - r + 1) * g.s));
-        if (cy + r <= g.gy - 1) lb = fminf(lb, (g.ymin + (float)(cy + r) * g.s) - p.y);
-        if (lb == INFINITY) break;
-        lb = fmaxf(0.0f, lb - g.slop);
-        if (lb * lb * (1.0f - 1e-5f) > lim) break;
+        // the parked keys, all lanes together
+#pragma unroll 1
+        for (int i = 0; i < nb; ++i) {
+            unsigned long long key = buf[i];
+            if (key < kk[KMAX - 1]) insert_key<KMAX>(key, kk);
+        }
+        if (kk[KMAX - 1] != ~0ull || !(lim0 < lim_max)) break;
+        lim0 = lim_max;  // fewer than k inside the predicted radius: search to r_obs
     }
     return cand;
 }
@@ -489,8 +520,21 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             float4 me4 = a.in.msg[t];
             p = make_float2(me4.x, me4.y);
             me = __float_as_uint(me4.w);
+            // search radius predicted from the previous step's k-th neighbour distance:
+            // no distance grows by more than the two agents' displacements, about 2 V dt
+            float V = a.prm.max_speed[t];
+            float lim0 = INFINITY;
+            if (a.prm.hint) {
+                float hd = sqrtf(a.prm.hint[t]) * (1.0f + 1e-3f) + 3.0f * V * dt + 1e-3f;
+                lim0 = hd * hd;  // NaN (no prediction) or infinite: the r_obs bound
+            }
             unsigned long long kk[KMAX];
-            cand = knn_dev<KMAX>(a, sv.g, sv.cell_off, sv.nd, t, p, sv.k, kk);
+            cand = knn_dev<KMAX, 2 * KP>(a, sv.g, sv.cell_off, sv.nd, t, p, sv.k, lim0,
+                                         reinterpret_cast<unsigned long long*>(row), kk);
+            if (a.prm.hint)
+                a.prm.hint[t] = kk[KMAX - 1] != ~0ull
+                                    ? __uint_as_float((unsigned)(kk[KMAX - 1] >> 32))
+                                    : __int_as_float(0x7fffffff);
             // park the neighbours' slots in the row (one unrolled store each), then build
             // the half-planes in a rolled loop: one copy of the line code keeps the kernel
             // small enough for the instruction cache
@@ -524,7 +568,6 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             }
             // ---- phase 2: preferred velocity (towards the goal at the preferred speed, or
             // onto the goal within one step) and LP2
-            float V = a.prm.max_speed[t];
             float2 o = pref_velocity_dev(p, a.prm.goal[t], a.prm.pref_speed[t], dt, idt);
             float ox = o.x, oy = o.y;
             RowLines rl{row};

@@ -127,10 +127,11 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
 
     AgentState src{(float2*)pos_xy, (float2*)vel_xy};
     AgentParams src_p{(float2*)goal_xy, (float*)radius, (float*)max_speed, (float*)pref_speed,
-                      (float*)time_horizon, (uint32_t*)(base + L.id)};
+                      (float*)time_horizon, (uint32_t*)(base + L.id), nullptr};
     Sorted sorted{(float4*)(base + L.msg), (float2*)(base + L.svel), (uint32_t*)(base + L.sslot)};
     AgentParams dst_p{(float2*)(base + L.goal), (float*)(base + L.radius), (float*)(base + L.vmax),
-                      (float*)(base + L.pref), (float*)(base + L.tau), (uint32_t*)(base + L.sid)};
+                      (float*)(base + L.pref), (float*)(base + L.tau), (uint32_t*)(base + L.sid),
+                      nullptr};
     AgentState out{(float2*)(base + L.opos), (float2*)(base + L.ovel)};
     BinBuffers bins;
     bins.keys[0] = (uint32_t*)(base + L.keys0);

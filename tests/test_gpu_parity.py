@@ -43,6 +43,25 @@ def test_bidirectional_after_steps():
     parity.gpu_step_and_compare(sc, steps_before=40)
 
 
+def test_dispersing_neighbours_outrun_the_predicted_radius():
+    # a nearly stationary agent among fast agents running radially outwards (1 m per
+    # step): its k-th neighbour distance grows far beyond the radius predicted from the
+    # previous step, so the neighbour search must fall back to the r_obs bound
+    rng = np.random.default_rng(41)
+    m = 40
+    ang = rng.uniform(0.0, 2.0 * np.pi, m)
+    rad = rng.uniform(1.0, 3.0, m)
+    ring = np.stack([rad * np.cos(ang), rad * np.sin(ang)], 1)
+    pos = np.concatenate([[[0.0, 0.0]], ring]).astype(np.float32)
+    goal = np.concatenate([[[0.0, 0.0]], ring / rad[:, None] * 1e4]).astype(np.float32)
+    vmax = np.concatenate([[0.01], np.full(m, 60.0)]).astype(np.float32)
+    sc = S.Scene("dispersing", pos, np.zeros_like(pos), goal, np.full(m + 1, 0.2, np.float32),
+                 vmax, vmax.copy(), np.full(m + 1, 2.0, np.float32), 50.0, 10, 1.0 / 60.0, 1)
+    for steps_before in (1, 4):
+        rep = parity.gpu_step_and_compare(sc, steps_before=steps_before)
+        assert rep["rows"] == m + 1
+
+
 @pytest.mark.parametrize("k", [10, 20])
 def test_dense_small(k):
     sc = S.dense(20011, seed=4)
