@@ -344,12 +344,17 @@ __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint
 
 // Exact k nearest neighbours of the agent at sorted slot t: keys (d2 bits << 32 | id)
 // kept ascending in kk; the first KMAX-k entries are permanent zero sentinels so that
-// the live window is the last k entries.  Ring search from the agent's cell (ring 0),
-// one visit per cell through a single loop (one copy of the candidate code).  Ring 1 is
-// visited nearest cells first -- the two sides the agent is closest to, their corner,
-// then the rest; wider rings go round the perimeter.  A cell is skipped when a
-// conservative lower bound of its agents' fl32 d^2 (cell box minus the cell-assignment
-// slop, d^2 rounding 1e-5) exceeds lim; the search stops when the next ring's bound does.
+// the live window is the last k entries.
+//
+// The search goes row by row: the agent's row of cells first, then always the nearer of
+// the next rows above and below.  Cells are numbered row-major, so the cells of one row
+// that can hold a candidate form one contiguous slot range, read in one pass.  In a row
+// whose vertical gap to the agent is at least h, a candidate with fl32 d^2 <= lim lies
+// within w = sqrt(lim (1 + 1e-5) - h^2) horizontally (the factor covers the rounding of
+// d^2); the range runs from the cell of p.x - w to the cell of p.x + w, widened by twice
+// the cell-assignment slop (the cell map is monotone in x, so no such candidate is
+// outside it).  h is the row's distance minus the slop; the search stops when the next
+// row's h^2 exceeds lim.  lim shrinks as the list fills, narrowing later rows.
 //
 // lim starts at lim0 <= the largest float below r_obs^2 (a radius predicted from the
 // agent's previous step).  Every candidate with d^2 <= lim0 is offered, and all others
@@ -361,68 +366,40 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
                                             float nd, int t, float2 p, int k, float lim0,
                                             unsigned long long* buf,
                                             unsigned long long (&kk)[KMAX]) {
-    // ring-1 visiting order as offsets (ax*sx, ay*sy), ax+1 and ay+1 packed 2 bits each
-    constexpr unsigned kAx = 2u | 1u << 2 | 2u << 4 | 0u << 6 | 1u << 8 | 0u << 10 | 2u << 12 | 0u << 14;
-    constexpr unsigned kAy = 1u | 2u << 2 | 2u << 4 | 1u << 6 | 0u << 8 | 2u << 10 | 0u << 12 | 0u << 14;
-    int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
-    int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
+    const int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
     float nd2 = __fmul_rn(nd, nd);
     const float lim_max = __int_as_float(__float_as_int(nd2) - 1);  // largest float below r_obs^2
     lim0 = fminf(lim0, lim_max);  // a NaN prediction gives lim_max
-    float ox = p.x - (g.xmin + (float)cx * g.s), oy = p.y - (g.ymin + (float)cy * g.s);
-    int sx = ox > 0.5f * g.s ? 1 : -1, sy = oy > 0.5f * g.s ? 1 : -1;
     unsigned cand = 0;
 #pragma unroll 1
     for (;;) {
 #pragma unroll
         for (int l = 0; l < KMAX; ++l) kk[l] = (l < KMAX - k) ? 0ull : ~0ull;
         float lim = lim0;
-        int nb = 0, r = 0, e = 0;
+        int nb = 0, y = cy, up = cy + 1, dn = cy - 1;
+        float h = 0.0f;
 #pragma unroll 1
         for (;;) {
-            int dx, dy;
-            if (r == 0) {
-                dx = dy = 0;
-            } else if (r == 1) {
-                dx = ((int)((kAx >> (2 * e)) & 3u) - 1) * sx;
-                dy = ((int)((kAy >> (2 * e)) & 3u) - 1) * sy;
-            } else if (e < 2 * r + 1) {
-                dx = e - r;
-                dy = -r;
-            } else if (e < 4 * r + 2) {
-                dx = e - (3 * r + 1);
-                dy = r;
-            } else if (e < 6 * r + 1) {
-                dx = -r;
-                dy = e - (5 * r + 1);
+            float w = sqrtf(fmaxf(lim * (1.0f + 1e-5f) - h * h, 0.0f)) + 2.0f * g.slop;
+            int x0 = cell_coord(p.x - w, g.xmin, g.inv, g.gx);
+            int x1 = cell_coord(p.x + w, g.xmin, g.inv, g.gx);
+            int c = cell_off + y * g.gx;
+            uint32_t q0 = a.cell_start[c + x0], q1 = a.cell_start[c + x1 + 1];
+            cand += q1 - q0;
+            offer_range<KMAX, CAP>(a.in.msg, q0, q1, t, p, kk, buf, nb, lim);
+            // the nearer of the next rows above and below (none left: infinite gaps)
+            float hu = up < g.gy ? (g.ymin + (float)up * g.s) - p.y : INFINITY;
+            float hd = dn >= 0 ? p.y - (g.ymin + (float)(dn + 1) * g.s) : INFINITY;
+            if (hu <= hd) {
+                y = up++;
+                h = hu;
             } else {
-                dx = r;
-                dy = e - 7 * r;
+                y = dn--;
+                h = hd;
             }
-            int x = cx + dx, y = cy + dy;
-            if (x >= 0 && y >= 0 && x < g.gx && y < g.gy) {
-                float bx0 = g.xmin + (float)x * g.s, by0 = g.ymin + (float)y * g.s;
-                float ddx = fmaxf(0.0f, fmaxf(bx0 - p.x, p.x - (bx0 + g.s)) - g.slop);
-                float ddy = fmaxf(0.0f, fmaxf(by0 - p.y, p.y - (by0 + g.s)) - g.slop);
-                if ((ddx * ddx + ddy * ddy) * (1.0f - 1e-5f) <= lim) {
-                    int c = cell_off + y * g.gx + x;
-                    uint32_t q0 = a.cell_start[c], q1 = a.cell_start[c + 1];
-                    cand += q1 - q0;
-                    offer_range<KMAX, CAP>(a.in.msg, q0, q1, t, p, kk, buf, nb, lim);
-                }
-            }
-            if (++e < (r == 0 ? 1 : 8 * r)) continue;
-            // next ring: does any of its cells exist and possibly lie within reach?
-            ++r;
-            e = 0;
-            float lb = INFINITY;
-            if (cx - r >= 0) lb = fminf(lb, p.x - (g.xmin + (float)(cx - r + 1) * g.s));
-            if (cx + r <= g.gx - 1) lb = fminf(lb, (g.xmin + (float)(cx + r) * g.s) - p.x);
-            if (cy - r >= 0) lb = fminf(lb, p.y - (g.ymin + (float)(cy - r + 1) * g.s));
-            if (cy + r <= g.gy - 1) lb = fminf(lb, (g.ymin + (float)(cy + r) * g.s) - p.y);
-            if (lb == INFINITY) break;
-            lb = fmaxf(0.0f, lb - g.slop);
-            if (lb * lb * (1.0f - 1e-5f) > lim) break;
+            if (h == INFINITY) break;
+            h = fmaxf(0.0f, h - g.slop);
+            if (h * h * (1.0f - 1e-5f) > lim) break;
         }
         // the parked keys, all lanes together
 #pragma unroll 1
