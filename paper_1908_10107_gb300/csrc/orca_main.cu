@@ -296,49 +296,62 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
     }
 }
 
-// Insert key into the ascending list kk (its largest entry drops out); the caller has
-// checked key < kk[KMAX-1].
+// Insert key into the ascending list kk; its largest entry drops out, and a key not below
+// kk[KMAX-1] leaves the list unchanged.  With c_l = (key < kk[l]) (all independent, and
+// monotone in l because kk is sorted) the new entry l is kk[l-1] if c_{l-1}, else key if
+// c_l, else kk[l]: no chain of dependent decisions.
 template <int KMAX>
 __device__ __forceinline__ void insert_key(unsigned long long key, unsigned long long (&kk)[KMAX]) {
-    bool done = false;
+    bool c[KMAX];
 #pragma unroll
-    for (int l = KMAX - 1; l > 0; --l) {
-        if (!done) {
-            if (key < kk[l - 1]) {
-                kk[l] = kk[l - 1];
-            } else {
-                kk[l] = key;
-                done = true;
-            }
-        }
-    }
-    if (!done) kk[0] = key;
+    for (int l = 0; l < KMAX; ++l) c[l] = key < kk[l];
+#pragma unroll
+    for (int l = KMAX - 1; l > 0; --l) kk[l] = c[l - 1] ? kk[l - 1] : (c[l] ? key : kk[l]);
+    if (c[0]) kk[0] = key;
 }
 
-// Candidates q0..q1-1 (sorted slots) offered to the top-k list of the agent at slot t.
-// A candidate enters when its fl32 d^2 <= lim; the first CAP entrants are parked in buf
-// (shared memory) and inserted after the search, later ones are inserted at once and
-// tighten lim to the k-th key's d^2 once the list is full (equal d^2 is settled by the
-// 64-bit key).  Parking keeps the divergent insertion out of the candidate loop.
+// Insert the nb parked keys into kk; once the list is full, lim becomes its k-th d^2.
+template <int KMAX>
+__device__ __forceinline__ void drain(const unsigned long long* buf, int nb,
+                                      unsigned long long (&kk)[KMAX], float& lim) {
+#pragma unroll 1
+    for (int i = 0; i < nb; ++i) insert_key<KMAX>(buf[i], kk);
+    if (kk[KMAX - 1] != ~0ull) lim = fminf(lim, __uint_as_float((unsigned)(kk[KMAX - 1] >> 32)));
+}
+
+// Candidates q0..q1-1 (sorted slots) offered to the top-k list of the agent at slot t,
+// kU at a time (their loads in flight together).  A candidate enters when its fl32 d^2
+// <= lim; entrants are parked in buf (shared memory) and inserted in bulk -- when fewer
+// than kU free places are left, and after the search -- which keeps the divergent
+// insertion out of the candidate loop.  Equal d^2 is settled by the 64-bit key.
+constexpr int kU = 4;
 template <int KMAX, int CAP>
 __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint32_t q0, uint32_t q1,
                                             int t, float2 p, unsigned long long (&kk)[KMAX],
                                             unsigned long long* buf, int& nb, float& lim) {
+    static_assert(CAP > kU, "parking space for one batch");
 #pragma unroll 1
-    for (uint32_t q = q0; q < q1; ++q) {
-        float4 mj = msg[q];
-        float ddx = __fsub_rn(mj.x, p.x), ddy = __fsub_rn(mj.y, p.y);
-        float d2 = __fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy));
-        if (!(d2 <= lim) || (int)q == t) continue;
-        unsigned long long key =
-            ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(mj.w);
-        if (nb < CAP) {
-            buf[nb++] = key;
-            continue;
+    for (uint32_t q = q0; q < q1; q += kU) {
+        float d2[kU];
+        unsigned id[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t qu = q + u;
+            float4 mj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (qu < q1) mj = msg[qu];
+            float ddx = __fsub_rn(mj.x, p.x), ddy = __fsub_rn(mj.y, p.y);
+            d2[u] = __fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy));
+            id[u] = __float_as_uint(mj.w);
+            if (qu >= q1 || (int)qu == t) d2[u] = INFINITY;
         }
-        if (key >= kk[KMAX - 1]) continue;
-        insert_key<KMAX>(key, kk);
-        if (kk[KMAX - 1] != ~0ull) lim = __uint_as_float((unsigned)(kk[KMAX - 1] >> 32));
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (d2[u] <= lim)
+                buf[nb++] = ((unsigned long long)__float_as_uint(d2[u]) << 32) | id[u];
+        if (nb > CAP - kU) {
+            drain<KMAX>(buf, nb, kk, lim);
+            nb = 0;
+        }
     }
 }
 
@@ -401,12 +414,7 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
             h = fmaxf(0.0f, h - g.slop);
             if (h * h * (1.0f - 1e-5f) > lim) break;
         }
-        // the parked keys, all lanes together
-#pragma unroll 1
-        for (int i = 0; i < nb; ++i) {
-            unsigned long long key = buf[i];
-            if (key < kk[KMAX - 1]) insert_key<KMAX>(key, kk);
-        }
+        drain<KMAX>(buf, nb, kk, lim);  // the parked keys, all lanes together
         if (kk[KMAX - 1] != ~0ull || !(lim0 < lim_max)) break;
         lim0 = lim_max;  // fewer than k inside the predicted radius: search to r_obs
     }
