@@ -44,6 +44,20 @@ struct LpTape {
     }
 };
 
+// Line j is (nearly) parallel to the unit line it bounds: |det| <= eps |n_j| (|n_j| = 1
+// for unit lines; squares otherwise, no root).
+template <bool kUnit>
+__device__ __forceinline__ bool parallel_to(float den, float4 lj) {
+    if (kUnit) return fabsf(den) <= kEps;
+    return den * den <= kEps * kEps * (lj.x * lj.x + lj.y * lj.y);
+}
+
+// The same half-plane with a unit normal.
+__device__ __forceinline__ float4 unit_line(float4 l) {
+    float inv = rsqrtf(l.x * l.x + l.y * l.y);
+    return make_float4(l.x * inv, l.y * inv, l.z * inv, l.w);
+}
+
 // LP1: best point on the boundary of line i inside the disc |x| <= V and the half-planes
 // 0..i-1.  x(t) = c_i n_i + t d_i with d_i = (n_i.y, -n_i.x).  The disc gives
 // |t| <= sqrt(V^2 - c_i^2); half-plane j gives -det(n_i, n_j) t >= c_j - c_i (n_i.n_j),
@@ -65,7 +79,7 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
         if (!line(j, lj)) continue;
         float den = det2f(li.x, li.y, lj.x, lj.y);
         float rhs = lj.z - li.z * (li.x * lj.x + li.y * lj.y);
-        if (fabsf(den) <= kEps) {
+        if (parallel_to<LineAt::kUnit>(den, lj)) {
             if (rhs > 0.0f) return false;
             continue;
         }
@@ -127,6 +141,7 @@ __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float
         float4 li;
         if (!line(i, li)) continue;
         if (li.z - (li.x * xx + li.y * xy) > 0.0f) {
+            if (!LineAt::kUnit) li = unit_line(li);
             float sx = xx, sy = xy;
             LpTape r1;
             if (!lp1_dev(line, i, li, V, ox, oy, dir_opt, xx, xy, rec ? &r1 : nullptr)) {
@@ -145,8 +160,9 @@ __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float
     return n;
 }
 
-// Lines of one agent: its shared-memory row.
+// Lines of one agent: its shared-memory row (unit normals).
 struct RowLines {
+    static constexpr bool kUnit = true;
     const float4* row;
     __device__ __forceinline__ bool operator()(int j, float4& l) const {
         l = row[j];
@@ -155,17 +171,19 @@ struct RowLines {
 };
 
 // Bisectors of line i with lines j < i (LP3's projected problem), formed on demand:
-// (n_j - n_i).x >= c_j - c_i, normalised; same-direction parallel lines give none.
+// (n_j - n_i).x >= c_j - c_i, NOT normalised; same-direction parallel lines give none.
+// Every use is scale-free -- the side of a point, an LP1 bound t = -rhs/den -- except the
+// parallel test, which compares |den| with eps |n| (parallel_to), and the line LP1 runs
+// on, which unit_line normalises.
 struct Bisectors {
+    static constexpr bool kUnit = false;
     const float4* row;
     float4 li;
     __device__ __forceinline__ bool operator()(int j, float4& q) const {
         float4 lj = row[j];
         float den = det2f(li.x, li.y, lj.x, lj.y);
         if (fabsf(den) <= kEps && li.x * lj.x + li.y * lj.y > 0.0f) return false;
-        float mx = lj.x - li.x, my = lj.y - li.y;
-        float inv = rsqrtf(mx * mx + my * my);
-        q = make_float4(mx * inv, my * inv, (lj.z - li.z) * inv, 0.0f);
+        q = make_float4(lj.x - li.x, lj.y - li.y, lj.z - li.z, 0.0f);
         return true;
     }
 };
@@ -251,6 +269,7 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
             if (f < 0) break;  // every bisector holds: LP2 succeeded
             float4 qf;
             bis(f, qf);
+            qf = unit_line(qf);
             float D = V * V - qf.z * qf.z;
             if (D < 0.0f) {
                 ok = false;
@@ -265,7 +284,7 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
                 if (!bis(j, qj)) continue;
                 float den = det2f(qf.x, qf.y, qj.x, qj.y);
                 float rhs = qj.z - qf.z * (qf.x * qj.x + qf.y * qj.y);
-                if (fabsf(den) <= kEps) {
+                if (parallel_to<false>(den, qj)) {
                     fail |= rhs > 0.0f;
                     continue;
                 }
