@@ -192,7 +192,7 @@ def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_d
     belongs to agent subset[q].  Returns a dict with pos, vel (float64[rows, 2]), nbr
     (int32[rows, k]), lp3 (bool[rows]), margin (float64[rows]), sens (float64[rows], the
     LP's sensitivity to FP32-sized perturbations of its half-planes, when
-    ``sensitivity``) and counters {scanned, lines, lp1_calls, lp3_agents}."""
+    ``sensitivity``) and operation counters (COUNTER_NAMES)."""
     d = lambda a: np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1))
     pos, vel, goal = d(pos), d(vel), d(goal)
     radius, max_speed, pref_speed, time_horizon = d(radius), d(max_speed), d(pref_speed), d(time_horizon)
@@ -208,7 +208,7 @@ def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_d
     nbr = np.zeros(max(rows * k, 1), np.int32)
     status = np.zeros(max(rows, 1), np.int32)
     margin = np.zeros(max(rows, 1))
-    counters = np.zeros(4, np.int64)
+    counters = np.zeros(8, np.int64)
     sens = np.zeros(max(rows, 1))
     if gf is not None:
         gf = np.ascontiguousarray(gf, np.float32)
@@ -225,9 +225,15 @@ def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_d
         "pos": pos_out[: 2 * rows].reshape(rows, 2), "vel": vel_out[: 2 * rows].reshape(rows, 2),
         "nbr": nbr[: rows * k].reshape(rows, k), "lp3": status[:rows].astype(bool),
         "margin": margin[:rows], "sens": sens[:rows],
-        "counters": dict(zip(("scanned", "lines", "lp1_calls", "lp3_agents"),
-                             (int(c) for c in counters))),
+        "counters": dict(zip(COUNTER_NAMES, (int(c) for c in counters))),
     }
+
+
+# operation counts of oracle_step, summed over the stepped agents: candidates scanned,
+# half-planes built, LP1 calls (LP2 and inside LP3), agents that needed LP3, LP1 bounds
+# evaluated, LP2/LP3 violation checks, LP3 bisectors formed
+COUNTER_NAMES = ("scanned", "lines", "lp1_calls", "lp3_agents", "lp1_bounds", "lp_checks",
+                 "bisectors")
 
 
 def step_scene(scene, **kw):

@@ -327,8 +327,13 @@ static line2 orca_line(v2 pa, v2 va, double ra, v2 pb, v2 vb, double rb, double 
  * otherwise the projection of o onto the line, clamped to the interval.
  * Returns 1 and writes *x on success, 0 when the interval is empty.
  * -------------------------------------------------------------------------------- */
+/* Operation counts of the LP (for the flop model of a step; no effect on results). */
+typedef struct {
+    long long lp1, bounds, checks, bisectors;
+} lpcount;
+
 static int lp1(const line2* L, int i, double V, v2 o, int dir_opt, v2* x, tags* tg,
-               long long* work) {
+               lpcount* work) {
     (void)tg;
     double a = dot(L[i].P, L[i].d);
     double D = a * a + V * V - dot(L[i].P, L[i].P);
@@ -338,7 +343,7 @@ static int lp1(const line2* L, int i, double V, v2 o, int dir_opt, v2* x, tags* 
     for (int j = 0; j < i; ++j) {
         double den = det2(L[i].d, L[j].d);
         double num = det2(L[j].d, sub(L[i].P, L[j].P));
-        if (work) ++*work;
+        if (work) ++work->bounds;
         if (fabs(den) <= OR_EPS) {
             if (num < 0.0) return 0;
             continue;
@@ -366,16 +371,17 @@ static int lp1(const line2* L, int i, double V, v2 o, int dir_opt, v2* x, tags* 
  * success, else the index of the line where LP1 found no point (x keeps its last
  * feasible value). */
 static int lp2(const line2* L, int n, double V, v2 o, int dir_opt, v2* x, tags* tg,
-               long long* work) {
+               lpcount* work) {
     (void)tg;
     if (dir_opt) *x = scl(o, V);
     else if (dot(o, o) > V * V) *x = scl(o, V / len(o));
     else *x = o;
     for (int i = 0; i < n; ++i) {
         double viol = det2(L[i].d, sub(L[i].P, *x));
+        if (work) ++work->checks;
         if (viol > 0.0) {
             v2 keep = *x;
-            if (work) ++*work;
+            if (work) ++work->lp1;
             if (!lp1(L, i, V, o, dir_opt, x, tg, work)) { *x = keep; return i; }
         }
     }
@@ -391,12 +397,13 @@ static int lp2(const line2* L, int n, double V, v2 o, int dir_opt, v2* x, tags* 
  * lines of the same direction give no constraint), and LP2 in direction mode maximises
  * progress along the normal (-d_i.y, d_i.x).  A numerically failed LP2 keeps x. */
 static void lp3(const line2* L, int n, int begin, double V, v2* x, tags* tg,
-                long long* work) {
+                lpcount* work) {
     (void)tg;
     line2 proj[OR_MAXK];
     double dist = 0.0;
     for (int i = begin; i < n; ++i) {
         double pen = det2(L[i].d, sub(L[i].P, *x));
+        if (work) ++work->checks;
         if (pen > dist) {
             int m = 0;
             for (int j = 0; j < i; ++j) {
@@ -413,7 +420,7 @@ static void lp3(const line2* L, int n, int begin, double V, v2* x, tags* tg,
                 proj[m++] = q;
             }
             v2 keep = *x;
-            if (work) ++*work;
+            if (work) work->bisectors += i;
             if (lp2(proj, m, V, mk(-L[i].d.y, L[i].d.x), 1, x, tg, work) < m) *x = keep;
             dist = det2(L[i].d, sub(L[i].P, *x));
         }
@@ -486,9 +493,9 @@ static v2 pref_velocity(v2 p, v2 goal, double pref_speed, double dt) {
  *   (their neighbours are still searched among all n agents) and output row q belongs to
  *   agent subset[q]; otherwise every agent is stepped and row i is agent i.
  * Outputs: pos_out, vel_out (2 per row), nbr (k per row, -1 padded, may be NULL), status
- * (1 per row: 1 if LP3 ran, may be NULL), margin (1 per row, may be NULL), counters[4] =
- * {candidates scanned, lines built, LP1 calls (incl. inside LP3), agents needing LP3}
- * (may be NULL), sens (1 per row, may be NULL; filled when cond_check != 0, see the
+ * (1 per row: 1 if LP3 ran, may be NULL), margin (1 per row, may be NULL), counters[8] =
+ * {candidates scanned, lines built, LP1 calls (incl. inside LP3), agents needing LP3,
+ * LP1 bounds evaluated, LP2/LP3 violation checks, LP3 bisectors formed, 0} (may be NULL), sens (1 per row, may be NULL; filled when cond_check != 0, see the
  * header).  Returns 0, or a negative value on bad arguments / allocation failure.
  * -------------------------------------------------------------------------------- */
 /* Velocity selection (LP2, then LP3 if needed) on given lines. */
@@ -544,7 +551,7 @@ typedef struct {
 
 static void step_agent(const step_in* S, int i, double* pos_out, double* vel_out, int32_t* nbr,
                        int32_t* status, double* margin, double* sens, long long* c_scan,
-                       long long* c_lines, long long* c_work, long long* c_lp3) {
+                       long long* c_lines, lpcount* c_work, long long* c_lp3) {
     cand list[OR_MAXK];
     line2 L[OR_MAXK];
     int cnt = 0;
@@ -563,11 +570,14 @@ static void step_agent(const step_in* S, int i, double* pos_out, double* vel_out
     *c_lines += cnt;
     v2 pv = pref_velocity(pa, mk(S->goal[2 * i], S->goal[2 * i + 1]), S->pref_speed[i], S->dt);
     v2 x;
-    long long w = 0;
+    lpcount w = {0, 0, 0, 0};
     int bfail = lp2(L, cnt, S->max_speed[i], pv, 0, &x, &tg, &w);
     int used3 = bfail < cnt;
     if (used3) { lp3(L, cnt, bfail, S->max_speed[i], &x, &tg, &w); ++*c_lp3; }
-    *c_work += w;
+    c_work->lp1 += w.lp1;
+    c_work->bounds += w.bounds;
+    c_work->checks += w.checks;
+    c_work->bisectors += w.bisectors;
     if (sens) *sens = S->cond ? lp_sensitivity(L, cnt, S->max_speed[i], pv, x) : 0.0;
     vel_out[0] = x.x;
     vel_out[1] = x.y;
@@ -590,7 +600,7 @@ int oracle_step(int n, const double* pos, const double* vel, const double* goal,
         if (n_subset < 0) return -1;
         for (int q = 0; q < n_subset; ++q) if (subset[q] < 0 || subset[q] >= n) return -1;
     }
-    if (counters) memset(counters, 0, 4 * sizeof(long long));
+    if (counters) memset(counters, 0, 8 * sizeof(long long));
     int rows = subset ? n_subset : n;
     if (n == 0 || rows == 0) return 0;
     float* pf = (float*)malloc(sizeof(float) * 2 * (size_t)n);
@@ -610,21 +620,30 @@ int oracle_step(int n, const double* pos, const double* vel, const double* goal,
         if (bins_build(&b, pf, n, gf, gi) != 0) { free(pf); return -2; }
         S.b = &b;
     }
-    long long c_scan = 0, c_lines = 0, c_work = 0, c_lp3 = 0;
+    long long c_scan = 0, c_lines = 0, c_lp3 = 0, c_lp1 = 0, c_bounds = 0, c_checks = 0, c_bis = 0;
 #ifdef _OPENMP
     if (nthreads < 1) nthreads = 1;
-#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads) reduction(+ : c_scan, c_lines, c_work, c_lp3)
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads) \
+    reduction(+ : c_scan, c_lines, c_lp3, c_lp1, c_bounds, c_checks, c_bis)
 #endif
     for (int q = 0; q < rows; ++q) {
         int i = subset ? subset[q] : q;
+        lpcount w = {0, 0, 0, 0};
         step_agent(&S, i, pos_out + 2 * (size_t)q, vel_out + 2 * (size_t)q,
                    nbr ? nbr + (size_t)q * k : NULL, status ? status + q : NULL,
                    margin ? margin + q : NULL, sens ? sens + q : NULL, &c_scan, &c_lines,
-                   &c_work, &c_lp3);
+                   &w, &c_lp3);
+        c_lp1 += w.lp1;
+        c_bounds += w.bounds;
+        c_checks += w.checks;
+        c_bis += w.bisectors;
     }
     if (S.b) bins_free(&b);
     free(pf);
-    if (counters) { counters[0] = c_scan; counters[1] = c_lines; counters[2] = c_work; counters[3] = c_lp3; }
+    if (counters) {
+        counters[0] = c_scan; counters[1] = c_lines; counters[2] = c_lp1; counters[3] = c_lp3;
+        counters[4] = c_bounds; counters[5] = c_checks; counters[6] = c_bis;
+    }
     return 0;
 }
 

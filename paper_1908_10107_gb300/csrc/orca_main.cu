@@ -44,18 +44,42 @@ struct LpTape {
     }
 };
 
+// The LP's arithmetic with every rounding spelled out (explicit fused and unfused
+// operations, no contraction left to the compiler), so that the one-lane and the
+// lane-group LP3 -- different code around the same formulas -- round identically and
+// take the same decisions.
+__device__ __forceinline__ float lp_dot(float ax, float ay, float bx, float by) {
+    return __fmaf_rn(ax, bx, __fmul_rn(ay, by));
+}
+__device__ __forceinline__ float lp_det(float ax, float ay, float bx, float by) {
+    return __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
+}
+// Violation of half-plane l at x: c - n.x (> 0: x is outside).
+__device__ __forceinline__ float lp_viol(float4 l, float x, float y) {
+    return __fsub_rn(l.z, lp_dot(l.x, l.y, x, y));
+}
+// c_j - c_i (n_i.n_j): LP1's right-hand side for bounding line j on base line i.
+__device__ __forceinline__ float lp_rhs(float4 li, float4 lj) {
+    return __fmaf_rn(-li.z, lp_dot(li.x, li.y, lj.x, lj.y), lj.z);
+}
+// The point c n + t d of a unit line (d = (n.y, -n.x)).
+__device__ __forceinline__ float2 lp_point(float4 l, float t) {
+    return make_float2(__fmaf_rn(t, l.y, __fmul_rn(l.z, l.x)),
+                       __fmaf_rn(t, -l.x, __fmul_rn(l.z, l.y)));
+}
+
 // Line j is (nearly) parallel to the unit line it bounds: |det| <= eps |n_j| (|n_j| = 1
 // for unit lines; squares otherwise, no root).
 template <bool kUnit>
 __device__ __forceinline__ bool parallel_to(float den, float4 lj) {
     if (kUnit) return fabsf(den) <= kEps;
-    return den * den <= kEps * kEps * (lj.x * lj.x + lj.y * lj.y);
+    return __fmul_rn(den, den) <= __fmul_rn(kEps * kEps, lp_dot(lj.x, lj.y, lj.x, lj.y));
 }
 
 // The same half-plane with a unit normal.
 __device__ __forceinline__ float4 unit_line(float4 l) {
-    float inv = rsqrtf(l.x * l.x + l.y * l.y);
-    return make_float4(l.x * inv, l.y * inv, l.z * inv, l.w);
+    float inv = rsqrtf(lp_dot(l.x, l.y, l.x, l.y));
+    return make_float4(__fmul_rn(l.x, inv), __fmul_rn(l.y, inv), __fmul_rn(l.z, inv), l.w);
 }
 
 // LP1: best point on the boundary of line i inside the disc |x| <= V and the half-planes
@@ -68,7 +92,7 @@ template <class LineAt>
 __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, float V, float ox,
                                         float oy, bool dir_opt, float& xx, float& xy,
                                         LpTape* rec = nullptr) {
-    float D = V * V - li.z * li.z;
+    float D = __fmaf_rn(-li.z, li.z, __fmul_rn(V, V));
     if (D < 0.0f) return false;
     float sq = sqrtf(D);
     float tL = -sq, tR = sq;
@@ -77,8 +101,8 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
     for (int j = 0; j < i; ++j) {
         float4 lj;
         if (!line(j, lj)) continue;
-        float den = det2f(li.x, li.y, lj.x, lj.y);
-        float rhs = lj.z - li.z * (li.x * lj.x + li.y * lj.y);
+        float den = lp_det(li.x, li.y, lj.x, lj.y);
+        float rhs = lp_rhs(li, lj);
         if (parallel_to<LineAt::kUnit>(den, lj)) {
             if (rhs > 0.0f) return false;
             continue;
@@ -93,8 +117,7 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
         }
         if (tL > tR) return false;
     }
-    float dx = li.y, dy = -li.x;
-    float t = ox * dx + oy * dy;
+    float t = lp_dot(ox, oy, li.y, -li.x);
     if (rec) {
         int side = -1;
         if (dir_opt) side = t > 0.0f ? 1 : 0;
@@ -107,8 +130,9 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
     }
     if (dir_opt) t = t > 0.0f ? tR : tL;
     else t = fminf(fmaxf(t, tL), tR);
-    xx = li.z * li.x + t * dx;
-    xy = li.z * li.y + t * dy;
+    float2 x = lp_point(li, t);
+    xx = x.x;
+    xy = x.y;
     return true;
 }
 
@@ -120,15 +144,15 @@ template <class LineAt>
 __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float ox, float oy,
                                        bool dir_opt, float& xx, float& xy, LpTape* rec = nullptr) {
     if (dir_opt) {
-        xx = ox * V;
-        xy = oy * V;
+        xx = __fmul_rn(ox, V);
+        xy = __fmul_rn(oy, V);
         if (rec) rec->mode = kTapeLp3Dir;
     } else {
-        float o2 = ox * ox + oy * oy;
-        if (o2 > V * V) {
-            float s = V * rsqrtf(o2);
-            xx = ox * s;
-            xy = oy * s;
+        float o2 = lp_dot(ox, oy, ox, oy);
+        if (o2 > __fmul_rn(V, V)) {
+            float s = __fmul_rn(V, rsqrtf(o2));
+            xx = __fmul_rn(ox, s);
+            xy = __fmul_rn(oy, s);
             if (rec) rec->mode = kTapePrefClip;
         } else {
             xx = ox;
@@ -136,28 +160,40 @@ __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float
             if (rec) rec->mode = kTapePref;
         }
     }
+    // Each pass scans ahead to the next violated line and then runs LP1 on it.  The lanes
+    // of a warp meet again after the scan, so LP1 runs for all of them together even when
+    // their violated lines have different indices (a loop over i with LP1 inside would
+    // run it once for every index at which any lane needs it).
+    int i = 0;
 #pragma unroll 1
-    for (int i = 0; i < n; ++i) {
-        float4 li;
-        if (!line(i, li)) continue;
-        if (li.z - (li.x * xx + li.y * xy) > 0.0f) {
-            if (!LineAt::kUnit) li = unit_line(li);
-            float sx = xx, sy = xy;
-            LpTape r1;
-            if (!lp1_dev(line, i, li, V, ox, oy, dir_opt, xx, xy, rec ? &r1 : nullptr)) {
-                xx = sx;
-                xy = sy;
-                return i;
-            }
-            if (rec) {
-                r1.mode = kTapeLine;
-                r1.i = i;
-                r1.f = 0;
-                *rec = r1;
+    for (;;) {
+        float4 li = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        bool hit = false;
+#pragma unroll 1
+        for (; i < n; ++i) {
+            if (!line(i, li)) continue;
+            if (lp_viol(li, xx, xy) > 0.0f) {
+                hit = true;
+                break;
             }
         }
+        if (!hit) return n;
+        if (!LineAt::kUnit) li = unit_line(li);
+        float sx = xx, sy = xy;
+        LpTape r1;
+        if (!lp1_dev(line, i, li, V, ox, oy, dir_opt, xx, xy, rec ? &r1 : nullptr)) {
+            xx = sx;
+            xy = sy;
+            return i;
+        }
+        if (rec) {
+            r1.mode = kTapeLine;
+            r1.i = i;
+            r1.f = 0;
+            *rec = r1;
+        }
+        ++i;
     }
-    return n;
 }
 
 // Lines of one agent: its shared-memory row (unit normals).
@@ -181,9 +217,9 @@ struct Bisectors {
     float4 li;
     __device__ __forceinline__ bool operator()(int j, float4& q) const {
         float4 lj = row[j];
-        float den = det2f(li.x, li.y, lj.x, lj.y);
-        if (fabsf(den) <= kEps && li.x * lj.x + li.y * lj.y > 0.0f) return false;
-        q = make_float4(lj.x - li.x, lj.y - li.y, lj.z - li.z, 0.0f);
+        float den = lp_det(li.x, li.y, lj.x, lj.y);
+        if (fabsf(den) <= kEps && lp_dot(li.x, li.y, lj.x, lj.y) > 0.0f) return false;
+        q = make_float4(__fsub_rn(lj.x, li.x), __fsub_rn(lj.y, li.y), __fsub_rn(lj.z, li.z), 0.0f);
         return true;
     }
 };
@@ -196,31 +232,43 @@ struct Bisectors {
 __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, float V, float& xx,
                                         float& xy, LpTape* rec = nullptr) {
     float dist = 0.0f;
+    int i = begin;
+    // scan ahead to the next line violated by more than dist, then solve for it (the
+    // lanes meet again after the scan, as in lp2_dev)
 #pragma unroll 1
-    for (int i = begin; i < n; ++i) {
-        float4 li = row[i];
-        if (li.z - (li.x * xx + li.y * xy) > dist) {
-            Bisectors bis{row, li};
-            float sx = xx, sy = xy;
-            LpTape r2;
-            if (lp2_dev(bis, i, V, li.x, li.y, true, xx, xy, rec ? &r2 : nullptr) < i) {
-                xx = sx;
-                xy = sy;
-            } else if (rec) {
-                if (r2.mode == kTapeLine) {  // LP1 on the bisector of lines i and r2.i
-                    r2.f = r2.i;
-                    r2.mode = kTapeLp3Line;
-                } else {
-                    r2.f = 0;
-                    r2.bound = kBoundFree;
-                    r2.j = 0;
-                    r2.side = 0;
-                }
-                r2.i = i;
-                *rec = r2;
+    for (;;) {
+        float4 li = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        bool hit = false;
+#pragma unroll 1
+        for (; i < n; ++i) {
+            li = row[i];
+            if (lp_viol(li, xx, xy) > dist) {
+                hit = true;
+                break;
             }
-            dist = li.z - (li.x * xx + li.y * xy);
         }
+        if (!hit) return;
+        Bisectors bis{row, li};
+        float sx = xx, sy = xy;
+        LpTape r2;
+        if (lp2_dev(bis, i, V, li.x, li.y, true, xx, xy, rec ? &r2 : nullptr) < i) {
+            xx = sx;
+            xy = sy;
+        } else if (rec) {
+            if (r2.mode == kTapeLine) {  // LP1 on the bisector of lines i and r2.i
+                r2.f = r2.i;
+                r2.mode = kTapeLp3Line;
+            } else {
+                r2.f = 0;
+                r2.bound = kBoundFree;
+                r2.j = 0;
+                r2.side = 0;
+            }
+            r2.i = i;
+            *rec = r2;
+        }
+        dist = lp_viol(li, xx, xy);
+        ++i;
     }
 }
 
@@ -246,9 +294,9 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
 #pragma unroll 1
     for (int i = begin; i < n; ++i) {
         const float4 li = row[i];
-        if (!(li.z - (li.x * xx + li.y * xy) > dist)) continue;
+        if (!(lp_viol(li, xx, xy) > dist)) continue;
         Bisectors bis{row, li};
-        float nx = li.x * V, ny = li.y * V;  // direction mode starts at V * n_i
+        float nx = __fmul_rn(li.x, V), ny = __fmul_rn(li.y, V);  // direction mode starts at V n_i
         bool ok = true;
         int start = 0;
 #pragma unroll 1
@@ -259,7 +307,7 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
                 int j = c0 + g;
                 bool viol = false;
                 float4 q;
-                if (j < i && bis(j, q)) viol = q.z - (q.x * nx + q.y * ny) > 0.0f;
+                if (j < i && bis(j, q)) viol = lp_viol(q, nx, ny) > 0.0f;
                 unsigned bal = (__ballot_sync(mask, viol) >> base) & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
                 if (bal) {
                     f = c0 + __ffs(bal) - 1;
@@ -270,7 +318,7 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
             float4 qf;
             bis(f, qf);
             qf = unit_line(qf);
-            float D = V * V - qf.z * qf.z;
+            float D = __fmaf_rn(-qf.z, qf.z, __fmul_rn(V, V));
             if (D < 0.0f) {
                 ok = false;
                 break;
@@ -282,8 +330,8 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
             for (int j = g; j < f; j += G) {
                 float4 qj;
                 if (!bis(j, qj)) continue;
-                float den = det2f(qf.x, qf.y, qj.x, qj.y);
-                float rhs = qj.z - qf.z * (qf.x * qj.x + qf.y * qj.y);
+                float den = lp_det(qf.x, qf.y, qj.x, qj.y);
+                float rhs = lp_rhs(qf, qj);
                 if (parallel_to<false>(den, qj)) {
                     fail |= rhs > 0.0f;
                     continue;
@@ -301,17 +349,17 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
                 ok = false;
                 break;
             }
-            float dx = qf.y, dy = -qf.x;
-            float t = (li.x * dx + li.y * dy > 0.0f) ? tR : tL;
-            nx = qf.z * qf.x + t * dx;
-            ny = qf.z * qf.y + t * dy;
+            float t = lp_dot(li.x, li.y, qf.y, -qf.x) > 0.0f ? tR : tL;
+            float2 x = lp_point(qf, t);
+            nx = x.x;
+            ny = x.y;
             start = f + 1;
         }
         if (ok) {
             xx = nx;
             xy = ny;
         }
-        dist = li.z - (li.x * xx + li.y * xy);
+        dist = lp_viol(li, xx, xy);
     }
 }
 
