@@ -38,16 +38,26 @@ UNIT = "agent-steps/s"
 WORKLOAD = ("bidirectional flow, 524,288 agents (two crowds in opposite 250 m bands of a 1 km "
             "square), radius U[0.3,0.5] m, speed U[1.2,1.6] m/s, r_obs 10 m, k 10, tau 5 s, dt 1/60 s")
 # algorithmic HBM bytes per agent of the per-agent ORCA kernel: read pos, vel, goal (8 B
-# each), radius, max speed, pref speed, tau, id (4 B each); write pos, vel (8 B each).
-# Neighbour reads are re-reads of the cell-sorted copy and are not counted.
-ORCA_KERNEL_BYTES_PER_AGENT = 44 + 16
+# each), radius, max speed, pref speed, tau, id, k-th-neighbour hint (4 B each); write pos,
+# vel (8 B each) and the hint (4 B).  Neighbour reads (candidate records, the id -> slot
+# map, neighbour velocities) are re-reads of cell-sorted data and are not counted.
+ORCA_KERNEL_BYTES_PER_AGENT = 48 + 20
+
+# Arithmetic model of one agent-step (FP32 operations of the formulas, an FMA counting as
+# two): 6 per candidate examined (d^2 and its test), 45 per half-plane built, 25 per LP1
+# call (disc interval, objective, point), 14 per LP1 bound, 6 per violation check, 24 per
+# LP3 bisector.  The counts come from the operation-counting replay of the timed steps.
+FLOPS = {"candidates": 6, "lines": 45, "lp1_calls": 25, "lp1_bounds": 14, "lp_checks": 6,
+         "bisectors": 24}
+FP32_LANES_PER_SM = 128
+RADIX_BITS = 9  # digit width of the library's LSD radix sort
 
 
 def step_bytes_per_agent(passes: int) -> int:
     """Algorithmic HBM bytes per agent of one whole step (see the design notes):
-    bbox 8, keys 12, radix passes (12 for pass 0, 20 after), cell table ~5, reorder 92,
-    ORCA kernel 60."""
-    return 8 + 12 + 12 + 20 * max(passes - 1, 0) + 5 + 92 + ORCA_KERNEL_BYTES_PER_AGENT
+    bbox 8, keys 12, radix passes (12 for pass 0, 20 after), cell table ~5, reorder 104,
+    ORCA kernel 68."""
+    return 8 + 12 + 12 + 20 * max(passes - 1, 0) + 5 + 104 + ORCA_KERNEL_BYTES_PER_AGENT
 
 
 def peaks():
@@ -451,6 +461,35 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def alu_roofline(sim, sc, abi, warmup, steps, main_ms, sms, sm_mhz):
+    """Arithmetic roofline of the ORCA kernel: the timed steps replayed (untimed, from the
+    same loaded state, so the trajectory is identical) with operation counting on, the
+    counts turned into FP32 operations by FLOPS, over the timed kernel's mean duration,
+    against sms x 128 FP32 lanes x 2 (FMA) x the SM clock."""
+    abi.orca_profile(sim.ctx, False)
+    abi.orca_count_ops(sim.ctx, True)
+    sim.set_scene(sc)
+    sim.step(warmup)
+    c0, o0 = sim.counters(), sim.op_counters()
+    sim.step(steps)
+    c1, o1 = sim.counters(), sim.op_counters()
+    abi.orca_count_ops(sim.ctx, False)
+    agents = max(c1["agent_steps"] - c0["agent_steps"], 1)
+    per = {"candidates": (c1["candidates"] - c0["candidates"]) / agents,
+           "lines": (c1["lines"] - c0["lines"]) / agents}
+    for k in ("lp1_calls", "lp1_bounds", "lp_checks", "bisectors"):
+        per[k] = (o1[k] - o0[k]) / agents
+    flops = sum(FLOPS[k] * v for k, v in per.items())
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops * sc.n / (main_ms * 1e-3) / 1e12
+    return {"kernel": "orca_main (neighbours + half-planes + LP + integrate)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops_per_agent": flops, "ops_per_agent": {k: round(v, 3) for k, v in per.items()},
+            "launch_ms": main_ms,
+            "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x "
+                           f"{sm_mhz:.0f} MHz (max SM clock)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -569,8 +608,16 @@ def main():
         sim_rec.close()
     except Exception:
         pass
-    passes = max(1, math.ceil(math.log2(max(grid_cells or c_cells, 2)) / 8))
+    passes = max(1, math.ceil(math.log2(max(grid_cells or c_cells, 2)) / RADIX_BITS))
     step_bytes = step_bytes_per_agent(passes)
+
+    # the ORCA kernel is bound by FP32 issue, not HBM: its arithmetic roofline from an
+    # operation-counting replay of exactly the timed steps
+    props = torch.cuda.get_device_properties(local)
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    alu = alu_roofline(sim, sc, abi, args.warmup, args.steps, main_ms, props.multi_processor_count,
+                       float(sm_max))
+    alu["traffic"] = traffic
 
     # end to end through the C ABI with pinned host buffers: upload, step, read back
     pinned = [torch.from_numpy(a).pin_memory().numpy() for a in sc.arrays()]
@@ -617,12 +664,14 @@ def main():
                    "launch_shape": list(shape["shape"]) if shape else [128, 1],
                    "launch_shape_tuning_ms": ({k: round(v, 4) for k, v in shape["timings_ms"].items()}
                                               if shape and shape["timings_ms"] else "fixed by --tpb")},
-        "roofline": {"kernel": "orca_main (neighbours + half-planes + LP + integrate)",
-                     "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": traffic,
-                     "alg_bytes_per_agent": ORCA_KERNEL_BYTES_PER_AGENT,
-                     "launch_ms": main_ms, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-                     if peak_kind == "measured" else "fallback 6800 GB/s"},
+        "roofline": alu,
+        "hbm_roofline": {"kernel": "orca_main (neighbours + half-planes + LP + integrate)",
+                         "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": traffic,
+                         "alg_bytes_per_agent": ORCA_KERNEL_BYTES_PER_AGENT,
+                         "launch_ms": main_ms,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                         if peak_kind == "measured" else "fallback 6800 GB/s"},
         "step_roofline": {"bound": "hbm", "alg_bytes_per_agent": step_bytes,
                           "achieved": step_bytes * n / (ms_per_step * 1e-3) / 1e9,
                           "peak": hbm_peak, "unit": "GB/s",

@@ -203,6 +203,23 @@ ORCA_API int orca_get_cells(orca_ctx* ctx, uint32_t* cell, float* grid_f, int32_
 ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
 
 /*
+ * Operation counting (measurement; the paper has no counterpart).  With on != 0, later
+ * steps launch an instantiation of the ORCA kernel that also counts the LP's algorithmic
+ * operations of Section 3: LP1 calls, LP1 bounds evaluated, violation checks of the LP2
+ * and LP3 scans, and LP3 bisectors formed (i per line i that LP3 solves for).  Results are
+ * unchanged; the counting kernel is slower, so time nothing with it on.  Switching drops
+ * the captured CUDA graphs.  Returns ORCA_OK or ORCA_ERR_ARG (null ctx).
+ */
+ORCA_API int orca_count_ops(orca_ctx* ctx, int32_t on);
+
+/*
+ * The four operation counts above, summed over the steps launched with counting on since
+ * orca_set_agents (synchronises `stream`): counters4[0] LP1 calls, [1] LP1 bounds,
+ * [2] violation checks, [3] bisectors.  Zero when counting was never on.
+ */
+ORCA_API int orca_get_op_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
+
+/*
  * Per-phase device timing.  With enable != 0 the step records CUDA events (event-record
  * nodes inside the captured graph) between its three phases: binning (bounding box, cell
  * keys, radix sort, cell table), reorder (gather into cell order) and the per-agent

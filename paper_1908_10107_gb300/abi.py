@@ -80,6 +80,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_get_neighbors": ([vp, vp, c.c_int, vp], c.c_int),
         "orca_get_cells": ([vp, vp, vp, vp, c.c_int, vp], c.c_int),
         "orca_get_counters": ([vp, vp, vp], c.c_int),
+        "orca_count_ops": ([vp, i32], c.c_int),
+        "orca_get_op_counters": ([vp, vp, vp], c.c_int),
         "orca_sync": ([vp, vp], c.c_int),
         "orca_profile": ([vp, c.c_int], c.c_int),
         "orca_profile_read": ([vp, vp], c.c_int),
@@ -224,6 +226,17 @@ def orca_get_counters(ctx, stream=None) -> np.ndarray:
     out = np.zeros(4, np.int64)
     _check(load_library().orca_get_counters(ctx, ctypes.c_void_p(out.ctypes.data),
                                             _stream(stream)), ctx)
+    return out
+
+
+def orca_count_ops(ctx, on: bool):
+    _check(load_library().orca_count_ops(ctx, int(bool(on))), ctx)
+
+
+def orca_get_op_counters(ctx, stream=None) -> np.ndarray:
+    out = np.zeros(4, np.int64)
+    _check(load_library().orca_get_op_counters(ctx, ctypes.c_void_p(out.ctypes.data),
+                                               _stream(stream)), ctx)
     return out
 
 
@@ -404,6 +417,10 @@ class OrcaSim:
     def counters(self, stream=None) -> dict:
         c = orca_get_counters(self.ctx, stream)
         return dict(zip(("agent_steps", "lp3_agent_steps", "candidates", "lines"), map(int, c)))
+
+    def op_counters(self, stream=None) -> dict:
+        c = orca_get_op_counters(self.ctx, stream)
+        return dict(zip(("lp1_calls", "lp1_bounds", "lp_checks", "bisectors"), map(int, c)))
 
     def sync(self, stream=None):
         orca_sync(self.ctx, stream)

@@ -78,7 +78,7 @@ static bool make_plan(const orca_params& p, Plan& pl) {
     pl.o_slot = p.max_scenes > 1 ? L.add(N * 4) : (size_t)-1;
     pl.o_part = L.add(kBboxBlocks * sizeof(float4));
     pl.o_misc = L.add(sizeof(DeviceMisc));
-    pl.o_blk = L.add((size_t)pl.nmb * 4 * sizeof(unsigned long long));
+    pl.o_blk = L.add((size_t)pl.nmb * kBlockCounters * sizeof(unsigned long long));
     if (p.flags & ORCA_FLAG_RECORD) {
         pl.o_rnbr = L.add(N * pl.K * 4);
         pl.o_rcell = L.add(N * 4);
@@ -114,6 +114,7 @@ struct orca_ctx {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int graph_n = -1;
     bool prof = false;
+    bool count_ops = false;  // steps launch the operation-counting ORCA kernel
     int n_scenes = 0;  // 0: single scene (orca_set_agents); else a batch
     SceneDev* scenes = nullptr;
     int* slot_scene = nullptr;
@@ -218,6 +219,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     a.prm = c->PR[par ^ 1];
     a.out = c->PV[0];
     a.block_counters = c->blk;
+    a.count_ops = c->count_ops ? 1 : 0;
     a.rec_nbr = c->rec_nbr;
     a.rec_cell = c->rec_cell;
     a.scenes = c->n_scenes > 0 ? c->scenes : nullptr;
@@ -256,6 +258,7 @@ static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, ui
     a.prm = c->PR[par ^ 1];
     a.out = c->PV[0];
     a.block_counters = c->blk;
+    a.count_ops = 0;
     a.rec_nbr = nbr;
     a.rec_cell = nullptr;
     a.scenes = nullptr;
@@ -438,7 +441,7 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy, cons
         CK(cudaMemsetAsync(ctx->PR[0].hint, 0xff, N * 4, st), "reset hint");
     }
     CK(cudaMemsetAsync(ctx->bins.misc, 0, sizeof(DeviceMisc), st), "reset misc");
-    CK(cudaMemsetAsync(ctx->blk, 0, (size_t)ctx->plan.nmb * 4 * sizeof(unsigned long long), st),
+    CK(cudaMemsetAsync(ctx->blk, 0, (size_t)ctx->plan.nmb * kBlockCounters * sizeof(unsigned long long), st),
        "reset counters");
     if (ctx->rec_nbr && n > 0) CK(cudaMemsetAsync(ctx->rec_nbr, 0xff, N * ctx->plan.K * 4, st), "reset record");
     if (ctx->rec_cell && n > 0) CK(cudaMemsetAsync(ctx->rec_cell, 0, N * 4, st), "reset record");
@@ -610,10 +613,10 @@ ORCA_API int orca_get_cells(orca_ctx* ctx, uint32_t* cell, float* grid_f, int32_
     return ORCA_OK;
 }
 
-ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream) {
-    if (!ctx || !counters4) return ORCA_ERR_ARG;
+// Sum of per-CTA counters first..first+3 over the CTAs.
+static int sum_counters(orca_ctx* ctx, int first, int64_t* out4, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    size_t cnt = (size_t)ctx->plan.nmb * 4;
+    size_t cnt = (size_t)ctx->plan.nmb * kBlockCounters;
     unsigned long long* h = new (std::nothrow) unsigned long long[cnt];
     if (!h) return fail(ctx, ORCA_ERR_NOMEM, "host allocation failed");
     cudaError_t e = cudaMemcpyAsync(h, ctx->blk, cnt * 8, cudaMemcpyDeviceToHost, st);
@@ -622,11 +625,31 @@ ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream) 
         delete[] h;
         return cuda_fail(ctx, e, "copy counters");
     }
-    for (int q = 0; q < 4; ++q) counters4[q] = 0;
+    for (int q = 0; q < 4; ++q) out4[q] = 0;
     for (size_t b = 0; b < (size_t)ctx->plan.nmb; ++b)
-        for (int q = 0; q < 4; ++q) counters4[q] += (int64_t)h[4 * b + q];
+        for (int q = 0; q < 4; ++q) out4[q] += (int64_t)h[kBlockCounters * b + first + q];
     delete[] h;
     return ORCA_OK;
+}
+
+ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream) {
+    if (!ctx || !counters4) return ORCA_ERR_ARG;
+    return sum_counters(ctx, 0, counters4, stream);
+}
+
+ORCA_API int orca_count_ops(orca_ctx* ctx, int32_t on) {
+    if (!ctx) return ORCA_ERR_ARG;
+    bool want = on != 0;
+    if (want != ctx->count_ops) {
+        ctx->count_ops = want;
+        drop_graphs(ctx);
+    }
+    return ORCA_OK;
+}
+
+ORCA_API int orca_get_op_counters(orca_ctx* ctx, int64_t* counters4, void* stream) {
+    if (!ctx || !counters4) return ORCA_ERR_ARG;
+    return sum_counters(ctx, 4, counters4, stream);
 }
 
 // Rollout workspace: checkpoints, parameters in agent order, one segment's recomputed

@@ -18,6 +18,9 @@ namespace orca {
 
 constexpr int kMaxNeighbors = 32;
 constexpr int kRadixBits = 9;
+// per-CTA counters of the ORCA kernel: agents, LP3 agents, candidates, half-planes, then
+// (operation-counting launches only) LP1 calls, LP1 bounds, violation checks, bisectors
+constexpr int kBlockCounters = 8;
 constexpr int kRadixBuckets = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;  // items per thread per tile
@@ -110,7 +113,8 @@ struct MainArgs {
     Sorted in;                           // sorted messages and velocities (read)
     AgentParams prm;                     // sorted parameters (read)
     AgentState out;                      // new state, same slots
-    unsigned long long* block_counters;  // 4 per block, accumulated
+    unsigned long long* block_counters;  // kBlockCounters per block, accumulated
+    int count_ops;                       // launch the operation-counting instantiation
     int32_t* rec_nbr;                    // n*k in agent order, or null
     uint32_t* rec_cell;                  // n in agent order, or null
 };

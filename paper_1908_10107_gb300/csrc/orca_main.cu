@@ -36,6 +36,13 @@ namespace orca {
 constexpr int kTapePref = 0, kTapePrefClip = 1, kTapeLine = 2, kTapeLp3Dir = 3, kTapeLp3Line = 4;
 constexpr int kBoundFree = 0, kBoundDisc = 1, kBoundLine = 2;
 
+// Algorithmic operation counts of the LP (operation-counting launches only): LP1 calls,
+// LP1 bounds evaluated, violation checks (LP2 and LP3 scans), LP3 bisectors formed -- the
+// quantities the oracle counts, for the kernel's arithmetic roofline.
+struct OpCount {
+    unsigned lp1, bounds, checks, bis;
+};
+
 struct LpTape {
     int mode, i, f, bound, j, side;
     __device__ __forceinline__ unsigned pack() const {
@@ -91,7 +98,7 @@ __device__ __forceinline__ float4 unit_line(float4 l) {
 template <class LineAt>
 __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, float V, float ox,
                                         float oy, bool dir_opt, float& xx, float& xy,
-                                        LpTape* rec = nullptr) {
+                                        LpTape* rec = nullptr, OpCount* oc = nullptr) {
     float D = __fmaf_rn(-li.z, li.z, __fmul_rn(V, V));
     if (D < 0.0f) return false;
     float sq = sqrtf(D);
@@ -101,6 +108,7 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
     for (int j = 0; j < i; ++j) {
         float4 lj;
         if (!line(j, lj)) continue;
+        if (oc) ++oc->bounds;
         float den = lp_det(li.x, li.y, lj.x, lj.y);
         float rhs = lp_rhs(li, lj);
         if (parallel_to<LineAt::kUnit>(den, lj)) {
@@ -142,7 +150,8 @@ __device__ __forceinline__ bool lp1_dev(const LineAt& line, int i, float4 li, fl
 // kTapePrefClip, or kTapeLp3Dir in direction mode) or the last LP1 (kTapeLine, line i).
 template <class LineAt>
 __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float ox, float oy,
-                                       bool dir_opt, float& xx, float& xy, LpTape* rec = nullptr) {
+                                       bool dir_opt, float& xx, float& xy, LpTape* rec = nullptr,
+                                       OpCount* oc = nullptr) {
     if (dir_opt) {
         xx = __fmul_rn(ox, V);
         xy = __fmul_rn(oy, V);
@@ -172,16 +181,18 @@ __device__ __forceinline__ int lp2_dev(const LineAt& line, int n, float V, float
 #pragma unroll 1
         for (; i < n; ++i) {
             if (!line(i, li)) continue;
+            if (oc) ++oc->checks;
             if (lp_viol(li, xx, xy) > 0.0f) {
                 hit = true;
                 break;
             }
         }
         if (!hit) return n;
+        if (oc) ++oc->lp1;
         if (!LineAt::kUnit) li = unit_line(li);
         float sx = xx, sy = xy;
         LpTape r1;
-        if (!lp1_dev(line, i, li, V, ox, oy, dir_opt, xx, xy, rec ? &r1 : nullptr)) {
+        if (!lp1_dev(line, i, li, V, ox, oy, dir_opt, xx, xy, rec ? &r1 : nullptr, oc)) {
             xx = sx;
             xy = sy;
             return i;
@@ -230,7 +241,7 @@ struct Bisectors {
 // numerically failed LP2 keeps x.
 // rec (may be null) keeps the record of the LP2 phase until an LP3 solve succeeds.
 __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, float V, float& xx,
-                                        float& xy, LpTape* rec = nullptr) {
+                                        float& xy, LpTape* rec = nullptr, OpCount* oc = nullptr) {
     float dist = 0.0f;
     int i = begin;
     // scan ahead to the next line violated by more than dist, then solve for it (the
@@ -242,16 +253,18 @@ __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, flo
 #pragma unroll 1
         for (; i < n; ++i) {
             li = row[i];
+            if (oc) ++oc->checks;
             if (lp_viol(li, xx, xy) > dist) {
                 hit = true;
                 break;
             }
         }
         if (!hit) return;
+        if (oc) oc->bis += i;
         Bisectors bis{row, li};
         float sx = xx, sy = xy;
         LpTape r2;
-        if (lp2_dev(bis, i, V, li.x, li.y, true, xx, xy, rec ? &r2 : nullptr) < i) {
+        if (lp2_dev(bis, i, V, li.x, li.y, true, xx, xy, rec ? &r2 : nullptr, oc) < i) {
             xx = sx;
             xy = sy;
         } else if (rec) {
@@ -530,7 +543,7 @@ __device__ __forceinline__ void scene_view(const MainArgs& a, int t, SceneView& 
 
 // Persistent over tiles of TPB consecutive agents: tile blockIdx.x first, then
 // tiles taken from a per-step counter (with one CTA per tile this loop runs once).
-template <int KMAX, int TPB, int G, bool TAPE = false>
+template <int KMAX, int TPB, int G, bool TAPE = false, bool COUNT = false>
 __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_kernel(MainArgs a) {
     constexpr int KP = KMAX + 1;  // padded rows: conflict-free float4 accesses
     extern __shared__ float4 s_lines[];  // TPB * KP half-planes
@@ -543,13 +556,16 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     __shared__ LpTape s_tape[TAPE ? TPB : 1];
     __shared__ int s_qn, s_tile;
     __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3;
+    __shared__ unsigned long long s_ops[COUNT ? 4 : 1];
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_cand = 0;
         s_lines_n = 0;
         s_act = 0;
         s_lp3 = 0;
+        for (int q = 0; q < (COUNT ? 4 : 1); ++q) s_ops[q] = 0;
     }
+    OpCount oc{0u, 0u, 0u, 0u};
     const int ntiles = (a.n + TPB - 1) / TPB;
     float4* row = s_lines + tid * KP;
 #pragma unroll 1
@@ -625,7 +641,8 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             RowLines rl{row};
             LpTape tape;
             tape.i = tape.f = tape.bound = tape.j = tape.side = 0;
-            int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy, TAPE ? &tape : nullptr);
+            int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy, TAPE ? &tape : nullptr,
+                            COUNT ? &oc : nullptr);
             if (TAPE) s_tape[tid] = tape;
             if (b < cnt) {
                 int slot = atomicAdd(&s_qn, 1);
@@ -644,7 +661,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             int ag = s_queue[q];
             float2 x = s_x[ag];
             if (G == 1) lp3_dev(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y,
-                                TAPE ? &s_tape[TAPE ? ag : 0] : nullptr);
+                                TAPE ? &s_tape[TAPE ? ag : 0] : nullptr, COUNT ? &oc : nullptr);
             else lp3_group_dev<G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
             if ((tid & (G - 1)) == 0) s_x[ag] = x;
         }
@@ -673,6 +690,15 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             atomicAdd(&s_act, (unsigned long long)wa);
         }
         if (tid == 0) s_lp3 += (unsigned long long)nq;
+        if (COUNT) {
+            unsigned v[4] = {oc.lp1, oc.bounds, oc.checks, oc.bis};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                unsigned w = __reduce_add_sync(0xffffffffu, v[q]);
+                if ((tid & 31) == 0) atomicAdd(&s_ops[q], (unsigned long long)w);
+            }
+            oc = OpCount{0u, 0u, 0u, 0u};
+        }
         if ((int)gridDim.x >= ntiles) break;  // one CTA per tile: no work queue
         if (tid == 0) s_tile = (int)atomicAdd(&a.misc_rw->tile_counter, 1u) + (int)gridDim.x;
         __syncthreads();
@@ -680,11 +706,13 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     }
     __syncthreads();
     if (tid == 0) {
-        unsigned long long* c = a.block_counters + 4 * (size_t)blockIdx.x;
+        unsigned long long* c = a.block_counters + kBlockCounters * (size_t)blockIdx.x;
         c[0] += s_act;
         c[1] += s_lp3;
         c[2] += s_cand;
         c[3] += s_lines_n;
+        if (COUNT)
+            for (int q = 0; q < 4; ++q) c[4 + q] += s_ops[COUNT ? q : 0];
     }
 }
 
@@ -739,6 +767,18 @@ static cudaError_t dispatch_tpb(const MainArgs& a, const LaunchShape& sh, int gr
     return dispatch_g<KMAX, 128>(a, sh.lp3_group, grid_blocks, st, resident);
 }
 
+// Operation-counting launch: 128 threads, serial LP3, one CTA per tile (the counts are
+// algorithmic, so any launch shape gives the same numbers).
+template <int KMAX>
+static cudaError_t launch_count_k(const MainArgs& a, cudaStream_t st) {
+    constexpr size_t smem = main_smem_bytes<KMAX, 128>();
+    cudaError_t e = cudaFuncSetAttribute(orca_main_kernel<KMAX, 128, 1, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    orca_main_kernel<KMAX, 128, 1, false, true><<<(a.n + 127) / 128, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int KMAX>
 static cudaError_t launch_tape_k(const MainArgs& a, cudaStream_t st) {
     constexpr size_t smem = main_smem_bytes<KMAX, 128>();
@@ -756,6 +796,12 @@ static cudaError_t dispatch(const MainArgs& a, int kmax, const LaunchShape& sh, 
         if (kmax <= 16) return launch_tape_k<16>(a, st);
         if (kmax <= 20) return launch_tape_k<20>(a, st);
         return launch_tape_k<32>(a, st);
+    }
+    if (a.count_ops && !resident) {
+        if (kmax <= 10) return launch_count_k<10>(a, st);
+        if (kmax <= 16) return launch_count_k<16>(a, st);
+        if (kmax <= 20) return launch_count_k<20>(a, st);
+        return launch_count_k<32>(a, st);
     }
     if (kmax <= 10) return dispatch_tpb<10>(a, sh, grid_blocks, st, resident);
     if (kmax <= 16) return dispatch_tpb<16>(a, sh, grid_blocks, st, resident);

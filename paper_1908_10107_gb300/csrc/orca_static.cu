@@ -59,7 +59,7 @@ constexpr StaticLayout static_layout() {
     L.sid = o; o += al256(N * 4);
     L.opos = o; o += al256(N * 8);
     L.ovel = o; o += al256(N * 8);
-    L.blk = o; o += al256((size_t)nmb * 4 * 8);
+    L.blk = o; o += al256((size_t)nmb * kBlockCounters * 8);
     L.total = o;
     return L;
 }
@@ -167,6 +167,7 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
         a.prm = dst_p;
         a.out = out;
         a.block_counters = (unsigned long long*)(base + L.blk);
+        a.count_ops = 0;
         a.rec_nbr = nullptr;
         a.rec_cell = nullptr;
         a.scenes = nullptr;

@@ -220,6 +220,35 @@ def test_counters():
     assert c["candidates"] >= c["lines"]
 
 
+def test_operation_counts_match_the_oracle():
+    # the counting launch counts the LP operations the oracle counts on the same state
+    # (they can differ only where an FP32 decision differs from the FP64 one), and
+    # counting changes no result
+    import oracle
+    sc = S.jitter_velocities(S.bidirectional(8190, seed=16), 16)
+    ref = oracle.step_scene(sc, knn_mode=1)["counters"]
+    sim = parity.make_sim(sc)
+    sim.set_scene(sc)
+    abi.orca_count_ops(sim.ctx, True)
+    sim.step(1)
+    ops, c = sim.op_counters(), sim.counters()
+    pos, vel = sim.get_state()
+    sim.close()
+    assert c["lines"] == ref["lines"]
+    assert abs(c["lp3_agent_steps"] - ref["lp3_agents"]) <= 0.002 * sc.n
+    for key in ("lp1_calls", "lp1_bounds", "lp_checks", "bisectors"):
+        assert ref[key] > 0
+        assert abs(ops[key] - ref[key]) <= 0.01 * ref[key], (key, ops[key], ref[key])
+    plain = parity.make_sim(sc)
+    plain.set_scene(sc)
+    plain.step(1)
+    assert not any(plain.op_counters().values())
+    p2, v2 = plain.get_state()
+    plain.close()
+    np.testing.assert_array_equal(pos, p2)
+    np.testing.assert_array_equal(vel, v2)
+
+
 def test_non_finite_input_is_reported():
     sc = _tiny(np.random.default_rng(15).uniform(0, 10, (64, 2)))
     sc.pos[3] = np.nan
