@@ -619,14 +619,19 @@ def main():
                        float(sm_max))
     alu["traffic"] = traffic
 
-    # end to end through the C ABI with pinned host buffers: upload, step, read back
-    pinned = [torch.from_numpy(a).pin_memory().numpy() for a in sc.arrays()]
-    out_pos = torch.empty((n, 2), dtype=torch.float32).pin_memory().numpy()
-    out_vel = torch.empty((n, 2), dtype=torch.float32).pin_memory().numpy()
+    # end to end through the C ABI, a host-driven loop over the same crowd: each step
+    # uploads the state and parameters from pinned host memory, steps, and reads the new
+    # state back into the buffers the next step uploads
     abi.orca_profile(sim.ctx, False)
-    sim.set_agents(*pinned)
+    sim.set_scene(sc)
+    sim.step(args.warmup)
+    pos_h, vel_h = sim.get_state()
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+              for a in [pos_h, vel_h] + list(sc.arrays()[2:])]
+    out_pos, out_vel = pinned[0], pinned[1]
+    abi.orca_set_agents(sim.ctx, n, *pinned, stream=stream)
     sim.step(1)
-    sim.get_state()
+    abi.orca_get_state(sim.ctx, out_pos, out_vel, stream=stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):

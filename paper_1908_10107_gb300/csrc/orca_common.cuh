@@ -73,7 +73,7 @@ struct AgentParams {  // one of PR[0] / PR[1]
     float* pref_speed;
     float* tau;
     uint32_t* id;
-    float* hint;  // k-th neighbour d^2 of the agent's previous step (NaN: none), or null
+    float* hint;  // last step's k-th neighbour d^2 (NaN: none; +inf: fewer than k), or null
 };
 
 struct AgentState {  // one of PV[0] / PV[1]

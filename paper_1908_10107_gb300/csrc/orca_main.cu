@@ -449,11 +449,11 @@ __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint
 // outside it).  h is the row's distance minus the slop; the search stops when the next
 // row's h^2 exceeds lim.  lim shrinks as the list fills, narrowing later rows.
 //
-// lim starts at lim0 <= the largest float below r_obs^2 (a radius predicted from the
-// agent's previous step).  Every candidate with d^2 <= lim0 is offered, and all others
-// have larger d^2, so when at least k candidates were offered the list is exact; when
-// fewer were and lim0 was below the r_obs bound, the search is repeated with that bound.
-// buf holds CAP parked keys.
+// lim starts at lim0 (a predicted radius capped below r_obs^2; NaN: one cell edge).
+// Every candidate with d^2 <= lim0 is offered, and all others have larger d^2, so when at
+// least k candidates were offered the list is exact; when fewer were and lim0 was below
+// the r_obs bound, the search is repeated with 1.5 x the radius (capped at the r_obs
+// bound).  buf holds CAP parked keys.
 template <int KMAX, int CAP>
 __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g, int cell_off,
                                             float nd, int t, float2 p, int k, float lim0,
@@ -462,7 +462,10 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
     const int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
     float nd2 = __fmul_rn(nd, nd);
     const float lim_max = __int_as_float(__float_as_int(nd2) - 1);  // largest float below r_obs^2
-    lim0 = fminf(lim0, lim_max);  // a NaN prediction gives lim_max
+    // no prediction: one cell edge (the tuned edge is about the k-th neighbour distance; a
+    // start that misses costs a warp a whole extra pass, so it errs on the wide side)
+    if (lim0 != lim0) lim0 = g.s * g.s;
+    lim0 = fminf(lim0, lim_max);
     unsigned cand = 0;
 #pragma unroll 1
     for (;;) {
@@ -496,7 +499,9 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
         }
         drain<KMAX>(buf, nb, kk, lim);  // the parked keys, all lanes together
         if (kk[KMAX - 1] != ~0ull || !(lim0 < lim_max)) break;
-        lim0 = lim_max;  // fewer than k inside the predicted radius: search to r_obs
+        // fewer than k inside: 1.5 x the radius (from at least 1e-3 r_obs, so the bound
+        // reaches r_obs within 18 passes whatever the prediction was)
+        lim0 = fminf(fmaxf(2.25f * lim0, 1e-6f * lim_max), lim_max);
     }
     return cand;
 }
@@ -588,13 +593,15 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             float4 me4 = a.in.msg[t];
             p = make_float2(me4.x, me4.y);
             me = __float_as_uint(me4.w);
-            // search radius predicted from the previous step's k-th neighbour distance:
-            // no distance grows by more than the two agents' displacements, about 2 V dt
+            // search radius predicted from the previous step's k-th neighbour distance
+            // (no distance grows by more than the two agents' displacements, about 2 V dt);
+            // +inf (fewer than k inside r_obs last time) starts at the r_obs bound, NaN (no
+            // prediction) at one cell edge
             float V = a.prm.max_speed[t];
-            float lim0 = INFINITY;
+            float lim0 = __int_as_float(0x7fffffff);
             if (a.prm.hint) {
                 float hd = sqrtf(a.prm.hint[t]) * (1.0f + 1e-3f) + 3.0f * V * dt + 1e-3f;
-                lim0 = hd * hd;  // NaN (no prediction) or infinite: the r_obs bound
+                lim0 = hd * hd;
             }
             unsigned long long kk[KMAX];
             cand = knn_dev<KMAX, 2 * KP>(a, sv.g, sv.cell_off, sv.nd, t, p, sv.k, lim0,
@@ -602,7 +609,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             if (a.prm.hint)
                 a.prm.hint[t] = kk[KMAX - 1] != ~0ull
                                     ? __uint_as_float((unsigned)(kk[KMAX - 1] >> 32))
-                                    : __int_as_float(0x7fffffff);
+                                    : INFINITY;
             // park the neighbours' slots in the row (one unrolled store each), then build
             // the half-planes in a rolled loop: one copy of the line code keeps the kernel
             // small enough for the instruction cache

@@ -76,6 +76,20 @@ def test_cell_size_does_not_change_results(cell_size):
     parity.gpu_step_and_compare(sc, cell_size=cell_size)
 
 
+@pytest.mark.parametrize("spacing,steps_before", [(3.0, 0), (3.0, 3), (6.0, 0), (6.0, 3)])
+def test_sparse_lattice_with_tiny_cells(spacing, steps_before):
+    # cells far smaller than the neighbour distances: with no radius prediction the search
+    # starts at 1.5 cell edges and doubles the radius many times; at spacing 6 most agents
+    # have fewer than k = 10 neighbours inside r_obs = 10 (the prediction then says so)
+    rng = np.random.default_rng(int(spacing * 10) + steps_before)
+    g = np.stack(np.meshgrid(np.arange(24.0), np.arange(24.0)), -1).reshape(-1, 2) * spacing
+    g = g + rng.uniform(-0.2, 0.2, g.shape)
+    sc = _tiny(g, r=0.4, nd=10.0, dt=0.1)
+    sc = S.jitter_velocities(sc, 7)
+    rep = parity.gpu_step_and_compare(sc, cell_size=0.05, steps_before=steps_before)
+    assert rep["rows"] == g.shape[0]
+
+
 def test_cell_capacity_doubling():
     sc = S.jitter_velocities(S.bidirectional(5000, seed=7), 7)
     parity.gpu_step_and_compare(sc, cell_size=0.1, max_cells=1000)
