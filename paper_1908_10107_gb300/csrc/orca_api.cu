@@ -232,9 +232,11 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     return e;
 }
 
-// kernels per step: bbox, keys+histogram, per radix pass (upsweep except pass 0, scan,
-// downsweep), cell table, reorder, ORCA kernel
-static int launches_per_step(const orca_ctx* c) { return 2 + 3 * c->plan.max_passes - 1 + 3; }
+// kernels per step: bounding box (a batch: scene boxes and scene prefix), keys+histogram,
+// per radix pass (upsweep except pass 0, scan, downsweep), reorder + cell table, ORCA kernel
+static int launches_per_step(const orca_ctx* c) {
+    return (c->n_scenes > 0 ? 3 : 2) + 3 * c->plan.max_passes - 1 + 2;
+}
 
 // One step launched directly with the neighbour lists and LP records written in agent
 // order (recomputation inside orca_rollout_backward).

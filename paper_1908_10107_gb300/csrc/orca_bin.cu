@@ -4,11 +4,12 @@
 //   bbox_grid       exact min/max of positions -> grid descriptor (cell edge, gx, gy).
 //   keys_hist       cell key of every agent + digit histogram of radix pass 0.
 //   radix_upsweep / radix_scan / radix_downsweep   stable LSD radix sort of
-//                   (cell key, slot) with 8-bit digits; only ceil(bits(num_cells)/8)
+//                   (cell key, slot) with 9-bit digits; only ceil(bits(num_cells)/9)
 //                   passes do work, the rest return at once.
-//   cell_table      cell_start[c] = first sorted slot of cell c, for every c in
-//                   [0, num_cells] (empty cells included, no memset needed).
-//   reorder         gathers state and parameters into the new cell order.
+//   reorder         gathers state and parameters into the new cell order, writes the
+//                   id -> slot map, and the cell table: cell_start[c] = first sorted slot
+//                   of cell c for every c in [0, num_cells] (empty cells included, no
+//                   memset needed).
 //
 // The sort is stable with respect to the previous step's cell order, so the layout is
 // deterministic; nothing downstream depends on the order inside a cell (neighbours are
@@ -314,29 +315,29 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     }
 }
 
-// cell_start[c] for c in [0, num_cells]: slot t writes every cell in (key[t-1], key[t]].
-__global__ void __launch_bounds__(256) cell_table_kernel(int n, const uint32_t* __restrict__ keys_a,
-                                                         const uint32_t* __restrict__ keys_b,
-                                                         const DeviceMisc* __restrict__ misc,
-                                                         uint32_t* __restrict__ cell_start) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t > n) return;
-    const GridDev& g = misc->grid;
-    const uint32_t* keys = (g.passes & 1) ? keys_b : keys_a;
-    int prev = t == 0 ? -1 : (int)keys[t - 1];
-    int cur = t == n ? g.num_cells : (int)keys[t];
-    for (int c = prev + 1; c <= cur; ++c) cell_start[c] = (uint32_t)t;
-}
-
 // Gather state and parameters into the sorted order; build the message records.
 __global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __restrict__ vals_a,
                                                       const uint32_t* __restrict__ vals_b,
+                                                      const uint32_t* __restrict__ keys_a,
+                                                      const uint32_t* __restrict__ keys_b,
                                                       const DeviceMisc* __restrict__ misc,
+                                                      uint32_t* __restrict__ cell_start,
                                                       AgentState src_s, Sorted dst_s,
                                                       AgentParams src_p, AgentParams dst_p) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    const uint32_t* vals = (misc->grid.passes & 1) ? vals_b : vals_a;
+    const GridDev& g = misc->grid;
+    {
+        // cell table: slot t starts every cell in (key[t-1], key[t]]; the last slot also
+        // closes the cells after its own with cell_start = n
+        const uint32_t* keys = (g.passes & 1) ? keys_b : keys_a;
+        int prev = t == 0 ? -1 : (int)keys[t - 1];
+        int cur = (int)keys[t];
+        for (int c = prev + 1; c <= cur; ++c) cell_start[c] = (uint32_t)t;
+        if (t == n - 1)
+            for (int c = cur + 1; c <= g.num_cells; ++c) cell_start[c] = (uint32_t)n;
+    }
+    const uint32_t* vals = (g.passes & 1) ? vals_b : vals_a;
     uint32_t s = vals[t];
     float2 p = src_s.pos[s];
     float r = src_p.radius[s];
@@ -389,7 +390,7 @@ cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_
     return cudaGetLastError();
 }
 
-// Radix passes over the keys written by keys_hist, then the cell table.
+// Radix passes over the keys written by keys_hist (the reorder kernel builds the cell table).
 void launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cudaStream_t st) {
     for (int pass = 0; pass < max_passes; ++pass) {
         int src = pass & 1, dst = src ^ 1;
@@ -401,15 +402,14 @@ void launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cu
             n, pass, b.misc, b.keys[src], pass == 0 ? nullptr : b.vals[src], b.keys[dst],
             b.vals[dst], b.hist, b.digit_totals);
     }
-    cell_table_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(n, b.keys[0], b.keys[1], b.misc,
-                                                            b.cell_start);
 }
 
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
                            const Sorted& dst_s, const AgentParams& src_p,
                            const AgentParams& dst_p, cudaStream_t st) {
-    reorder_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, b.vals[0], b.vals[1], b.misc, src_s, dst_s,
-                                                    src_p, dst_p);
+    reorder_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, b.vals[0], b.vals[1], b.keys[0], b.keys[1],
+                                                    b.misc, b.cell_start, src_s, dst_s, src_p,
+                                                    dst_p);
     return cudaGetLastError();
 }
 
