@@ -315,7 +315,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     }
 }
 
-// Gather state and parameters into the sorted order; build the message records.
+// Gather state and parameters into the sorted order; build the message records, the
+// id -> slot map and the cell table.  Each thread takes kReorderR slots (blockDim apart)
+// and issues all their loads before any store, so that more gathers are in flight.
+constexpr int kReorderR = 2;
 __global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __restrict__ vals_a,
                                                       const uint32_t* __restrict__ vals_b,
                                                       const uint32_t* __restrict__ keys_a,
@@ -324,34 +327,57 @@ __global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __r
                                                       uint32_t* __restrict__ cell_start,
                                                       AgentState src_s, Sorted dst_s,
                                                       AgentParams src_p, AgentParams dst_p) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
     const GridDev& g = misc->grid;
-    {
+    const uint32_t* vals = (g.passes & 1) ? vals_b : vals_a;
+    const uint32_t* keys = (g.passes & 1) ? keys_b : keys_a;
+    const int t0 = blockIdx.x * blockDim.x * kReorderR + threadIdx.x;
+    uint32_t s[kReorderR];
+    int prev[kReorderR], cur[kReorderR];
+#pragma unroll
+    for (int r = 0; r < kReorderR; ++r) {
+        int t = t0 + r * blockDim.x;
+        bool ok = t < n;
+        s[r] = ok ? vals[t] : 0u;
+        cur[r] = ok ? (int)keys[t] : 0;
+        prev[r] = (ok && t > 0) ? (int)keys[t - 1] : -1;
+    }
+    float2 p[kReorderR], v[kReorderR], goal[kReorderR];
+    float rad[kReorderR], vmax[kReorderR], pref[kReorderR], tau[kReorderR], hint[kReorderR];
+    uint32_t id[kReorderR];
+#pragma unroll
+    for (int r = 0; r < kReorderR; ++r) {
+        if (t0 + r * (int)blockDim.x >= n) continue;
+        uint32_t q = s[r];
+        p[r] = src_s.pos[q];
+        v[r] = src_s.vel[q];
+        goal[r] = src_p.goal[q];
+        rad[r] = src_p.radius[q];
+        vmax[r] = src_p.max_speed[q];
+        pref[r] = src_p.pref_speed[q];
+        tau[r] = src_p.tau[q];
+        id[r] = src_p.id[q];
+        hint[r] = dst_p.hint ? src_p.hint[q] : 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < kReorderR; ++r) {
+        int t = t0 + r * blockDim.x;
+        if (t >= n) continue;
+        dst_s.msg[t] = make_float4(p[r].x, p[r].y, rad[r], __uint_as_float(id[r]));
+        dst_s.slot[id[r]] = (uint32_t)t;
+        dst_s.vel[t] = v[r];
+        dst_p.goal[t] = goal[r];
+        dst_p.radius[t] = rad[r];
+        dst_p.max_speed[t] = vmax[r];
+        dst_p.pref_speed[t] = pref[r];
+        dst_p.tau[t] = tau[r];
+        dst_p.id[t] = id[r];
+        if (dst_p.hint) dst_p.hint[t] = hint[r];
         // cell table: slot t starts every cell in (key[t-1], key[t]]; the last slot also
         // closes the cells after its own with cell_start = n
-        const uint32_t* keys = (g.passes & 1) ? keys_b : keys_a;
-        int prev = t == 0 ? -1 : (int)keys[t - 1];
-        int cur = (int)keys[t];
-        for (int c = prev + 1; c <= cur; ++c) cell_start[c] = (uint32_t)t;
+        for (int c = prev[r] + 1; c <= cur[r]; ++c) cell_start[c] = (uint32_t)t;
         if (t == n - 1)
-            for (int c = cur + 1; c <= g.num_cells; ++c) cell_start[c] = (uint32_t)n;
+            for (int c = cur[r] + 1; c <= g.num_cells; ++c) cell_start[c] = (uint32_t)n;
     }
-    const uint32_t* vals = (g.passes & 1) ? vals_b : vals_a;
-    uint32_t s = vals[t];
-    float2 p = src_s.pos[s];
-    float r = src_p.radius[s];
-    uint32_t id = src_p.id[s];
-    dst_s.msg[t] = make_float4(p.x, p.y, r, __uint_as_float(id));
-    dst_s.slot[id] = (uint32_t)t;
-    dst_s.vel[t] = src_s.vel[s];
-    dst_p.goal[t] = src_p.goal[s];
-    dst_p.radius[t] = r;
-    dst_p.max_speed[t] = src_p.max_speed[s];
-    dst_p.pref_speed[t] = src_p.pref_speed[s];
-    dst_p.tau[t] = src_p.tau[s];
-    dst_p.id[t] = id;
-    if (dst_p.hint) dst_p.hint[t] = src_p.hint[s];
 }
 
 // State back to agent order (readout).
@@ -407,7 +433,9 @@ void launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cu
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
                            const Sorted& dst_s, const AgentParams& src_p,
                            const AgentParams& dst_p, cudaStream_t st) {
-    reorder_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, b.vals[0], b.vals[1], b.keys[0], b.keys[1],
+    if (n <= 0) return cudaSuccess;
+    reorder_kernel<<<(n + 256 * kReorderR - 1) / (256 * kReorderR), 256, 0, st>>>(
+                                                    n, b.vals[0], b.vals[1], b.keys[0], b.keys[1],
                                                     b.misc, b.cell_start, src_s, dst_s, src_p,
                                                     dst_p);
     return cudaGetLastError();
