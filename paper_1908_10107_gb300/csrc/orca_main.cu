@@ -662,9 +662,15 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             }
         }
         __syncthreads();
-        // ---- phase 3: least penetration for the queued agents, G lanes each
+        // ---- phase 3: least penetration for the queued agents, G lanes each.  Queue
+        // entries are dealt round-robin over the warps (entry q to warp q % warps), so a
+        // short queue keeps every warp busy instead of filling the first warp and leaving
+        // the others waiting at the barrier.
         const int nq = s_qn;
-        for (int q = tid / G; q < nq; q += TPB / G) {
+        constexpr int kGroupsPerWarp = 32 / G, kWarps = TPB / 32;
+        const int gi = tid / G;
+        const int q0 = (gi % kGroupsPerWarp) * kWarps + gi / kGroupsPerWarp;
+        for (int q = q0; q < nq; q += TPB / G) {
             int ag = s_queue[q];
             float2 x = s_x[ag];
             if (G == 1) lp3_dev(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y,
