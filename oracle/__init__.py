@@ -81,6 +81,8 @@ def _bind(lib):
                                 c.c_int, _F64P, _F64P, c.c_void_p, c.c_void_p, c.c_void_p,
                                 c.c_void_p, c.c_int, c.c_void_p])
     lib.oracle_step.restype = c.c_int
+    lib.oracle_arrived.argtypes = [c.c_int, _F32P, _F32P, _F32P, _I32P]
+    lib.oracle_arrived.restype = c.c_int
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = c.c_int
     return lib
@@ -234,6 +236,27 @@ def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_d
 # evaluated, LP2/LP3 violation checks, LP3 bisectors formed
 COUNTER_NAMES = ("scanned", "lines", "lp1_calls", "lp3_agents", "lp1_bounds", "lp_checks",
                  "bisectors")
+
+
+def arrived(pos, goal, radius) -> np.ndarray:
+    """Which agents have reached their goal (Section 4: they leave the simulation):
+    |goal - p| <= radius, decided in FP32 (bool[n])."""
+    pos = np.ascontiguousarray(np.asarray(pos, np.float32).reshape(-1))
+    goal = np.ascontiguousarray(np.asarray(goal, np.float32).reshape(-1))
+    radius = np.ascontiguousarray(np.asarray(radius, np.float32).reshape(-1))
+    n = radius.size
+    out = np.zeros(max(n, 1), np.int32)
+    _load().oracle_arrived(n, pos, goal, radius, out)
+    return out[:n].astype(bool)
+
+
+def remove_arrived(scene):
+    """The scene without the agents that have arrived, and the kept agents' indices."""
+    keep = np.flatnonzero(~arrived(scene.pos, scene.goal, scene.radius))
+    out = scene.copy()
+    for name in ("pos", "vel", "goal", "radius", "max_speed", "pref_speed", "time_horizon"):
+        setattr(out, name, np.ascontiguousarray(getattr(scene, name)[keep]))
+    return out, keep
 
 
 def step_scene(scene, **kw):

@@ -648,6 +648,30 @@ int oracle_step(int n, const double* pos, const double* vel, const double* goal,
 }
 
 /* Number of OpenMP threads the oracle would use by default (1 without OpenMP). */
+/* ----------------------------------------------------------------------------------
+ * Arrival (Section 4: a person who reaches the goal location is removed from the
+ * simulation).  Reading: agent i has arrived when its goal lies within its own radius,
+ * |goal - p| <= r, decided in FP32 with one rounding per operation:
+ * dx = fl(gx - px), dy = fl(gy - py), arrived iff fl(fl(dx dx) + fl(dy dy)) <= fl(r r).
+ * pos, goal: 2n floats (x, y interleaved); radius: n floats; arrived: n int32 (1 or 0).
+ * Returns the number of agents that have arrived.
+ * -------------------------------------------------------------------------------- */
+int oracle_arrived(int n, const float* pos, const float* goal, const float* radius,
+                   int32_t* arrived) {
+    int count = 0;
+    for (int i = 0; i < n; ++i) {
+        float dx = goal[2 * i] - pos[2 * i];
+        float dy = goal[2 * i + 1] - pos[2 * i + 1];
+        float dx2 = dx * dx;
+        float dy2 = dy * dy;
+        float d2 = dx2 + dy2;
+        float r2 = radius[i] * radius[i];
+        arrived[i] = d2 <= r2;
+        count += arrived[i];
+    }
+    return count;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

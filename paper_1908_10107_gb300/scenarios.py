@@ -237,3 +237,121 @@ def patch(scene: Scene, m: int, seed: int = 0) -> Scene:
     for f in ("pos", "vel", "goal", "radius", "max_speed", "pref_speed", "time_horizon"):
         setattr(s, f, np.ascontiguousarray(getattr(scene, f)[idx]))
     return s
+
+
+# ----------------------------------------------------------------------------------
+# The paper's own test cases (Section 4): crowds spawned without overlap in start
+# regions, each agent heading for its own goal in an associated end region.  The paper
+# gives the agent parameters and the crowd layout in words only; the region sizes, the
+# spawn density and the ORCA parameters below are readings (stated in the docstrings).
+# ----------------------------------------------------------------------------------
+
+def spawn_without_overlap(rng, lo, hi, radius, clearance, max_tries: int = 200) -> np.ndarray:
+    """Positions uniform in the box [lo, hi) (lo, hi: float64[m, 2] per agent) such that
+    no two agents are closer than radius_i + radius_j + clearance_i + clearance_j, by
+    rejection sampling in agent order (a grid over the boxes finds the agents already
+    placed nearby).  Raises if an agent finds no free spot in ``max_tries`` draws."""
+    m = radius.shape[0]
+    reach = 2.0 * float(np.max(radius + clearance)) if m else 1.0
+    cells: dict = {}
+    pos = np.zeros((m, 2))
+    span = radius + clearance
+    for i in range(m):
+        for _ in range(max_tries):
+            p = lo[i] + rng.random(2) * (hi[i] - lo[i])
+            cx, cy = int(math.floor(p[0] / reach)), int(math.floor(p[1] / reach))
+            ok = True
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for j in cells.get((cx + dx, cy + dy), ()):
+                        if (p[0] - pos[j, 0]) ** 2 + (p[1] - pos[j, 1]) ** 2 < (span[i] + span[j]) ** 2:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                pos[i] = p
+                cells.setdefault((cx, cy), []).append(i)
+                break
+        else:
+            raise ValueError(f"agent {i}: no free spawn spot after {max_tries} draws")
+    return pos
+
+
+def _crossing_parameters(rng, m: int, heterogeneous: bool):
+    """Section 4's agent parameters.  Equal agents: radius 0.5 m, desired speed 1 m/s,
+    maximum 1.33 m/s.  Varied agents: radius 0.5, 0.75 or 1 m and, independently, desired
+    speed 1, 1.33 or 2 m/s, each with probability 1/3; maximum = 1.25 x desired."""
+    if not heterogeneous:
+        return _full(m, 0.5), _full(m, 1.0), _full(m, 1.33)
+    radius = _f32(rng.choice([0.5, 0.75, 1.0], m))
+    pref = _f32(rng.choice([1.0, 1.33, 2.0], m))
+    return radius, pref, _f32(1.25 * pref.astype(np.float64))
+
+
+def _region_boxes(centres, side):
+    c = np.asarray(centres, np.float64)
+    return c - 0.5 * side, c + 0.5 * side
+
+
+def _region_side(radius, pref, dt, groups, coverage):
+    """Side of square start regions in which the agents' spawn discs (radius plus one
+    step of travel) cover ``coverage`` of the area, for the most crowded group."""
+    disc = math.pi * (radius.astype(np.float64) + pref.astype(np.float64) * dt) ** 2
+    need = max(float(disc[g].sum()) for g in groups) if len(radius) else 1.0
+    return math.sqrt(need / coverage)
+
+
+def two_way_crossing(n: int = 2500, heterogeneous: bool = False, seed: int = 1914,
+                     coverage: float = 0.3, neighbor_dist: float = 10.0, max_neighbors: int = 10,
+                     time_horizon: float = 5.0, dt: float = 0.1, steps: int = 3000) -> Scene:
+    """Two-way crossing (Section 4, Figs. 3-4): two crowds of n/2; each crowd's start
+    region is the other's end region, so they pass through each other.  Readings: square
+    regions in which the spawn discs (radius plus one step of travel at the desired speed,
+    the spawn clearance) cover 30% of the area (0.27 agents/m^2 for equal agents), centred
+    one side length either side of the origin on the x axis; goals uniform in the end
+    region; r_obs 10 m, k 10, tau 5 s, dt 0.1 s (the paper does not state its ORCA
+    parameters)."""
+    rng = np.random.default_rng(seed)
+    h = n // 2
+    radius, pref, vmax = _crossing_parameters(rng, n, heterogeneous)
+    side = _region_side(radius, pref, dt, [slice(0, h), slice(h, n)], coverage)
+    centre = np.array([[-side, 0.0]] * h + [[side, 0.0]] * (n - h)).reshape(-1, 2)
+    lo, hi = _region_boxes(centre, side)
+    pos = spawn_without_overlap(rng, lo, hi, radius.astype(np.float64), pref.astype(np.float64) * dt)
+    glo, ghi = _region_boxes(-centre, side)
+    goal = glo + rng.random((n, 2)) * (ghi - glo)
+    name = "two_way_varied" if heterogeneous else "two_way"
+    return Scene(name, _f32(pos), np.zeros((n, 2), np.float32), _f32(goal), radius, vmax, pref,
+                 _full(n, time_horizon), neighbor_dist, max_neighbors, dt, steps)
+
+
+def eight_way_crossing(n: int = 10000, seed: int = 1915, coverage: float = 0.3,
+                       neighbor_dist: float = 10.0, max_neighbors: int = 10,
+                       time_horizon: float = 5.0, dt: float = 0.1, steps: int = 4000) -> Scene:
+    """Eight-way crossing (Section 4, Fig. 5): eight crowds of n/8 whose start regions sit
+    at 45-degree steps around a circle; each crowd's end region is the one 135 degrees
+    further round, so the crowds cross near the centre and turn into a vortex.  Readings:
+    square regions sized as in two_way_crossing, centred on a circle of radius twice the
+    side (neighbouring regions do not touch); goals uniform in the end region; the equal
+    agents of the two-way case; spawn clearance and ORCA parameters as two_way_crossing."""
+    rng = np.random.default_rng(seed)
+    m = n // 8
+    counts = [m + (1 if c < n - 8 * m else 0) for c in range(8)]
+    starts = np.cumsum([0] + counts)
+    radius, pref, vmax = _crossing_parameters(rng, n, False)
+    side = _region_side(radius, pref, dt, [slice(starts[c], starts[c + 1]) for c in range(8)],
+                        coverage)
+    rc = 2.0 * side
+    ang = np.repeat(np.arange(8) * (math.pi / 4.0), counts)
+    centre = rc * np.stack([np.cos(ang), np.sin(ang)], 1)
+    gang = ang + 3.0 * math.pi / 4.0
+    gcentre = rc * np.stack([np.cos(gang), np.sin(gang)], 1)
+    lo, hi = _region_boxes(centre, side)
+    pos = spawn_without_overlap(rng, lo, hi, radius.astype(np.float64), pref.astype(np.float64) * dt)
+    glo, ghi = _region_boxes(gcentre, side)
+    goal = glo + rng.random((n, 2)) * (ghi - glo)
+    return Scene("eight_way", _f32(pos), np.zeros((n, 2), np.float32), _f32(goal), radius, vmax,
+                 pref, _full(n, time_horizon), neighbor_dist, max_neighbors, dt, steps)

@@ -15,6 +15,7 @@ import oracle
 import test_oracle_halfplane as H
 import test_oracle_knn as K
 import test_oracle_lp as LP
+import test_oracle_population as POP
 import test_oracle_step as ST
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "orca_oracle.c")
@@ -44,6 +45,9 @@ MUTANTS = {
                                "if (dist > 0.0) return scl(g, pref_speed / dist);"),
     "integrate_old_velocity": ("pos_out[0] = pa.x + x.x * S->dt;", "pos_out[0] = pa.x + va.x * S->dt;"),
     "knn_wrong_agent": ("float dx = pf[2 * j] - pf[2 * i];", "float dx = pf[2 * j] - pf[2 * j + 1];"),
+    "arrival_strict": ("arrived[i] = d2 <= r2;", "arrived[i] = d2 < r2;"),
+    "arrival_mixed_square": ("float dy2 = dy * dy;", "float dy2 = dx * dy;"),
+    "arrival_radius_not_squared": ("float r2 = radius[i] * radius[i];", "float r2 = radius[i];"),
 }
 
 
@@ -67,6 +71,8 @@ def _pins():
         ("lone_agent", lambda: (ST.test_lone_agent_prefers_goal_direction(o),
                                 ST.test_lone_agent_lands_on_goal(o))),
         ("collision_free", lambda: ST.test_feasible_mutual_pairs_do_not_collide_within_tau(o, 0)),
+        ("arrival_boundary", POP.test_boundary_cases),
+        ("arrival_exact", POP.test_matches_exact_arithmetic_away_from_the_boundary),
     ]
 
 

@@ -1,5 +1,6 @@
 """The seeded workload generators (shared by the GPU path and the oracle)."""
 import numpy as np
+import pytest
 
 from paper_1908_10107_gb300 import scenarios as S
 
@@ -39,3 +40,58 @@ def test_batch_counts_log_uniform():
     assert off[-1] == b.n == sum(a.shape[0] for a in b.arrays()[:1])
     kinds = {s.name for s in b.scenes}
     assert kinds == {"circle_swap", "bidirectional"}
+
+
+def _min_gap(sc):
+    """Smallest (distance - r_i - r_j - c_i - c_j) over all pairs (brute force)."""
+    p = sc.pos.astype(np.float64)
+    span = sc.radius.astype(np.float64) + sc.pref_speed.astype(np.float64) * sc.dt
+    d = np.sqrt(((p[:, None, :] - p[None, :, :]) ** 2).sum(-1))
+    gap = d - span[:, None] - span[None, :]
+    np.fill_diagonal(gap, np.inf)
+    return gap.min()
+
+
+@pytest.mark.parametrize("heterogeneous", [False, True])
+def test_two_way_crossing_layout(heterogeneous):
+    sc = S.two_way_crossing(1200, heterogeneous=heterogeneous, seed=5)
+    assert sc.n == 1200 and _min_gap(sc) >= -1e-4  # spawned without overlap (float32 storage)
+    h = sc.n // 2
+    # crowd A starts left of the origin and heads right, crowd B the other way; each
+    # crowd's goals lie in the other's start region
+    assert (sc.pos[:h, 0] < 0).all() and (sc.pos[h:, 0] > 0).all()
+    for a, b in ((slice(0, h), slice(h, None)), (slice(h, None), slice(0, h))):
+        lo, hi = sc.pos[b].min(0), sc.pos[b].max(0)
+        assert (sc.goal[a] >= lo - 1.5).all() and (sc.goal[a] <= hi + 1.5).all()
+    if heterogeneous:
+        assert set(np.unique(sc.radius)) == {np.float32(0.5), np.float32(0.75), np.float32(1.0)}
+        assert set(np.unique(sc.pref_speed)) == {np.float32(1.0), np.float32(1.33), np.float32(2.0)}
+        np.testing.assert_allclose(sc.max_speed, 1.25 * sc.pref_speed.astype(np.float64), rtol=1e-6)
+    else:
+        assert (sc.radius == np.float32(0.5)).all() and (sc.pref_speed == np.float32(1.0)).all()
+        assert (sc.max_speed == np.float32(1.33)).all()
+    again = S.two_way_crossing(1200, heterogeneous=heterogeneous, seed=5)
+    np.testing.assert_array_equal(sc.pos, again.pos)
+    np.testing.assert_array_equal(sc.goal, again.goal)
+
+
+def test_eight_way_crossing_layout():
+    sc = S.eight_way_crossing(2000, seed=6)
+    assert sc.n == 2000 and _min_gap(sc) >= -1e-4
+    ang = np.arctan2(sc.pos[:, 1].astype(np.float64), sc.pos[:, 0])
+    gang = np.arctan2(sc.goal[:, 1].astype(np.float64), sc.goal[:, 0])
+    m = sc.n // 8
+    for c in range(8):
+        rows = slice(c * m, (c + 1) * m)
+        start = np.angle(np.exp(1j * ang[rows]).mean())
+        turn = np.angle(np.exp(1j * gang[rows]).mean() / np.exp(1j * start))
+        # the crowd starts at 45-degree step c and heads 135 degrees further round
+        assert abs(np.angle(np.exp(1j * (start - c * np.pi / 4)))) < 0.05
+        assert abs(turn - 3 * np.pi / 4) < 0.05
+
+
+def test_spawn_rejects_a_full_region():
+    rng = np.random.default_rng(0)
+    lo, hi = np.zeros((50, 2)), np.full((50, 2), 3.0)
+    with pytest.raises(ValueError):
+        S.spawn_without_overlap(rng, lo, hi, np.full(50, 0.5), np.zeros(50), max_tries=50)
