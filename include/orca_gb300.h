@@ -203,6 +203,21 @@ ORCA_API int orca_get_cells(orca_ctx* ctx, uint32_t* cell, float* grid_f, int32_
 ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
 
 /*
+ * Remove the agents that have reached their goal (Section 4: a person who reaches the
+ * goal location is removed from the simulation).  An agent has arrived when its goal lies
+ * within its radius on the current state, decided in FP32 with one rounding per operation:
+ * dx = fl(gx - px), dy = fl(gy - py), arrived iff fl(fl(dx*dx) + fl(dy*dy)) <= fl(r*r).
+ * The survivors keep their relative order and are renumbered 0..n'-1 (the next step sorts
+ * them into cells again; their radius predictions are kept).  *n_remaining receives n';
+ * kept_ids (n' int32, host or device memory per `where`, may be NULL) receives each new
+ * index's old index.  Synchronises `stream` (the host needs n').  The next orca_step
+ * re-captures its CUDA graphs for the new count.  Single-scene contexts only:
+ * ORCA_ERR_STATE for a batch; ORCA_ERR_ARG for a null ctx or n_remaining.
+ */
+ORCA_API int orca_remove_arrived(orca_ctx* ctx, int32_t* n_remaining, int32_t* kept_ids, int where,
+                                 void* stream);
+
+/*
  * Operation counting (measurement; the paper has no counterpart).  With on != 0, later
  * steps launch an instantiation of the ORCA kernel that also counts the LP's algorithmic
  * operations of Section 3: LP1 calls, LP1 bounds evaluated, violation checks of the LP2

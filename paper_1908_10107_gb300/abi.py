@@ -81,6 +81,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_get_cells": ([vp, vp, vp, vp, c.c_int, vp], c.c_int),
         "orca_get_counters": ([vp, vp, vp], c.c_int),
         "orca_count_ops": ([vp, i32], c.c_int),
+        "orca_remove_arrived": ([vp, c.POINTER(i32), vp, c.c_int, vp], c.c_int),
         "orca_get_op_counters": ([vp, vp, vp], c.c_int),
         "orca_sync": ([vp, vp], c.c_int),
         "orca_profile": ([vp, c.c_int], c.c_int),
@@ -227,6 +228,17 @@ def orca_get_counters(ctx, stream=None) -> np.ndarray:
     _check(load_library().orca_get_counters(ctx, ctypes.c_void_p(out.ctypes.data),
                                             _stream(stream)), ctx)
     return out
+
+
+def orca_remove_arrived(ctx, kept_ids=None, stream=None) -> int:
+    """Remove the agents at their goal; returns the new count.  kept_ids: None, a host
+    int32 array or a device tensor of at least the old count (receives old indices)."""
+    m = ctypes.c_int32(0)
+    ptr, where = _ptr(kept_ids, np.int32)
+    _check(load_library().orca_remove_arrived(ctx, ctypes.byref(m), ptr,
+                                              int(ORCA_HOST if where is None else where),
+                                              _stream(stream)), ctx)
+    return int(m.value)
 
 
 def orca_count_ops(ctx, on: bool):
@@ -417,6 +429,13 @@ class OrcaSim:
     def counters(self, stream=None) -> dict:
         c = orca_get_counters(self.ctx, stream)
         return dict(zip(("agent_steps", "lp3_agent_steps", "candidates", "lines"), map(int, c)))
+
+    def remove_arrived(self, stream=None):
+        """Remove the agents that have reached their goal; returns (count, kept old
+        indices as int32[count])."""
+        kept = np.zeros(max(self.n, 1), np.int32)
+        m = orca_remove_arrived(self.ctx, kept, stream)
+        return m, kept[:m].copy()
 
     def op_counters(self, stream=None) -> dict:
         c = orca_get_op_counters(self.ctx, stream)

@@ -639,6 +639,46 @@ ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream) 
     return sum_counters(ctx, 0, counters4, stream);
 }
 
+ORCA_API int orca_remove_arrived(orca_ctx* ctx, int32_t* n_remaining, int32_t* kept_ids, int where,
+                                 void* stream) {
+    if (!ctx || !n_remaining) return ORCA_ERR_ARG;
+    if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
+    if (ctx->n_scenes > 0) return fail(ctx, ORCA_ERR_STATE, "removal needs a single-scene context");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = ctx->n, par = ctx->cur;
+    if (n == 0) {
+        *n_remaining = 0;
+        return ORCA_OK;
+    }
+    // scratch between steps: sort keys (keep flags, new indices), sort values (old
+    // indices), digit histograms (tile sums), digit totals (the count); the survivors'
+    // state goes through the readout staging buffers, their parameters to the other
+    // parameter copy, which becomes the current one
+    CK(launch_remove_arrived(n, ctx->PV[0], ctx->PR[par], ctx->PR[par ^ 1], ctx->stage[0],
+                             ctx->stage[1], ctx->bins.keys[0], ctx->bins.keys[1],
+                             ctx->bins.vals[0], ctx->bins.hist, ctx->bins.digit_totals, st),
+       "removal kernels");
+    uint32_t total = 0;
+    CK(cudaMemcpyAsync(&total, ctx->bins.digit_totals, 4, cudaMemcpyDeviceToHost, st), "copy count");
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    const int m = (int)total;
+    if (m > 0) {
+        CK(cudaMemcpyAsync(ctx->PV[0].pos, ctx->stage[0], (size_t)m * 8, cudaMemcpyDeviceToDevice, st),
+           "copy pos");
+        CK(cudaMemcpyAsync(ctx->PV[0].vel, ctx->stage[1], (size_t)m * 8, cudaMemcpyDeviceToDevice, st),
+           "copy vel");
+        if (kept_ids)
+            CK(cudaMemcpyAsync(kept_ids, ctx->bins.vals[0], (size_t)m * 4,
+                               where == ORCA_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st),
+               "copy kept ids");
+    }
+    if (where == ORCA_HOST) CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    ctx->n = m;
+    ctx->cur = par ^ 1;
+    *n_remaining = m;
+    return ORCA_OK;
+}
+
 ORCA_API int orca_count_ops(orca_ctx* ctx, int32_t on) {
     if (!ctx) return ORCA_ERR_ARG;
     bool want = on != 0;

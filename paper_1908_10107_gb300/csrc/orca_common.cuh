@@ -146,6 +146,11 @@ int default_lp3_group(int kmax);
 cudaError_t launch_main(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
                         cudaStream_t st);
 int main_resident_blocks(int kmax, const LaunchShape& sh);
+// orca_population.cu: remove the agents that have reached their goal (see there)
+cudaError_t launch_remove_arrived(int n, const AgentState& cur, const AgentParams& cur_p,
+                                  const AgentParams& dst_p, float2* pos_tmp, float2* vel_tmp,
+                                  uint32_t* keep, uint32_t* new_id, uint32_t* old_id,
+                                  uint32_t* tile_sums, uint32_t* total, cudaStream_t st);
 
 // Reverse step of a rollout (orca_adjoint.cu); everything in agent order.
 struct AdjointArgs {

@@ -87,6 +87,10 @@ def test_null_context_is_rejected(lib):
     assert lib.orca_step(None, 1, None) == abi.ORCA_ERR_ARG
     assert lib.orca_get_state(None, None, None, 0, None) == abi.ORCA_ERR_ARG
     assert lib.orca_destroy(None) == abi.ORCA_ERR_ARG
+    m = ctypes.c_int32(-1)
+    assert lib.orca_remove_arrived(None, ctypes.byref(m), None, 0, None) == abi.ORCA_ERR_ARG
+    assert lib.orca_count_ops(None, 1) == abi.ORCA_ERR_ARG
+    assert lib.orca_get_op_counters(None, None, None) == abi.ORCA_ERR_ARG
 
 
 def test_status_strings(lib):
