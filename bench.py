@@ -531,6 +531,57 @@ def run_crossing(args):
     print(json.dumps(line), flush=True)
 
 
+def run_lp_ab(args):
+    """A/B of the LP modes -- one lane per solve, four-lane groups for LP3, and warp work
+    units (the paper's load-balanced LP) -- on LP3-heavy and lighter crowds.  Each mode
+    replays the same steps from the same saved state (the modes give bitwise-equal
+    trajectories); the ORCA kernel's mean time comes from the library's phase events."""
+    import torch
+    from paper_1908_10107_gb300 import abi, scenarios
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    modes = ((64, 1), (64, 4), (64, 32), (128, 32))
+    cases = []
+    flow = scenarios.bidirectional()
+    cases.append(("flow_524288_steps_1_30", flow, 1, {}))
+    cases.append(("flow_524288_steps_300_330", flow, 300, {}))
+    dense = scenarios.dense()
+    cases.append(("dense_2097152_k20_steps_10_40", dense, 10, {}))
+    eight = scenarios.eight_way_crossing(10000)
+    cases.append(("eight_way_10000_steps_1500_1530", eight, 1500, {}))
+    out = {}
+    for name, sc, skip, _ in cases:
+        sim = abi.OrcaSim.for_scene(sc)
+        sim.set_scene(sc)
+        if skip > 1:
+            sim.step(skip - 1)
+        pos, vel = sim.get_state()
+        start = sc.copy()
+        start.pos, start.vel = pos, vel
+        row = {}
+        for tpb, lanes in modes:
+            abi.orca_set_launch(sim.ctx, tpb, lanes)
+            abi.orca_profile(sim.ctx, False)
+            sim.set_scene(start)
+            sim.step(1)  # graph capture; the first step from a loaded state has no radius hint
+            abi.orca_profile(sim.ctx, True)
+            ts = []
+            for _ in range(args.ab_steps):
+                sim.step(1)
+                ts.append(float(abi.orca_profile_read(sim.ctx)[2]))
+            c = sim.counters()
+            row[f"{tpb}x{lanes}"] = {"orca_kernel_ms": float(np.mean(ts)),
+                                     "lp3_fraction": c["lp3_agent_steps"] / max(c["agent_steps"], 1)}
+        out[name] = row
+        sim.close()
+    line = {"metric": "ORCA kernel ms per LP mode (one lane / 4-lane LP3 groups / warp work units)",
+            "value": None, "unit": "ms", "n_gpus": 1, "steps": args.ab_steps, "warmup": 1,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": "LP-mode A/B on the 524,288-agent flow (early and later steps), "
+                                   "the 2,097,152-agent dense crowd (k 20) and the eight-way crossing"},
+            "cases": out}
+    print(json.dumps(line), flush=True)
+
+
 def alu_roofline(sim, sc, abi, warmup, steps, main_ms, sms, sm_mhz):
     """Arithmetic roofline of the ORCA kernel: the timed steps replayed (untimed, from the
     same loaded state, so the trajectory is identical) with operation counting on, the
@@ -572,7 +623,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--clocks-out", default=None)
-    ap.add_argument("--workload", choices=["plain", "batched", "adjoint", "crossing"], default="plain")
+    ap.add_argument("--workload", choices=["plain", "batched", "adjoint", "crossing", "lp_ab"],
+                    default="plain")
+    ap.add_argument("--ab-steps", type=int, default=30, help="lp_ab workload: timed steps per mode")
     ap.add_argument("--remove-every", type=int, default=20,
                     help="crossing workload: steps between removals of arrived agents")
     ap.add_argument("--crossing-max-steps", type=int, default=30000)
@@ -589,6 +642,9 @@ def main():
         return
     if args.workload == "crossing" and args.impl == "ours":
         run_crossing(args)
+        return
+    if args.workload == "lp_ab" and args.impl == "ours":
+        run_lp_ab(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

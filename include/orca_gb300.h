@@ -292,9 +292,12 @@ ORCA_API int orca_set_cell_size(orca_ctx* ctx, float cell_size);
 
 /*
  * Launch shape of the per-agent ORCA kernel: threads per CTA (64, 128 or 256; default 128)
- * and lanes that share one agent's least-penetration solve (1 or 4; 0 -> default: 1 for
- * max_neighbors <= 16, else 4).  Results do not depend on it; speed does.  Rebuilds the
- * step graphs.
+ * and the LP mode, lp3_lanes: 1 -- each lane solves its agent's LPs alone; 4 -- groups of
+ * four lanes share one agent's least-penetration solve; 32 -- work units: every lane keeps
+ * its agent's LPs, but the bound evaluations of all the LP1 solves a warp needs at once are
+ * dealt out over its 32 lanes (the paper's load-balanced LP, Section 3); 0 -> default: 1
+ * for max_neighbors <= 16, else 32.  Results are bitwise the same in every mode; speed
+ * differs.  Rebuilds the step graphs.
  */
 ORCA_API int orca_set_launch(orca_ctx* ctx, int32_t threads_per_block, int32_t lp3_lanes);
 

@@ -11,7 +11,7 @@ conditions (an L2 flush, say) while tuning.  Results are cached in a JSON file k
 (agent-count bucket, density bucket, k).
 
 ``tune_launch`` then tries the per-agent kernel's launch shapes (threads per CTA 64 / 128 /
-256, and 1 or 4 lanes per least-penetration solve); ``tune_batch`` does both for a batch of
+256) and LP modes (one lane per solve, 4-lane LP3 groups, warp work units); ``tune_batch`` does both for a batch of
 scenes, where each scene's edge is a common factor times its own expected k-th neighbour
 distance.
 """
@@ -99,7 +99,7 @@ def tune_cell_size(sim: "abi.OrcaSim", scene, steps: int = STEPS, factors=FACTOR
     return {"cell_size": best, "timings_ms": timings, "kth_distance": rk, "cached": False}
 
 
-SHAPES = ((64, 1), (128, 1), (256, 1), (64, 4), (128, 4), (256, 4))
+SHAPES = ((64, 1), (128, 1), (256, 1), (64, 4), (128, 4), (256, 4), (64, 32), (128, 32))
 
 
 def _time_steps(sim, reload, steps, between=None):

@@ -399,8 +399,8 @@ ORCA_API int orca_set_launch(orca_ctx* ctx, int32_t threads_per_block, int32_t l
     if (!ctx) return ORCA_ERR_ARG;
     if (threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256)
         return fail(ctx, ORCA_ERR_ARG, "threads_per_block must be 64, 128 or 256");
-    if (lp3_lanes != 0 && lp3_lanes != 1 && lp3_lanes != 4)
-        return fail(ctx, ORCA_ERR_ARG, "lp3_lanes must be 0 (default), 1 or 4");
+    if (lp3_lanes != 0 && lp3_lanes != 1 && lp3_lanes != 4 && lp3_lanes != 32)
+        return fail(ctx, ORCA_ERR_ARG, "lp3_lanes must be 0 (default), 1, 4 or 32");
     LaunchShape sh{threads_per_block, lp3_lanes ? lp3_lanes : default_lp3_group(ctx->plan.K)};
     if (sh.tpb != ctx->shape.tpb || sh.lp3_group != ctx->shape.lp3_group) {
         ctx->shape = sh;

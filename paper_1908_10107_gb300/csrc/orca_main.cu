@@ -376,6 +376,243 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Work-unit LP: the paper's load-balanced LP (Section 3: the new-velocity computations
+// are cut into equal work units that idle threads take over), built warp-cooperatively.
+// Every lane keeps its own agent's incremental LP.  In each round every lane scans ahead
+// to the next line on which it must run LP1 (or finishes); then the bound evaluations of
+// all those LP1s -- one per earlier line of each -- are dealt out as work units over the
+// warp's 32 lanes, and each LP1's interval is the min / max of its units' bounds
+// (shared-memory atomics on order-preserving integer codes).  The bounds, intervals and
+// every decision are the one-lane solve's, so the results are bitwise equal.  All 32
+// lanes of a warp must call these routines; lanes without a problem only help.
+// ---------------------------------------------------------------------------------
+struct WarpLpShared {  // one per warp
+    int tl[32], tr[32];     // LP1 interval ends, order-preserving integer codes
+    int bad[32];            // LP1 infeasible (empty disc chord or parallel bound)
+    int pre[32];            // exclusive prefix of the lanes' unit counts
+    int base[32];           // LP2: the line LP1 runs on
+    int row[32];            // the owner's half-plane row (float4 offset into s_lines)
+    float4 li[32], qf[32];  // LP3: the line i and the unit bisector LP1 runs on
+};
+
+__device__ __forceinline__ int ord_key(float f) {
+    int k = __float_as_int(f);
+    return k >= 0 ? k : k ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord_val(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+// Exclusive prefix of cnt over the warp into S.pre; returns the warp total.
+__device__ __forceinline__ int units_prefix(WarpLpShared& S, int cnt) {
+    const int lane = threadIdx.x & 31;
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    S.pre[lane] = inc - cnt;
+    return __shfl_sync(0xffffffffu, inc, 31);
+}
+
+// The lane owning unit u: the last lane whose prefix is <= u (it has units).
+__device__ __forceinline__ int unit_owner(const WarpLpShared& S, int u) {
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (S.pre[lo + step] <= u) lo += step;
+    return lo;
+}
+
+// One LP1 bound of line lj on the unit line lb, merged into the owner's interval.
+template <bool kUnit>
+__device__ __forceinline__ void unit_bound(WarpLpShared& S, int o, float4 lb, float4 lj) {
+    float den = lp_det(lb.x, lb.y, lj.x, lj.y);
+    float rhs = lp_rhs(lb, lj);
+    if (parallel_to<kUnit>(den, lj)) {
+        if (rhs > 0.0f) S.bad[o] = 1;
+        return;
+    }
+    float t = __fdividef(-rhs, den);
+    if (den >= 0.0f) atomicMin(&S.tr[o], ord_key(t));
+    else atomicMax(&S.tl[o], ord_key(t));
+}
+
+// The disc's chord on unit line l: opens the lane's interval (or marks it empty).
+__device__ __forceinline__ void open_interval(WarpLpShared& S, int lane, float4 l, float V) {
+    float D = __fmaf_rn(-l.z, l.z, __fmul_rn(V, V));
+    float sq = D < 0.0f ? 0.0f : sqrtf(D);
+    S.tl[lane] = ord_key(-sq);
+    S.tr[lane] = ord_key(sq);
+    S.bad[lane] = D < 0.0f;
+}
+
+// LP2 (objective: closest to o) over the n half-planes of the lane's row; returns n, or
+// the line where LP1 failed (x keeps its last value).  The lp2_dev of one lane, with the
+// LP1 bounds shared out.
+__device__ __forceinline__ int warp_lp2_units(WarpLpShared& S, const float4* s_lines, int row_off,
+                                              bool active, int n, float V, float ox, float oy,
+                                              float& xx, float& xy) {
+    const int lane = threadIdx.x & 31;
+    const float4* row = s_lines + row_off;
+    if (active) {
+        float o2 = lp_dot(ox, oy, ox, oy);
+        if (o2 > __fmul_rn(V, V)) {
+            float sc = __fmul_rn(V, rsqrtf(o2));
+            xx = __fmul_rn(ox, sc);
+            xy = __fmul_rn(oy, sc);
+        } else {
+            xx = ox;
+            xy = oy;
+        }
+    }
+    int i = 0, result = n;
+    bool done = !active;
+#pragma unroll 1
+    for (;;) {
+        bool need = false;
+        float4 li = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (!done) {
+#pragma unroll 1
+            for (; i < n; ++i) {
+                li = row[i];
+                if (lp_viol(li, xx, xy) > 0.0f) {
+                    need = true;
+                    break;
+                }
+            }
+            if (!need) {
+                done = true;
+                result = n;
+            }
+        }
+        if (__ballot_sync(0xffffffffu, need) == 0u) break;
+        const int total = units_prefix(S, need ? i : 0);
+        if (need) {
+            open_interval(S, lane, li, V);
+            S.base[lane] = i;
+            S.row[lane] = row_off;
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int u = lane; u < total; u += 32) {
+            const int o = unit_owner(S, u);
+            const float4* ro = s_lines + S.row[o];
+            unit_bound<true>(S, o, ro[S.base[o]], ro[u - S.pre[o]]);
+        }
+        __syncwarp();
+        if (need) {
+            float tL = ord_val(S.tl[lane]), tR = ord_val(S.tr[lane]);
+            if (S.bad[lane] || tL > tR) {
+                done = true;
+                result = i;
+            } else {
+                float t = fminf(fmaxf(lp_dot(ox, oy, li.y, -li.x), tL), tR);
+                float2 x = lp_point(li, t);
+                xx = x.x;
+                xy = x.y;
+                ++i;
+            }
+        }
+        __syncwarp();
+    }
+    return result;
+}
+
+// LP3 (least penetration) of the lane's queued agent, if it has one: the lp3_dev of one
+// lane (outer scan over the lines, inner direction-mode LP2 over the bisectors), with the
+// bounds of every bisector LP1 shared out.
+__device__ __forceinline__ void warp_lp3_units(WarpLpShared& S, const float4* s_lines, int row_off,
+                                               bool has, int n, int begin, float V, float& xx,
+                                               float& xy) {
+    const int lane = threadIdx.x & 31;
+    const float4* row = s_lines + row_off;
+    float dist = 0.0f, sx = 0.0f, sy = 0.0f;
+    int i = begin, f = 0;
+    bool done = !has, inner = false;
+    float4 li = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 1
+    for (;;) {
+        bool need = false;
+        float4 qraw = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 1
+        while (!done) {
+            if (!inner) {
+                bool hit = false;
+#pragma unroll 1
+                for (; i < n; ++i) {
+                    li = row[i];
+                    if (lp_viol(li, xx, xy) > dist) {
+                        hit = true;
+                        break;
+                    }
+                }
+                if (!hit) {
+                    done = true;
+                    break;
+                }
+                inner = true;
+                f = 0;
+                sx = xx;
+                sy = xy;
+                xx = __fmul_rn(li.x, V);  // direction mode starts at V n_i
+                xy = __fmul_rn(li.y, V);
+            }
+            Bisectors bis{row, li};
+#pragma unroll 1
+            for (; f < i; ++f) {
+                float4 q;
+                if (!bis(f, q)) continue;
+                if (lp_viol(q, xx, xy) > 0.0f) {
+                    need = true;
+                    qraw = q;
+                    break;
+                }
+            }
+            if (need) break;
+            dist = lp_viol(li, xx, xy);  // every bisector holds: the inner LP2 succeeded
+            inner = false;
+            ++i;
+        }
+        if (__ballot_sync(0xffffffffu, need) == 0u) break;
+        const int total = units_prefix(S, need ? f : 0);
+        if (need) {
+            float4 qf = unit_line(qraw);
+            open_interval(S, lane, qf, V);
+            S.li[lane] = li;
+            S.qf[lane] = qf;
+            S.row[lane] = row_off;
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int u = lane; u < total; u += 32) {
+            const int o = unit_owner(S, u);
+            Bisectors bo{s_lines + S.row[o], S.li[o]};
+            float4 qj;
+            if (bo(u - S.pre[o], qj)) unit_bound<false>(S, o, S.qf[o], qj);
+        }
+        __syncwarp();
+        if (need) {
+            float tL = ord_val(S.tl[lane]), tR = ord_val(S.tr[lane]);
+            if (S.bad[lane] || tL > tR) {  // the inner LP2 failed: keep the point from before it
+                xx = sx;
+                xy = sy;
+                dist = lp_viol(li, xx, xy);
+                inner = false;
+                ++i;
+            } else {
+                float4 qf = S.qf[lane];
+                float t = lp_dot(li.x, li.y, qf.y, -qf.x) > 0.0f ? tR : tL;
+                float2 x = lp_point(qf, t);
+                xx = x.x;
+                xy = x.y;
+                ++f;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Insert key into the ascending list kk; its largest entry drops out, and a key not below
 // kk[KMAX-1] leaves the list unchanged.  With c_l = (key < kk[l]) (all independent, and
 // monotone in l because kk is sorted) the new entry l is kk[l-1] if c_{l-1}, else key if
@@ -513,11 +750,12 @@ constexpr int main_min_blocks() {
     return ((KMAX <= 10 ? 28 : (KMAX <= 20 ? 16 : 8)) * 32 + TPB - 1) / TPB;
 }
 
-// Default lanes per queued agent in LP3 (one thread, or a group of four sharing the
-// bisector scans and LP1 bounds).  Measured on the 524,288-agent flow (k = 10): one thread
-// 0.289 ms against 0.353 ms for the group code; with 20-32 half-planes per agent the
-// group's longer scans pay for its ballots and shuffles (the autotuner checks both).
-int default_lp3_group(int kmax) { return kmax <= 16 ? 1 : 4; }
+// Default LP mode: each lane solves alone for k <= 16, warp work units above.  Measured on
+// the 524,288-agent flow (k = 10): one lane 0.135 ms, 4-lane LP3 groups 0.160, work units
+// 0.167; on the 2,097,152-agent dense crowd (k = 20): one lane 1.89 ms, groups 2.00, work
+// units 1.70 -- with 20 half-planes an LP1 has enough bounds to share (the autotuner
+// checks every mode).
+int default_lp3_group(int kmax) { return kmax <= 16 ? 1 : 32; }
 
 template <int KMAX, int TPB>
 constexpr size_t main_smem_bytes() { return sizeof(float4) * TPB * (KMAX + 1); }
@@ -562,6 +800,8 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     __shared__ int s_qn, s_tile;
     __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3;
     __shared__ unsigned long long s_ops[COUNT ? 4 : 1];
+    constexpr bool WU = G == 32;  // work-unit LP (warp-cooperative) instead of per-lane LP
+    __shared__ WarpLpShared s_wlp[WU ? TPB / 32 : 1];
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_cand = 0;
@@ -581,10 +821,20 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         const int t = tile * TPB + tid;
         const bool active = t < a.n;
         float2 p = make_float2(0.0f, 0.0f);
-        float xx = 0.0f, xy = 0.0f, dt = 1.0f;
+        float xx = 0.0f, xy = 0.0f, dt = 1.0f, V = 0.0f, ox = 0.0f, oy = 0.0f;
         uint32_t me = 0;
         int cnt = 0;
         unsigned cand = 0;
+        // an agent whose LP2 failed at line b joins the CTA's least-penetration queue
+        auto enqueue = [&](int b) {
+            int slot = atomicAdd(&s_qn, 1);
+            s_queue[slot] = (unsigned char)tid;
+            s_queued[tid] = 1;
+            s_x[tid] = make_float2(xx, xy);
+            s_b[tid] = (unsigned char)b;
+            s_cnt[tid] = (unsigned char)cnt;
+            s_V[tid] = V;
+        };
         if (active) {
             SceneView sv;
             scene_view(a, t, sv);
@@ -597,7 +847,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             // (no distance grows by more than the two agents' displacements, about 2 V dt);
             // +inf (fewer than k inside r_obs last time) starts at the r_obs bound, NaN (no
             // prediction) at one cell edge
-            float V = a.prm.max_speed[t];
+            V = a.prm.max_speed[t];
             float lim0 = __int_as_float(0x7fffffff);
             if (a.prm.hint) {
                 float hd = sqrtf(a.prm.hint[t]) * (1.0f + 1e-3f) + 3.0f * V * dt + 1e-3f;
@@ -644,22 +894,23 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             // ---- phase 2: preferred velocity (towards the goal at the preferred speed, or
             // onto the goal within one step) and LP2
             float2 o = pref_velocity_dev(p, a.prm.goal[t], a.prm.pref_speed[t], dt, idt);
-            float ox = o.x, oy = o.y;
-            RowLines rl{row};
-            LpTape tape;
-            tape.i = tape.f = tape.bound = tape.j = tape.side = 0;
-            int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy, TAPE ? &tape : nullptr,
-                            COUNT ? &oc : nullptr);
-            if (TAPE) s_tape[tid] = tape;
-            if (b < cnt) {
-                int slot = atomicAdd(&s_qn, 1);
-                s_queue[slot] = (unsigned char)tid;
-                s_queued[tid] = 1;
-                s_x[tid] = make_float2(xx, xy);
-                s_b[tid] = (unsigned char)b;
-                s_cnt[tid] = (unsigned char)cnt;
-                s_V[tid] = V;
+            ox = o.x;
+            oy = o.y;
+            if (!WU) {
+                RowLines rl{row};
+                LpTape tape;
+                tape.i = tape.f = tape.bound = tape.j = tape.side = 0;
+                int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy, TAPE ? &tape : nullptr,
+                                COUNT ? &oc : nullptr);
+                if (TAPE) s_tape[tid] = tape;
+                if (b < cnt) enqueue(b);
             }
+        }
+        if (WU) {
+            // the whole warp runs its LP2s together (lanes past the crowd's end only help)
+            int b = warp_lp2_units(s_wlp[WU ? tid >> 5 : 0], s_lines, tid * KP, active, cnt, V, ox,
+                                   oy, xx, xy);
+            if (active && b < cnt) enqueue(b);
         }
         __syncthreads();
         // ---- phase 3: least penetration for the queued agents, G lanes each.  Queue
@@ -667,15 +918,29 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         // short queue keeps every warp busy instead of filling the first warp and leaving
         // the others waiting at the barrier.
         const int nq = s_qn;
-        constexpr int kGroupsPerWarp = 32 / G, kWarps = TPB / 32;
-        const int gi = tid / G;
+        constexpr int GL = WU ? 1 : G;  // lanes per queue entry
+        constexpr int kGroupsPerWarp = 32 / GL, kWarps = TPB / 32;
+        const int gi = tid / GL;
         const int q0 = (gi % kGroupsPerWarp) * kWarps + gi / kGroupsPerWarp;
-        for (int q = q0; q < nq; q += TPB / G) {
+        if (WU) {
+            // every lane of every warp takes part in each round (warp-uniform trip count)
+#pragma unroll 1
+            for (int q1 = 0; q1 < nq; q1 += TPB) {
+                const int q = q1 + q0;
+                const bool has = q < nq;
+                const int ag = has ? s_queue[q] : 0;
+                float2 x = has ? s_x[ag] : make_float2(0.0f, 0.0f);
+                warp_lp3_units(s_wlp[WU ? tid >> 5 : 0], s_lines, ag * KP, has, has ? s_cnt[ag] : 0,
+                               has ? s_b[ag] : 0, has ? s_V[ag] : 0.0f, x.x, x.y);
+                if (has) s_x[ag] = x;
+            }
+        }
+        for (int q = q0; !WU && q < nq; q += TPB / GL) {
             int ag = s_queue[q];
             float2 x = s_x[ag];
             if (G == 1) lp3_dev(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y,
                                 TAPE ? &s_tape[TAPE ? ag : 0] : nullptr, COUNT ? &oc : nullptr);
-            else lp3_group_dev<G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
+            else lp3_group_dev<WU ? 4 : G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
             if ((tid & (G - 1)) == 0) s_x[ag] = x;
         }
         __syncthreads();
@@ -764,6 +1029,10 @@ static cudaError_t launch_main_k(const MainArgs& a, int grid_blocks, cudaStream_
 // return the resident CTA count instead of launching.
 template <int KMAX, int TPB>
 static cudaError_t dispatch_g(const MainArgs& a, int g, int grid_blocks, cudaStream_t st, int* resident) {
+    if (g == 32) {
+        if (resident) { *resident = resident_blocks_k<KMAX, TPB, 32>(); return cudaSuccess; }
+        return launch_main_k<KMAX, TPB, 32>(a, grid_blocks, st);
+    }
     if (g == 4) {
         if (resident) { *resident = resident_blocks_k<KMAX, TPB, 4>(); return cudaSuccess; }
         return launch_main_k<KMAX, TPB, 4>(a, grid_blocks, st);

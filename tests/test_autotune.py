@@ -52,7 +52,7 @@ def fake(monkeypatch):
 
 
 SHAPE_MS = {(64, 1): 0.01, (128, 1): 0.0, (256, 1): 0.03, (64, 4): 0.02, (128, 4): 0.04,
-            (256, 4): 0.05}
+            (256, 4): 0.05, (64, 32): 0.015, (128, 32): 0.025}
 
 
 def test_expected_kth_distance_uniform():

@@ -234,6 +234,32 @@ def test_counters():
     assert c["candidates"] >= c["lines"]
 
 
+@pytest.mark.parametrize("scene", ["flow", "dense20", "circle"])
+def test_lp_modes_agree_bitwise(scene):
+    # one lane per solve, four-lane groups and warp work units take the same decisions
+    # with the same roundings: identical states after several steps
+    if scene == "flow":
+        sc = S.jitter_velocities(S.bidirectional(8190, seed=17), 17)
+    elif scene == "dense20":
+        sc = S.dense(20011, seed=18)
+        sc.max_neighbors = 20
+        sc = S.jitter_velocities(sc, 18)
+    else:
+        sc = S.circle_swap()
+    states = {}
+    for tpb, lanes in ((64, 1), (128, 4), (64, 32), (256, 32)):
+        sim = parity.make_sim(sc, flags=0)
+        abi.orca_set_launch(sim.ctx, tpb, lanes)
+        sim.set_scene(sc)
+        sim.step(12)
+        states[(tpb, lanes)] = sim.get_state()
+        sim.close()
+    ref = states[(64, 1)]
+    for key, (pos, vel) in states.items():
+        np.testing.assert_array_equal(pos, ref[0], err_msg=str(key))
+        np.testing.assert_array_equal(vel, ref[1], err_msg=str(key))
+
+
 def test_operation_counts_match_the_oracle():
     # the counting launch counts the LP operations the oracle counts on the same state
     # (they can differ only where an FP32 decision differs from the FP64 one), and
