@@ -582,6 +582,51 @@ def run_lp_ab(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dense(args):
+    """The dense stress crowd (2,097,152 agents uniform in 2 km x 2 km, r 0.4 m, v_max 1.5
+    m/s, r_obs 8 m, tau 4 s, dt 1/60 s): k = 10 and 20, each over the cell edges 1, 2, 4 and
+    8 m and the autotuned edge, L2 flushed between steps, CUDA events on the stream."""
+    import torch
+    from paper_1908_10107_gb300 import abi, autotune, scenarios
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    base = scenarios.dense()
+    n = base.n
+    results = {}
+    for k in (10, 20):
+        sc = base.copy()
+        sc.max_neighbors = k
+        sim = abi.OrcaSim.for_scene(sc)
+        sim.set_scene(sc)
+        tune = autotune.tune_cell_size(sim, sc, use_cache=False, cache_path=None,
+                                       between=lambda: flush.fill_(0x5a))
+        shape = autotune.tune_launch(sim, lambda: sim.set_scene(sc),
+                                     between=lambda: flush.fill_(0x5a))
+        row = {"tuned_cell_m": tune["cell_size"], "tuned_shape": list(shape["shape"])}
+        for cs in (1.0, 2.0, 4.0, 8.0, tune["cell_size"]):
+            abi.orca_set_cell_size(sim.ctx, cs)
+            sim.set_scene(sc)
+            ms = timed_steps(torch, lambda: sim.step(1), args.dense_steps, args.warmup, flush, stream)
+            key = "tuned" if cs == tune["cell_size"] else f"{cs:g}m"
+            row[key] = {"ms_per_step": ms / args.dense_steps,
+                        "agent_steps_per_s": n * args.dense_steps / (ms * 1e-3)}
+        c = sim.counters()
+        row["lp3_fraction"] = c["lp3_agent_steps"] / max(c["agent_steps"], 1)
+        results[f"k{k}"] = row
+        sim.close()
+    best = max(r["tuned"]["agent_steps_per_s"] for r in results.values())
+    line = {"metric": "dense-crowd ORCA agent-steps/sec (2,097,152 agents)", "value": best,
+            "unit": UNIT, "n_gpus": 1, "steps": args.dense_steps, "warmup": args.warmup,
+            "ms_per_step": n / best * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": "dense stress: 2,097,152 agents uniform in 2 km x 2 km, goals "
+                                   "uniform, r 0.4 m, v_max 1.5 m/s, r_obs 8 m, k 10 / 20, tau 4 s, "
+                                   "dt 1/60 s; cell edge swept", "l2": "flushed between steps"},
+            "results": results}
+    print(json.dumps(line), flush=True)
+
+
 def alu_roofline(sim, sc, abi, warmup, steps, main_ms, sms, sm_mhz):
     """Arithmetic roofline of the ORCA kernel: the timed steps replayed (untimed, from the
     same loaded state, so the trajectory is identical) with operation counting on, the
@@ -623,8 +668,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--clocks-out", default=None)
-    ap.add_argument("--workload", choices=["plain", "batched", "adjoint", "crossing", "lp_ab"],
-                    default="plain")
+    ap.add_argument("--workload", choices=["plain", "batched", "adjoint", "crossing", "lp_ab",
+                                           "dense"], default="plain")
+    ap.add_argument("--dense-steps", type=int, default=100, help="dense workload: timed steps")
     ap.add_argument("--ab-steps", type=int, default=30, help="lp_ab workload: timed steps per mode")
     ap.add_argument("--remove-every", type=int, default=20,
                     help="crossing workload: steps between removals of arrived agents")
@@ -645,6 +691,9 @@ def main():
         return
     if args.workload == "lp_ab" and args.impl == "ours":
         run_lp_ab(args)
+        return
+    if args.workload == "dense" and args.impl == "ours":
+        run_dense(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))
