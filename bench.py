@@ -728,6 +728,14 @@ def main():
         tune = autotune.tune_cell_size(sim, sc, use_cache=False, cache_path=None,
                                        between=flush_l2)
         args.cell_size = tune["cell_size"]
+    # a cell table sized to the tuned grid: the step graph then provisions only the radix
+    # passes the grid needs (two for the 1 km flow at ~2 m cells, instead of the three a
+    # 4n-cell table provisions)
+    cap = autotune.radix_capacity(sc, args.cell_size)
+    if cap < (sim.params.max_cells or min(max(4 * sc.n, 65536), 1 << 30)):
+        sim.close()
+        sim = abi.OrcaSim.for_scene(sc, cell_size=args.cell_size, max_cells=cap)
+        sim.set_scene(sc)
     if args.tpb:
         abi.orca_set_launch(sim.ctx, args.tpb, args.lanes)
         shape = {"shape": (args.tpb, args.lanes), "timings_ms": None}
@@ -773,6 +781,7 @@ def main():
     hbm_peak, peak_kind = peaks()
     _, gf, gi = None, None, None
     c_cells = int(sim.params.max_cells) or min(max(4 * n, 65536), 1 << 30)
+    sim_cap = c_cells
     achieved = ORCA_KERNEL_BYTES_PER_AGENT * n / (main_ms * 1e-3) / 1e9
     traffic = profiled_traffic()
     counters = sim.counters()
@@ -843,6 +852,7 @@ def main():
         "config": {"workload": WORKLOAD, "n_agents": n, "replicas": world,
                    "cell_size_m": float(gf[2]) if gf is not None else None,
                    "grid": [int(gi[0]), int(gi[1])] if gi is not None else None,
+                   "cell_table_capacity": int(sim_cap),
                    "l2": "flushed between steps (256 MiB write); per-step CUDA events summed",
                    "graph": "one CUDA graph replay per step",
                    "cell_size_tuning_ms": ({f"{k:.4g}": round(v, 4) for k, v in tune["timings_ms"].items()}

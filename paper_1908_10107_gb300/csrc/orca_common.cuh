@@ -23,7 +23,7 @@ constexpr int kRadixBits = 9;
 constexpr int kBlockCounters = 8;
 constexpr int kRadixBuckets = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;  // items per thread per tile
+constexpr int kSortItems = 4;  // items per thread per tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kBboxBlocks = 304;  // 2 x 152 SMs
 
