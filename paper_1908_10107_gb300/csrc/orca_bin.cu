@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(256) bbox_grid_kernel(int n, const float2* __r
                                                         float cell_size, long long max_cells,
                                                         int max_passes, float4* partials,
                                                         DeviceMisc* misc) {
+    pdl_wait();
     float xmin = INFINITY, ymin = INFINITY, xmax = -INFINITY, ymax = -INFINITY;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float2 p = pos[i];
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(kSortThreads) keys_hist_kernel(int n, const fl
                                                                  const int* __restrict__ slot_scene,
                                                                  uint32_t* __restrict__ keys,
                                                                  uint32_t* __restrict__ hist) {
+    pdl_wait();
     __shared__ uint32_t s_hist[kRadixBuckets];
     for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) s_hist[d] = 0;
     __syncthreads();
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(int n, int 
                                                                      const DeviceMisc* __restrict__ misc,
                                                                      const uint32_t* __restrict__ keys,
                                                                      uint32_t* __restrict__ hist) {
+    pdl_wait();
     if (pass >= misc->grid.passes) return;
     __shared__ uint32_t s_hist[kRadixBuckets];
     for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) s_hist[d] = 0;
@@ -211,6 +214,7 @@ __global__ void __launch_bounds__(kScanWarps * 32) radix_scan_kernel(int nblocks
                                                                      const DeviceMisc* __restrict__ misc,
                                                                      uint32_t* __restrict__ hist,
                                                                      uint32_t* __restrict__ totals) {
+    pdl_wait();
     if (pass >= misc->grid.passes) return;
     int lane = threadIdx.x & 31;
     int d = blockIdx.x * kScanWarps + (threadIdx.x >> 5);
@@ -240,6 +244,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ offsets,
     const uint32_t* __restrict__ totals) {
+    pdl_wait();
     if (pass >= misc->grid.passes) return;
     constexpr int kWarps = kSortThreads / 32;
     constexpr int kPer = kRadixBuckets / kSortThreads;  // digits per thread below
@@ -327,6 +332,7 @@ __global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __r
                                                       uint32_t* __restrict__ cell_start,
                                                       AgentState src_s, Sorted dst_s,
                                                       AgentParams src_p, AgentParams dst_p) {
+    pdl_wait();
     const GridDev& g = misc->grid;
     const uint32_t* vals = (g.passes & 1) ? vals_b : vals_a;
     const uint32_t* keys = (g.passes & 1) ? keys_b : keys_a;
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(256) iota_kernel(int n, uint32_t* __restrict__
 // ---------------------------------------------------------------------------------
 int sort_blocks(int n) { return (n + kSortTile - 1) / kSortTile; }
 
-void launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cudaStream_t st);
+cudaError_t launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cudaStream_t st);
 
 cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_passes,
                            const AgentState& cur, const BinBuffers& b, cudaStream_t st) {
@@ -409,36 +415,46 @@ cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_
     if (nb_bbox > kBboxBlocks) nb_bbox = kBboxBlocks;
     bbox_grid_kernel<<<nb_bbox, 256, 0, st>>>(n, cur.pos, cell_size, max_cells, max_passes,
                                               b.bbox_partials, b.misc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     int nsb = sort_blocks(n);
-    keys_hist_kernel<<<nsb, kSortThreads, 0, st>>>(n, cur.pos, b.misc, nullptr, nullptr, b.keys[0],
-                                                   b.hist);
-    launch_radix_passes(n, nsb, max_passes, b, st);
-    return cudaGetLastError();
+    e = launch_pdl(keys_hist_kernel, nsb, kSortThreads, 0, st, n, (const float2*)cur.pos,
+                   (const DeviceMisc*)b.misc, (const SceneDev*)nullptr, (const int*)nullptr,
+                   b.keys[0], b.hist);
+    if (e != cudaSuccess) return e;
+    return launch_radix_passes(n, nsb, max_passes, b, st);
 }
 
 // Radix passes over the keys written by keys_hist (the reorder kernel builds the cell table).
-void launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cudaStream_t st) {
+cudaError_t launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cudaStream_t st) {
+    const DeviceMisc* misc = b.misc;
     for (int pass = 0; pass < max_passes; ++pass) {
         int src = pass & 1, dst = src ^ 1;
+        cudaError_t e = cudaSuccess;
         if (pass > 0)
-            radix_upsweep_kernel<<<nsb, kSortThreads, 0, st>>>(n, pass, b.misc, b.keys[src], b.hist);
-        radix_scan_kernel<<<kRadixBuckets / kScanWarps, kScanWarps * 32, 0, st>>>(
-            nsb, pass, b.misc, b.hist, b.digit_totals);
-        radix_downsweep_kernel<<<nsb, kSortThreads, 0, st>>>(
-            n, pass, b.misc, b.keys[src], pass == 0 ? nullptr : b.vals[src], b.keys[dst],
-            b.vals[dst], b.hist, b.digit_totals);
+            e = launch_pdl(radix_upsweep_kernel, nsb, kSortThreads, 0, st, n, pass, misc,
+                           (const uint32_t*)b.keys[src], b.hist);
+        if (e == cudaSuccess)
+            e = launch_pdl(radix_scan_kernel, kRadixBuckets / kScanWarps, kScanWarps * 32, 0, st, nsb,
+                           pass, misc, b.hist, b.digit_totals);
+        if (e == cudaSuccess)
+            e = launch_pdl(radix_downsweep_kernel, nsb, kSortThreads, 0, st, n, pass, misc,
+                           (const uint32_t*)b.keys[src],
+                           (const uint32_t*)(pass == 0 ? nullptr : b.vals[src]), b.keys[dst],
+                           b.vals[dst], (const uint32_t*)b.hist, (const uint32_t*)b.digit_totals);
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
 
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
                            const Sorted& dst_s, const AgentParams& src_p,
                            const AgentParams& dst_p, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    reorder_kernel<<<(n + 256 * kReorderR - 1) / (256 * kReorderR), 256, 0, st>>>(
-                                                    n, b.vals[0], b.vals[1], b.keys[0], b.keys[1],
-                                                    b.misc, b.cell_start, src_s, dst_s, src_p,
-                                                    dst_p);
-    return cudaGetLastError();
+    return launch_pdl(reorder_kernel, (n + 256 * kReorderR - 1) / (256 * kReorderR), 256, 0, st, n,
+                      (const uint32_t*)b.vals[0], (const uint32_t*)b.vals[1],
+                      (const uint32_t*)b.keys[0], (const uint32_t*)b.keys[1],
+                      (const DeviceMisc*)b.misc, b.cell_start, src_s, dst_s, src_p, dst_p);
 }
 
 cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, float2* pos_out,
@@ -462,6 +478,7 @@ cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st) {
 __global__ void __launch_bounds__(1024) scene_bbox_grid_kernel(const float2* __restrict__ pos,
                                                                SceneDev* scenes, int max_passes,
                                                                DeviceMisc* misc) {
+    pdl_wait();
     SceneDev* sc = scenes + blockIdx.x;
     const int off = sc->off, cnt = sc->cnt;
     float4 r = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
@@ -501,6 +518,7 @@ __global__ void __launch_bounds__(1024) scene_bbox_grid_kernel(const float2* __r
 // radix passes it needs; resets the persistent kernel's tile counter.
 __global__ void __launch_bounds__(1024) scene_prefix_kernel(int n_scenes, SceneDev* scenes,
                                                             int max_passes, DeviceMisc* misc) {
+    pdl_wait();
     __shared__ long long s_sum[1024];
     int per = (n_scenes + blockDim.x - 1) / blockDim.x;
     int s0 = threadIdx.x * per, s1 = min(s0 + per, n_scenes);
@@ -557,12 +575,16 @@ cudaError_t launch_binning_batch(int n, int n_scenes, SceneDev* scenes, const in
                                  int max_passes, const AgentState& cur, const BinBuffers& b,
                                  cudaStream_t st) {
     scene_bbox_grid_kernel<<<n_scenes, 1024, 0, st>>>(cur.pos, scenes, max_passes, b.misc);
-    scene_prefix_kernel<<<1, 1024, 0, st>>>(n_scenes, scenes, max_passes, b.misc);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_pdl(scene_prefix_kernel, 1, 1024, 0, st, n_scenes, scenes, max_passes, b.misc);
     int nsb = sort_blocks(n);
-    keys_hist_kernel<<<nsb, kSortThreads, 0, st>>>(n, cur.pos, b.misc, scenes, slot_scene,
-                                                   b.keys[0], b.hist);
-    launch_radix_passes(n, nsb, max_passes, b, st);
-    return cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_pdl(keys_hist_kernel, nsb, kSortThreads, 0, st, n, (const float2*)cur.pos,
+                       (const DeviceMisc*)b.misc, (const SceneDev*)scenes, slot_scene, b.keys[0],
+                       b.hist);
+    if (e != cudaSuccess) return e;
+    return launch_radix_passes(n, nsb, max_passes, b, st);
 }
 
 }  // namespace orca

@@ -180,6 +180,33 @@ cudaError_t launch_axpy2(int n, float2* y, const float2* x, cudaStream_t st);
 
 // Cell coordinate along one axis in FP32, one rounding per operation:
 // floor(fl(fl(v - vmin) * inv)) clamped to [0, g - 1].
+// Programmatic dependent launch (sm_90+): the kernels of a step are launched with the
+// programmatic-serialisation attribute, so the launch of the next kernel is prepared while
+// the current one runs; each step kernel starts with pdl_wait(), which blocks until the
+// preceding kernel of the stream has completed and its writes are visible (a no-op without
+// such a dependency).  No kernel releases its dependents early: measured on the
+// 524,288-agent flow, dependents made resident before their predecessor finished slowed
+// the step (0.2111 ms) against the release at completion (0.2072 ms; 0.2086 without the
+// attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch with the programmatic-stream-serialisation attribute (see pdl_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __device__ __forceinline__ int cell_coord(float v, float vmin, float inv, int g) {
     float q = __fmul_rn(__fsub_rn(v, vmin), inv);
     int c = __float2int_rd(q);

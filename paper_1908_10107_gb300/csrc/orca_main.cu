@@ -788,6 +788,7 @@ __device__ __forceinline__ void scene_view(const MainArgs& a, int t, SceneView& 
 // tiles taken from a per-step counter (with one CTA per tile this loop runs once).
 template <int KMAX, int TPB, int G, bool TAPE = false, bool COUNT = false>
 __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_kernel(MainArgs a) {
+    pdl_wait();
     constexpr int KP = KMAX + 1;  // padded rows: conflict-free float4 accesses
     extern __shared__ float4 s_lines[];  // TPB * KP half-planes
     __shared__ float2 s_x[TPB];
@@ -1021,8 +1022,7 @@ static cudaError_t launch_main_k(const MainArgs& a, int grid_blocks, cudaStream_
     if (e != cudaSuccess) return e;
     int nb = (a.n + TPB - 1) / TPB;
     if (grid_blocks > 0 && grid_blocks < nb) nb = grid_blocks;
-    orca_main_kernel<KMAX, TPB, G><<<nb, TPB, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(orca_main_kernel<KMAX, TPB, G>, nb, TPB, smem, st, a);
 }
 
 // Dispatch over (k bound, threads per CTA, LP3 lanes per agent).  resident != null:
@@ -1057,8 +1057,7 @@ static cudaError_t launch_count_k(const MainArgs& a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(orca_main_kernel<KMAX, 128, 1, false, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    orca_main_kernel<KMAX, 128, 1, false, true><<<(a.n + 127) / 128, 128, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(orca_main_kernel<KMAX, 128, 1, false, true>, (a.n + 127) / 128, 128, smem, st, a);
 }
 
 template <int KMAX>
@@ -1067,8 +1066,7 @@ static cudaError_t launch_tape_k(const MainArgs& a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(orca_main_kernel<KMAX, 128, 1, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    orca_main_kernel<KMAX, 128, 1, true><<<(a.n + 127) / 128, 128, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(orca_main_kernel<KMAX, 128, 1, true>, (a.n + 127) / 128, 128, smem, st, a);
 }
 
 static cudaError_t dispatch(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
