@@ -81,6 +81,13 @@ def _bind(lib):
                                 c.c_int, _F64P, _F64P, c.c_void_p, c.c_void_p, c.c_void_p,
                                 c.c_void_p, c.c_int, c.c_void_p])
     lib.oracle_step.restype = c.c_int
+    lib.oracle_step_obstacles.argtypes = lib.oracle_step.argtypes + [c.c_int, c.c_void_p, c.c_double,
+                                                                     c.c_int, c.c_void_p]
+    lib.oracle_step_obstacles.restype = c.c_int
+    lib.oracle_solve_fixed.argtypes = [_F64P, c.c_int, c.c_int, c.c_double, _F64P, _F64P]
+    lib.oracle_solve_fixed.restype = c.c_int
+    lib.oracle_obstacle_line.argtypes = [_F64P, c.c_double, _F64P, c.c_double, c.c_double, _F64P]
+    lib.oracle_obstacle_line.restype = c.c_int
     lib.oracle_arrived.argtypes = [c.c_int, _F32P, _F32P, _F32P, _I32P]
     lib.oracle_arrived.restype = c.c_int
     lib.oracle_max_threads.argtypes = []
@@ -186,8 +193,13 @@ def solve(lines, V: float, o):
 def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_dist: float,
          max_neighbors: int, dt: float, knn_mode: int = 1, fp64_knn: bool = False,
          gf=None, gi=None, nthreads: int | None = None, subset=None,
-         sensitivity: bool = False):
+         sensitivity: bool = False, obstacles=None, obstacle_time_horizon: float = 2.0,
+         max_obstacle_neighbors: int = 4):
     """One synchronous ORCA step (Sections 2-3) in FP64.
+
+    ``obstacles``: optional static segments, float[m, 4] (x1, y1, x2, y2); each agent
+    takes the ``max_obstacle_neighbors`` nearest reachable ones as hard half-planes (see
+    the C source) and the result gains ``obst`` (int32[rows, max_obstacle_neighbors]).
 
     Arrays are promoted to float64.  With ``subset`` (agent indices) only those agents are
     stepped -- their neighbours are still searched among all agents -- and output row q
@@ -215,20 +227,32 @@ def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_d
     if gf is not None:
         gf = np.ascontiguousarray(gf, np.float32)
         gi = np.ascontiguousarray(gi, np.int32)
-    r = _load().oracle_step(n, pos, vel, goal, radius, max_speed, pref_speed, time_horizon,
-                            float(neighbor_dist), k, float(dt), int(knn_mode), int(bool(fp64_knn)),
-                            _ptr(gf), _ptr(gi), _ptr(subset), int(rows),
-                            int(nthreads or max_threads()), pos_out, vel_out,
-                            _ptr(nbr), _ptr(status), _ptr(margin), _ptr(counters),
-                            int(bool(sensitivity)), _ptr(sens))
+    common = (n, pos, vel, goal, radius, max_speed, pref_speed, time_horizon,
+              float(neighbor_dist), k, float(dt), int(knn_mode), int(bool(fp64_knn)),
+              _ptr(gf), _ptr(gi), _ptr(subset), int(rows), int(nthreads or max_threads()),
+              pos_out, vel_out, _ptr(nbr), _ptr(status), _ptr(margin), _ptr(counters),
+              int(bool(sensitivity)), _ptr(sens))
+    obst = None
+    if obstacles is None:
+        r = _load().oracle_step(*common)
+    else:
+        seg = np.ascontiguousarray(np.asarray(obstacles, np.float64).reshape(-1))
+        ko = int(max_obstacle_neighbors)
+        obst = np.full(max(rows * max(ko, 1), 1), -1, np.int32)
+        r = _load().oracle_step_obstacles(*common, seg.size // 4, _ptr(seg),
+                                          float(obstacle_time_horizon), ko, _ptr(obst))
     if r != 0:
         raise ValueError(f"oracle_step failed ({r})")
-    return {
+    out = {
         "pos": pos_out[: 2 * rows].reshape(rows, 2), "vel": vel_out[: 2 * rows].reshape(rows, 2),
         "nbr": nbr[: rows * k].reshape(rows, k), "lp3": status[:rows].astype(bool),
         "margin": margin[:rows], "sens": sens[:rows],
         "counters": dict(zip(COUNTER_NAMES, (int(c) for c in counters))),
     }
+    if obst is not None:
+        ko = max(int(max_obstacle_neighbors), 1)
+        out["obst"] = obst[: rows * ko].reshape(rows, ko)
+    return out
 
 
 # operation counts of oracle_step, summed over the stepped agents: candidates scanned,
@@ -236,6 +260,26 @@ def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_d
 # evaluated, LP2/LP3 violation checks, LP3 bisectors formed
 COUNTER_NAMES = ("scanned", "lines", "lp1_calls", "lp3_agents", "lp1_bounds", "lp_checks",
                  "bisectors")
+
+
+def obstacle_line(p, r, seg, time_horizon: float, dt: float):
+    """Obstacle half-plane of an agent at p with radius r against segment seg (x1, y1,
+    x2, y2): ((Px, Py, dx, dy), overlapping)."""
+    line4 = np.zeros(4)
+    ov = _load().oracle_obstacle_line(np.asarray(p, np.float64), float(r),
+                                      np.asarray(seg, np.float64), float(time_horizon), float(dt), line4)
+    return line4, bool(ov)
+
+
+def solve_fixed(lines, nobst: int, V: float, o):
+    """LP2 then LP3 with the first nobst lines hard (static obstacles); lines: [n, 4]."""
+    lines = np.ascontiguousarray(np.asarray(lines, np.float64).reshape(-1))
+    x = np.zeros(2)
+    r = _load().oracle_solve_fixed(lines, lines.size // 4, int(nobst), float(V),
+                                   np.asarray(o, np.float64), x)
+    if r < 0:
+        raise ValueError("oracle_solve_fixed failed")
+    return x, bool(r)
 
 
 def arrived(pos, goal, radius) -> np.ndarray:
@@ -261,6 +305,10 @@ def remove_arrived(scene):
 
 def step_scene(scene, **kw):
     """oracle step on a ``scenarios.Scene``'s current state."""
+    obs = getattr(scene, "obstacles", None)
+    if obs is not None and "obstacles" not in kw:
+        kw = dict(kw, obstacles=obs, obstacle_time_horizon=scene.obstacle_time_horizon,
+                  max_obstacle_neighbors=scene.max_obstacle_neighbors)
     return step(scene.pos, scene.vel, scene.goal, scene.radius, scene.max_speed,
                 scene.pref_speed, scene.time_horizon, scene.neighbor_dist,
                 scene.max_neighbors, scene.dt, **kw)

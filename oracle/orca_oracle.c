@@ -390,13 +390,15 @@ static int lp2(const line2* L, int n, double V, v2 o, int dir_opt, v2* x, tags* 
 
 /* LP3: least-penetration fallback (Section 3).  Minimises, over the disc, the largest
  * violation max_i det(d_i, P_i - x), starting from line `begin` with penetration 0.
+ * The first nobst lines (static obstacles) are hard constraints: they are copied into
+ * every projected problem unchanged, and only the other lines get bisectors.
  * When line i is violated by more than the current penetration, the optimum lies on
  * the set where line i's violation equals the others'; each earlier line j gives the
  * bisecting half-plane (through the intersection of lines i and j, direction
  * normalise(d_j - d_i); parallel lines of opposite direction give the midline, parallel
  * lines of the same direction give no constraint), and LP2 in direction mode maximises
  * progress along the normal (-d_i.y, d_i.x).  A numerically failed LP2 keeps x. */
-static void lp3(const line2* L, int n, int begin, double V, v2* x, tags* tg,
+static void lp3(const line2* L, int n, int nobst, int begin, double V, v2* x, tags* tg,
                 lpcount* work) {
     (void)tg;
     line2 proj[OR_MAXK];
@@ -405,8 +407,11 @@ static void lp3(const line2* L, int n, int begin, double V, v2* x, tags* tg,
         double pen = det2(L[i].d, sub(L[i].P, *x));
         if (work) ++work->checks;
         if (pen > dist) {
+            /* the first nobst lines (static obstacles) stay hard constraints: they enter
+               the projected problem unchanged; bisectors come from the others */
             int m = 0;
-            for (int j = 0; j < i; ++j) {
+            for (int j = 0; j < nobst && j < OR_MAXK; ++j) proj[m++] = L[j];
+            for (int j = nobst; j < i; ++j) {
                 line2 q;
                 double den = det2(L[i].d, L[j].d);
                 if (fabs(den) <= OR_EPS) {
@@ -420,7 +425,7 @@ static void lp3(const line2* L, int n, int begin, double V, v2* x, tags* tg,
                 proj[m++] = q;
             }
             v2 keep = *x;
-            if (work) work->bisectors += i;
+            if (work) work->bisectors += i > nobst ? i - nobst : 0;
             if (lp2(proj, m, V, mk(-L[i].d.y, L[i].d.x), 1, x, tg, work) < m) *x = keep;
             dist = det2(L[i].d, sub(L[i].P, *x));
         }
@@ -461,14 +466,28 @@ int oracle_lp2(const double* lines, int n, double V, const double* o, int dir_op
     return r;
 }
 
+int oracle_solve_fixed(const double* lines, int n, int nobst, double V, const double* o,
+                       double* x2);
+
+/* Obstacle half-plane of an agent at p (px, py) with radius r against a segment
+ * (x1, y1, x2, y2): line4 = {Px, Py, dx, dy}; returns 1 if the agent overlaps it. */
+int oracle_obstacle_line(const double* p, double r, const double* seg, double tau_o, double dt,
+                         double* line4);
+
 /* Full velocity selection: LP2, then LP3 from the failing line.  Returns 1 if LP3 ran. */
 int oracle_solve(const double* lines, int n, double V, const double* o, double* x2) {
+    return oracle_solve_fixed(lines, n, 0, V, o, x2);
+}
+
+/* As oracle_solve, with the first nobst lines hard (static obstacles) in LP3. */
+int oracle_solve_fixed(const double* lines, int n, int nobst, double V, const double* o,
+                       double* x2) {
     line2 L[OR_MAXK];
-    if (n < 0 || n > OR_MAXK) return -1;
+    if (n < 0 || n > OR_MAXK || nobst < 0 || nobst > n) return -1;
     unpack(lines, n, L);
     v2 x;
     int b = lp2(L, n, V, mk(o[0], o[1]), 0, &x, NULL, NULL);
-    if (b < n) lp3(L, n, b, V, &x, NULL, NULL);
+    if (b < n) lp3(L, n, nobst, b, V, &x, NULL, NULL);
     x2[0] = x.x; x2[1] = x.y;
     return b < n;
 }
@@ -480,6 +499,78 @@ static v2 pref_velocity(v2 p, v2 goal, double pref_speed, double dt) {
     double dist = len(g);
     if (dist > pref_speed * dt) return scl(g, pref_speed / dist);
     return scl(g, 1.0 / dt);
+}
+
+/* ----------------------------------------------------------------------------------
+ * Static obstacles (line segments; not in the paper's experiments -- the ORCA rule for
+ * obstacles of van den Berg et al., which the paper defers to).  The optimisation
+ * velocity for an obstacle is 0 and the agent takes full responsibility, so the half-plane
+ * follows from the point of the truncated velocity obstacle nearest the origin.  With q
+ * the point of the segment nearest the agent (relative to it) and d = |q|, that point is
+ * (d - r) q / (d tau_o), and the permitted velocities are v.q/d <= (d - r)/tau_o: along
+ * the direction to the segment the agent may close at most d - r within tau_o.  (The
+ * segment lies beyond the supporting line through its nearest point, so such a velocity
+ * keeps the agent at least r from it for tau_o.)  An agent already closer than r uses dt
+ * in place of tau_o (it must open the gap within one step), like overlapping agents; an
+ * agent exactly on the segment takes the segment's left normal.  In normal form:
+ * n = -q/d, c = -(d - r)/tau_o (or -(d - r)/dt).
+ *
+ * Which segments: those whose FP32 squared distance (nearest point by the clamped
+ * projection, one rounding per operation) is strictly below fl(fl(V tau_o) + r)^2, the
+ * segments the agent could reach within tau_o; the kobst nearest by (d^2, segment index).
+ * -------------------------------------------------------------------------------- */
+static float seg_dist2_f32(const float* sg, float px, float py) {
+    float ex = sg[2] - sg[0], ey = sg[3] - sg[1];
+    float wx = px - sg[0], wy = py - sg[1];
+    float exx = ex * ex, eyy = ey * ey;
+    float l2 = exx + eyy;
+    float t = 0.0f;
+    if (l2 > 0.0f) {
+        float wex = wx * ex, wey = wy * ey;
+        float pr = wex + wey;
+        t = pr / l2;
+        t = t < 0.0f ? 0.0f : (t > 1.0f ? 1.0f : t);
+    }
+    float tex = t * ex, tey = t * ey;
+    float cx = sg[0] + tex, cy = sg[1] + tey;
+    float qx = cx - px, qy = cy - py;
+    float qxx = qx * qx, qyy = qy * qy;
+    return qxx + qyy;
+}
+
+static line2 obstacle_line(v2 pa, double ra, const double* sg, double tau_o, double dt,
+                           tags* tg) {
+    v2 a = mk(sg[0], sg[1]), e = mk(sg[2] - sg[0], sg[3] - sg[1]);
+    double l2 = dot(e, e), t = 0.0;
+    if (l2 > 0.0) {
+        t = dot(sub(pa, a), e) / l2;
+        t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    }
+    v2 q = sub(add(a, scl(e, t)), pa);
+    double d = len(q);
+    v2 n;
+    double c;
+    note(tg, d, ra, ra);  /* overlap or not */
+    if (d > 0.0) n = scl(q, -1.0 / d);
+    else n = l2 > 0.0 ? scl(mk(-e.y, e.x), 1.0 / sqrt(l2)) : mk(1.0, 0.0);
+    c = d > ra ? -(d - ra) / tau_o : -(d - ra) / dt;
+    line2 L;
+    L.d = mk(n.y, -n.x);
+    L.P = scl(n, c);
+    return L;
+}
+
+int oracle_obstacle_line(const double* p, double r, const double* seg, double tau_o, double dt,
+                         double* line4) {
+    line2 L = obstacle_line(mk(p[0], p[1]), r, seg, tau_o, dt, NULL);
+    line4[0] = L.P.x; line4[1] = L.P.y; line4[2] = L.d.x; line4[3] = L.d.y;
+    v2 a = mk(seg[0], seg[1]), e = mk(seg[2] - seg[0], seg[3] - seg[1]);
+    double l2 = dot(e, e), t = 0.0;
+    if (l2 > 0.0) {
+        t = dot(sub(mk(p[0], p[1]), a), e) / l2;
+        t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    }
+    return len(sub(add(a, scl(e, t)), mk(p[0], p[1]))) <= r;
 }
 
 /* ----------------------------------------------------------------------------------
@@ -499,17 +590,17 @@ static v2 pref_velocity(v2 p, v2 goal, double pref_speed, double dt) {
  * header).  Returns 0, or a negative value on bad arguments / allocation failure.
  * -------------------------------------------------------------------------------- */
 /* Velocity selection (LP2, then LP3 if needed) on given lines. */
-static v2 select_velocity(const line2* L, int n, double V, v2 o) {
+static v2 select_velocity(const line2* L, int n, int nobst, double V, v2 o) {
     v2 x;
     int b = lp2(L, n, V, o, 0, &x, NULL, NULL);
-    if (b < n) lp3(L, n, b, V, &x, NULL, NULL);
+    if (b < n) lp3(L, n, nobst, b, V, &x, NULL, NULL);
     return x;
 }
 
 /* Largest move of the selected velocity when one half-plane at a time is shifted along
  * its normal by +-eta_c (4 FP32 ulps of max(|offset|, V)) or turned by +-2^-22 rad about
  * its point nearest the origin. */
-static double lp_sensitivity(const line2* L, int n, double V, v2 o, v2 x) {
+static double lp_sensitivity(const line2* L, int n, int nobst, double V, v2 o, v2 x) {
     line2 Q[OR_MAXK];
     double worst = 0.0;
     const double eta_r = ldexp(1.0, -22);
@@ -532,7 +623,7 @@ static double lp_sensitivity(const line2* L, int n, double V, v2 o, v2 x) {
             }
             Q[q].d = mk(nn.y, -nn.x);
             Q[q].P = scl(nn, cc);
-            v2 y = select_velocity(Q, n, V, o);
+            v2 y = select_velocity(Q, n, nobst, V, o);
             double dv = fabs(y.x - x.x) > fabs(y.y - x.y) ? fabs(y.x - x.x) : fabs(y.y - x.y);
             if (dv > worst) worst = dv;
         }
@@ -547,23 +638,54 @@ typedef struct {
     float ndf;
     const float* pf;
     const bins* b;
+    int nseg, kobst;          /* static obstacle segments; obstacle lines kept per agent */
+    const double* seg;        /* 4 per segment: x1, y1, x2, y2 */
+    const float* segf;        /* the same in FP32 (selection) */
+    double tau_o;
 } step_in;
 
 static void step_agent(const step_in* S, int i, double* pos_out, double* vel_out, int32_t* nbr,
-                       int32_t* status, double* margin, double* sens, long long* c_scan,
-                       long long* c_lines, lpcount* c_work, long long* c_lp3) {
+                       int32_t* obst, int32_t* status, double* margin, double* sens,
+                       long long* c_scan, long long* c_lines, lpcount* c_work, long long* c_lp3) {
     cand list[OR_MAXK];
     line2 L[OR_MAXK];
-    int cnt = 0;
+    int cnt = 0, nob = 0;
     tags tg = {1e300};
     const double* pos = S->pos;
     const double* vel = S->vel;
+    /* obstacle lines first: the kobst nearest reachable segments, by (d^2, index) */
+    if (S->nseg > 0 && S->kobst > 0) {
+        float px = S->pf[2 * i], py = S->pf[2 * i + 1];
+        float vr = (float)S->max_speed[i] * (float)S->tau_o;
+        float rng = vr + (float)S->radius[i];
+        float rng2 = rng * rng;
+        float od2[OR_MAXK];
+        int oj[OR_MAXK];
+        for (int j = 0; j < S->nseg; ++j) {
+            float d2 = seg_dist2_f32(S->segf + 4 * j, px, py);
+            if (!(d2 < rng2)) continue;
+            int at = nob < S->kobst ? nob : S->kobst;
+            while (at > 0 && (od2[at - 1] > d2 || (od2[at - 1] == d2 && oj[at - 1] > j))) {
+                if (at < S->kobst) { od2[at] = od2[at - 1]; oj[at] = oj[at - 1]; }
+                --at;
+            }
+            if (at < S->kobst) {
+                od2[at] = d2;
+                oj[at] = j;
+                if (nob < S->kobst) ++nob;
+            }
+        }
+        for (int q = 0; q < nob; ++q)
+            L[q] = obstacle_line(mk(pos[2 * i], pos[2 * i + 1]), S->radius[i], S->seg + 4 * oj[q],
+                                 S->tau_o, S->dt, &tg);
+        if (obst) for (int q = 0; q < S->kobst; ++q) obst[q] = q < nob ? oj[q] : -1;
+    }
     if (S->b) *c_scan += knn_grid_one(S->b, S->pf, pos, S->fp64, i, S->ndf, S->nd, list, &cnt, S->k);
     else { knn_brute_one(S->pf, pos, S->fp64, S->n, i, S->ndf, S->nd, list, &cnt, S->k); *c_scan += S->n - 1; }
     v2 pa = mk(pos[2 * i], pos[2 * i + 1]), va = mk(vel[2 * i], vel[2 * i + 1]);
     for (int q = 0; q < cnt; ++q) {
         int j = list[q].j;
-        L[q] = orca_line(pa, va, S->radius[i], mk(pos[2 * j], pos[2 * j + 1]),
+        L[nob + q] = orca_line(pa, va, S->radius[i], mk(pos[2 * j], pos[2 * j + 1]),
                          mk(vel[2 * j], vel[2 * j + 1]), S->radius[j], S->tau[i], S->dt, i, j,
                          &tg, NULL, NULL);
     }
@@ -571,14 +693,15 @@ static void step_agent(const step_in* S, int i, double* pos_out, double* vel_out
     v2 pv = pref_velocity(pa, mk(S->goal[2 * i], S->goal[2 * i + 1]), S->pref_speed[i], S->dt);
     v2 x;
     lpcount w = {0, 0, 0, 0};
-    int bfail = lp2(L, cnt, S->max_speed[i], pv, 0, &x, &tg, &w);
-    int used3 = bfail < cnt;
-    if (used3) { lp3(L, cnt, bfail, S->max_speed[i], &x, &tg, &w); ++*c_lp3; }
+    int nl = nob + cnt;
+    int bfail = lp2(L, nl, S->max_speed[i], pv, 0, &x, &tg, &w);
+    int used3 = bfail < nl;
+    if (used3) { lp3(L, nl, nob, bfail, S->max_speed[i], &x, &tg, &w); ++*c_lp3; }
     c_work->lp1 += w.lp1;
     c_work->bounds += w.bounds;
     c_work->checks += w.checks;
     c_work->bisectors += w.bisectors;
-    if (sens) *sens = S->cond ? lp_sensitivity(L, cnt, S->max_speed[i], pv, x) : 0.0;
+    if (sens) *sens = S->cond ? lp_sensitivity(L, nl, nob, S->max_speed[i], pv, x) : 0.0;
     vel_out[0] = x.x;
     vel_out[1] = x.y;
     pos_out[0] = pa.x + x.x * S->dt;
@@ -588,14 +711,17 @@ static void step_agent(const step_in* S, int i, double* pos_out, double* vel_out
     if (margin) *margin = tg.m;
 }
 
-int oracle_step(int n, const double* pos, const double* vel, const double* goal,
-                const double* radius, const double* max_speed, const double* pref_speed,
-                const double* time_horizon, double neighbor_dist, int k, double dt,
-                int knn_mode, int fp64_knn, const float* grid_f_in, const int* grid_i_in,
-                const int32_t* subset, int n_subset, int nthreads, double* pos_out,
-                double* vel_out, int32_t* nbr, int32_t* status, double* margin,
-                long long* counters, int cond_check, double* sens) {
+static int step_all(int n, const double* pos, const double* vel, const double* goal,
+                    const double* radius, const double* max_speed, const double* pref_speed,
+                    const double* time_horizon, double neighbor_dist, int k, double dt,
+                    int knn_mode, int fp64_knn, const float* grid_f_in, const int* grid_i_in,
+                    const int32_t* subset, int n_subset, int nthreads, double* pos_out,
+                    double* vel_out, int32_t* nbr, int32_t* status, double* margin,
+                    long long* counters, int cond_check, double* sens, int nseg,
+                    const double* seg, double tau_o, int kobst, int32_t* obst) {
     if (n < 0 || k < 1 || k > OR_MAXK || !(dt > 0.0)) return -1;
+    if (nseg < 0 || kobst < 0 || k + kobst > OR_MAXK || (nseg > 0 && (!seg || !(tau_o > 0.0))))
+        return -1;
     if (subset) {
         if (n_subset < 0) return -1;
         for (int q = 0; q < n_subset; ++q) if (subset[q] < 0 || subset[q] >= n) return -1;
@@ -611,13 +737,21 @@ int oracle_step(int n, const double* pos, const double* vel, const double* goal,
     S.pos = pos; S.vel = vel; S.goal = goal; S.radius = radius; S.max_speed = max_speed;
     S.pref_speed = pref_speed; S.tau = time_horizon;
     S.nd = neighbor_dist; S.dt = dt; S.ndf = (float)neighbor_dist; S.pf = pf; S.b = NULL;
+    S.nseg = nseg; S.kobst = kobst; S.seg = seg; S.tau_o = tau_o; S.segf = NULL;
+    float* segf = NULL;
+    if (nseg > 0) {
+        segf = (float*)malloc(sizeof(float) * 4 * (size_t)nseg);
+        if (!segf) { free(pf); return -2; }
+        for (long long q = 0; q < 4LL * nseg; ++q) segf[q] = (float)seg[q];
+        S.segf = segf;
+    }
     bins b;
     if (knn_mode == 1) {
         float gf[4];
         int gi[2];
         if (grid_f_in && grid_i_in) { memcpy(gf, grid_f_in, sizeof gf); memcpy(gi, grid_i_in, sizeof gi); }
-        else if (oracle_grid(pf, n, S.ndf, (long long)4 * n + 1024, gf, gi) != 0) { free(pf); return -3; }
-        if (bins_build(&b, pf, n, gf, gi) != 0) { free(pf); return -2; }
+        else if (oracle_grid(pf, n, S.ndf, (long long)4 * n + 1024, gf, gi) != 0) { free(pf); free(segf); return -3; }
+        if (bins_build(&b, pf, n, gf, gi) != 0) { free(pf); free(segf); return -2; }
         S.b = &b;
     }
     long long c_scan = 0, c_lines = 0, c_lp3 = 0, c_lp1 = 0, c_bounds = 0, c_checks = 0, c_bis = 0;
@@ -630,7 +764,8 @@ int oracle_step(int n, const double* pos, const double* vel, const double* goal,
         int i = subset ? subset[q] : q;
         lpcount w = {0, 0, 0, 0};
         step_agent(&S, i, pos_out + 2 * (size_t)q, vel_out + 2 * (size_t)q,
-                   nbr ? nbr + (size_t)q * k : NULL, status ? status + q : NULL,
+                   nbr ? nbr + (size_t)q * k : NULL,
+                   obst ? obst + (size_t)q * (kobst > 0 ? kobst : 1) : NULL, status ? status + q : NULL,
                    margin ? margin + q : NULL, sens ? sens + q : NULL, &c_scan, &c_lines,
                    &w, &c_lp3);
         c_lp1 += w.lp1;
@@ -640,11 +775,42 @@ int oracle_step(int n, const double* pos, const double* vel, const double* goal,
     }
     if (S.b) bins_free(&b);
     free(pf);
+    free(segf);
     if (counters) {
         counters[0] = c_scan; counters[1] = c_lines; counters[2] = c_lp1; counters[3] = c_lp3;
         counters[4] = c_bounds; counters[5] = c_checks; counters[6] = c_bis;
     }
     return 0;
+}
+
+int oracle_step(int n, const double* pos, const double* vel, const double* goal,
+                const double* radius, const double* max_speed, const double* pref_speed,
+                const double* time_horizon, double neighbor_dist, int k, double dt,
+                int knn_mode, int fp64_knn, const float* grid_f_in, const int* grid_i_in,
+                const int32_t* subset, int n_subset, int nthreads, double* pos_out,
+                double* vel_out, int32_t* nbr, int32_t* status, double* margin,
+                long long* counters, int cond_check, double* sens) {
+    return step_all(n, pos, vel, goal, radius, max_speed, pref_speed, time_horizon,
+                    neighbor_dist, k, dt, knn_mode, fp64_knn, grid_f_in, grid_i_in, subset,
+                    n_subset, nthreads, pos_out, vel_out, nbr, status, margin, counters,
+                    cond_check, sens, 0, NULL, 1.0, 0, NULL);
+}
+
+/* As oracle_step, with nseg static obstacle segments (seg: 4 doubles each, x1 y1 x2 y2),
+ * obstacle time horizon tau_o and at most kobst obstacle lines per agent (k + kobst <=
+ * 64); obst (kobst per row, -1 padded, may be NULL) receives the segments used. */
+int oracle_step_obstacles(int n, const double* pos, const double* vel, const double* goal,
+                          const double* radius, const double* max_speed, const double* pref_speed,
+                          const double* time_horizon, double neighbor_dist, int k, double dt,
+                          int knn_mode, int fp64_knn, const float* grid_f_in, const int* grid_i_in,
+                          const int32_t* subset, int n_subset, int nthreads, double* pos_out,
+                          double* vel_out, int32_t* nbr, int32_t* status, double* margin,
+                          long long* counters, int cond_check, double* sens, int nseg,
+                          const double* seg, double tau_o, int kobst, int32_t* obst) {
+    return step_all(n, pos, vel, goal, radius, max_speed, pref_speed, time_horizon,
+                    neighbor_dist, k, dt, knn_mode, fp64_knn, grid_f_in, grid_i_in, subset,
+                    n_subset, nthreads, pos_out, vel_out, nbr, status, margin, counters,
+                    cond_check, sens, nseg, seg, tau_o, kobst, obst);
 }
 
 /* Number of OpenMP threads the oracle would use by default (1 without OpenMP). */

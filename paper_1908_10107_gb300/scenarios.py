@@ -42,12 +42,20 @@ class Scene:
     max_neighbors: int
     dt: float
     steps: int
+    # static obstacles (optional): float32[m, 4] segments (x1, y1, x2, y2), their time
+    # horizon, and the obstacle half-planes kept per agent
+    obstacles: np.ndarray | None = None
+    obstacle_time_horizon: float = 2.0
+    max_obstacle_neighbors: int = 4
 
     def __post_init__(self):
         # scene parameters are FP32 values, the precision the GPU receives them in, so
         # that both sides of a parity check start from identical numbers
         self.neighbor_dist = float(np.float32(self.neighbor_dist))
         self.dt = float(np.float32(self.dt))
+        self.obstacle_time_horizon = float(np.float32(self.obstacle_time_horizon))
+        if self.obstacles is not None:
+            self.obstacles = _f32(np.asarray(self.obstacles).reshape(-1, 4))
 
     @property
     def n(self) -> int:

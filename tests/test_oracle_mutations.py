@@ -15,6 +15,7 @@ import oracle
 import test_oracle_halfplane as H
 import test_oracle_knn as K
 import test_oracle_lp as LP
+import test_oracle_obstacles as OB
 import test_oracle_population as POP
 import test_oracle_step as ST
 
@@ -48,6 +49,13 @@ MUTANTS = {
     "arrival_strict": ("arrived[i] = d2 <= r2;", "arrived[i] = d2 < r2;"),
     "arrival_mixed_square": ("float dy2 = dy * dy;", "float dy2 = dx * dy;"),
     "arrival_radius_not_squared": ("float r2 = radius[i] * radius[i];", "float r2 = radius[i];"),
+    "obstacle_radius_dropped": ("c = d > ra ? -(d - ra) / tau_o : -(d - ra) / dt;",
+                                "c = d > ra ? -d / tau_o : -(d - ra) / dt;"),
+    "obstacle_uses_dt": ("c = d > ra ? -(d - ra) / tau_o : -(d - ra) / dt;",
+                         "c = d > ra ? -(d - ra) / dt : -(d - ra) / dt;"),
+    "obstacle_normal_sign": ("if (d > 0.0) n = scl(q, -1.0 / d);", "if (d > 0.0) n = scl(q, 1.0 / d);"),
+    "obstacle_lines_not_hard_in_lp3": ("for (int j = 0; j < nobst && j < OR_MAXK; ++j) proj[m++] = L[j];",
+                                       "for (int j = 0; j < 0; ++j) proj[m++] = L[j];"),
 }
 
 
@@ -72,6 +80,11 @@ def _pins():
                                 ST.test_lone_agent_lands_on_goal(o))),
         ("collision_free", lambda: ST.test_feasible_mutual_pairs_do_not_collide_within_tau(o, 0)),
         ("arrival_boundary", POP.test_boundary_cases),
+        ("obstacle_wall", OB.test_wall_ahead_closed_form),
+        ("obstacle_endpoint", OB.test_nearest_endpoint_closed_form),
+        ("obstacle_overlap", OB.test_overlap_pushes_out_within_one_step),
+        ("obstacle_lp3", OB.test_lp3_keeps_obstacle_lines_hard_and_minimises_the_rest),
+        ("obstacle_lone_agent", OB.test_lone_agent_into_a_wall_closed_form),
         ("arrival_exact", POP.test_matches_exact_arithmetic_away_from_the_boundary),
     ]
 
