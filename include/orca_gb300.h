@@ -203,6 +203,30 @@ ORCA_API int orca_get_cells(orca_ctx* ctx, uint32_t* cell, float* grid_f, int32_
 ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
 
 /*
+ * Static obstacles: n_seg line segments (0 <= n_seg <= 256; 0 clears them), seg_xyxy 4*n_seg
+ * floats (x1, y1, x2, y2 per segment, host or device per `where`).  Not in the paper's
+ * experiments; the ORCA obstacle rule the paper defers to (van den Berg et al.): the
+ * optimisation velocity is 0 and the agent takes full responsibility, so with q the
+ * segment's nearest point relative to the agent and d = |q|, the permitted velocities are
+ * v.q/d <= (d - r)/time_horizon (dt in place of time_horizon when the agent overlaps the
+ * segment).  Each agent keeps the max_obstacle_neighbors (1..4) nearest segments it could
+ * reach within time_horizon -- FP32 squared distance, by the clamped projection, strictly
+ * below fl(fl(max_speed*time_horizon) + radius)^2 -- ordered by (distance, index); their
+ * half-planes come first in the LP and stay hard in the least-penetration fallback.  The
+ * segments stay until replaced; they apply to single-scene steps (ORCA_ERR_STATE in a
+ * batch, with operation counting, or in rollouts).  Rebuilds the step graphs.
+ */
+ORCA_API int orca_set_obstacles(orca_ctx* ctx, int32_t n_seg, const float* seg_xyxy,
+                                float time_horizon, int32_t max_obstacle_neighbors, int where,
+                                void* stream);
+
+/*
+ * The segments each agent used in the last step (needs ORCA_FLAG_RECORD): n*4 int32 in agent
+ * order, nearest first, -1 padded.  Synchronises `stream` for host output.
+ */
+ORCA_API int orca_get_obstacle_neighbors(orca_ctx* ctx, int32_t* obst, int where, void* stream);
+
+/*
  * Remove the agents that have reached their goal (Section 4: a person who reaches the
  * goal location is removed from the simulation).  An agent has arrived when its goal lies
  * within its radius on the current state, decided in FP32 with one rounding per operation:

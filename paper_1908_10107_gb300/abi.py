@@ -82,6 +82,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_get_counters": ([vp, vp, vp], c.c_int),
         "orca_count_ops": ([vp, i32], c.c_int),
         "orca_remove_arrived": ([vp, c.POINTER(i32), vp, c.c_int, vp], c.c_int),
+        "orca_set_obstacles": ([vp, i32, vp, c.c_float, i32, c.c_int, vp], c.c_int),
+        "orca_get_obstacle_neighbors": ([vp, vp, c.c_int, vp], c.c_int),
         "orca_get_op_counters": ([vp, vp, vp], c.c_int),
         "orca_sync": ([vp, vp], c.c_int),
         "orca_profile": ([vp, c.c_int], c.c_int),
@@ -241,6 +243,30 @@ def orca_remove_arrived(ctx, kept_ids=None, stream=None) -> int:
     return int(m.value)
 
 
+MAX_OBSTACLE_NEIGHBORS = 4
+
+
+def orca_set_obstacles(ctx, segments, time_horizon: float = 2.0, max_obstacle_neighbors: int = 4,
+                       stream=None):
+    """Static obstacle segments (float32[m, 4]: x1, y1, x2, y2; None or empty clears)."""
+    if segments is None or len(segments) == 0:
+        _check(load_library().orca_set_obstacles(ctx, 0, None, float(time_horizon), 1, ORCA_HOST,
+                                                 _stream(stream)), ctx)
+        return
+    if isinstance(segments, np.ndarray):
+        segments = np.ascontiguousarray(segments, np.float32).reshape(-1, 4)
+    p, w = _ptr(segments, np.float32)
+    m = segments.shape[0]
+    _check(load_library().orca_set_obstacles(ctx, int(m), p, float(time_horizon),
+                                             int(max_obstacle_neighbors), int(w), _stream(stream)), ctx)
+
+
+def orca_get_obstacle_neighbors(ctx, out, where=None, stream=None):
+    p, w = _ptr(out, np.int32)
+    _check(load_library().orca_get_obstacle_neighbors(ctx, p, int(where if where is not None else w),
+                                                      _stream(stream)), ctx)
+
+
 def orca_count_ops(ctx, on: bool):
     _check(load_library().orca_count_ops(ctx, int(bool(on))), ctx)
 
@@ -389,7 +415,18 @@ class OrcaSim:
                         time_horizon, stream=stream)
 
     def set_scene(self, scene, stream=None):
+        """Load a ``scenarios.Scene``: its agents and its static obstacles (none clears them)."""
+        obs = getattr(scene, "obstacles", None)
+        if obs is not None or getattr(self, "_has_obstacles", False):
+            orca_set_obstacles(self.ctx, obs, getattr(scene, "obstacle_time_horizon", 2.0),
+                               getattr(scene, "max_obstacle_neighbors", 4), stream)
+            self._has_obstacles = obs is not None and len(obs) > 0
         self.set_agents(*scene.arrays(), stream=stream)
+
+    def get_obstacle_neighbors(self, stream=None) -> np.ndarray:
+        out = np.empty((self.n, MAX_OBSTACLE_NEIGHBORS), np.int32)
+        orca_get_obstacle_neighbors(self.ctx, out, stream=stream)
+        return out
 
     def set_batch(self, batch, cell_size: float = 0.0, stream=None):
         """Load a ``scenarios.Batch`` (needs max_scenes >= its scene count)."""

@@ -26,7 +26,7 @@ struct Layout {
 struct Plan {
     int N, K, S, max_cells, max_passes, nsb, nmb;
     size_t o_msg, o_sslot, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2], o_hint[2];
-    size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_scenes, o_slot, o_part, o_misc, o_blk, o_rnbr, o_rcell,
+    size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_scenes, o_slot, o_part, o_misc, o_blk, o_rnbr, o_rcell, o_robst, o_seg,
         o_stage[2];
     size_t total;
 };
@@ -79,11 +79,13 @@ static bool make_plan(const orca_params& p, Plan& pl) {
     pl.o_part = L.add(kBboxBlocks * sizeof(float4));
     pl.o_misc = L.add(sizeof(DeviceMisc));
     pl.o_blk = L.add((size_t)pl.nmb * kBlockCounters * sizeof(unsigned long long));
+    pl.o_seg = L.add((size_t)kMaxObstacles * sizeof(float4));
     if (p.flags & ORCA_FLAG_RECORD) {
         pl.o_rnbr = L.add(N * pl.K * 4);
         pl.o_rcell = L.add(N * 4);
+        pl.o_robst = L.add(N * kMaxObstacleNeighbors * 4);
     } else {
-        pl.o_rnbr = pl.o_rcell = (size_t)-1;
+        pl.o_rnbr = pl.o_rcell = pl.o_robst = (size_t)-1;
     }
     pl.total = L.total;
     return true;
@@ -106,6 +108,10 @@ struct orca_ctx {
     unsigned long long* blk = nullptr;
     int32_t* rec_nbr = nullptr;
     uint32_t* rec_cell = nullptr;
+    int32_t* rec_obst = nullptr;
+    float4* seg = nullptr;  // static obstacle segments
+    int nseg = 0, kobst = 0;
+    float tau_o = 1.0f;
     float2* stage[2];
     int n = 0;
     int cur = 0;  // which PR buffer holds the current parameters
@@ -180,6 +186,8 @@ static void bind_buffers(orca_ctx* c) {
     c->slot_scene = pl.o_slot == (size_t)-1 ? nullptr : (int*)(w + pl.o_slot);
     c->rec_nbr = pl.o_rnbr == (size_t)-1 ? nullptr : (int32_t*)(w + pl.o_rnbr);
     c->rec_cell = pl.o_rcell == (size_t)-1 ? nullptr : (uint32_t*)(w + pl.o_rcell);
+    c->rec_obst = pl.o_robst == (size_t)-1 ? nullptr : (int32_t*)(w + pl.o_robst);
+    c->seg = (float4*)(w + pl.o_seg);
 }
 
 static void drop_graphs(orca_ctx* c) {
@@ -220,6 +228,11 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     a.out = c->PV[0];
     a.block_counters = c->blk;
     a.count_ops = c->count_ops ? 1 : 0;
+    a.seg = c->seg;
+    a.nseg = c->n_scenes > 0 ? 0 : c->nseg;
+    a.kobst = c->kobst;
+    a.tau_o = c->tau_o;
+    a.rec_obst = c->rec_obst;
     a.rec_nbr = c->rec_nbr;
     a.rec_cell = c->rec_cell;
     a.scenes = c->n_scenes > 0 ? c->scenes : nullptr;
@@ -261,6 +274,11 @@ static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, ui
     a.out = c->PV[0];
     a.block_counters = c->blk;
     a.count_ops = 0;
+    a.seg = nullptr;
+    a.nseg = 0;
+    a.kobst = 0;
+    a.tau_o = 1.0f;
+    a.rec_obst = nullptr;
     a.rec_nbr = nbr;
     a.rec_cell = nullptr;
     a.scenes = nullptr;
@@ -463,6 +481,7 @@ ORCA_API int orca_set_scenes(orca_ctx* ctx, int32_t n_scenes, const orca_scene* 
                              const float* radius, const float* max_speed, const float* pref_speed,
                              const float* time_horizon, int where, void* stream) {
     if (!ctx) return ORCA_ERR_ARG;
+    if (ctx->nseg > 0) return fail(ctx, ORCA_ERR_STATE, "clear the static obstacles before a batch");
     if (!ctx->slot_scene) return fail(ctx, ORCA_ERR_STATE, "context created with max_scenes <= 1");
     if (n_scenes < 1 || !scenes) return fail(ctx, ORCA_ERR_ARG, "need at least one scene");
     if (n_scenes > ctx->plan.S) return fail(ctx, ORCA_ERR_CAPACITY, "n_scenes exceeds max_scenes");
@@ -590,6 +609,48 @@ ORCA_API int orca_get_neighbors(orca_ctx* ctx, int32_t* nbr, int where, void* st
     return ORCA_OK;
 }
 
+ORCA_API int orca_set_obstacles(orca_ctx* ctx, int32_t n_seg, const float* seg_xyxy,
+                                float time_horizon, int32_t max_obstacle_neighbors, int where,
+                                void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
+    if (n_seg < 0 || n_seg > kMaxObstacles)
+        return fail(ctx, ORCA_ERR_CAPACITY, "n_seg must be 0.." + std::to_string(kMaxObstacles));
+    if (n_seg > 0) {
+        if (!seg_xyxy) return fail(ctx, ORCA_ERR_ARG, "null segments");
+        if (!(time_horizon > 0.0f)) return fail(ctx, ORCA_ERR_ARG, "time_horizon must be > 0");
+        if (max_obstacle_neighbors < 1 || max_obstacle_neighbors > kMaxObstacleNeighbors)
+            return fail(ctx, ORCA_ERR_ARG,
+                        "max_obstacle_neighbors must be 1.." + std::to_string(kMaxObstacleNeighbors));
+        if (ctx->n_scenes > 0) return fail(ctx, ORCA_ERR_STATE, "obstacles need a single-scene context");
+        if (ctx->count_ops) return fail(ctx, ORCA_ERR_STATE, "operation counting is on");
+        cudaStream_t st = (cudaStream_t)stream;
+        CK(cudaMemcpyAsync(ctx->seg, seg_xyxy, (size_t)n_seg * 16,
+                           where == ORCA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st),
+           "copy segments");
+        if (where == ORCA_HOST) CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        ctx->kobst = max_obstacle_neighbors;
+        ctx->tau_o = time_horizon;
+    }
+    ctx->nseg = n_seg;
+    drop_graphs(ctx);  // the step graphs capture the obstacle parameters
+    return ORCA_OK;
+}
+
+ORCA_API int orca_get_obstacle_neighbors(orca_ctx* ctx, int32_t* obst, int where, void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (!ctx->rec_obst) return fail(ctx, ORCA_ERR_STATE, "context created without ORCA_FLAG_RECORD");
+    if (!obst) return fail(ctx, ORCA_ERR_ARG, "null obst");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = (size_t)ctx->n * kMaxObstacleNeighbors * 4;
+    if (bytes)
+        CK(cudaMemcpyAsync(obst, ctx->rec_obst, bytes,
+                           where == ORCA_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st),
+           "copy obstacle neighbours");
+    if (where == ORCA_HOST) CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return ORCA_OK;
+}
+
 ORCA_API int orca_get_cells(orca_ctx* ctx, uint32_t* cell, float* grid_f, int32_t* grid_i, int where,
                             void* stream) {
     if (!ctx) return ORCA_ERR_ARG;
@@ -682,6 +743,7 @@ ORCA_API int orca_remove_arrived(orca_ctx* ctx, int32_t* n_remaining, int32_t* k
 ORCA_API int orca_count_ops(orca_ctx* ctx, int32_t on) {
     if (!ctx) return ORCA_ERR_ARG;
     bool want = on != 0;
+    if (want && ctx->nseg > 0) return fail(ctx, ORCA_ERR_STATE, "operation counting has no obstacle kernel");
     if (want != ctx->count_ops) {
         ctx->count_ops = want;
         drop_graphs(ctx);
@@ -735,6 +797,7 @@ ORCA_API int orca_rollout_forward(orca_ctx* ctx, int32_t T, int32_t ckpt_every, 
     if (!ctx) return ORCA_ERR_ARG;
     if (T < 1 || ckpt_every < 1) return fail(ctx, ORCA_ERR_ARG, "T and ckpt_every must be >= 1");
     if (ctx->n_scenes > 0) return fail(ctx, ORCA_ERR_STATE, "rollouts need a single scene");
+    if (ctx->nseg > 0) return fail(ctx, ORCA_ERR_STATE, "the adjoint has no static obstacles");
     if (ctx->n < 1) return fail(ctx, ORCA_ERR_STATE, "no agents loaded");
     RolloutPlan r = rollout_plan(ctx, T, ckpt_every);
     if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < r.total)

@@ -21,6 +21,10 @@ constexpr int kRadixBits = 9;
 // per-CTA counters of the ORCA kernel: agents, LP3 agents, candidates, half-planes, then
 // (operation-counting launches only) LP1 calls, LP1 bounds, violation checks, bisectors
 constexpr int kBlockCounters = 8;
+// static obstacles: segments per context (staged in shared memory per CTA) and obstacle
+// half-planes per agent
+constexpr int kMaxObstacles = 256;
+constexpr int kMaxObstacleNeighbors = 4;
 constexpr int kRadixBuckets = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 4;  // items per thread per tile
@@ -115,6 +119,10 @@ struct MainArgs {
     AgentState out;                      // new state, same slots
     unsigned long long* block_counters;  // kBlockCounters per block, accumulated
     int count_ops;                       // launch the operation-counting instantiation
+    const float4* seg;                   // static obstacle segments (x1, y1, x2, y2), or null
+    int nseg, kobst;                     // segments; obstacle half-planes kept per agent
+    float tau_o;                         // obstacle time horizon
+    int32_t* rec_obst;                   // kMaxObstacleNeighbors per agent (agent order), or null
     int32_t* rec_nbr;                    // n*k in agent order, or null
     uint32_t* rec_cell;                  // n in agent order, or null
 };

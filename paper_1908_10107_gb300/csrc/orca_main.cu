@@ -222,12 +222,19 @@ struct RowLines {
 // Every use is scale-free -- the side of a point, an LP1 bound t = -rhs/den -- except the
 // parallel test, which compares |den| with eps |n| (parallel_to), and the line LP1 runs
 // on, which unit_line normalises.
+// With static obstacles the first nobst lines of the row are hard constraints: they enter
+// the projected problem unchanged (Bisectors returns them as they are).
 struct Bisectors {
     static constexpr bool kUnit = false;
     const float4* row;
     float4 li;
+    int nobst = 0;
     __device__ __forceinline__ bool operator()(int j, float4& q) const {
         float4 lj = row[j];
+        if (j < nobst) {
+            q = lj;
+            return true;
+        }
         float den = lp_det(li.x, li.y, lj.x, lj.y);
         if (fabsf(den) <= kEps && lp_dot(li.x, li.y, lj.x, lj.y) > 0.0f) return false;
         q = make_float4(__fsub_rn(lj.x, li.x), __fsub_rn(lj.y, li.y), __fsub_rn(lj.z, li.z), 0.0f);
@@ -241,7 +248,8 @@ struct Bisectors {
 // numerically failed LP2 keeps x.
 // rec (may be null) keeps the record of the LP2 phase until an LP3 solve succeeds.
 __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, float V, float& xx,
-                                        float& xy, LpTape* rec = nullptr, OpCount* oc = nullptr) {
+                                        float& xy, LpTape* rec = nullptr, OpCount* oc = nullptr,
+                                        int nobst = 0) {
     float dist = 0.0f;
     int i = begin;
     // scan ahead to the next line violated by more than dist, then solve for it (the
@@ -260,11 +268,14 @@ __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, flo
             }
         }
         if (!hit) return;
-        if (oc) oc->bis += i;
-        Bisectors bis{row, li};
+        if (oc) oc->bis += i > nobst ? i - nobst : 0;
+        Bisectors bis{row, li, nobst};
+        // the projected problem: every obstacle line, then the bisectors with the lines
+        // from nobst to i-1
+        const int m = i > nobst ? i : nobst;
         float sx = xx, sy = xy;
         LpTape r2;
-        if (lp2_dev(bis, i, V, li.x, li.y, true, xx, xy, rec ? &r2 : nullptr, oc) < i) {
+        if (lp2_dev(bis, m, V, li.x, li.y, true, xx, xy, rec ? &r2 : nullptr, oc) < m) {
             xx = sx;
             xy = sy;
         } else if (rec) {
@@ -627,6 +638,117 @@ __device__ __forceinline__ void insert_key(unsigned long long key, unsigned long
     if (c[0]) kk[0] = key;
 }
 
+// ---------------------------------------------------------------------------------
+// Static obstacles (segments; the ORCA obstacle rule): optimisation velocity 0 and full
+// responsibility, so with q the segment's nearest point relative to the agent and d = |q|
+// the permitted velocities are v.q/d <= (d - r)/tau_o (dt in place of tau_o when d <= r;
+// an agent exactly on the segment takes its left normal).  Normal form n = -q/d,
+// c = -(d - r)/tau_o.  An agent takes the kobst nearest segments it could reach within
+// tau_o -- FP32 squared distance (clamped projection, one rounding per operation) strictly
+// below fl(fl(V tau_o) + r)^2 -- ordered by (d^2, segment index).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float seg_dist2(float4 sg, float2 p) {
+    const float ex = __fsub_rn(sg.z, sg.x), ey = __fsub_rn(sg.w, sg.y);
+    const float wx = __fsub_rn(p.x, sg.x), wy = __fsub_rn(p.y, sg.y);
+    const float l2 = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
+    float t = 0.0f;
+    if (l2 > 0.0f) {
+        t = __fdiv_rn(__fadd_rn(__fmul_rn(wx, ex), __fmul_rn(wy, ey)), l2);
+        t = t < 0.0f ? 0.0f : (t > 1.0f ? 1.0f : t);
+    }
+    const float qx = __fsub_rn(__fadd_rn(sg.x, __fmul_rn(t, ex)), p.x);
+    const float qy = __fsub_rn(__fadd_rn(sg.y, __fmul_rn(t, ey)), p.y);
+    return __fadd_rn(__fmul_rn(qx, qx), __fmul_rn(qy, qy));
+}
+
+// a - b as an unevaluated pair hi + lo, exactly (Knuth's TwoSum on a and -b).
+__device__ __forceinline__ float2 two_diff(float a, float b) {
+    const float s = __fsub_rn(a, b);
+    const float bv = __fsub_rn(s, a);        // the part of -b that made it into s
+    const float av = __fsub_rn(s, bv);
+    const float e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(__fsub_rn(0.0f, b), bv));
+    return make_float2(s, e);
+}
+
+// The obstacle half-plane of an agent at p, radius r, against segment sg (the ORCA obstacle
+// rule: the obstacle does not move and takes no share of the avoidance).  With q the
+// closest point of the segment and d = |q - p|: n = (p - q)/d, c = -(d - r)/tau_o, or
+// -(d - r)/dt when the agent overlaps the segment (d <= r).  d = 0 takes the segment's
+// left normal, a point segment (1, 0).
+// The distance is formed from exact differences: p - a, p - b and b - a as TwoSum pairs and,
+// for a closest point inside the segment, the cross product det(b - a, p - a) with its
+// products' rounding errors (FMA) carried.  Its error is then a few ulps of d, where the
+// closest point written in absolute coordinates would carry ulp(|p|) -- which the 1/dt of
+// an overlapping agent turns into a velocity error of order 1e-4 m/s at 100 m from the origin.
+__device__ __forceinline__ float4 obstacle_line(float4 sg, float2 p, float r, float dt,
+                                                float tau_o) {
+    const float2 wx = two_diff(p.x, sg.x), wy = two_diff(p.y, sg.y);  // p - a
+    const float2 ex = two_diff(sg.z, sg.x), ey = two_diff(sg.w, sg.y); // b - a
+    const float l2 = __fadd_rn(__fmul_rn(ex.x, ex.x), __fmul_rn(ey.x, ey.x));
+    float t = 0.0f;
+    if (l2 > 0.0f) t = __fdiv_rn(__fadd_rn(__fmul_rn(wx.x, ex.x), __fmul_rn(wy.x, ey.x)), l2);
+    float d, nx = 1.0f, ny = 0.0f;
+    const float il = l2 > 0.0f ? __fdiv_rn(1.0f, sqrtf(l2)) : 0.0f;
+    if (t > 0.0f && t < 1.0f) {
+        // interior: d = |det(e, w)| / |e|, n = sign(det) (-e_y, e_x) / |e|
+        const float p1 = __fmul_rn(ex.x, wy.x), e1 = __fmaf_rn(ex.x, wy.x, -p1);
+        const float p2 = __fmul_rn(ey.x, wx.x), e2 = __fmaf_rn(ey.x, wx.x, -p2);
+        const float cross = __fsub_rn(__fadd_rn(__fmul_rn(ex.x, wy.y), __fmul_rn(ex.y, wy.x)),
+                                      __fadd_rn(__fmul_rn(ey.x, wx.y), __fmul_rn(ey.y, wx.x)));
+        const float det = __fadd_rn(__fsub_rn(p1, p2), __fadd_rn(__fsub_rn(e1, e2), cross));
+        d = __fmul_rn(fabsf(det), il);
+        const float s = det < 0.0f ? -il : il;
+        nx = -__fmul_rn(ey.x, s);
+        ny = __fmul_rn(ex.x, s);
+    } else {
+        // an end point is nearest: the agent's offset from it, p - a or p - b
+        float vx = wx.x, vy = wy.x;
+        if (t >= 1.0f) {
+            vx = two_diff(p.x, sg.z).x;
+            vy = two_diff(p.y, sg.w).x;
+        }
+        d = sqrtf(__fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy)));
+        if (d > 0.0f) {
+            nx = __fdiv_rn(vx, d);
+            ny = __fdiv_rn(vy, d);
+        } else if (l2 > 0.0f) {
+            nx = -__fmul_rn(ey.x, il);
+            ny = __fmul_rn(ex.x, il);
+        }
+    }
+    const float c = -__fdiv_rn(__fsub_rn(d, r), d > r ? tau_o : dt);
+    return make_float4(nx, ny, c, 0.0f);
+}
+
+// Writes the agent's obstacle half-planes to row[0..] (nearest first) and returns how many;
+// rec (may be null) receives the segments' indices, -1 padded to kMaxObstacleNeighbors.
+template <int KO>
+__device__ __forceinline__ int obstacle_lines(const float4* segs, int nseg, int kobst, float2 p,
+                                              float r, float V, float dt, float tau_o,
+                                              float4* row, int32_t* rec) {
+    const float rng = __fadd_rn(__fmul_rn(V, tau_o), r);
+    const float rng2 = __fmul_rn(rng, rng);
+    unsigned long long ok[KO];
+#pragma unroll
+    for (int l = 0; l < KO; ++l) ok[l] = (l < KO - kobst) ? 0ull : ~0ull;
+#pragma unroll 1
+    for (int j = 0; j < nseg; ++j) {
+        const float d2 = seg_dist2(segs[j], p);
+        if (d2 < rng2) insert_key<KO>(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j, ok);
+    }
+    int nob = 0;
+#pragma unroll
+    for (int l = 0; l < KO; ++l) {
+        if (l < KO - kobst || ok[l] == ~0ull) continue;
+        const int j = (int)(ok[l] & 0xffffffffu);
+        if (rec) rec[nob] = j;
+        row[nob++] = obstacle_line(segs[j], p, r, dt, tau_o);
+    }
+    if (rec)
+        for (int l = nob; l < kMaxObstacleNeighbors; ++l) rec[l] = -1;
+    return nob;
+}
+
 // Insert the nb parked keys into kk; once the list is full, lim becomes its k-th d^2.
 template <int KMAX>
 __device__ __forceinline__ void drain(const unsigned long long* buf, int nb,
@@ -757,8 +879,12 @@ constexpr int main_min_blocks() {
 // checks every mode).
 int default_lp3_group(int kmax) { return kmax <= 16 ? 1 : 32; }
 
-template <int KMAX, int TPB>
-constexpr size_t main_smem_bytes() { return sizeof(float4) * TPB * (KMAX + 1); }
+// Row of one agent: KMAX neighbour half-planes (plus kMaxObstacleNeighbors obstacle ones
+// in the obstacle instantiation) and one float4 of padding (conflict-free float4 rows).
+template <int KMAX, bool OBS = false>
+constexpr int row_len() { return KMAX + (OBS ? kMaxObstacleNeighbors : 0) + 1; }
+template <int KMAX, int TPB, bool OBS = false>
+constexpr size_t main_smem_bytes() { return sizeof(float4) * TPB * row_len<KMAX, OBS>(); }
 
 // Parameters of the scene an agent belongs to (the one scene, or its scene of a batch).
 struct SceneView {
@@ -786,10 +912,10 @@ __device__ __forceinline__ void scene_view(const MainArgs& a, int t, SceneView& 
 
 // Persistent over tiles of TPB consecutive agents: tile blockIdx.x first, then
 // tiles taken from a per-step counter (with one CTA per tile this loop runs once).
-template <int KMAX, int TPB, int G, bool TAPE = false, bool COUNT = false>
+template <int KMAX, int TPB, int G, bool TAPE = false, bool COUNT = false, bool OBS = false>
 __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_kernel(MainArgs a) {
     pdl_wait();
-    constexpr int KP = KMAX + 1;  // padded rows: conflict-free float4 accesses
+    constexpr int KP = row_len<KMAX, OBS>();  // padded rows: conflict-free float4 accesses
     extern __shared__ float4 s_lines[];  // TPB * KP half-planes
     __shared__ float2 s_x[TPB];
     __shared__ float s_V[TPB];
@@ -803,7 +929,11 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     __shared__ unsigned long long s_ops[COUNT ? 4 : 1];
     constexpr bool WU = G == 32;  // work-unit LP (warp-cooperative) instead of per-lane LP
     __shared__ WarpLpShared s_wlp[WU ? TPB / 32 : 1];
+    __shared__ float4 s_seg[OBS ? kMaxObstacles : 1];      // static obstacle segments
+    __shared__ unsigned char s_nob[OBS ? TPB : 1];         // obstacle lines in each row
     const int tid = threadIdx.x;
+    if (OBS)
+        for (int j = tid; j < a.nseg; j += TPB) s_seg[j] = a.seg[j];
     if (tid == 0) {
         s_cand = 0;
         s_lines_n = 0;
@@ -826,6 +956,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         uint32_t me = 0;
         int cnt = 0;
         unsigned cand = 0;
+        int nob = 0;  // obstacle half-planes at the front of the row
         // an agent whose LP2 failed at line b joins the CTA's least-penetration queue
         auto enqueue = [&](int b) {
             int slot = atomicAdd(&s_qn, 1);
@@ -833,8 +964,9 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             s_queued[tid] = 1;
             s_x[tid] = make_float2(xx, xy);
             s_b[tid] = (unsigned char)b;
-            s_cnt[tid] = (unsigned char)cnt;
+            s_cnt[tid] = (unsigned char)(nob + cnt);
             s_V[tid] = V;
+            if (OBS) s_nob[OBS ? tid : 0] = (unsigned char)nob;
         };
         if (active) {
             SceneView sv;
@@ -861,20 +993,25 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 a.prm.hint[t] = kk[KMAX - 1] != ~0ull
                                     ? __uint_as_float((unsigned)(kk[KMAX - 1] >> 32))
                                     : INFINITY;
+            // static obstacles first: their half-planes open the row
+            if (OBS)
+                nob = obstacle_lines<kMaxObstacleNeighbors>(
+                    s_seg, a.nseg, a.kobst, p, me4.z, V, dt, a.tau_o, row,
+                    a.rec_obst ? a.rec_obst + (size_t)me * kMaxObstacleNeighbors : nullptr);
             // park the neighbours' slots in the row (one unrolled store each), then build
             // the half-planes in a rolled loop: one copy of the line code keeps the kernel
             // small enough for the instruction cache
 #pragma unroll
             for (int l = 0; l < KMAX; ++l) {
                 if (l >= KMAX - sv.k && kk[l] != ~0ull)
-                    row[cnt++].w = __uint_as_float(a.in.slot[(uint32_t)kk[l]]);
+                    row[nob + cnt++].w = __uint_as_float(a.in.slot[(uint32_t)kk[l]]);
             }
             float2 v = a.in.vel[t];
             float itau = __fdividef(1.0f, a.prm.tau[t]);
             float idt = __fdividef(1.0f, dt);
             float half_idt = 0.5f * idt;
 #pragma unroll 1
-            for (int l = 0; l < cnt; ++l) {
+            for (int l = nob; l < nob + cnt; ++l) {
                 int q = __float_as_int(row[l].w);
                 row[l] = orca_line_dev(p, v, me4.z, itau, dt, half_idt, me, a.in.msg[q], a.in.vel[q]);
             }
@@ -901,10 +1038,10 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 RowLines rl{row};
                 LpTape tape;
                 tape.i = tape.f = tape.bound = tape.j = tape.side = 0;
-                int b = lp2_dev(rl, cnt, V, ox, oy, false, xx, xy, TAPE ? &tape : nullptr,
+                int b = lp2_dev(rl, nob + cnt, V, ox, oy, false, xx, xy, TAPE ? &tape : nullptr,
                                 COUNT ? &oc : nullptr);
                 if (TAPE) s_tape[tid] = tape;
-                if (b < cnt) enqueue(b);
+                if (b < nob + cnt) enqueue(b);
             }
         }
         if (WU) {
@@ -940,7 +1077,8 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             int ag = s_queue[q];
             float2 x = s_x[ag];
             if (G == 1) lp3_dev(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y,
-                                TAPE ? &s_tape[TAPE ? ag : 0] : nullptr, COUNT ? &oc : nullptr);
+                                TAPE ? &s_tape[TAPE ? ag : 0] : nullptr, COUNT ? &oc : nullptr,
+                                OBS ? s_nob[OBS ? ag : 0] : 0);
             else lp3_group_dev<WU ? 4 : G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
             if ((tid & (G - 1)) == 0) s_x[ag] = x;
         }
@@ -1049,6 +1187,23 @@ static cudaError_t dispatch_tpb(const MainArgs& a, const LaunchShape& sh, int gr
     return dispatch_g<KMAX, 128>(a, sh.lp3_group, grid_blocks, st, resident);
 }
 
+// Launch with static obstacles: one lane per solve, 64 or 128 threads, one CTA per tile.
+template <int KMAX, int TPB>
+static cudaError_t launch_obs_k(const MainArgs& a, cudaStream_t st) {
+    constexpr size_t smem = main_smem_bytes<KMAX, TPB, true>();
+    cudaError_t e = cudaFuncSetAttribute(orca_main_kernel<KMAX, TPB, 1, false, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(orca_main_kernel<KMAX, TPB, 1, false, false, true>, (a.n + TPB - 1) / TPB, TPB,
+                      smem, st, a);
+}
+
+template <int KMAX>
+static cudaError_t dispatch_obs(const MainArgs& a, const LaunchShape& sh, cudaStream_t st) {
+    if (sh.tpb == 64) return launch_obs_k<KMAX, 64>(a, st);
+    return launch_obs_k<KMAX, 128>(a, st);
+}
+
 // Operation-counting launch: 128 threads, serial LP3, one CTA per tile (the counts are
 // algorithmic, so any launch shape gives the same numbers).
 template <int KMAX>
@@ -1076,6 +1231,12 @@ static cudaError_t dispatch(const MainArgs& a, int kmax, const LaunchShape& sh, 
         if (kmax <= 16) return launch_tape_k<16>(a, st);
         if (kmax <= 20) return launch_tape_k<20>(a, st);
         return launch_tape_k<32>(a, st);
+    }
+    if (a.nseg > 0 && !resident) {  // static obstacles (single scene, no tape, no counting)
+        if (kmax <= 10) return dispatch_obs<10>(a, sh, st);
+        if (kmax <= 16) return dispatch_obs<16>(a, sh, st);
+        if (kmax <= 20) return dispatch_obs<20>(a, sh, st);
+        return dispatch_obs<32>(a, sh, st);
     }
     if (a.count_ops && !resident) {
         if (kmax <= 10) return launch_count_k<10>(a, st);

@@ -363,3 +363,29 @@ def eight_way_crossing(n: int = 10000, seed: int = 1915, coverage: float = 0.3,
     goal = glo + rng.random((n, 2)) * (ghi - glo)
     return Scene("eight_way", _f32(pos), np.zeros((n, 2), np.float32), _f32(goal), radius, vmax,
                  pref, _full(n, time_horizon), neighbor_dist, max_neighbors, dt, steps)
+
+
+def bottleneck(n: int = 2000, seed: int = 1916, door: float = 2.4, coverage: float = 0.3,
+               neighbor_dist: float = 10.0, max_neighbors: int = 10, time_horizon: float = 5.0,
+               dt: float = 0.1, steps: int = 1500, obstacle_time_horizon: float = 2.0) -> Scene:
+    """A room emptying through a door (static obstacles; not in the paper's experiments):
+    a wall along x = 0 with a door of width ``door`` around y = 0, and the room's side
+    walls.  Agents (r 0.4 m, desired speed 1.3 m/s, maximum 1.6) spawn without overlap in
+    a square room left of the wall, sized like the crossings' start regions (spawn discs
+    cover 30%), and head for goals 15 m past the door, spread over the door's width."""
+    rng = np.random.default_rng(seed)
+    radius = _full(n, 0.4)
+    pref = _full(n, 1.3)
+    vmax = _full(n, 1.6)
+    side = _region_side(radius, pref, dt, [slice(0, n)], coverage)
+    h = 0.5 * side + 1.0
+    segs = np.array([[0.0, -h, 0.0, -0.5 * door], [0.0, 0.5 * door, 0.0, h],
+                     [-side - 5.0, -h, 0.0, -h], [-side - 5.0, h, 0.0, h]], np.float32)
+    lo = np.tile([[-2.0 - side, -0.5 * side]], (n, 1))
+    hi = np.tile([[-2.0, 0.5 * side]], (n, 1))
+    pos = spawn_without_overlap(rng, lo, hi, radius.astype(np.float64), pref.astype(np.float64) * dt)
+    goal = np.stack([np.full(n, 15.0), rng.uniform(-0.4, 0.4, n) * door], 1)
+    return Scene("bottleneck", _f32(pos), np.zeros((n, 2), np.float32), _f32(goal), radius, vmax,
+                 pref, _full(n, time_horizon), neighbor_dist, max_neighbors, dt, steps,
+                 obstacles=segs, obstacle_time_horizon=obstacle_time_horizon,
+                 max_obstacle_neighbors=4)

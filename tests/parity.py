@@ -40,7 +40,7 @@ def effective_max_cells(n, max_cells):
 
 
 def compare_step(scene, gpu_pos, gpu_vel, gpu_nbr, gpu_cells=None, gpu_grid=None,
-                 cell_size=0.0, max_cells=0, subset=None):
+                 cell_size=0.0, max_cells=0, subset=None, gpu_obst=None):
     """Oracle one step from ``scene``'s FP32 state; compare with the GPU's results (rows of
     agents ``subset`` if given).  Returns a report dict; raises AssertionError on failure."""
     n = scene.n
@@ -56,6 +56,10 @@ def compare_step(scene, gpu_pos, gpu_vel, gpu_nbr, gpu_cells=None, gpu_grid=None
     ref = oracle.step_scene(scene, knn_mode=1, subset=None if subset is None else rows,
                             sensitivity=True)
     np.testing.assert_array_equal(gpu_nbr[rows], ref["nbr"], err_msg="neighbour lists differ")
+    if gpu_obst is not None:
+        ko = ref["obst"].shape[1]
+        np.testing.assert_array_equal(gpu_obst[rows][:, :ko], ref["obst"],
+                                      err_msg="obstacle neighbours differ")
     dv = np.abs(gpu_vel[rows].astype(np.float64) - ref["vel"]).max(axis=1)
     tagged = (ref["margin"] < MARGIN) | (ref["sens"] > SENS_MAX)
     bad = dv > VEL_TOL
@@ -93,7 +97,8 @@ def gpu_step_and_compare(scene, steps_before=0, cell_size=0.0, max_cells=0, sim=
     pos, vel = sim.get_state()
     nbr = sim.get_neighbors()
     cells, gf, gi = sim.get_cells()
-    rep = compare_step(st, pos, vel, nbr, cells, (gf, gi), cell_size, max_cells, subset)
+    obst = sim.get_obstacle_neighbors() if getattr(st, "obstacles", None) is not None else None
+    rep = compare_step(st, pos, vel, nbr, cells, (gf, gi), cell_size, max_cells, subset, obst)
     if own:
         sim.close()
     return rep

@@ -95,3 +95,20 @@ def test_spawn_rejects_a_full_region():
     lo, hi = np.zeros((50, 2)), np.full((50, 2), 3.0)
     with pytest.raises(ValueError):
         S.spawn_without_overlap(rng, lo, hi, np.full(50, 0.5), np.zeros(50), max_tries=50)
+
+
+def test_bottleneck_layout():
+    sc = S.bottleneck(800, seed=7)
+    assert sc.obstacles.dtype == np.float32 and sc.obstacles.shape == (4, 4)
+    assert sc.max_obstacle_neighbors == 4 and sc.obstacle_time_horizon == np.float32(2.0)
+    # the door: the two wall pieces on x = 0 leave a gap of the door's width around y = 0
+    wall = sc.obstacles[:2]
+    assert np.all(wall[:, [0, 2]] == 0.0)
+    assert np.isclose(wall[1, 1] - wall[0, 3], 2.4)
+    # every agent in the room, clear of every wall by its radius, and the spawn discs apart
+    h = sc.obstacles[0, 1]
+    assert np.all(sc.pos[:, 0] < -sc.radius) and np.all(np.abs(sc.pos[:, 1]) < -h - sc.radius)
+    d = np.linalg.norm(sc.pos[:, None].astype(np.float64) - sc.pos[None], axis=2)
+    np.fill_diagonal(d, np.inf)
+    assert d.min() >= 2 * sc.radius.max()
+    assert np.all(sc.goal[:, 0] == 15.0) and np.all(np.abs(sc.goal[:, 1]) <= 0.4 * 2.4 + 1e-6)
