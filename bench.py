@@ -627,6 +627,109 @@ def run_dense(args):
     print(json.dumps(line), flush=True)
 
 
+def run_obstacles(args):
+    """Static obstacles (the ORCA obstacle rule; not in the paper's experiments): a
+    2,000-agent room emptying through a 2.4 m door until everyone has left, timed on the
+    wall clock with removals every ``--remove-every`` steps; then the cost of the obstacle
+    half-planes on two 524,288-agent crowds -- the bottleneck room and the bidirectional
+    flow with 256 random segments -- each stepped from the same state with and without its
+    obstacles (L2 flushed between steps, CUDA events on the stream; the ORCA kernel's time
+    from the library's phase events)."""
+    import torch
+    from paper_1908_10107_gb300 import abi, scenarios
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    every = args.remove_every
+    # 1. evacuation until the room is empty
+    sc = scenarios.bottleneck(2000)
+    sim = abi.OrcaSim.for_scene(sc)
+    for timed in (False, True):  # an untimed pass first (library load, first captures)
+        sim.set_scene(sc)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, agent_steps, n = 0, 0, sc.n
+        while n > 0 and steps < args.crossing_max_steps:
+            sim.step(every)
+            steps += every
+            agent_steps += n * every
+            n = abi.orca_remove_arrived(sim.ctx)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    evac = {"agents": sc.n, "steps_until_all_arrived": steps if n == 0 else None,
+            "agents_left": n, "simulated_s": steps * sc.dt, "wall_s": wall,
+            "agent_steps_per_s": agent_steps / wall, "ms_per_step": 1e3 * wall / max(steps, 1)}
+    sim.close()
+    # 2. obstacle cost on large crowds
+    room = scenarios.bottleneck(524288)
+    flow = scenarios.bidirectional()
+    rng = np.random.default_rng(1917)
+    lo, hi = flow.pos.min(0), flow.pos.max(0)
+    a = rng.uniform(lo, hi, (256, 2))
+    flow.obstacles = np.concatenate([a, a + rng.normal(0, 4, (256, 2))], 1).astype(np.float32)
+    flow.obstacle_time_horizon = np.float32(3.0)
+    flow.max_obstacle_neighbors = 4
+    cases = {}
+    for name, sc, skip in (("bottleneck_524288_steps_100_150", room, 100),
+                           ("flow_524288_256_segments_steps_1_50", flow, 0)):
+        sim = abi.OrcaSim.for_scene(sc)
+        sim.set_scene(sc)
+        if skip:
+            sim.step(skip)
+        pos, vel = sim.get_state()
+        start = sc.copy()
+        start.pos, start.vel = pos, vel
+        bare = start.copy()
+        bare.obstacles = None
+        row = {"segments": int(len(sc.obstacles))}
+        for key, s0 in (("obstacles", start), ("none", bare)):
+            sim.set_scene(s0)
+            ms = timed_steps(torch, lambda: sim.step(1), args.obst_steps, args.warmup, flush, stream)
+            abi.orca_profile(sim.ctx, True)
+            ks = []
+            for _ in range(10):
+                flush.fill_(0x5a)
+                sim.step(1)
+                ks.append(float(abi.orca_profile_read(sim.ctx)[2]))
+            abi.orca_profile(sim.ctx, False)
+            c = sim.counters()
+            row[key] = {"ms_per_step": ms / args.obst_steps,
+                        "agent_steps_per_s": sc.n * args.obst_steps / (ms * 1e-3),
+                        "orca_kernel_ms": float(np.mean(ks)),
+                        "lp3_fraction": c["lp3_agent_steps"] / max(c["agent_steps"], 1)}
+        row["agents_within_reach_of_a_segment"] = agents_within_reach(start)
+        cases[name] = row
+        sim.close()
+    head = cases["bottleneck_524288_steps_100_150"]["obstacles"]
+    line = {"metric": "agent-steps/sec with static obstacles (524,288-agent bottleneck room)",
+            "value": head["agent_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.obst_steps, "warmup": args.warmup,
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": "bottleneck rooms (2,000 agents until empty; 524,288 agents "
+                                   "steady) and the 524,288-agent flow with 256 random segments; "
+                                   "obstacle time horizon 2 s / 3 s, 4 obstacle lines per agent",
+                       "remove_every_steps": every, "l2": "flushed between steps"},
+            "evacuation_2000": evac, "cases": cases}
+    print(json.dumps(line), flush=True)
+
+
+def agents_within_reach(scene) -> int:
+    """How many agents have a segment within their reach V tau_o + r (host geometry, FP64)."""
+    seg = scene.obstacles.astype(np.float64)
+    p = scene.pos.astype(np.float64)
+    reach = scene.max_speed.astype(np.float64) * float(scene.obstacle_time_horizon) + scene.radius
+    a, e = seg[:, :2], seg[:, 2:] - seg[:, :2]
+    l2 = np.maximum((e * e).sum(1), 1e-300)
+    best = np.full(len(p), np.inf)
+    for lo in range(0, len(p), 1 << 14):
+        w = p[lo:lo + (1 << 14), None, :] - a[None]
+        t = np.clip((w * e[None]).sum(2) / l2[None], 0.0, 1.0)
+        q = w - t[..., None] * e[None]
+        best[lo:lo + (1 << 14)] = np.sqrt((q * q).sum(2)).min(1)
+    return int((best < reach).sum())
+
+
 def alu_roofline(sim, sc, abi, warmup, steps, main_ms, sms, sm_mhz):
     """Arithmetic roofline of the ORCA kernel: the timed steps replayed (untimed, from the
     same loaded state, so the trajectory is identical) with operation counting on, the
@@ -668,9 +771,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--clocks-out", default=None)
-    ap.add_argument("--workload", choices=["plain", "batched", "adjoint", "crossing", "lp_ab",
+    ap.add_argument("--workload", choices=["plain", "batched", "adjoint", "crossing", "lp_ab", "obstacles",
                                            "dense"], default="plain")
     ap.add_argument("--dense-steps", type=int, default=100, help="dense workload: timed steps")
+    ap.add_argument("--obst-steps", type=int, default=50, help="obstacles workload: timed steps")
     ap.add_argument("--ab-steps", type=int, default=30, help="lp_ab workload: timed steps per mode")
     ap.add_argument("--remove-every", type=int, default=20,
                     help="crossing workload: steps between removals of arrived agents")
@@ -694,6 +798,9 @@ def main():
         return
     if args.workload == "dense" and args.impl == "ours":
         run_dense(args)
+        return
+    if args.workload == "obstacles" and args.impl == "ours":
+        run_obstacles(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

@@ -215,6 +215,11 @@ ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
  * half-planes come first in the LP and stay hard in the least-penetration fallback.  The
  * segments stay until replaced; they apply to single-scene steps (ORCA_ERR_STATE in a
  * batch, with operation counting, or in rollouts).  Rebuilds the step graphs.
+ * A step with segments runs two more kernels: one flags the tiles of agents that could
+ * reach a segment, and an obstacle instantiation of the ORCA kernel steps those tiles on a
+ * second stream beside the plain launch (joined before the step ends, so a step stays
+ * ordered on the caller's stream).  The first call with segments creates that stream and
+ * two events; orca_destroy frees them.
  */
 ORCA_API int orca_set_obstacles(orca_ctx* ctx, int32_t n_seg, const float* seg_xyxy,
                                 float time_horizon, int32_t max_obstacle_neighbors, int where,

@@ -26,7 +26,7 @@ struct Layout {
 struct Plan {
     int N, K, S, max_cells, max_passes, nsb, nmb;
     size_t o_msg, o_sslot, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2], o_hint[2];
-    size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_scenes, o_slot, o_part, o_misc, o_blk, o_rnbr, o_rcell, o_robst, o_seg,
+    size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_scenes, o_slot, o_part, o_misc, o_blk, o_rnbr, o_rcell, o_robst, o_seg, o_near, o_otiles,
         o_stage[2];
     size_t total;
 };
@@ -80,6 +80,8 @@ static bool make_plan(const orca_params& p, Plan& pl) {
     pl.o_misc = L.add(sizeof(DeviceMisc));
     pl.o_blk = L.add((size_t)pl.nmb * kBlockCounters * sizeof(unsigned long long));
     pl.o_seg = L.add((size_t)kMaxObstacles * sizeof(float4));
+    pl.o_near = L.add((size_t)pl.nmb);       // a flag per 64-agent tile (obstacle steps)
+    pl.o_otiles = L.add((size_t)pl.nmb * 4);  // the flagged tiles
     if (p.flags & ORCA_FLAG_RECORD) {
         pl.o_rnbr = L.add(N * pl.K * 4);
         pl.o_rcell = L.add(N * 4);
@@ -109,6 +111,9 @@ struct orca_ctx {
     int32_t* rec_nbr = nullptr;
     uint32_t* rec_cell = nullptr;
     int32_t* rec_obst = nullptr;
+    unsigned char* tile_near = nullptr;  // obstacle steps: tiles near a segment, and their list
+    int* obs_tiles = nullptr;
+    SideStream side{nullptr, nullptr, nullptr};  // created with the first obstacles
     float4* seg = nullptr;  // static obstacle segments
     int nseg = 0, kobst = 0;
     float tau_o = 1.0f;
@@ -188,6 +193,8 @@ static void bind_buffers(orca_ctx* c) {
     c->rec_cell = pl.o_rcell == (size_t)-1 ? nullptr : (uint32_t*)(w + pl.o_rcell);
     c->rec_obst = pl.o_robst == (size_t)-1 ? nullptr : (int32_t*)(w + pl.o_robst);
     c->seg = (float4*)(w + pl.o_seg);
+    c->tile_near = (unsigned char*)(w + pl.o_near);
+    c->obs_tiles = (int*)(w + pl.o_otiles);
 }
 
 static void drop_graphs(orca_ctx* c) {
@@ -215,7 +222,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     e = launch_reorder(c->n, c->bins, c->PV[0], c->sorted, c->PR[par], c->PR[par ^ 1], st);
     if (e != cudaSuccess) return e;
     if (c->prof && (e = cudaEventRecordWithFlags(c->pev[2], st, cudaEventRecordExternal)) != cudaSuccess) return e;
-    MainArgs a;
+    MainArgs a{};
     a.n = c->n;
     a.k = pl.K;
     a.nd = c->p.neighbor_dist;
@@ -233,13 +240,18 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     a.kobst = c->kobst;
     a.tau_o = c->tau_o;
     a.rec_obst = c->rec_obst;
+    if (a.nseg > 0) {
+        a.tile_near = c->tile_near;
+        a.obs_tiles = c->obs_tiles;
+    }
     a.rec_nbr = c->rec_nbr;
     a.rec_cell = c->rec_cell;
     a.scenes = c->n_scenes > 0 ? c->scenes : nullptr;
     a.slot_scene = c->n_scenes > 0 ? c->slot_scene : nullptr;
     a.rec_stride = pl.K;
     a.tape = nullptr;
-    e = launch_main(a, pl.K, c->shape, c->n_scenes > 0 ? c->resident : 0, st);
+    e = launch_main(a, pl.K, c->shape, c->n_scenes > 0 ? c->resident : 0, st,
+                    a.nseg > 0 && c->side.st ? &c->side : nullptr);
     if (e != cudaSuccess) return e;
     if (c->prof) e = cudaEventRecordWithFlags(c->pev[3], st, cudaEventRecordExternal);
     return e;
@@ -247,8 +259,10 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
 
 // kernels per step: bounding box (a batch: scene boxes and scene prefix), keys+histogram,
 // per radix pass (upsweep except pass 0, scan, downsweep), reorder + cell table, ORCA kernel
+// (with obstacles: tile flags, the plain ORCA launch and the obstacle launch)
 static int launches_per_step(const orca_ctx* c) {
-    return (c->n_scenes > 0 ? 3 : 2) + 3 * c->plan.max_passes - 1 + 2;
+    const int obstacles = c->n_scenes == 0 && c->nseg > 0 ? 2 : 0;  // tile flags, obstacle launch
+    return (c->n_scenes > 0 ? 3 : 2) + 3 * c->plan.max_passes - 1 + 2 + obstacles;
 }
 
 // One step launched directly with the neighbour lists and LP records written in agent
@@ -261,7 +275,7 @@ static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, ui
     if (e != cudaSuccess) return e;
     e = launch_reorder(c->n, c->bins, c->PV[0], c->sorted, c->PR[par], c->PR[par ^ 1], st);
     if (e != cudaSuccess) return e;
-    MainArgs a;
+    MainArgs a{};
     a.n = c->n;
     a.k = pl.K;
     a.nd = c->p.neighbor_dist;
@@ -380,6 +394,9 @@ ORCA_API int orca_destroy(orca_ctx* ctx) {
     for (int q = 0; q < 4; ++q)
         if (ctx->pev[q]) cudaEventDestroy(ctx->pev[q]);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->side.st) cudaStreamDestroy(ctx->side.st);
+    if (ctx->side.fork) cudaEventDestroy(ctx->side.fork);
+    if (ctx->side.join) cudaEventDestroy(ctx->side.join);
     if (ctx->own_ws) cudaFree(ctx->ws);
     delete ctx;
     return ORCA_OK;
@@ -629,6 +646,11 @@ ORCA_API int orca_set_obstacles(orca_ctx* ctx, int32_t n_seg, const float* seg_x
                            where == ORCA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st),
            "copy segments");
         if (where == ORCA_HOST) CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        if (!ctx->side.st) {
+            CK(cudaStreamCreateWithFlags(&ctx->side.st, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+            CK(cudaEventCreateWithFlags(&ctx->side.fork, cudaEventDisableTiming), "cudaEventCreateWithFlags");
+            CK(cudaEventCreateWithFlags(&ctx->side.join, cudaEventDisableTiming), "cudaEventCreateWithFlags");
+        }
         ctx->kobst = max_obstacle_neighbors;
         ctx->tau_o = time_horizon;
     }

@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(256) bbox_grid_kernel(int n, const float2* __r
     }
     misc->bbox_ticket = 0;
     misc->tile_counter = 0;
+    misc->obs_tiles = 0;
     int err = 0;
     misc->grid = derive_grid(r, cell_size, max_cells, max_passes, &err);
     if (err) atomicOr(&misc->error, err);

@@ -52,7 +52,7 @@ struct DeviceMisc {
     unsigned int bbox_ticket;  // last-block-done counter of the bbox reduction
     int error;                 // kErr* bits
     unsigned int tile_counter; // next tile of the persistent ORCA kernel (reset every step)
-    int pad_;
+    unsigned int obs_tiles;    // tiles listed for the obstacle launch (reset every step)
     unsigned long long counters[4];  // agent-steps, LP3 agent-steps, candidates, lines
 };
 
@@ -123,6 +123,12 @@ struct MainArgs {
     int nseg, kobst;                     // segments; obstacle half-planes kept per agent
     float tau_o;                         // obstacle time horizon
     int32_t* rec_obst;                   // kMaxObstacleNeighbors per agent (agent order), or null
+    int row_stride;                      // float4s per shared-memory row (obstacle launches)
+    // With obstacles the tiles some agent of which could reach a segment are flagged and
+    // listed (obstacle_tiles_kernel); the plain launch skips them, the obstacle launch
+    // steps only them.  Null without obstacles.
+    unsigned char* tile_near = nullptr;
+    int* obs_tiles = nullptr;
     int32_t* rec_nbr;                    // n*k in agent order, or null
     uint32_t* rec_cell;                  // n in agent order, or null
 };
@@ -151,8 +157,15 @@ struct LaunchShape {
 };
 int default_lp3_group(int kmax);
 // kmax: template bound (>= every scene's k); grid_blocks > 0: persistent launch
+// A second stream and two events for a step with static obstacles: the obstacle launch
+// forks onto `st` after the tile flags and joins the step's stream before it continues.
+struct SideStream {
+    cudaStream_t st;
+    cudaEvent_t fork, join;
+};
 cudaError_t launch_main(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
-                        cudaStream_t st);
+                        cudaStream_t st,
+                        const SideStream* side = nullptr);
 int main_resident_blocks(int kmax, const LaunchShape& sh);
 // orca_population.cu: remove the agents that have reached their goal (see there)
 cudaError_t launch_remove_arrived(int n, const AgentState& cur, const AgentParams& cur_p,

@@ -16,8 +16,12 @@ constexpr int kLineRightLeg = 2;
 constexpr int kLineOverlap = 3;       // agents overlap: one-step disc
 constexpr int kLineOverlapFixed = 4;  // overlap with q = 0: direction fixed by a rule
 
+// Every formula below is written with explicit FP32 operations (fused where a product
+// feeds a sum), none left to the compiler's contraction: each kernel that builds a
+// half-plane -- the plain and the obstacle instantiations of the step, the adjoint --
+// then rounds it identically, whatever code surrounds the call.
 __device__ __forceinline__ float det2f(float ax, float ay, float bx, float by) {
-    return ax * by - ay * bx;
+    return __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
 }
 
 // Half-plane of agent (p, v, r, 1/tau) induced by neighbour message mj = (x, y, r, id)
@@ -32,56 +36,59 @@ __device__ __forceinline__ float det2f(float ax, float ay, float bx, float by) {
 __device__ __forceinline__ float4 orca_line_dev(float2 p, float2 v, float r, float itau,
                                                 float dt, float half_idt, uint32_t me,
                                                 float4 mj, float2 vj, int* branch = nullptr) {
-    float px = mj.x - p.x, py = mj.y - p.y;
-    float vx = v.x - vj.x, vy = v.y - vj.y;
-    float R = r + mj.z;
-    float p2 = px * px + py * py, R2 = R * R;
+    const float px = __fsub_rn(mj.x, p.x), py = __fsub_rn(mj.y, p.y);
+    const float vx = __fsub_rn(v.x, vj.x), vy = __fsub_rn(v.y, vj.y);
+    const float R = __fadd_rn(r, mj.z);
+    const float p2 = __fmaf_rn(px, px, __fmul_rn(py, py)), R2 = __fmul_rn(R, R);
     float4 L;
     L.w = 0.0f;
     if (p2 > R2) {
-        float wx = vx - px * itau, wy = vy - py * itau;
-        float w2 = wx * wx + wy * wy, wp = wx * px + wy * py;
-        if (wp < 0.0f && wp * wp > R2 * w2) {
+        const float wx = __fmaf_rn(-px, itau, vx), wy = __fmaf_rn(-py, itau, vy);
+        const float w2 = __fmaf_rn(wx, wx, __fmul_rn(wy, wy));
+        const float wp = __fmaf_rn(wx, px, __fmul_rn(wy, py));
+        if (wp < 0.0f && __fmul_rn(wp, wp) > __fmul_rn(R2, w2)) {
             if (branch) *branch = kLineCutoff;
-            float iw = rsqrtf(w2);
-            L.x = wx * iw;
-            L.y = wy * iw;
-            L.z = L.x * v.x + L.y * v.y + 0.5f * (R * itau - w2 * iw);
+            const float iw = rsqrtf(w2);
+            L.x = __fmul_rn(wx, iw);
+            L.y = __fmul_rn(wy, iw);
+            const float half_gap = __fmul_rn(0.5f, __fmaf_rn(R, itau, -__fmul_rn(w2, iw)));
+            L.z = __fmaf_rn(L.x, v.x, __fmaf_rn(L.y, v.y, half_gap));
         } else {
-            float l2 = p2 - R2;
-            float leg = l2 * rsqrtf(l2);
-            float ip2 = __fdividef(1.0f, p2);
+            const float l2 = __fsub_rn(p2, R2);
+            const float leg = __fmul_rn(l2, rsqrtf(l2));
+            const float ip2 = __fdividef(1.0f, p2);
             if (det2f(px, py, wx, wy) > 0.0f) {  // left leg
                 if (branch) *branch = kLineLeftLeg;
-                L.x = -(px * R + py * leg) * ip2;
-                L.y = (px * leg - py * R) * ip2;
+                L.x = -__fmul_rn(__fmaf_rn(px, R, __fmul_rn(py, leg)), ip2);
+                L.y = __fmul_rn(__fmaf_rn(px, leg, -__fmul_rn(py, R)), ip2);
             } else {  // right leg
                 if (branch) *branch = kLineRightLeg;
-                L.x = (py * leg - px * R) * ip2;
-                L.y = -(px * leg + py * R) * ip2;
+                L.x = __fmul_rn(__fmaf_rn(py, leg, -__fmul_rn(px, R)), ip2);
+                L.y = -__fmul_rn(__fmaf_rn(px, leg, __fmul_rn(py, R)), ip2);
             }
-            L.z = 0.5f * (L.x * (v.x + vj.x) + L.y * (v.y + vj.y));
+            L.z = __fmul_rn(0.5f, __fmaf_rn(L.x, __fadd_rn(v.x, vj.x),
+                                            __fmul_rn(L.y, __fadd_rn(v.y, vj.y))));
         }
     } else {
-        float qx = px - vx * dt, qy = py - vy * dt;  // = -w dt
-        float ql = sqrtf(qx * qx + qy * qy);
+        const float qx = __fmaf_rn(-vx, dt, px), qy = __fmaf_rn(-vy, dt, py);  // = -w dt
+        const float ql = sqrtf(__fmaf_rn(qx, qx, __fmul_rn(qy, qy)));
         float nx, ny;
         if (branch) *branch = ql > 0.0f ? kLineOverlap : kLineOverlapFixed;
         if (ql > 0.0f) {
-            float iq = __fdividef(1.0f, ql);
-            nx = -qx * iq;
-            ny = -qy * iq;
+            const float iq = __fdividef(1.0f, ql);
+            nx = -__fmul_rn(qx, iq);
+            ny = -__fmul_rn(qy, iq);
         } else if (p2 > 0.0f) {
-            float ip = rsqrtf(p2);
-            nx = -px * ip;
-            ny = -py * ip;
+            const float ip = rsqrtf(p2);
+            nx = -__fmul_rn(px, ip);
+            ny = -__fmul_rn(py, ip);
         } else {
             nx = me < __float_as_uint(mj.w) ? 1.0f : -1.0f;
             ny = 0.0f;
         }
         L.x = nx;
         L.y = ny;
-        L.z = nx * v.x + ny * v.y + (R - ql) * half_idt;
+        L.z = __fmaf_rn(nx, v.x, __fmaf_rn(ny, v.y, __fmul_rn(__fsub_rn(R, ql), half_idt)));
     }
     return L;
 }
@@ -91,15 +98,16 @@ __device__ __forceinline__ float4 orca_line_dev(float2 p, float2 v, float r, flo
 // first case.
 __device__ __forceinline__ float2 pref_velocity_dev(float2 p, float2 goal, float pref, float dt,
                                                     float idt, int* far = nullptr) {
-    float gx_ = goal.x - p.x, gy_ = goal.y - p.y;
-    float g2 = gx_ * gx_ + gy_ * gy_;
-    float ig = rsqrtf(g2);
-    if (g2 * ig > pref * dt) {
+    const float gx_ = __fsub_rn(goal.x, p.x), gy_ = __fsub_rn(goal.y, p.y);
+    const float g2 = __fmaf_rn(gx_, gx_, __fmul_rn(gy_, gy_));
+    const float ig = rsqrtf(g2);
+    if (__fmul_rn(g2, ig) > __fmul_rn(pref, dt)) {
         if (far) *far = 1;
-        return make_float2(gx_ * (pref * ig), gy_ * (pref * ig));
+        const float s = __fmul_rn(pref, ig);
+        return make_float2(__fmul_rn(gx_, s), __fmul_rn(gy_, s));
     }
     if (far) *far = 0;
-    return make_float2(gx_ * idt, gy_ * idt);
+    return make_float2(__fmul_rn(gx_, idt), __fmul_rn(gy_, idt));
 }
 
 }  // namespace orca

@@ -720,20 +720,84 @@ __device__ __forceinline__ float4 obstacle_line(float4 sg, float2 p, float r, fl
     return make_float4(nx, ny, c, 0.0f);
 }
 
+// Whether segment sg could be within reach R of some point of the box [x0, x1] x [y0, y1]:
+// its own box against the box widened by R and a margin well above the FP32 rounding of
+// the distance test (a few ulps of the largest coordinate involved).  False means the
+// segment is farther than R from every point of the box.
+__device__ __forceinline__ bool segment_in_reach(float4 sg, float x0, float y0, float x1, float y1,
+                                                 float R) {
+    const float M = fmaxf(fmaxf(fabsf(x0), fabsf(x1)), fmaxf(fabsf(y0), fabsf(y1)));
+    const float ms = fmaxf(fmaxf(fabsf(sg.x), fabsf(sg.z)), fmaxf(fabsf(sg.y), fabsf(sg.w)));
+    const float g = R + 1e-4f * (1.0f + fmaxf(M, ms) + R);
+    return fminf(sg.x, sg.z) <= x1 + g && fmaxf(sg.x, sg.z) >= x0 - g &&
+           fminf(sg.y, sg.w) <= y1 + g && fmaxf(sg.y, sg.w) >= y0 - g;
+}
+
+// Segments some agent of the tile could select.  The tile's agents are neighbours in the
+// cell order, so their bounding box is small; each segment is tested against it and the
+// tile's largest reach fl(fl(V tau_o) + r) (segment_in_reach).  The selection keys
+// carry the segment index, so the kept subset, in any order, selects what a scan of all
+// segments selects.  Ends with a barrier; nsel must be 0 on entry.
+template <int TPB>
+__device__ __forceinline__ void cull_segments(const MainArgs& a, int t, bool active,
+                                              unsigned short* sel, int* nsel, float (*box)[5]) {
+    float x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY, R = 0.0f;
+    if (active) {
+        const float4 m = a.in.msg[t];
+        x0 = x1 = m.x;
+        y0 = y1 = m.y;
+        R = __fadd_rn(__fmul_rn(a.prm.max_speed[t], a.tau_o), m.z);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+        R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        float* b = box[threadIdx.x >> 5];
+        b[0] = x0;
+        b[1] = y0;
+        b[2] = x1;
+        b[3] = y1;
+        b[4] = R;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < TPB / 32; ++w) {
+        x0 = fminf(x0, box[w][0]);
+        y0 = fminf(y0, box[w][1]);
+        x1 = fmaxf(x1, box[w][2]);
+        y1 = fmaxf(y1, box[w][3]);
+        R = fmaxf(R, box[w][4]);
+    }
+#pragma unroll 1
+    for (int j = threadIdx.x; j < a.nseg; j += TPB)
+        if (segment_in_reach(__ldg(a.seg + j), x0, y0, x1, y1, R))
+            sel[atomicAdd(nsel, 1)] = (unsigned short)j;
+    __syncthreads();
+}
+
 // Writes the agent's obstacle half-planes to row[0..] (nearest first) and returns how many;
 // rec (may be null) receives the segments' indices, -1 padded to kMaxObstacleNeighbors.
+// Only the segments sel[0..nsel) are scanned (cull_segments keeps every one that an agent
+// of the tile could select).
 template <int KO>
-__device__ __forceinline__ int obstacle_lines(const float4* segs, int nseg, int kobst, float2 p,
-                                              float r, float V, float dt, float tau_o,
-                                              float4* row, int32_t* rec) {
+__device__ __forceinline__ int obstacle_lines(const float4* __restrict__ segs,
+                                              const unsigned short* sel,
+                                              int nsel, int kobst, float2 p, float r, float V,
+                                              float dt, float tau_o, float4* row, int32_t* rec) {
     const float rng = __fadd_rn(__fmul_rn(V, tau_o), r);
     const float rng2 = __fmul_rn(rng, rng);
     unsigned long long ok[KO];
 #pragma unroll
     for (int l = 0; l < KO; ++l) ok[l] = (l < KO - kobst) ? 0ull : ~0ull;
 #pragma unroll 1
-    for (int j = 0; j < nseg; ++j) {
-        const float d2 = seg_dist2(segs[j], p);
+    for (int q = 0; q < nsel; ++q) {
+        const int j = sel[q];
+        const float d2 = seg_dist2(__ldg(segs + j), p);
         if (d2 < rng2) insert_key<KO>(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j, ok);
     }
     int nob = 0;
@@ -742,7 +806,7 @@ __device__ __forceinline__ int obstacle_lines(const float4* segs, int nseg, int 
         if (l < KO - kobst || ok[l] == ~0ull) continue;
         const int j = (int)(ok[l] & 0xffffffffu);
         if (rec) rec[nob] = j;
-        row[nob++] = obstacle_line(segs[j], p, r, dt, tau_o);
+        row[nob++] = obstacle_line(__ldg(segs + j), p, r, dt, tau_o);
     }
     if (rec)
         for (int l = nob; l < kMaxObstacleNeighbors; ++l) rec[l] = -1;
@@ -879,12 +943,15 @@ constexpr int main_min_blocks() {
 // checks every mode).
 int default_lp3_group(int kmax) { return kmax <= 16 ? 1 : 32; }
 
-// Row of one agent: KMAX neighbour half-planes (plus kMaxObstacleNeighbors obstacle ones
-// in the obstacle instantiation) and one float4 of padding (conflict-free float4 rows).
-template <int KMAX, bool OBS = false>
-constexpr int row_len() { return KMAX + (OBS ? kMaxObstacleNeighbors : 0) + 1; }
-template <int KMAX, int TPB, bool OBS = false>
-constexpr size_t main_smem_bytes() { return sizeof(float4) * TPB * row_len<KMAX, OBS>(); }
+// Row of one agent: KMAX neighbour half-planes and one float4 of padding (an odd stride in
+// float4s: conflict-free float4 rows).  With static obstacles the row also holds the
+// kobst obstacle half-planes; its stride is set per launch (obs_row_len), so a few
+// obstacle lines cost a few float4s of shared memory per agent, not the maximum.
+template <int KMAX>
+constexpr int row_len() { return KMAX + 1; }
+template <int KMAX, int TPB>
+constexpr size_t main_smem_bytes() { return sizeof(float4) * TPB * row_len<KMAX>(); }
+constexpr int obs_row_len(int kmax, int kobst) { return (kmax + kobst) | 1; }
 
 // Parameters of the scene an agent belongs to (the one scene, or its scene of a batch).
 struct SceneView {
@@ -912,11 +979,53 @@ __device__ __forceinline__ void scene_view(const MainArgs& a, int t, SceneView& 
 
 // Persistent over tiles of TPB consecutive agents: tile blockIdx.x first, then
 // tiles taken from a per-step counter (with one CTA per tile this loop runs once).
+// Tiles (TPB consecutive sorted slots, the ORCA kernel's CTAs) with a segment within reach
+// of some agent: one warp per tile, the same reach test as cull_segments.  Flags them for
+// the plain launch to skip and lists them for the obstacle launch, so a crowd pays for the
+// obstacle instantiation (wider rows, culling) only near obstacles.  The list's order
+// varies between runs; each tile's results do not depend on it.
+__global__ void __launch_bounds__(256) obstacle_tiles_kernel(MainArgs a, int tpb) {
+    pdl_wait();
+    const int ntiles = (a.n + tpb - 1) / tpb;
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= ntiles) return;  // whole warps
+    float x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY, R = 0.0f;
+    for (int i = lane; i < tpb; i += 32) {
+        const int t = w * tpb + i;
+        if (t >= a.n) break;
+        const float4 m = a.in.msg[t];
+        x0 = fminf(x0, m.x);
+        y0 = fminf(y0, m.y);
+        x1 = fmaxf(x1, m.x);
+        y1 = fmaxf(y1, m.y);
+        R = fmaxf(R, __fadd_rn(__fmul_rn(a.prm.max_speed[t], a.tau_o), m.z));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+        R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
+    }
+    bool near = false;
+    for (int j = lane; j < a.nseg && !near; j += 32)
+        near = segment_in_reach(__ldg(a.seg + j), x0, y0, x1, y1, R);
+    near = __any_sync(0xffffffffu, near);
+    if (lane == 0) {
+        a.tile_near[w] = near ? 1 : 0;
+        if (near) a.obs_tiles[atomicAdd(&a.misc_rw->obs_tiles, 1u)] = w;
+    }
+}
+
 template <int KMAX, int TPB, int G, bool TAPE = false, bool COUNT = false, bool OBS = false>
 __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_kernel(MainArgs a) {
     pdl_wait();
-    constexpr int KP = row_len<KMAX, OBS>();  // padded rows: conflict-free float4 accesses
-    extern __shared__ float4 s_lines[];  // TPB * KP half-planes
+    // padded rows: conflict-free float4 accesses; KP float4s always (the kNN parking space)
+    constexpr int KP = row_len<KMAX>();
+    const int kp = OBS ? a.row_stride : KP;
+    extern __shared__ float4 s_lines[];  // TPB * kp half-planes
     __shared__ float2 s_x[TPB];
     __shared__ float s_V[TPB];
     __shared__ unsigned char s_b[TPB];
@@ -929,11 +1038,11 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     __shared__ unsigned long long s_ops[COUNT ? 4 : 1];
     constexpr bool WU = G == 32;  // work-unit LP (warp-cooperative) instead of per-lane LP
     __shared__ WarpLpShared s_wlp[WU ? TPB / 32 : 1];
-    __shared__ float4 s_seg[OBS ? kMaxObstacles : 1];      // static obstacle segments
     __shared__ unsigned char s_nob[OBS ? TPB : 1];         // obstacle lines in each row
+    __shared__ unsigned short s_sel[OBS ? kMaxObstacles : 1];  // segments the tile can reach
+    __shared__ float s_box[OBS ? TPB / 32 : 1][5];
+    __shared__ int s_nsel;
     const int tid = threadIdx.x;
-    if (OBS)
-        for (int j = tid; j < a.nseg; j += TPB) s_seg[j] = a.seg[j];
     if (tid == 0) {
         s_cand = 0;
         s_lines_n = 0;
@@ -943,14 +1052,25 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     }
     OpCount oc{0u, 0u, 0u, 0u};
     const int ntiles = (a.n + TPB - 1) / TPB;
-    float4* row = s_lines + tid * KP;
+    float4* row = s_lines + tid * kp;
+    // the obstacle launch steps the listed tiles li = blockIdx.x, + gridDim.x, ...
+    const int nlist = OBS ? (int)a.misc->obs_tiles : 0;
+    int li = blockIdx.x;
+    int tile = OBS ? (li < nlist ? a.obs_tiles[li] : ntiles) : (int)blockIdx.x;
 #pragma unroll 1
-    for (int tile = blockIdx.x; tile < ntiles;) {
-        if (tid == 0) s_qn = 0;
+    while (tile < ntiles) {
+        // with obstacles the plain launch (one CTA per tile) leaves flagged tiles to the
+        // obstacle launch
+        if (!OBS && a.tile_near != nullptr && a.tile_near[tile]) break;
+        if (tid == 0) {
+            s_qn = 0;
+            s_nsel = 0;
+        }
         s_queued[tid] = 0;
         __syncthreads();
         const int t = tile * TPB + tid;
         const bool active = t < a.n;
+        if (OBS) cull_segments<TPB>(a, t, active, s_sel, &s_nsel, s_box);
         float2 p = make_float2(0.0f, 0.0f);
         float xx = 0.0f, xy = 0.0f, dt = 1.0f, V = 0.0f, ox = 0.0f, oy = 0.0f;
         uint32_t me = 0;
@@ -993,10 +1113,14 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 a.prm.hint[t] = kk[KMAX - 1] != ~0ull
                                     ? __uint_as_float((unsigned)(kk[KMAX - 1] >> 32))
                                     : INFINITY;
-            // static obstacles first: their half-planes open the row
+            // static obstacles first: their half-planes open the row (a plain launch records
+            // none)
+            if (!OBS && a.rec_obst)
+                for (int l = 0; l < kMaxObstacleNeighbors; ++l)
+                    a.rec_obst[(size_t)me * kMaxObstacleNeighbors + l] = -1;
             if (OBS)
                 nob = obstacle_lines<kMaxObstacleNeighbors>(
-                    s_seg, a.nseg, a.kobst, p, me4.z, V, dt, a.tau_o, row,
+                    a.seg, s_sel, s_nsel, a.kobst, p, me4.z, V, dt, a.tau_o, row,
                     a.rec_obst ? a.rec_obst + (size_t)me * kMaxObstacleNeighbors : nullptr);
             // park the neighbours' slots in the row (one unrolled store each), then build
             // the half-planes in a rolled loop: one copy of the line code keeps the kernel
@@ -1046,7 +1170,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         }
         if (WU) {
             // the whole warp runs its LP2s together (lanes past the crowd's end only help)
-            int b = warp_lp2_units(s_wlp[WU ? tid >> 5 : 0], s_lines, tid * KP, active, cnt, V, ox,
+            int b = warp_lp2_units(s_wlp[WU ? tid >> 5 : 0], s_lines, tid * kp, active, cnt, V, ox,
                                    oy, xx, xy);
             if (active && b < cnt) enqueue(b);
         }
@@ -1068,7 +1192,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 const bool has = q < nq;
                 const int ag = has ? s_queue[q] : 0;
                 float2 x = has ? s_x[ag] : make_float2(0.0f, 0.0f);
-                warp_lp3_units(s_wlp[WU ? tid >> 5 : 0], s_lines, ag * KP, has, has ? s_cnt[ag] : 0,
+                warp_lp3_units(s_wlp[WU ? tid >> 5 : 0], s_lines, ag * kp, has, has ? s_cnt[ag] : 0,
                                has ? s_b[ag] : 0, has ? s_V[ag] : 0.0f, x.x, x.y);
                 if (has) s_x[ag] = x;
             }
@@ -1076,10 +1200,10 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         for (int q = q0; !WU && q < nq; q += TPB / GL) {
             int ag = s_queue[q];
             float2 x = s_x[ag];
-            if (G == 1) lp3_dev(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y,
+            if (G == 1) lp3_dev(s_lines + ag * kp, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y,
                                 TAPE ? &s_tape[TAPE ? ag : 0] : nullptr, COUNT ? &oc : nullptr,
                                 OBS ? s_nob[OBS ? ag : 0] : 0);
-            else lp3_group_dev<WU ? 4 : G>(s_lines + ag * KP, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
+            else lp3_group_dev<WU ? 4 : G>(s_lines + ag * kp, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
             if ((tid & (G - 1)) == 0) s_x[ag] = x;
         }
         __syncthreads();
@@ -1090,7 +1214,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 xx = x.x;
                 xy = x.y;
             }
-            float nx = p.x + xx * dt, ny = p.y + xy * dt;
+            const float nx = __fmaf_rn(xx, dt, p.x), ny = __fmaf_rn(xy, dt, p.y);
             if (!isfinite(xx) || !isfinite(xy) || !isfinite(nx) || !isfinite(ny))
                 atomicOr(&a.misc_rw->error, kErrNumeric);
             a.out.vel[t] = make_float2(xx, xy);
@@ -1116,20 +1240,28 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             }
             oc = OpCount{0u, 0u, 0u, 0u};
         }
+        if (OBS) {
+            li += gridDim.x;
+            tile = li < nlist ? a.obs_tiles[li] : ntiles;
+            __syncthreads();
+            continue;
+        }
         if ((int)gridDim.x >= ntiles) break;  // one CTA per tile: no work queue
         if (tid == 0) s_tile = (int)atomicAdd(&a.misc_rw->tile_counter, 1u) + (int)gridDim.x;
         __syncthreads();
         tile = s_tile;
     }
     __syncthreads();
+    // atomic: with obstacles the plain and the obstacle launch run side by side and their
+    // CTAs share rows
     if (tid == 0) {
         unsigned long long* c = a.block_counters + kBlockCounters * (size_t)blockIdx.x;
-        c[0] += s_act;
-        c[1] += s_lp3;
-        c[2] += s_cand;
-        c[3] += s_lines_n;
+        atomicAdd(c + 0, s_act);
+        atomicAdd(c + 1, s_lp3);
+        atomicAdd(c + 2, s_cand);
+        atomicAdd(c + 3, s_lines_n);
         if (COUNT)
-            for (int q = 0; q < 4; ++q) c[4 + q] += s_ops[COUNT ? q : 0];
+            for (int q = 0; q < 4; ++q) atomicAdd(c + 4 + q, s_ops[COUNT ? q : 0]);
     }
 }
 
@@ -1187,21 +1319,52 @@ static cudaError_t dispatch_tpb(const MainArgs& a, const LaunchShape& sh, int gr
     return dispatch_g<KMAX, 128>(a, sh.lp3_group, grid_blocks, st, resident);
 }
 
-// Launch with static obstacles: one lane per solve, 64 or 128 threads, one CTA per tile.
+// Obstacle launch: one lane per solve, 64 or 128 threads; the listed tiles are dealt over
+// at most 2048 CTAs (one pass each when fewer tiles are listed).
 template <int KMAX, int TPB>
 static cudaError_t launch_obs_k(const MainArgs& a, cudaStream_t st) {
-    constexpr size_t smem = main_smem_bytes<KMAX, TPB, true>();
+    constexpr size_t smem_max = sizeof(float4) * TPB * obs_row_len(KMAX, kMaxObstacleNeighbors);
     cudaError_t e = cudaFuncSetAttribute(orca_main_kernel<KMAX, TPB, 1, false, false, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     if (e != cudaSuccess) return e;
-    return launch_pdl(orca_main_kernel<KMAX, TPB, 1, false, false, true>, (a.n + TPB - 1) / TPB, TPB,
-                      smem, st, a);
+    MainArgs b = a;
+    b.row_stride = obs_row_len(KMAX, a.kobst);
+    const int ntiles = (a.n + TPB - 1) / TPB;
+    return launch_pdl(orca_main_kernel<KMAX, TPB, 1, false, false, true>, ntiles < 2048 ? ntiles : 2048,
+                      TPB, sizeof(float4) * TPB * b.row_stride, st, b);
 }
 
+// A step with static obstacles: flag and list the tiles near a segment, then the plain
+// launch over the other tiles and the obstacle launch over the listed ones.  The two
+// touch disjoint tiles, so with a side stream they run concurrently (a fork after the
+// flags, a join before the step goes on): the few obstacle tiles, often the slowest
+// (agents pressed into walls need least penetration), then overlap the bulk instead of
+// trailing it.  Tiles are 64 or 128 agents in both (a 256-thread shape runs as 128).
 template <int KMAX>
-static cudaError_t dispatch_obs(const MainArgs& a, const LaunchShape& sh, cudaStream_t st) {
-    if (sh.tpb == 64) return launch_obs_k<KMAX, 64>(a, st);
-    return launch_obs_k<KMAX, 128>(a, st);
+static cudaError_t dispatch_obs(const MainArgs& a, const LaunchShape& sh, cudaStream_t st,
+                                const SideStream* side) {
+    if (a.n == 0) return cudaSuccess;
+    const int tpb = sh.tpb == 64 ? 64 : 128;
+    const int ntiles = (a.n + tpb - 1) / tpb;
+    cudaError_t e = launch_pdl(obstacle_tiles_kernel, (ntiles * 32 + 255) / 256, 256, 0, st, a, tpb);
+    if (e != cudaSuccess) return e;
+    MainArgs b = a;
+    b.tile_near = nullptr;
+    cudaStream_t obs_st = st;
+    if (side) {
+        if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side->st, side->fork, 0)) != cudaSuccess) return e;
+        obs_st = side->st;
+        e = tpb == 64 ? launch_obs_k<KMAX, 64>(b, obs_st) : launch_obs_k<KMAX, 128>(b, obs_st);
+        if (e != cudaSuccess) return e;
+    }
+    e = dispatch_tpb<KMAX>(a, LaunchShape{tpb, sh.lp3_group}, 0, st, nullptr);
+    if (e != cudaSuccess) return e;
+    if (side) {
+        if ((e = cudaEventRecord(side->join, side->st)) != cudaSuccess) return e;
+        return cudaStreamWaitEvent(st, side->join, 0);
+    }
+    return tpb == 64 ? launch_obs_k<KMAX, 64>(b, st) : launch_obs_k<KMAX, 128>(b, st);
 }
 
 // Operation-counting launch: 128 threads, serial LP3, one CTA per tile (the counts are
@@ -1225,7 +1388,7 @@ static cudaError_t launch_tape_k(const MainArgs& a, cudaStream_t st) {
 }
 
 static cudaError_t dispatch(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
-                            cudaStream_t st, int* resident) {
+                            cudaStream_t st, int* resident, const SideStream* side = nullptr) {
     if (a.tape && !resident) {  // recording step of a rollout: 128 threads, serial LP3
         if (kmax <= 10) return launch_tape_k<10>(a, st);
         if (kmax <= 16) return launch_tape_k<16>(a, st);
@@ -1233,10 +1396,10 @@ static cudaError_t dispatch(const MainArgs& a, int kmax, const LaunchShape& sh, 
         return launch_tape_k<32>(a, st);
     }
     if (a.nseg > 0 && !resident) {  // static obstacles (single scene, no tape, no counting)
-        if (kmax <= 10) return dispatch_obs<10>(a, sh, st);
-        if (kmax <= 16) return dispatch_obs<16>(a, sh, st);
-        if (kmax <= 20) return dispatch_obs<20>(a, sh, st);
-        return dispatch_obs<32>(a, sh, st);
+        if (kmax <= 10) return dispatch_obs<10>(a, sh, st, side);
+        if (kmax <= 16) return dispatch_obs<16>(a, sh, st, side);
+        if (kmax <= 20) return dispatch_obs<20>(a, sh, st, side);
+        return dispatch_obs<32>(a, sh, st, side);
     }
     if (a.count_ops && !resident) {
         if (kmax <= 10) return launch_count_k<10>(a, st);
@@ -1258,8 +1421,8 @@ int main_resident_blocks(int kmax, const LaunchShape& sh) {
 }
 
 cudaError_t launch_main(const MainArgs& a, int kmax, const LaunchShape& sh, int grid_blocks,
-                        cudaStream_t st) {
-    return dispatch(a, kmax, sh, grid_blocks, st, nullptr);
+                        cudaStream_t st, const SideStream* side) {
+    return dispatch(a, kmax, sh, grid_blocks, st, nullptr, side);
 }
 
 }  // namespace orca

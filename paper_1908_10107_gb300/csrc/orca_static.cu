@@ -155,7 +155,7 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
     if (e == cudaSuccess) e = launch_binning(n, cs, kStaticMaxCells, max_passes, src, bins, st);
     if (e == cudaSuccess) e = launch_reorder(n, bins, src, sorted, src_p, dst_p, st);
     if (e == cudaSuccess) {
-        MainArgs a;
+        MainArgs a{};
         a.n = n;
         a.k = max_neighbors;
         a.nd = neighbor_dist;
@@ -168,6 +168,9 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
         a.out = out;
         a.block_counters = (unsigned long long*)(base + L.blk);
         a.count_ops = 0;
+        a.seg = nullptr;  // no static obstacles here
+        a.nseg = 0;
+        a.rec_obst = nullptr;
         a.rec_nbr = nullptr;
         a.rec_cell = nullptr;
         a.scenes = nullptr;

@@ -372,7 +372,9 @@ def bottleneck(n: int = 2000, seed: int = 1916, door: float = 2.4, coverage: flo
     a wall along x = 0 with a door of width ``door`` around y = 0, and the room's side
     walls.  Agents (r 0.4 m, desired speed 1.3 m/s, maximum 1.6) spawn without overlap in
     a square room left of the wall, sized like the crossings' start regions (spawn discs
-    cover 30%), and head for goals 15 m past the door, spread over the door's width."""
+    cover 30%), and head for goals past the door: within the door's width across, so that
+    an agent pressed against the wall slides towards the door, and spread from 10 m to a
+    room side beyond it, so that arrivals do not crowd one spot."""
     rng = np.random.default_rng(seed)
     radius = _full(n, 0.4)
     pref = _full(n, 1.3)
@@ -384,7 +386,7 @@ def bottleneck(n: int = 2000, seed: int = 1916, door: float = 2.4, coverage: flo
     lo = np.tile([[-2.0 - side, -0.5 * side]], (n, 1))
     hi = np.tile([[-2.0, 0.5 * side]], (n, 1))
     pos = spawn_without_overlap(rng, lo, hi, radius.astype(np.float64), pref.astype(np.float64) * dt)
-    goal = np.stack([np.full(n, 15.0), rng.uniform(-0.4, 0.4, n) * door], 1)
+    goal = np.stack([rng.uniform(10.0, 10.0 + side, n), rng.uniform(-0.4, 0.4, n) * door], 1)
     return Scene("bottleneck", _f32(pos), np.zeros((n, 2), np.float32), _f32(goal), radius, vmax,
                  pref, _full(n, time_horizon), neighbor_dist, max_neighbors, dt, steps,
                  obstacles=segs, obstacle_time_horizon=obstacle_time_horizon,

@@ -58,6 +58,25 @@ def test_bottleneck_far_from_the_origin(steps_before):
     assert rep["rows"] == sc.n
 
 
+def test_graph_direct_and_launch_shapes_agree_bitwise():
+    # the obstacle launch runs beside the plain one (a forked stream inside the step graph);
+    # a direct launch, and every launch shape, give the same trajectory
+    sc = S.bottleneck(3000, seed=39)
+    out = []
+    for flags, tpb, lanes in ((0, 0, 0), (abi.ORCA_FLAG_NO_GRAPH, 0, 0), (0, 128, 1),
+                              (0, 256, 4), (0, 64, 32)):
+        sim = parity.make_sim(sc, flags=flags)
+        if tpb:
+            abi.orca_set_launch(sim.ctx, tpb, lanes)
+        sim.set_scene(sc)
+        sim.step(60)
+        out.append(sim.get_state())
+        sim.close()
+    for got in out[1:]:
+        np.testing.assert_array_equal(got[0], out[0][0])
+        np.testing.assert_array_equal(got[1], out[0][1])
+
+
 def test_lone_agent_into_a_wall():
     for ang, want in ((np.pi / 2, (0.0, 0.25)), (np.pi / 4, (1.5 / np.sqrt(2.0), 0.25))):
         pos = np.array([[0.0, 0.0]], np.float32)
@@ -92,6 +111,41 @@ def test_clearing_obstacles_restores_the_plain_step():
     sim.close()
     np.testing.assert_array_equal(got[0], want[0])
     np.testing.assert_array_equal(got[1], want[1])
+
+
+def test_segments_out_of_reach_change_nothing():
+    # every tile takes the plain launch; the obstacle launch gets an empty list
+    sc = S.jitter_velocities(S.bidirectional(3000, seed=37), 37)
+    plain = parity.make_sim(sc)
+    plain.set_scene(sc)
+    base = abi.orca_launches_per_step(plain.ctx)
+    plain.step(4)
+    want = plain.get_state()
+    plain.close()
+    far = sc.copy()
+    far.obstacles = np.array([[5000.0, 5000.0, 5010.0, 5000.0], [-900.0, 40.0, -900.0, 80.0]],
+                             np.float32)
+    sim = parity.make_sim(sc)
+    sim.set_scene(far)
+    assert abi.orca_launches_per_step(sim.ctx) == base + 2
+    sim.step(4)
+    got = sim.get_state()
+    assert np.all(sim.get_obstacle_neighbors() == -1)
+    sim.close()
+    np.testing.assert_array_equal(got[0], want[0])
+    np.testing.assert_array_equal(got[1], want[1])
+
+
+def test_obstacles_everywhere():
+    # a lattice of short walls over the whole crowd: every tile takes the obstacle launch
+    sc = S.jitter_velocities(S.bidirectional(2500, seed=38), 38)
+    lo, hi = sc.pos.min(0), sc.pos.max(0)
+    gx, gy = np.meshgrid(np.linspace(lo[0], hi[0], 16), np.linspace(lo[1], hi[1], 16))
+    a = np.stack([gx.ravel(), gy.ravel()], 1)
+    sc.obstacles = np.concatenate([a, a + [1.5, 0.5]], 1).astype(np.float32)
+    sc.obstacle_time_horizon = np.float32(4.0)
+    rep = parity.gpu_step_and_compare(sc, steps_before=5)
+    assert rep["rows"] == sc.n
 
 
 def test_obstacles_are_refused_where_unsupported():

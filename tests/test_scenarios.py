@@ -111,4 +111,5 @@ def test_bottleneck_layout():
     d = np.linalg.norm(sc.pos[:, None].astype(np.float64) - sc.pos[None], axis=2)
     np.fill_diagonal(d, np.inf)
     assert d.min() >= 2 * sc.radius.max()
-    assert np.all(sc.goal[:, 0] == 15.0) and np.all(np.abs(sc.goal[:, 1]) <= 0.4 * 2.4 + 1e-6)
+    # goals past the door, within its width across
+    assert np.all(sc.goal[:, 0] >= 10.0) and np.all(np.abs(sc.goal[:, 1]) <= 0.4 * 2.4 + 1e-6)
