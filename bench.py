@@ -917,8 +917,9 @@ def main():
     alu["traffic"] = traffic
 
     # end to end through the C ABI, a host-driven loop over the same crowd: each step
-    # uploads the state and parameters from pinned host memory, steps, and reads the new
-    # state back into the buffers the next step uploads
+    # writes the state from pinned host memory into the simulation (orca_update_state:
+    # parameters and search-radius predictions stay on the device), steps, and reads the
+    # new state back into the buffers the next step writes
     abi.orca_profile(sim.ctx, False)
     sim.set_scene(sc)
     sim.step(args.warmup)
@@ -926,23 +927,34 @@ def main():
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
               for a in [pos_h, vel_h] + list(sc.arrays()[2:])]
     out_pos, out_vel = pinned[0], pinned[1]
-    abi.orca_set_agents(sim.ctx, n, *pinned, stream=stream)
-    sim.step(1)
-    abi.orca_get_state(sim.ctx, out_pos, out_vel, stream=stream)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        abi.orca_set_agents(sim.ctx, n, *pinned, stream=stream)
+
+    def host_loop(upload, steps):
+        upload()
         sim.step(1)
         abi.orca_get_state(sim.ctx, out_pos, out_vel, stream=stream)
-    e2e_dt = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            upload()
+            sim.step(1)
+            abi.orca_get_state(sim.ctx, out_pos, out_vel, stream=stream)
+        return time.perf_counter() - t0
+
+    e2e_dt = host_loop(lambda: abi.orca_update_state(sim.ctx, out_pos, out_vel, stream=stream),
+                       args.e2e_steps)
     e2e_val = n * args.e2e_steps / e2e_dt
     if dist:
         t = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_val = world * n * args.e2e_steps / float(t.item())
-    h2d = sum(a.nbytes for a in pinned)
+    h2d = out_pos.nbytes + out_vel.nbytes
     d2h = out_pos.nbytes + out_vel.nbytes
+    # the same loop re-loading the whole crowd every step (orca_set_agents: parameters
+    # uploaded too, predictions reset), for comparison
+    full_dt = host_loop(lambda: abi.orca_set_agents(sim.ctx, n, *pinned, stream=stream),
+                        args.e2e_steps)
+    full_upload = {"value": n * args.e2e_steps / full_dt, "unit": UNIT,
+                   "h2d_bytes_per_step": sum(a.nbytes for a in pinned), "d2h_bytes_per_step": d2h}
     sim.close()
 
     if rank != 0:
@@ -984,7 +996,9 @@ def main():
         "lp3_fraction": counters["lp3_agent_steps"] / max(counters["agent_steps"], 1),
         "candidates_per_agent": counters["candidates"] / max(counters["agent_steps"], 1),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                "api": "orca_update_state + orca_step + orca_get_state, pinned host buffers",
+                "full_reload_per_step": full_upload},
         "gpu_launches": launches,
         "clocks": clocks,
         "wall_s_timed_region": wall1 - wall0,

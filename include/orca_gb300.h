@@ -143,6 +143,21 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy,
                              const float* time_horizon, int where, void* stream);
 
 /*
+ * Replace the positions and/or velocities of the current agents and keep everything else:
+ * their parameters, their order in memory and each agent's search-radius prediction (its
+ * last k-th neighbour distance).  For a host-driven loop that writes back a state it read
+ * (or edited), so the next step keeps its full speed; orca_set_agents would reset the
+ * predictions.  The neighbour search is exact whatever the predictions, so any new state is
+ * valid; one far from the old state only makes the next search slower.
+ *   pos_xy, vel_xy  2*n floats each in agent order (n = the current count), host or device
+ *                   per `where`; either may be NULL to keep that half.
+ * Host arrays go through the context's staging buffers and the call synchronises `stream`
+ * before returning.  A context without agents ignores the call.
+ */
+ORCA_API int orca_update_state(orca_ctx* ctx, const float* pos_xy, const float* vel_xy, int where,
+                               void* stream);
+
+/*
  * Load a batch of n_scenes independent scenes (1 <= n_scenes <= max_scenes) that advance
  * together: scene s owns the next scenes[s].count agents of the arrays (laid out as for
  * orca_set_agents, scene after scene), and its agents see only each other.  Each scene has

@@ -73,6 +73,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_create": ([P, vp, sz, c.POINTER(vp)], c.c_int),
         "orca_destroy": ([vp], c.c_int),
         "orca_set_agents": ([vp, i32] + [vp] * 7 + [c.c_int, vp], c.c_int),
+        "orca_update_state": ([vp, vp, vp, c.c_int, vp], c.c_int),
         "orca_set_scenes": ([vp, i32, vp] + [vp] * 7 + [c.c_int, vp], c.c_int),
         "orca_get_scene_grids": ([vp, vp, vp, vp], c.c_int),
         "orca_step": ([vp, i32, vp], c.c_int),
@@ -175,6 +176,16 @@ def orca_set_agents(ctx, n, pos_xy, vel_xy, goal_xy, radius, max_speed, pref_spe
     w = where if where is not None else ptrs[0][1]
     _check(load_library().orca_set_agents(ctx, int(n), *[p for p, _ in ptrs], int(w),
                                           _stream(stream) if w == ORCA_DEVICE or stream is not None else None),
+           ctx)
+
+
+def orca_update_state(ctx, pos_xy=None, vel_xy=None, where=None, stream=None):
+    """New positions and/or velocities for the current agents (agent order); parameters,
+    memory order and search-radius predictions are kept."""
+    (pp, pw), (vp_, vw) = _ptr(pos_xy, np.float32), _ptr(vel_xy, np.float32)
+    w = where if where is not None else (pw if pw is not None else (vw if vw is not None else ORCA_HOST))
+    _check(load_library().orca_update_state(ctx, pp, vp_, int(w),
+                                            _stream(stream) if w == ORCA_DEVICE or stream is not None else None),
            ctx)
 
 
@@ -435,6 +446,10 @@ class OrcaSim:
 
     def get_scene_grids(self, stream=None):
         return orca_get_scene_grids(self.ctx, self.n_scenes, stream)
+
+    def update_state(self, pos=None, vel=None, stream=None):
+        """Replace positions and/or velocities; parameters and predictions are kept."""
+        orca_update_state(self.ctx, pos, vel, stream=stream)
 
     def step(self, nsteps: int = 1, stream=None):
         orca_step(self.ctx, nsteps, stream)

@@ -493,6 +493,26 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy, cons
     return ORCA_OK;
 }
 
+ORCA_API int orca_update_state(orca_ctx* ctx, const float* pos_xy, const float* vel_xy, int where,
+                               void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
+    if (ctx->n == 0 || (!pos_xy && !vel_xy)) return ORCA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)ctx->n;
+    const float2* pin = (const float2*)pos_xy;
+    const float2* vin = (const float2*)vel_xy;
+    if (where == ORCA_HOST) {  // through the staging buffers
+        if (pos_xy) CK(cudaMemcpyAsync(ctx->stage[0], pos_xy, N * 8, cudaMemcpyHostToDevice, st), "copy pos");
+        if (vel_xy) CK(cudaMemcpyAsync(ctx->stage[1], vel_xy, N * 8, cudaMemcpyHostToDevice, st), "copy vel");
+        pin = pos_xy ? ctx->stage[0] : nullptr;
+        vin = vel_xy ? ctx->stage[1] : nullptr;
+    }
+    CK(launch_permute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, pin, vin, st), "permute kernel");
+    if (where == ORCA_HOST) CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return ORCA_OK;
+}
+
 ORCA_API int orca_set_scenes(orca_ctx* ctx, int32_t n_scenes, const orca_scene* scenes,
                              const float* pos_xy, const float* vel_xy, const float* goal_xy,
                              const float* radius, const float* max_speed, const float* pref_speed,

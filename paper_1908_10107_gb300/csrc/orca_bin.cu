@@ -398,6 +398,17 @@ __global__ void __launch_bounds__(256) unpermute_kernel(int n, AgentState s, con
     if (vel_out) vel_out[i] = s.vel[t];
 }
 
+// The inverse of unpermute: agent-order arrays into the current slots (either may be null).
+__global__ void __launch_bounds__(256) permute_kernel(int n, AgentState s, const uint32_t* __restrict__ id,
+                                                      const float2* __restrict__ pos_in,
+                                                      const float2* __restrict__ vel_in) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    uint32_t i = id[t];
+    if (pos_in) s.pos[t] = pos_in[i];
+    if (vel_in) s.vel[t] = vel_in[i];
+}
+
 __global__ void __launch_bounds__(256) iota_kernel(int n, uint32_t* __restrict__ id) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) id[t] = (uint32_t)t;
@@ -462,6 +473,13 @@ cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, flo
                              float2* vel_out, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     unpermute_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s, id, pos_out, vel_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute(int n, const AgentState& s, const uint32_t* id, const float2* pos_in,
+                           const float2* vel_in, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    permute_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s, id, pos_in, vel_in);
     return cudaGetLastError();
 }
 

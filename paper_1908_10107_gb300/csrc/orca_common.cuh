@@ -148,6 +148,8 @@ cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
                            const AgentParams& dst_p, cudaStream_t st);
 cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, float2* pos_out,
                              float2* vel_out, cudaStream_t st);
+cudaError_t launch_permute(int n, const AgentState& s, const uint32_t* id, const float2* pos_in,
+                           const float2* vel_in, cudaStream_t st);
 cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st);
 // Launch shape of the ORCA kernel: threads per CTA (64, 128 or 256) and lanes per queued
 // agent in the least-penetration phase (1 or 4).

@@ -90,6 +90,7 @@ def test_null_context_is_rejected(lib):
     m = ctypes.c_int32(-1)
     assert lib.orca_remove_arrived(None, ctypes.byref(m), None, 0, None) == abi.ORCA_ERR_ARG
     assert lib.orca_count_ops(None, 1) == abi.ORCA_ERR_ARG
+    assert lib.orca_update_state(None, None, None, 0, None) == abi.ORCA_ERR_ARG
     assert lib.orca_get_op_counters(None, None, None) == abi.ORCA_ERR_ARG
 
 

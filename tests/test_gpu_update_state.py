@@ -1,0 +1,95 @@
+"""orca_update_state: new positions / velocities for the current agents, with parameters,
+memory order and search-radius predictions kept."""
+import numpy as np
+import pytest
+
+import parity
+from paper_1908_10107_gb300 import abi
+from paper_1908_10107_gb300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_10107_gb300 import build
+    build.build()
+
+
+def test_writing_back_the_read_state_changes_nothing():
+    sc = S.jitter_velocities(S.bidirectional(6000, seed=51), 51)
+    a = parity.make_sim(sc, flags=0)
+    b = parity.make_sim(sc, flags=0)
+    a.set_scene(sc)
+    b.set_scene(sc)
+    a.step(5)
+    b.step(5)
+    for _ in range(10):
+        pos, vel = b.get_state()
+        b.update_state(pos, vel)
+        b.step(1)
+        a.step(1)
+    pa, va = a.get_state()
+    pb, vb = b.get_state()
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(va, vb)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_an_edited_state_steps_like_the_oracle(device):
+    import torch
+    sc = S.jitter_velocities(S.bidirectional(4000, seed=52), 52)
+    sim = parity.make_sim(sc)
+    sim.set_scene(sc)
+    sim.step(7)  # the memory order is now the cell order, not the agent order
+    pos, vel = sim.get_state()
+    rng = np.random.default_rng(52)
+    pos2 = (pos + rng.normal(0, 0.05, pos.shape)).astype(np.float32)
+    vel2 = (vel + rng.normal(0, 0.3, vel.shape)).astype(np.float32)
+    if device:
+        sim.update_state(torch.from_numpy(pos2).cuda(), torch.from_numpy(vel2).cuda())
+    else:
+        sim.update_state(pos2, vel2)
+    got = sim.get_state()
+    np.testing.assert_array_equal(got[0], pos2)
+    np.testing.assert_array_equal(got[1], vel2)
+    st = sc.copy()
+    st.pos, st.vel = pos2, vel2
+    sim.step(1)
+    p3, v3 = sim.get_state()
+    nbr = sim.get_neighbors()
+    cells, gf, gi = sim.get_cells()
+    parity.compare_step(st, p3, v3, nbr, cells, (gf, gi))
+    sim.close()
+
+
+def test_one_half_at_a_time_and_in_a_batch():
+    sc = S.bidirectional(3000, seed=53)
+    sim = parity.make_sim(sc, flags=0)
+    sim.set_scene(sc)
+    sim.step(3)
+    pos, vel = sim.get_state()
+    sim.update_state(vel=np.zeros_like(vel))
+    p1, v1 = sim.get_state()
+    np.testing.assert_array_equal(p1, pos)
+    assert not v1.any()
+    sim.update_state(pos=pos + np.float32(1.0))
+    p2, v2 = sim.get_state()
+    np.testing.assert_array_equal(p2, pos + np.float32(1.0))
+    assert not v2.any()
+    sim.close()
+    batch = S.Batch([S.bidirectional(700, seed=54), S.two_way_crossing(500, seed=55)])
+    bs = abi.OrcaSim.for_batch(batch)
+    bs.set_batch(batch)
+    bs.step(4)
+    pos, vel = bs.get_state()
+    bs.update_state(pos, -vel)
+    p, v = bs.get_state()
+    np.testing.assert_array_equal(p, pos)
+    np.testing.assert_array_equal(v, -vel)
+    bs.close()
