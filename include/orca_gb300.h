@@ -151,8 +151,9 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy,
  * valid; one far from the old state only makes the next search slower.
  *   pos_xy, vel_xy  2*n floats each in agent order (n = the current count), host or device
  *                   per `where`; either may be NULL to keep that half.
- * Host arrays go through the context's staging buffers and the call synchronises `stream`
- * before returning.  A context without agents ignores the call.
+ * Pinned (page-locked) host arrays are read by a kernel directly over the CPU-GPU link;
+ * other host arrays go through the context's staging buffers.  For host input the call
+ * synchronises `stream` before returning.  A context without agents ignores the call.
  */
 ORCA_API int orca_update_state(orca_ctx* ctx, const float* pos_xy, const float* vel_xy, int where,
                                void* stream);
@@ -190,7 +191,9 @@ ORCA_API int orca_step(orca_ctx* ctx, int32_t nsteps, void* stream);
 
 /*
  * Read the current state in agent order: pos_xy and vel_xy (2*n floats each; either may be
- * NULL).  With ORCA_HOST the call synchronises `stream` and reports device-side errors.
+ * NULL).  With ORCA_HOST the call synchronises `stream` and reports device-side errors;
+ * pinned host arrays are written by a kernel directly over the CPU-GPU link, other host
+ * arrays through staging copies.
  */
 ORCA_API int orca_get_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int where,
                             void* stream);

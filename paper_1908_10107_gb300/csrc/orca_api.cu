@@ -322,6 +322,18 @@ static int build_graphs(orca_ctx* ctx) {
     return ORCA_OK;
 }
 
+// The device-side address of a pinned (page-locked, mapped) host array, or null for other
+// memory.  Kernels read and write such arrays directly over the CPU-GPU link.
+static void* mapped_host_ptr(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the (non-sticky) error of an unknown pointer
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 static int check_device_error(orca_ctx* ctx, cudaStream_t st) {
     int herr = 0;
     CK(cudaMemcpyAsync(&herr, &ctx->bins.misc->error, sizeof(int), cudaMemcpyDeviceToHost, st),
@@ -502,7 +514,18 @@ ORCA_API int orca_update_state(orca_ctx* ctx, const float* pos_xy, const float* 
     const size_t N = (size_t)ctx->n;
     const float2* pin = (const float2*)pos_xy;
     const float2* vin = (const float2*)vel_xy;
-    if (where == ORCA_HOST) {  // through the staging buffers
+    if (where == ORCA_HOST) {
+        // pinned arrays: one kernel reads them over the link into the current slots
+        void* mp = mapped_host_ptr(pos_xy);
+        void* mv = mapped_host_ptr(vel_xy);
+        if ((mp || !pos_xy) && (mv || !vel_xy)) {
+            CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (uint32_t*)ctx->stage[0],
+                                 (float2*)mp, (float2*)mv, false, st),
+               "host state kernel");
+            CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+            return ORCA_OK;
+        }
+        // other host memory: through the staging buffers
         if (pos_xy) CK(cudaMemcpyAsync(ctx->stage[0], pos_xy, N * 8, cudaMemcpyHostToDevice, st), "copy pos");
         if (vel_xy) CK(cudaMemcpyAsync(ctx->stage[1], vel_xy, N * 8, cudaMemcpyHostToDevice, st), "copy vel");
         pin = pos_xy ? ctx->stage[0] : nullptr;
@@ -621,6 +644,12 @@ ORCA_API int orca_get_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int whe
         if (where == ORCA_DEVICE) {
             CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (float2*)pos_xy,
                                 (float2*)vel_xy, st), "unpermute kernel");
+        } else if ((mapped_host_ptr(pos_xy) || !pos_xy) && (mapped_host_ptr(vel_xy) || !vel_xy)) {
+            // pinned arrays: one kernel writes them over the link in agent order
+            CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (uint32_t*)ctx->stage[0],
+                                 (float2*)mapped_host_ptr(pos_xy), (float2*)mapped_host_ptr(vel_xy),
+                                 true, st),
+               "host state kernel");
         } else {
             CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, ctx->stage[0],
                                 ctx->stage[1], st), "unpermute kernel");

@@ -409,6 +409,32 @@ __global__ void __launch_bounds__(256) permute_kernel(int n, AgentState s, const
     if (vel_in) s.vel[t] = vel_in[i];
 }
 
+// Agent -> slot map from the slot -> agent ids.
+__global__ void __launch_bounds__(256) slot_map_kernel(int n, const uint32_t* __restrict__ id,
+                                                       uint32_t* __restrict__ slot_of) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) slot_of[id[t]] = (uint32_t)t;
+}
+
+// State to or from agent-order arrays that live in pinned host memory, read or written by
+// the kernel over the CPU-GPU link: one thread per agent, so the host side is contiguous
+// and the scattered side is device memory.  to_host: agent arrays <- slots, else slots <-
+// agent arrays.  Null arrays are skipped.
+__global__ void __launch_bounds__(256) host_state_kernel(int n, AgentState s,
+                                                         const uint32_t* __restrict__ slot_of,
+                                                         float2* pos, float2* vel, int to_host) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t t = slot_of[i];
+    if (to_host) {
+        if (pos) pos[i] = s.pos[t];
+        if (vel) vel[i] = s.vel[t];
+    } else {
+        if (pos) s.pos[t] = pos[i];
+        if (vel) s.vel[t] = vel[i];
+    }
+}
+
 __global__ void __launch_bounds__(256) iota_kernel(int n, uint32_t* __restrict__ id) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) id[t] = (uint32_t)t;
@@ -480,6 +506,14 @@ cudaError_t launch_permute(int n, const AgentState& s, const uint32_t* id, const
                            const float2* vel_in, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     permute_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s, id, pos_in, vel_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_host_state(int n, const AgentState& s, const uint32_t* id, uint32_t* slot_of,
+                              float2* pos, float2* vel, bool to_host, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    slot_map_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, id, slot_of);
+    host_state_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s, slot_of, pos, vel, to_host ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -93,3 +93,29 @@ def test_one_half_at_a_time_and_in_a_batch():
     np.testing.assert_array_equal(p, pos)
     np.testing.assert_array_equal(v, -vel)
     bs.close()
+
+
+def test_pinned_host_arrays_take_the_direct_path_and_agree():
+    # pinned host memory is read and written by the kernels over the CPU-GPU link; pageable
+    # memory goes through staging copies: both give the same state
+    import torch
+    sc = S.jitter_velocities(S.bidirectional(5000, seed=56), 56)
+    sim = parity.make_sim(sc, flags=0)
+    sim.set_scene(sc)
+    sim.step(6)
+    pos, vel = sim.get_state()
+    ppos = torch.empty(pos.shape, dtype=torch.float32).pin_memory()
+    pvel = torch.empty(vel.shape, dtype=torch.float32).pin_memory()
+    abi.orca_get_state(sim.ctx, ppos, pvel)
+    np.testing.assert_array_equal(ppos.numpy(), pos)
+    np.testing.assert_array_equal(pvel.numpy(), vel)
+    rng = np.random.default_rng(56)
+    ppos.copy_(torch.from_numpy((pos + rng.normal(0, 0.02, pos.shape)).astype(np.float32)))
+    pvel.copy_(torch.from_numpy((-vel).astype(np.float32)))
+    sim.update_state(ppos, pvel)
+    got = sim.get_state()
+    np.testing.assert_array_equal(got[0], ppos.numpy())
+    np.testing.assert_array_equal(got[1], pvel.numpy())
+    sim.update_state(pos=None, vel=pvel.numpy())  # a numpy view of pinned memory
+    np.testing.assert_array_equal(sim.get_state()[1], pvel.numpy())
+    sim.close()
