@@ -642,24 +642,26 @@ def run_obstacles(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     every = args.remove_every
     # 1. evacuation until the room is empty
-    sc = scenarios.bottleneck(2000)
-    sim = abi.OrcaSim.for_scene(sc)
-    for timed in (False, True):  # an untimed pass first (library load, first captures)
-        sim.set_scene(sc)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        steps, agent_steps, n = 0, 0, sc.n
-        while n > 0 and steps < args.crossing_max_steps:
-            sim.step(every)
-            steps += every
-            agent_steps += n * every
-            n = abi.orca_remove_arrived(sim.ctx)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    evac = {"agents": sc.n, "steps_until_all_arrived": steps if n == 0 else None,
-            "agents_left": n, "simulated_s": steps * sc.dt, "wall_s": wall,
-            "agent_steps_per_s": agent_steps / wall, "ms_per_step": 1e3 * wall / max(steps, 1)}
-    sim.close()
+    evac = None
+    if args.evacuation:
+        sc = scenarios.bottleneck(2000)
+        sim = abi.OrcaSim.for_scene(sc)
+        for timed in (False, True):  # an untimed pass first (library load, first captures)
+            sim.set_scene(sc)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps, agent_steps, n = 0, 0, sc.n
+            while n > 0 and steps < args.crossing_max_steps:
+                sim.step(every)
+                steps += every
+                agent_steps += n * every
+                n = abi.orca_remove_arrived(sim.ctx)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        evac = {"agents": sc.n, "steps_until_all_arrived": steps if n == 0 else None,
+                "agents_left": n, "simulated_s": steps * sc.dt, "wall_s": wall,
+                "agent_steps_per_s": agent_steps / wall, "ms_per_step": 1e3 * wall / max(steps, 1)}
+        sim.close()
     # 2. obstacle cost on large crowds
     room = scenarios.bottleneck(524288)
     flow = scenarios.bidirectional()
@@ -775,6 +777,8 @@ def main():
                                            "dense"], default="plain")
     ap.add_argument("--dense-steps", type=int, default=100, help="dense workload: timed steps")
     ap.add_argument("--obst-steps", type=int, default=50, help="obstacles workload: timed steps")
+    ap.add_argument("--no-evacuation", dest="evacuation", action="store_false",
+                    help="obstacles workload: only the two large crowds")
     ap.add_argument("--ab-steps", type=int, default=30, help="lp_ab workload: timed steps per mode")
     ap.add_argument("--remove-every", type=int, default=20,
                     help="crossing workload: steps between removals of arrived agents")
