@@ -21,8 +21,8 @@ constexpr int kRadixBits = 9;
 // per-CTA counters of the ORCA kernel: agents, LP3 agents, candidates, half-planes, then
 // (operation-counting launches only) LP1 calls, LP1 bounds, violation checks, bisectors
 constexpr int kBlockCounters = 8;
-// static obstacles: segments per context (staged in shared memory per CTA) and obstacle
-// half-planes per agent
+// static obstacles: segments per context (read through L1; each CTA lists the ones its
+// tile can reach) and obstacle half-planes per agent
 constexpr int kMaxObstacles = 256;
 constexpr int kMaxObstacleNeighbors = 4;
 constexpr int kRadixBuckets = 1 << kRadixBits;

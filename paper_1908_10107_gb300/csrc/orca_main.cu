@@ -977,8 +977,6 @@ __device__ __forceinline__ void scene_view(const MainArgs& a, int t, SceneView& 
     }
 }
 
-// Persistent over tiles of TPB consecutive agents: tile blockIdx.x first, then
-// tiles taken from a per-step counter (with one CTA per tile this loop runs once).
 // Tiles (TPB consecutive sorted slots, the ORCA kernel's CTAs) with a segment within reach
 // of some agent: one warp per tile, the same reach test as cull_segments.  Flags them for
 // the plain launch to skip and lists them for the obstacle launch, so a crowd pays for the
@@ -1019,6 +1017,10 @@ __global__ void __launch_bounds__(256) obstacle_tiles_kernel(MainArgs a, int tpb
     }
 }
 
+// Persistent over tiles of TPB consecutive agents: tile blockIdx.x first, then
+// tiles taken from a per-step counter (with one CTA per tile this loop runs once).  The
+// obstacle instantiation (OBS) steps the tiles obstacle_tiles_kernel listed instead,
+// entries blockIdx.x, blockIdx.x + gridDim.x, ...
 template <int KMAX, int TPB, int G, bool TAPE = false, bool COUNT = false, bool OBS = false>
 __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_kernel(MainArgs a) {
     pdl_wait();
