@@ -291,12 +291,14 @@ ORCA_API int orca_profile(orca_ctx* ctx, int enable);
 
 /*
  * Durations in milliseconds of the three phases of the most recent profiled step:
- * ms3[0] binning, ms3[1] reorder, ms3[2] ORCA kernel.  Waits for that step to finish.
+ * ms3[0] binning, ms3[1] reorder, ms3[2] ORCA kernel (with obstacles: the tile flags and
+ * the plain and obstacle launches together).  Waits for that step to finish.
  */
 ORCA_API int orca_profile_read(orca_ctx* ctx, float* ms3);
 
 /* Number of kernels one orca_step enqueues per step (some exit at once when the radix
- * sort needs fewer passes than the cell capacity allows). */
+ * sort needs fewer passes than the cell capacity allows; static obstacles add two: the
+ * tile flags and the obstacle launch). */
 ORCA_API int orca_launches_per_step(const orca_ctx* ctx, int32_t* count);
 
 /*
