@@ -121,6 +121,7 @@ struct orca_ctx {
     int n = 0;
     int cur = 0;  // which PR buffer holds the current parameters
     bool stepped = false;
+    bool slot_ok = false;  // sorted.slot maps every agent to its slot in the current order
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int graph_n = -1;
@@ -322,8 +323,8 @@ static int build_graphs(orca_ctx* ctx) {
     return ORCA_OK;
 }
 
-// The device-side address of a pinned (page-locked, mapped) host array, or null for other
-// memory.  Kernels read and write such arrays directly over the CPU-GPU link.
+// The device-side address of a pinned (page-locked, mapped) host array that starts on a
+// 16-byte boundary, or null for other memory.  Kernels read and write such arrays directly over the CPU-GPU link.
 static void* mapped_host_ptr(const void* p) {
     if (!p) return nullptr;
     cudaPointerAttributes at;
@@ -331,7 +332,14 @@ static void* mapped_host_ptr(const void* p) {
         cudaGetLastError();  // clear the (non-sticky) error of an unknown pointer
         return nullptr;
     }
-    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+    if (at.type != cudaMemoryTypeHost || ((uintptr_t)at.devicePointer & 15)) return nullptr;
+    return at.devicePointer;
+}
+
+// The agent -> slot map for pinned transfers: the one the last step's reorder wrote, or
+// scratch to build it in (slot_ok false).
+static uint32_t* slot_map(orca_ctx* ctx) {
+    return ctx->slot_ok ? ctx->sorted.slot : (uint32_t*)ctx->stage[0];
 }
 
 static int check_device_error(orca_ctx* ctx, cudaStream_t st) {
@@ -498,6 +506,7 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy, cons
     ctx->n = n;
     ctx->cur = 0;
     ctx->stepped = false;
+    ctx->slot_ok = false;
     if (ctx->n_scenes != 0) {
         ctx->n_scenes = 0;
         drop_graphs(ctx);
@@ -519,7 +528,7 @@ ORCA_API int orca_update_state(orca_ctx* ctx, const float* pos_xy, const float* 
         void* mp = mapped_host_ptr(pos_xy);
         void* mv = mapped_host_ptr(vel_xy);
         if ((mp || !pos_xy) && (mv || !vel_xy)) {
-            CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (uint32_t*)ctx->stage[0],
+            CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, slot_map(ctx), !ctx->slot_ok,
                                  (float2*)mp, (float2*)mv, false, st),
                "host state kernel");
             CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
@@ -632,6 +641,7 @@ ORCA_API int orca_step(orca_ctx* ctx, int32_t nsteps, void* stream) {
         ctx->cur ^= 1;
     }
     ctx->stepped = true;
+    ctx->slot_ok = true;  // the last reorder wrote the map of the order the step left
     return ORCA_OK;
 }
 
@@ -646,7 +656,7 @@ ORCA_API int orca_get_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int whe
                                 (float2*)vel_xy, st), "unpermute kernel");
         } else if ((mapped_host_ptr(pos_xy) || !pos_xy) && (mapped_host_ptr(vel_xy) || !vel_xy)) {
             // pinned arrays: one kernel writes them over the link in agent order
-            CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (uint32_t*)ctx->stage[0],
+            CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, slot_map(ctx), !ctx->slot_ok,
                                  (float2*)mapped_host_ptr(pos_xy), (float2*)mapped_host_ptr(vel_xy),
                                  true, st),
                "host state kernel");
@@ -807,6 +817,7 @@ ORCA_API int orca_remove_arrived(orca_ctx* ctx, int32_t* n_remaining, int32_t* k
     if (where == ORCA_HOST) CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     ctx->n = m;
     ctx->cur = par ^ 1;
+    ctx->slot_ok = false;  // survivors renumbered
     *n_remaining = m;
     return ORCA_OK;
 }
@@ -866,6 +877,7 @@ ORCA_API int orca_rollout_workspace_size(const orca_ctx* ctx, int32_t T, int32_t
 ORCA_API int orca_rollout_forward(orca_ctx* ctx, int32_t T, int32_t ckpt_every, float* traj_pos,
                                   void* workspace, size_t workspace_bytes, void* stream) {
     if (!ctx) return ORCA_ERR_ARG;
+    ctx->slot_ok = false;  // rollouts reload and step the state on their own
     if (T < 1 || ckpt_every < 1) return fail(ctx, ORCA_ERR_ARG, "T and ckpt_every must be >= 1");
     if (ctx->n_scenes > 0) return fail(ctx, ORCA_ERR_STATE, "rollouts need a single scene");
     if (ctx->nseg > 0) return fail(ctx, ORCA_ERR_STATE, "the adjoint has no static obstacles");
@@ -903,6 +915,7 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
                                    float* g_vel0, void* workspace, size_t workspace_bytes,
                                    void* stream) {
     if (!ctx) return ORCA_ERR_ARG;
+    ctx->slot_ok = false;  // rollouts reload and step the state on their own
     if (!dL_dpos) return fail(ctx, ORCA_ERR_ARG, "dL_dpos is required");
     if (workspace != ctx->roll_ws || ctx->roll_T < 1)
         return fail(ctx, ORCA_ERR_STATE, "no orca_rollout_forward with this workspace");

@@ -417,15 +417,41 @@ __global__ void __launch_bounds__(256) slot_map_kernel(int n, const uint32_t* __
 }
 
 // State to or from agent-order arrays that live in pinned host memory, read or written by
-// the kernel over the CPU-GPU link: one thread per agent, so the host side is contiguous
-// and the scattered side is device memory.  to_host: agent arrays <- slots, else slots <-
-// agent arrays.  Null arrays are skipped.
+// the kernel over the CPU-GPU link: two agents per thread, so the host side moves in
+// contiguous 16-byte pieces (arrays 16-byte aligned) and the scattered side is device
+// memory.  to_host: agent arrays <- slots, else slots <- agent arrays.  Null arrays are
+// skipped.
 __global__ void __launch_bounds__(256) host_state_kernel(int n, AgentState s,
                                                          const uint32_t* __restrict__ slot_of,
                                                          float2* pos, float2* vel, int to_host) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (i >= n) return;
-    uint32_t t = slot_of[i];
+    if (i + 1 < n) {
+        const uint2 t = *reinterpret_cast<const uint2*>(slot_of + i);
+        if (to_host) {
+            if (pos) {
+                const float2 a = s.pos[t.x], b = s.pos[t.y];
+                *reinterpret_cast<float4*>(pos + i) = make_float4(a.x, a.y, b.x, b.y);
+            }
+            if (vel) {
+                const float2 a = s.vel[t.x], b = s.vel[t.y];
+                *reinterpret_cast<float4*>(vel + i) = make_float4(a.x, a.y, b.x, b.y);
+            }
+        } else {
+            if (pos) {
+                const float4 q = *reinterpret_cast<const float4*>(pos + i);
+                s.pos[t.x] = make_float2(q.x, q.y);
+                s.pos[t.y] = make_float2(q.z, q.w);
+            }
+            if (vel) {
+                const float4 q = *reinterpret_cast<const float4*>(vel + i);
+                s.vel[t.x] = make_float2(q.x, q.y);
+                s.vel[t.y] = make_float2(q.z, q.w);
+            }
+        }
+        return;
+    }
+    const uint32_t t = slot_of[i];  // the last agent of an odd count
     if (to_host) {
         if (pos) pos[i] = s.pos[t];
         if (vel) vel[i] = s.vel[t];
@@ -510,10 +536,11 @@ cudaError_t launch_permute(int n, const AgentState& s, const uint32_t* id, const
 }
 
 cudaError_t launch_host_state(int n, const AgentState& s, const uint32_t* id, uint32_t* slot_of,
-                              float2* pos, float2* vel, bool to_host, cudaStream_t st) {
+                              bool build_map, float2* pos, float2* vel, bool to_host, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    slot_map_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, id, slot_of);
-    host_state_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, s, slot_of, pos, vel, to_host ? 1 : 0);
+    if (build_map) slot_map_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, id, slot_of);
+    const int pairs = (n + 1) / 2;
+    host_state_kernel<<<(pairs + 255) / 256, 256, 0, st>>>(n, s, slot_of, pos, vel, to_host ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -150,10 +150,11 @@ cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, flo
                              float2* vel_out, cudaStream_t st);
 cudaError_t launch_permute(int n, const AgentState& s, const uint32_t* id, const float2* pos_in,
                            const float2* vel_in, cudaStream_t st);
-// pos / vel: device-mapped pointers of pinned host arrays (agent order); slot_of: n uint32
-// of scratch for the agent -> slot map built from id
+// pos / vel: device-mapped pointers of pinned host arrays (agent order, 16-byte aligned);
+// slot_of: the agent -> slot map, built from id first when build_map (then n uint32 of
+// scratch), else already valid for the current order
 cudaError_t launch_host_state(int n, const AgentState& s, const uint32_t* id, uint32_t* slot_of,
-                              float2* pos, float2* vel, bool to_host, cudaStream_t st);
+                              bool build_map, float2* pos, float2* vel, bool to_host, cudaStream_t st);
 cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st);
 // Launch shape of the ORCA kernel: threads per CTA (64, 128 or 256) and lanes per queued
 // agent in the least-penetration phase (1 or 4).

@@ -119,3 +119,57 @@ def test_pinned_host_arrays_take_the_direct_path_and_agree():
     sim.update_state(pos=None, vel=pvel.numpy())  # a numpy view of pinned memory
     np.testing.assert_array_equal(sim.get_state()[1], pvel.numpy())
     sim.close()
+
+
+def test_pinned_transfers_across_reorders_odd_counts_and_unaligned_views():
+    # the agent -> slot map is the last reorder's after a step, built afresh after a load or
+    # a removal; an odd count leaves one agent outside the 16-byte pairs; a view that does
+    # not start on 16 bytes takes the staging path
+    import torch
+    sc = S.jitter_velocities(S.two_way_crossing(5001, seed=57), 57)
+    sim = parity.make_sim(sc, flags=0)
+    sim.set_scene(sc)
+    n = sc.n
+    assert n % 2 == 1
+    pin = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+    pin_v = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+    wide = torch.empty((n + 1, 2), dtype=torch.float32).pin_memory()
+    odd = wide[1:]  # pinned, but 8 bytes past a 16-byte boundary
+
+    def check():
+        pos, vel = sim.get_state()  # pageable: staging copies
+        abi.orca_get_state(sim.ctx, pin, pin_v)
+        np.testing.assert_array_equal(pin.numpy(), pos)
+        np.testing.assert_array_equal(pin_v.numpy(), vel)
+        abi.orca_get_state(sim.ctx, odd, None)
+        np.testing.assert_array_equal(odd.numpy(), pos)
+        return pos, vel
+
+    check()  # no step yet: agent order, map built from the ids
+    sim.step(9)
+    pos, vel = check()  # map from the last reorder
+    rng = np.random.default_rng(57)
+    new_pos = (pos + rng.normal(0, 0.01, pos.shape)).astype(np.float32)
+    odd.copy_(torch.from_numpy(new_pos))
+    sim.update_state(odd, None)  # staging path
+    np.testing.assert_array_equal(sim.get_state()[0], new_pos)
+    pin_v.copy_(torch.from_numpy((0.5 * vel).astype(np.float32)))
+    sim.update_state(None, pin_v)  # direct path, map from the last reorder
+    np.testing.assert_array_equal(sim.get_state()[1], (0.5 * vel).astype(np.float32))
+    # after a removal the survivors are renumbered and the map is rebuilt
+    sc2 = sc.copy()
+    sc2.pos, sc2.vel = sim.get_state()
+    sc2.goal = sc2.goal.copy()
+    sc2.goal[::3] = sc2.pos[::3]
+    sim.set_scene(sc2)
+    sim.step(1)
+    m, kept = sim.remove_arrived()
+    assert 0 < m < n
+    pos_m, vel_m = sim.get_state()
+    p_m = torch.empty((m, 2), dtype=torch.float32).pin_memory()
+    abi.orca_get_state(sim.ctx, p_m, None)
+    np.testing.assert_array_equal(p_m.numpy(), pos_m)
+    p_m.copy_(torch.from_numpy((pos_m + np.float32(0.25)).astype(np.float32)))
+    sim.update_state(p_m, None)
+    np.testing.assert_array_equal(sim.get_state()[0], pos_m + np.float32(0.25))
+    sim.close()
