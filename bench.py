@@ -769,7 +769,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--agents", type=int, default=524288)
     ap.add_argument("--cell-size", type=float, default=0.0)
-    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--clocks-out", default=None)
@@ -921,9 +921,9 @@ def main():
     alu["traffic"] = traffic
 
     # end to end through the C ABI, a host-driven loop over the same crowd: each step
-    # writes the state from pinned host memory into the simulation (orca_update_state:
-    # parameters and search-radius predictions stay on the device), steps, and reads the
-    # new state back into the buffers the next step writes
+    # writes the state from pinned host memory into the simulation (parameters and
+    # search-radius predictions stay on the device), steps, and reads the new state back
+    # into the buffers the next step writes
     abi.orca_profile(sim.ctx, False)
     sim.set_scene(sc)
     sim.step(args.warmup)
@@ -944,8 +944,16 @@ def main():
             abi.orca_get_state(sim.ctx, out_pos, out_vel, stream=stream)
         return time.perf_counter() - t0
 
-    e2e_dt = host_loop(lambda: abi.orca_update_state(sim.ctx, out_pos, out_vel, stream=stream),
-                       args.e2e_steps)
+    # one call per step: state in, step, state out (orca_step_host, one synchronisation)
+    abi.orca_step_host(sim.ctx, out_pos, out_vel, 1, out_pos, out_vel, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        abi.orca_step_host(sim.ctx, out_pos, out_vel, 1, out_pos, out_vel, stream=stream)
+    e2e_dt = time.perf_counter() - t0
+    # the same as three calls (orca_update_state, orca_step, orca_get_state)
+    three_dt = host_loop(lambda: abi.orca_update_state(sim.ctx, out_pos, out_vel, stream=stream),
+                         args.e2e_steps)
     e2e_val = n * args.e2e_steps / e2e_dt
     if dist:
         t = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
@@ -959,6 +967,8 @@ def main():
                         args.e2e_steps)
     full_upload = {"value": n * args.e2e_steps / full_dt, "unit": UNIT,
                    "h2d_bytes_per_step": sum(a.nbytes for a in pinned), "d2h_bytes_per_step": d2h}
+    three_calls = {"value": n * args.e2e_steps / three_dt, "unit": UNIT,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     sim.close()
 
     if rank != 0:
@@ -1001,7 +1011,8 @@ def main():
         "candidates_per_agent": counters["candidates"] / max(counters["agent_steps"], 1),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-                "api": "orca_update_state + orca_step + orca_get_state, pinned host buffers",
+                "api": "orca_step_host (state in, step, state out), pinned host buffers",
+                "three_calls_per_step": three_calls,
                 "full_reload_per_step": full_upload},
         "gpu_launches": launches,
         "clocks": clocks,

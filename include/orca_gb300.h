@@ -159,6 +159,19 @@ ORCA_API int orca_update_state(orca_ctx* ctx, const float* pos_xy, const float* 
                                void* stream);
 
 /*
+ * One round of a host-driven loop in a single call: write positions and/or velocities from
+ * host arrays (as orca_update_state; either may be NULL to keep that half), advance nsteps
+ * steps (as orca_step), and read the new state into host arrays (as orca_get_state; either
+ * may be NULL).  Input and output arrays may be the same.  Everything is enqueued on
+ * `stream` and the call synchronises once, at the end, reporting device-side errors as
+ * orca_get_state does; host arrays may be reused when it returns.  Pinned arrays are read
+ * and written by kernels over the CPU-GPU link, others through staging copies.
+ *   pos_in, vel_in, pos_out, vel_out  2*n floats each, agent order, host memory.
+ */
+ORCA_API int orca_step_host(orca_ctx* ctx, const float* pos_in, const float* vel_in, int32_t nsteps,
+                            float* pos_out, float* vel_out, void* stream);
+
+/*
  * Load a batch of n_scenes independent scenes (1 <= n_scenes <= max_scenes) that advance
  * together: scene s owns the next scenes[s].count agents of the arrays (laid out as for
  * orca_set_agents, scene after scene), and its agents see only each other.  Each scene has

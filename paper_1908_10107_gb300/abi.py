@@ -74,6 +74,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_destroy": ([vp], c.c_int),
         "orca_set_agents": ([vp, i32] + [vp] * 7 + [c.c_int, vp], c.c_int),
         "orca_update_state": ([vp, vp, vp, c.c_int, vp], c.c_int),
+        "orca_step_host": ([vp, vp, vp, i32, vp, vp, vp], c.c_int),
         "orca_set_scenes": ([vp, i32, vp] + [vp] * 7 + [c.c_int, vp], c.c_int),
         "orca_get_scene_grids": ([vp, vp, vp, vp], c.c_int),
         "orca_step": ([vp, i32, vp], c.c_int),
@@ -187,6 +188,17 @@ def orca_update_state(ctx, pos_xy=None, vel_xy=None, where=None, stream=None):
     _check(load_library().orca_update_state(ctx, pp, vp_, int(w),
                                             _stream(stream) if w == ORCA_DEVICE or stream is not None else None),
            ctx)
+
+
+def orca_step_host(ctx, pos_in=None, vel_in=None, nsteps=1, pos_out=None, vel_out=None,
+                   stream=None):
+    """Write a host state, advance nsteps, read the new state back: one call, one
+    synchronisation.  All arrays are host memory (numpy or CPU tensors); None skips one."""
+    ptrs = [_ptr(a, np.float32) for a in (pos_in, vel_in, pos_out, vel_out)]
+    if any(w == ORCA_DEVICE for _, w in ptrs):
+        raise TypeError("orca_step_host takes host arrays")
+    _check(load_library().orca_step_host(ctx, ptrs[0][0], ptrs[1][0], int(nsteps), ptrs[2][0],
+                                         ptrs[3][0], _stream(stream)), ctx)
 
 
 def orca_set_scenes(ctx, scenes, pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed,
@@ -450,6 +462,11 @@ class OrcaSim:
     def update_state(self, pos=None, vel=None, stream=None):
         """Replace positions and/or velocities; parameters and predictions are kept."""
         orca_update_state(self.ctx, pos, vel, stream=stream)
+
+    def step_host(self, pos_in=None, vel_in=None, nsteps: int = 1, pos_out=None, vel_out=None,
+                  stream=None):
+        """Host state in, nsteps, host state out (one synchronisation)."""
+        orca_step_host(self.ctx, pos_in, vel_in, nsteps, pos_out, vel_out, stream=stream)
 
     def step(self, nsteps: int = 1, stream=None):
         orca_step(self.ctx, nsteps, stream)

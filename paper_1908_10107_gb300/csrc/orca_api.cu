@@ -354,6 +354,52 @@ static int check_device_error(orca_ctx* ctx, cudaStream_t st) {
     return ORCA_OK;
 }
 
+// Enqueue the write of agent-order positions / velocities (either may be null) into the
+// current slots, on st, without synchronising.  Pinned host arrays are read by one kernel
+// over the CPU-GPU link; other host arrays go through the staging buffers.
+static int enqueue_write_state(orca_ctx* ctx, const float* pos_xy, const float* vel_xy, int where,
+                               cudaStream_t st) {
+    const size_t N = (size_t)ctx->n;
+    const float2* pin = (const float2*)pos_xy;
+    const float2* vin = (const float2*)vel_xy;
+    if (where == ORCA_HOST) {
+        void* mp = mapped_host_ptr(pos_xy);
+        void* mv = mapped_host_ptr(vel_xy);
+        if ((mp || !pos_xy) && (mv || !vel_xy)) {
+            CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, slot_map(ctx), !ctx->slot_ok,
+                                 (float2*)mp, (float2*)mv, false, st),
+               "host state kernel");
+            return ORCA_OK;
+        }
+        if (pos_xy) CK(cudaMemcpyAsync(ctx->stage[0], pos_xy, N * 8, cudaMemcpyHostToDevice, st), "copy pos");
+        if (vel_xy) CK(cudaMemcpyAsync(ctx->stage[1], vel_xy, N * 8, cudaMemcpyHostToDevice, st), "copy vel");
+        pin = pos_xy ? ctx->stage[0] : nullptr;
+        vin = vel_xy ? ctx->stage[1] : nullptr;
+    }
+    CK(launch_permute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, pin, vin, st), "permute kernel");
+    return ORCA_OK;
+}
+
+// Enqueue the read of the state in agent order (either output may be null) on st, without
+// synchronising.  Pinned host arrays are written by one kernel over the CPU-GPU link.
+static int enqueue_read_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int where, cudaStream_t st) {
+    const size_t N = (size_t)ctx->n;
+    if (where == ORCA_DEVICE) {
+        CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (float2*)pos_xy, (float2*)vel_xy, st),
+           "unpermute kernel");
+    } else if ((mapped_host_ptr(pos_xy) || !pos_xy) && (mapped_host_ptr(vel_xy) || !vel_xy)) {
+        CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, slot_map(ctx), !ctx->slot_ok,
+                             (float2*)mapped_host_ptr(pos_xy), (float2*)mapped_host_ptr(vel_xy), true, st),
+           "host state kernel");
+    } else {
+        CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, ctx->stage[0], ctx->stage[1], st),
+           "unpermute kernel");
+        if (pos_xy) CK(cudaMemcpyAsync(pos_xy, ctx->stage[0], N * 8, cudaMemcpyDeviceToHost, st), "copy pos");
+        if (vel_xy) CK(cudaMemcpyAsync(vel_xy, ctx->stage[1], N * 8, cudaMemcpyDeviceToHost, st), "copy vel");
+    }
+    return ORCA_OK;
+}
+
 extern "C" {
 
 ORCA_API int orca_workspace_size(const orca_params* params, size_t* bytes) {
@@ -520,27 +566,8 @@ ORCA_API int orca_update_state(orca_ctx* ctx, const float* pos_xy, const float* 
     if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
     if (ctx->n == 0 || (!pos_xy && !vel_xy)) return ORCA_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t N = (size_t)ctx->n;
-    const float2* pin = (const float2*)pos_xy;
-    const float2* vin = (const float2*)vel_xy;
-    if (where == ORCA_HOST) {
-        // pinned arrays: one kernel reads them over the link into the current slots
-        void* mp = mapped_host_ptr(pos_xy);
-        void* mv = mapped_host_ptr(vel_xy);
-        if ((mp || !pos_xy) && (mv || !vel_xy)) {
-            CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, slot_map(ctx), !ctx->slot_ok,
-                                 (float2*)mp, (float2*)mv, false, st),
-               "host state kernel");
-            CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-            return ORCA_OK;
-        }
-        // other host memory: through the staging buffers
-        if (pos_xy) CK(cudaMemcpyAsync(ctx->stage[0], pos_xy, N * 8, cudaMemcpyHostToDevice, st), "copy pos");
-        if (vel_xy) CK(cudaMemcpyAsync(ctx->stage[1], vel_xy, N * 8, cudaMemcpyHostToDevice, st), "copy vel");
-        pin = pos_xy ? ctx->stage[0] : nullptr;
-        vin = vel_xy ? ctx->stage[1] : nullptr;
-    }
-    CK(launch_permute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, pin, vin, st), "permute kernel");
+    int r = enqueue_write_state(ctx, pos_xy, vel_xy, where, st);
+    if (r != ORCA_OK) return r;
     if (where == ORCA_HOST) CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     return ORCA_OK;
 }
@@ -649,26 +676,30 @@ ORCA_API int orca_get_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int whe
     if (!ctx) return ORCA_ERR_ARG;
     if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
     cudaStream_t st = (cudaStream_t)stream;
-    size_t N = (size_t)ctx->n;
     if (ctx->n > 0) {
-        if (where == ORCA_DEVICE) {
-            CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (float2*)pos_xy,
-                                (float2*)vel_xy, st), "unpermute kernel");
-        } else if ((mapped_host_ptr(pos_xy) || !pos_xy) && (mapped_host_ptr(vel_xy) || !vel_xy)) {
-            // pinned arrays: one kernel writes them over the link in agent order
-            CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, slot_map(ctx), !ctx->slot_ok,
-                                 (float2*)mapped_host_ptr(pos_xy), (float2*)mapped_host_ptr(vel_xy),
-                                 true, st),
-               "host state kernel");
-        } else {
-            CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, ctx->stage[0],
-                                ctx->stage[1], st), "unpermute kernel");
-            if (pos_xy) CK(cudaMemcpyAsync(pos_xy, ctx->stage[0], N * 8, cudaMemcpyDeviceToHost, st), "copy pos");
-            if (vel_xy) CK(cudaMemcpyAsync(vel_xy, ctx->stage[1], N * 8, cudaMemcpyDeviceToHost, st), "copy vel");
-        }
+        int r = enqueue_read_state(ctx, pos_xy, vel_xy, where, st);
+        if (r != ORCA_OK) return r;
     }
     if (where == ORCA_HOST) return check_device_error(ctx, st);
     return ORCA_OK;
+}
+
+ORCA_API int orca_step_host(orca_ctx* ctx, const float* pos_in, const float* vel_in, int32_t nsteps,
+                            float* pos_out, float* vel_out, void* stream) {
+    if (!ctx) return ORCA_ERR_ARG;
+    if (nsteps < 0) return fail(ctx, ORCA_ERR_ARG, "nsteps < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->n > 0 && (pos_in || vel_in)) {
+        int r = enqueue_write_state(ctx, pos_in, vel_in, ORCA_HOST, st);
+        if (r != ORCA_OK) return r;
+    }
+    int r = orca_step(ctx, nsteps, stream);
+    if (r != ORCA_OK) return r;
+    if (ctx->n > 0 && (pos_out || vel_out)) {
+        r = enqueue_read_state(ctx, pos_out, vel_out, ORCA_HOST, st);
+        if (r != ORCA_OK) return r;
+    }
+    return check_device_error(ctx, st);
 }
 
 ORCA_API int orca_get_neighbors(orca_ctx* ctx, int32_t* nbr, int where, void* stream) {

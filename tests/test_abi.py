@@ -91,6 +91,7 @@ def test_null_context_is_rejected(lib):
     assert lib.orca_remove_arrived(None, ctypes.byref(m), None, 0, None) == abi.ORCA_ERR_ARG
     assert lib.orca_count_ops(None, 1) == abi.ORCA_ERR_ARG
     assert lib.orca_update_state(None, None, None, 0, None) == abi.ORCA_ERR_ARG
+    assert lib.orca_step_host(None, None, None, 1, None, None, None) == abi.ORCA_ERR_ARG
     assert lib.orca_get_op_counters(None, None, None) == abi.ORCA_ERR_ARG
 
 

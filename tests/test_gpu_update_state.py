@@ -173,3 +173,43 @@ def test_pinned_transfers_across_reorders_odd_counts_and_unaligned_views():
     sim.update_state(p_m, None)
     np.testing.assert_array_equal(sim.get_state()[0], pos_m + np.float32(0.25))
     sim.close()
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_step_host_is_write_step_read(pinned):
+    # the fused call equals orca_update_state + orca_step + orca_get_state, bitwise, also
+    # with the output written over the input
+    import torch
+    sc = S.jitter_velocities(S.bidirectional(4001, seed=58), 58)
+    a = parity.make_sim(sc, flags=0)
+    b = parity.make_sim(sc, flags=0)
+    a.set_scene(sc)
+    b.set_scene(sc)
+    a.step(4)
+    b.step(4)
+
+    def buf(x):
+        if not pinned:
+            return np.ascontiguousarray(x)
+        t = torch.empty(x.shape, dtype=torch.float32).pin_memory()
+        t.copy_(torch.from_numpy(np.ascontiguousarray(x)))
+        return t.numpy()
+
+    pos, vel = a.get_state()
+    io_pos, io_vel = buf(pos), buf(vel)
+    for it in range(5):
+        nsteps = 2 if it % 2 else 1
+        # a: separate calls; b: one fused call writing its result over its input
+        pa, va = a.get_state()
+        a.update_state(pa, va)
+        a.step(nsteps)
+        want = a.get_state()
+        b.step_host(io_pos, io_vel, nsteps, io_pos, io_vel)
+        np.testing.assert_array_equal(io_pos, want[0])
+        np.testing.assert_array_equal(io_vel, want[1])
+    # nothing in, nothing stepped: a plain read
+    out = buf(np.zeros_like(pos))
+    b.step_host(None, None, 0, out, None)
+    np.testing.assert_array_equal(out, want[0])
+    a.close()
+    b.close()
