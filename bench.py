@@ -932,28 +932,29 @@ def main():
               for a in [pos_h, vel_h] + list(sc.arrays()[2:])]
     out_pos, out_vel = pinned[0], pinned[1]
 
-    def host_loop(upload, steps):
+    def host_loop(one_step):
+        # every variant runs the same stretch of the crowd: reload, warm up, one untimed step
+        sim.set_scene(sc)
+        sim.step(args.warmup)
+        abi.orca_get_state(sim.ctx, out_pos, out_vel, stream=stream)
+        one_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            one_step()
+        return time.perf_counter() - t0
+
+    def three_calls_step(upload):
         upload()
         sim.step(1)
         abi.orca_get_state(sim.ctx, out_pos, out_vel, stream=stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            upload()
-            sim.step(1)
-            abi.orca_get_state(sim.ctx, out_pos, out_vel, stream=stream)
-        return time.perf_counter() - t0
 
     # one call per step: state in, step, state out (orca_step_host, one synchronisation)
-    abi.orca_step_host(sim.ctx, out_pos, out_vel, 1, out_pos, out_vel, stream=stream)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        abi.orca_step_host(sim.ctx, out_pos, out_vel, 1, out_pos, out_vel, stream=stream)
-    e2e_dt = time.perf_counter() - t0
+    e2e_dt = host_loop(lambda: abi.orca_step_host(sim.ctx, out_pos, out_vel, 1, out_pos, out_vel,
+                                                  stream=stream))
     # the same as three calls (orca_update_state, orca_step, orca_get_state)
-    three_dt = host_loop(lambda: abi.orca_update_state(sim.ctx, out_pos, out_vel, stream=stream),
-                         args.e2e_steps)
+    three_dt = host_loop(lambda: three_calls_step(
+        lambda: abi.orca_update_state(sim.ctx, out_pos, out_vel, stream=stream)))
     e2e_val = n * args.e2e_steps / e2e_dt
     if dist:
         t = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
@@ -963,8 +964,8 @@ def main():
     d2h = out_pos.nbytes + out_vel.nbytes
     # the same loop re-loading the whole crowd every step (orca_set_agents: parameters
     # uploaded too, predictions reset), for comparison
-    full_dt = host_loop(lambda: abi.orca_set_agents(sim.ctx, n, *pinned, stream=stream),
-                        args.e2e_steps)
+    full_dt = host_loop(lambda: three_calls_step(
+        lambda: abi.orca_set_agents(sim.ctx, n, *pinned, stream=stream)))
     full_upload = {"value": n * args.e2e_steps / full_dt, "unit": UNIT,
                    "h2d_bytes_per_step": sum(a.nbytes for a in pinned), "d2h_bytes_per_step": d2h}
     three_calls = {"value": n * args.e2e_steps / three_dt, "unit": UNIT,
