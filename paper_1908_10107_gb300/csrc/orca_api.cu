@@ -384,12 +384,14 @@ static int enqueue_write_state(orca_ctx* ctx, const float* pos_xy, const float* 
 // synchronising.  Pinned host arrays are written by one kernel over the CPU-GPU link.
 static int enqueue_read_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int where, cudaStream_t st) {
     const size_t N = (size_t)ctx->n;
+    void* mp = where == ORCA_HOST ? mapped_host_ptr(pos_xy) : nullptr;
+    void* mv = where == ORCA_HOST ? mapped_host_ptr(vel_xy) : nullptr;
     if (where == ORCA_DEVICE) {
         CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (float2*)pos_xy, (float2*)vel_xy, st),
            "unpermute kernel");
-    } else if ((mapped_host_ptr(pos_xy) || !pos_xy) && (mapped_host_ptr(vel_xy) || !vel_xy)) {
+    } else if ((mp || !pos_xy) && (mv || !vel_xy)) {
         CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, slot_map(ctx), !ctx->slot_ok,
-                             (float2*)mapped_host_ptr(pos_xy), (float2*)mapped_host_ptr(vel_xy), true, st),
+                             (float2*)mp, (float2*)mv, true, st),
            "host state kernel");
     } else {
         CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, ctx->stage[0], ctx->stage[1], st),
