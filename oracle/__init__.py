@@ -84,6 +84,8 @@ def _bind(lib):
     lib.oracle_step_obstacles.argtypes = lib.oracle_step.argtypes + [c.c_int, c.c_void_p, c.c_double,
                                                                      c.c_int, c.c_void_p]
     lib.oracle_step_obstacles.restype = c.c_int
+    lib.oracle_lp_sensitivity.argtypes = [_F64P, c.c_int, c.c_int, c.c_double, _F64P, _F64P]
+    lib.oracle_lp_sensitivity.restype = c.c_double
     lib.oracle_solve_fixed.argtypes = [_F64P, c.c_int, c.c_int, c.c_double, _F64P, _F64P]
     lib.oracle_solve_fixed.restype = c.c_int
     lib.oracle_obstacle_line.argtypes = [_F64P, c.c_double, _F64P, c.c_double, c.c_double, _F64P]
@@ -188,6 +190,20 @@ def solve(lines, V: float, o):
     x = np.zeros(2)
     r = _load().oracle_solve(lines, lines.size // 4, float(V), np.asarray(o, np.float64), x)
     return bool(r), x
+
+
+def lp_sensitivity(lines, V: float, o, nobst: int = 0):
+    """Conditioning of the velocity selection (LP2, then LP3) for FP32 parity: the largest
+    move of the selected velocity (max-norm) when one half-plane at a time is shifted
+    along its normal by +-4 FP32 ulps of max(|offset|, V) or turned by +-2^-22 rad.
+    Returns (sens, x) with x the unperturbed selection."""
+    lines = np.ascontiguousarray(lines, np.float64).reshape(-1)
+    x = np.zeros(2)
+    s = _load().oracle_lp_sensitivity(lines, lines.size // 4, int(nobst), float(V),
+                                      np.asarray(o, np.float64), x)
+    if s < 0:
+        raise ValueError("oracle_lp_sensitivity: bad arguments")
+    return float(s), x
 
 
 def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_dist: float,

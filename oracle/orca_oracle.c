@@ -631,6 +631,19 @@ static double lp_sensitivity(const line2* L, int n, int nobst, double V, v2 o, v
     return worst;
 }
 
+/* Sensitivity of the full velocity selection (LP2, then LP3 with the first nobst lines
+ * hard) to FP32-sized perturbations of the lines, one at a time (lp_sensitivity); x2
+ * receives the unperturbed selection.  Returns a negative value on bad arguments. */
+double oracle_lp_sensitivity(const double* lines, int n, int nobst, double V, const double* o,
+                             double* x2) {
+    line2 L[OR_MAXK];
+    if (n < 0 || n > OR_MAXK || nobst < 0 || nobst > n) return -1.0;
+    unpack(lines, n, L);
+    v2 x = select_velocity(L, n, nobst, V, mk(o[0], o[1]));
+    x2[0] = x.x; x2[1] = x.y;
+    return lp_sensitivity(L, n, nobst, V, mk(o[0], o[1]), x);
+}
+
 typedef struct {
     int n, k, fp64, cond;
     const double *pos, *vel, *goal, *radius, *max_speed, *pref_speed, *tau;

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+import test_oracle_conditioning as C
 import test_oracle_halfplane as H
 import test_oracle_knn as K
 import test_oracle_lp as LP
@@ -54,6 +55,13 @@ MUTANTS = {
     "obstacle_uses_dt": ("c = d > ra ? -(d - ra) / tau_o : -(d - ra) / dt;",
                          "c = d > ra ? -(d - ra) / dt : -(d - ra) / dt;"),
     "obstacle_normal_sign": ("if (d > 0.0) n = scl(q, -1.0 / d);", "if (d > 0.0) n = scl(q, 1.0 / d);"),
+    # the conditioning tags that decide which agents the GPU parity gate may excuse
+    "sens_ulp_scale": ("double eta_c = ldexp(1.0, e2 - 22);", "double eta_c = ldexp(1.0, e2 - 21);"),
+    "sens_turn_angle": ("const double eta_r = ldexp(1.0, -22);", "const double eta_r = ldexp(1.0, -21);"),
+    "sens_perturbs_wrong_line": ("Q[q].P = scl(nn, cc);", "Q[0].P = scl(nn, cc);"),
+    "sens_offset_from_wrong_point": ("double c = dot(nq, L[q].P);", "double c = dot(nq, L[q].d);"),
+    "margin_overlap_scale": ("note(tg, p2, R2, R2);", "note(tg, p2, R2, 1.0);"),
+    "margin_leg_scale": ("note(tg, side, 0.0, sqrt(p2 * w2));", "note(tg, side, 0.0, p2);"),
     "obstacle_lines_not_hard_in_lp3": ("for (int j = 0; j < nobst && j < OR_MAXK; ++j) proj[m++] = L[j];",
                                        "for (int j = 0; j < 0; ++j) proj[m++] = L[j];"),
 }
@@ -63,6 +71,14 @@ def _pins():
     """Quick versions of the pins: (name, callable raising AssertionError on failure)."""
     o = oracle
     return [
+        ("sens_shift", C.test_single_line_shift_moves_the_answer_by_four_ulps),
+        ("sens_turn", C.test_single_line_turn_dominates_far_from_the_line),
+        ("sens_parallel", lambda: C.test_near_parallel_vertex_is_tagged(1e-3)),
+        ("sens_tangent", C.test_near_tangent_line_is_tagged),
+        ("sens_vertex", C.test_well_separated_vertex_is_not_tagged),
+        ("sens_lp3", C.test_least_penetration_answer_is_probed_too),
+        ("margin_overlap", lambda: [C.test_overlap_decision_margin(d) for d in (3e-5, -3e-5)]),
+        ("margin_leg", lambda: C.test_leg_side_margin(2e-5)),
         ("head_on", lambda: H.test_head_on_pair_closed_form(o)),
         ("cutoff", lambda: H.test_resting_pair_cutoff_closed_form(o)),
         ("overlap", lambda: [H.test_resting_overlap_closed_form(o, dt, v)
@@ -89,7 +105,9 @@ def _pins():
     ]
 
 
-def _failing_pins(lib_path):
+def _failing_pins(lib_path, first_only=False):
+    """Names of the pins that fail against the library (stopping at the first failure
+    when first_only: a mutant needs only one pin to catch it)."""
     failed = []
     with oracle.use_library(lib_path):
         for name, fn in _pins():
@@ -97,6 +115,8 @@ def _failing_pins(lib_path):
                 fn()
             except (AssertionError, ValueError, FloatingPointError, ZeroDivisionError):
                 failed.append(name)
+                if first_only:
+                    break
     return failed
 
 
@@ -115,5 +135,5 @@ def test_mutant_is_caught(mutant):
             f.write(src.replace(old, new))
         lib = oracle.compile_source(path, os.path.join(td, f"lib_{mutant}.so"))
         with np.errstate(all="ignore"):
-            failed = _failing_pins(lib)
+            failed = _failing_pins(lib, first_only=True)
     assert failed, f"no pin catches mutant {mutant}"
