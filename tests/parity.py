@@ -15,9 +15,9 @@ The bar (the same in every GPU test):
     |p_gpu - p_oracle| <= max(VEL_TOL, |v_gpu - v_oracle|) * dt + 2 ulp(|p|) (FP32 storage
     of p): a tagged agent's position may differ only by its velocity's difference.
 """
-import math
-
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
