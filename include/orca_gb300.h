@@ -332,8 +332,12 @@ ORCA_API int orca_launches_per_step(const orca_ctx* ctx, int32_t* count);
  * library until the process exits); n above 65,536 returns ORCA_ERR_CAPACITY.  More cells
  * than that only coarsen the grid (results do not change).  The first call on a device
  * looks up the array's device address; make that first call before any stream capture.
- * The call is asynchronous on `stream`; non-finite inputs give non-finite outputs and
- * are not reported here.  Every call shares the one array, so calls whose work overlaps
+ * The call is asynchronous on `stream` and never synchronises, so errors that arise on
+ * the GPU are not reported here: non-finite inputs give non-finite outputs, and a crowd
+ * whose extent fits no grid of the scratch's cell table (which, with the cell edge
+ * doubling until the grid fits, happens only for non-finite or astronomically large
+ * coordinates) is stepped in a single cell -- slowly, still exactly -- without an error
+ * code.  Every call shares the one array, so calls whose work overlaps
  * on the GPU (different streams, or different host threads) race and corrupt each other:
  * order them.  Errors: ORCA_ERR_ARG, ORCA_ERR_CAPACITY, ORCA_ERR_CUDA, with a message in
  * orca_last_error(NULL).
@@ -405,7 +409,9 @@ ORCA_API int orca_sync(orca_ctx* ctx, void* stream);
 /* Agents currently loaded (0 if none). */
 ORCA_API int orca_num_agents(const orca_ctx* ctx, int32_t* n);
 
-/* Message of the last failure on ctx ("" if none); ctx may be NULL for creation errors. */
+/* Message of the last failure on ctx ("" if none).  ctx may be NULL for the entry points
+ * without a context (orca_create, orca_workspace_size, orca_step_static); that message is
+ * kept per host thread, so it is the calling thread's own last failure. */
 ORCA_API const char* orca_last_error(const orca_ctx* ctx);
 
 /* Fixed text for a status code. */

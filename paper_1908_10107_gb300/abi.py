@@ -356,17 +356,34 @@ def orca_launches_per_step(ctx) -> int:
 def orca_step_static(n, pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed, time_horizon,
                      neighbor_dist, max_neighbors, dt, cell_size, pos_out_xy, vel_out_xy,
                      stream=None):
-    """One step with no allocation (library-internal fixed scratch); device tensors only."""
-    ptrs = []
-    for a in (pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed, time_horizon, pos_out_xy,
-              vel_out_xy):
-        p, w = _ptr(a, np.float32)
-        if w != ORCA_DEVICE:
+    """One step with no allocation (library-internal fixed scratch); device tensors only.
+
+    The library launches on the current CUDA device and reads 2n / n floats from each
+    input, so every tensor must live on one device, which becomes current for the call,
+    and hold at least that many elements; anything else is refused before any launch."""
+    import torch
+    n = int(n)
+    if n < 0:
+        raise ValueError("orca_step_static: n < 0")
+    arrays = (pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed, time_horizon, pos_out_xy,
+              vel_out_xy)
+    per_agent = (2, 2, 2, 1, 1, 1, 1, 2, 2)
+    ptrs, devices = [], set()
+    for a, m in zip(arrays, per_agent):
+        if not isinstance(a, torch.Tensor) or not a.is_cuda:
             raise TypeError("orca_step_static takes CUDA tensors")
+        if a.numel() < m * n:
+            raise ValueError(f"orca_step_static: a tensor of {a.numel()} elements, "
+                             f"{m * n} needed for {n} agents")
+        p, _ = _ptr(a, np.float32)
         ptrs.append(p)
-    _check(load_library().orca_step_static(int(n), *ptrs[:7], float(neighbor_dist),
-                                           int(max_neighbors), float(dt), float(cell_size),
-                                           ptrs[7], ptrs[8], _stream(stream)))
+        devices.add(a.device)
+    if len(devices) != 1:
+        raise ValueError("orca_step_static: tensors on more than one device")
+    with torch.cuda.device(devices.pop()):
+        _check(load_library().orca_step_static(n, *ptrs[:7], float(neighbor_dist),
+                                               int(max_neighbors), float(dt), float(cell_size),
+                                               ptrs[7], ptrs[8], _stream(stream)))
 
 
 def orca_num_agents(ctx) -> int:

@@ -138,7 +138,9 @@ struct orca_ctx {
     std::string err;
 };
 
-static std::string g_create_err;
+// Message of the last failure of an entry point without a context, per host thread: two
+// threads failing at once each keep their own message.
+static thread_local std::string g_create_err;
 
 static int fail(orca_ctx* c, int code, const std::string& msg) {
     if (c) c->err = msg;
@@ -323,16 +325,27 @@ static int build_graphs(orca_ctx* ctx) {
     return ORCA_OK;
 }
 
-// The device-side address of a pinned (page-locked, mapped) host array that starts on a
-// 16-byte boundary, or null for other memory.  Kernels read and write such arrays directly over the CPU-GPU link.
-static void* mapped_host_ptr(const void* p) {
-    if (!p) return nullptr;
-    cudaPointerAttributes at;
+// The device-side address of a pinned (page-locked, mapped) host array of `bytes` bytes
+// that starts on a 16-byte boundary, or null for other memory.  Kernels read and write
+// such arrays directly over the CPU-GPU link, so its last byte must be pinned too and
+// mapped contiguously with the first (one registration); otherwise the caller falls back
+// to the staging copy.
+static void* mapped_host_ptr(const void* p, size_t bytes) {
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes at, end;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();  // clear the (non-sticky) error of an unknown pointer
         return nullptr;
     }
     if (at.type != cudaMemoryTypeHost || ((uintptr_t)at.devicePointer & 15)) return nullptr;
+    const char* last = (const char*)p + (bytes - 1);
+    if (cudaPointerGetAttributes(&end, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (end.type != cudaMemoryTypeHost ||
+        (const char*)end.devicePointer != (const char*)at.devicePointer + (bytes - 1))
+        return nullptr;
     return at.devicePointer;
 }
 
@@ -363,8 +376,8 @@ static int enqueue_write_state(orca_ctx* ctx, const float* pos_xy, const float* 
     const float2* pin = (const float2*)pos_xy;
     const float2* vin = (const float2*)vel_xy;
     if (where == ORCA_HOST) {
-        void* mp = mapped_host_ptr(pos_xy);
-        void* mv = mapped_host_ptr(vel_xy);
+        void* mp = mapped_host_ptr(pos_xy, N * 8);
+        void* mv = mapped_host_ptr(vel_xy, N * 8);
         if ((mp || !pos_xy) && (mv || !vel_xy)) {
             CK(launch_host_state(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, slot_map(ctx), !ctx->slot_ok,
                                  (float2*)mp, (float2*)mv, false, st),
@@ -384,8 +397,8 @@ static int enqueue_write_state(orca_ctx* ctx, const float* pos_xy, const float* 
 // synchronising.  Pinned host arrays are written by one kernel over the CPU-GPU link.
 static int enqueue_read_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int where, cudaStream_t st) {
     const size_t N = (size_t)ctx->n;
-    void* mp = where == ORCA_HOST ? mapped_host_ptr(pos_xy) : nullptr;
-    void* mv = where == ORCA_HOST ? mapped_host_ptr(vel_xy) : nullptr;
+    void* mp = where == ORCA_HOST ? mapped_host_ptr(pos_xy, N * 8) : nullptr;
+    void* mv = where == ORCA_HOST ? mapped_host_ptr(vel_xy, N * 8) : nullptr;
     if (where == ORCA_DEVICE) {
         CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (float2*)pos_xy, (float2*)vel_xy, st),
            "unpermute kernel");
