@@ -295,9 +295,20 @@ ORCA_API int orca_count_ops(orca_ctx* ctx, int32_t on);
 ORCA_API int orca_get_op_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
 
 /*
+ * FP32 FMA throughput microbenchmark (measurement; the paper has no counterpart): the peak
+ * against which the ORCA kernel's arithmetic roofline is quoted.  Enqueues one kernel on
+ * `stream` of `blocks` CTAs of 256 threads (blocks <= 0: 8 per SM), each thread running
+ * iters x 32 dependent-free FMAs; out (device, >= blocks floats) receives one value per CTA
+ * that keeps the work live.  *flops receives the FP32 operations enqueued (an FMA counts
+ * two); the caller times the kernel (CUDA events on `stream`).  Asynchronous.  Errors:
+ * ORCA_ERR_ARG (null pointer, iters < 1), ORCA_ERR_CUDA (launch failure).
+ */
+ORCA_API int orca_fma_bench(int32_t blocks, int32_t iters, float* out, int64_t* flops, void* stream);
+
+/*
  * Per-phase device timing.  With enable != 0 the step records CUDA events (event-record
  * nodes inside the captured graph) between its three phases: binning (bounding box, cell
- * keys, radix sort, cell table), reorder (gather into cell order) and the per-agent
+ * keys and counts, cell table), reorder (agents into cell order) and the per-agent
  * ORCA kernel.  Toggling rebuilds the graphs on the next orca_step.
  */
 ORCA_API int orca_profile(orca_ctx* ctx, int enable);
@@ -309,9 +320,10 @@ ORCA_API int orca_profile(orca_ctx* ctx, int enable);
  */
 ORCA_API int orca_profile_read(orca_ctx* ctx, float* ms3);
 
-/* Number of kernels one orca_step enqueues per step (some exit at once when the radix
- * sort needs fewer passes than the cell capacity allows; static obstacles add two: the
- * tile flags and the obstacle launch). */
+/* Number of kernels one orca_step enqueues per step: five for one scene (bounding box,
+ * cell keys and counts, cell table, reorder, ORCA kernel), six for a batch (scene boxes
+ * and scene offsets in place of the bounding box); static obstacles add two: the tile
+ * flags and the obstacle launch. */
 ORCA_API int orca_launches_per_step(const orca_ctx* ctx, int32_t* count);
 
 /*

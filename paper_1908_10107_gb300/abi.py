@@ -98,6 +98,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_set_launch": ([vp, i32, i32], c.c_int),
         "orca_step_static": ([i32] + [vp] * 7 + [c.c_float, i32, c.c_float, c.c_float, vp, vp, vp],
                              c.c_int),
+        "orca_fma_bench": ([i32, i32, vp, c.POINTER(c.c_int64), vp], c.c_int),
         "orca_num_agents": ([vp, c.POINTER(i32)], c.c_int),
         "orca_last_error": ([vp], c.c_char_p),
         "orca_status_string": ([c.c_int], c.c_char_p),
@@ -384,6 +385,18 @@ def orca_step_static(n, pos_xy, vel_xy, goal_xy, radius, max_speed, pref_speed, 
         _check(load_library().orca_step_static(n, *ptrs[:7], float(neighbor_dist),
                                                int(max_neighbors), float(dt), float(cell_size),
                                                ptrs[7], ptrs[8], _stream(stream)))
+
+
+def orca_fma_bench(blocks: int, iters: int, out, stream=None) -> int:
+    """Enqueue the FP32 FMA microbenchmark (``out``: CUDA float32 tensor of >= blocks, or
+    of >= 8 x SMs elements when blocks <= 0); returns the FP32 operations enqueued."""
+    p, w = _ptr(out, np.float32)
+    if w != ORCA_DEVICE:
+        raise TypeError("orca_fma_bench takes a CUDA tensor")
+    flops = ctypes.c_int64(0)
+    _check(load_library().orca_fma_bench(int(blocks), int(iters), p, ctypes.byref(flops),
+                                         _stream(stream)))
+    return int(flops.value)
 
 
 def orca_num_agents(ctx) -> int:

@@ -151,25 +151,6 @@ def tune_launch(sim: "abi.OrcaSim", reload, steps: int = STEPS, shapes=SHAPES,
     return {"shape": best, "timings_ms": {f"{a}x{b}": v for (a, b), v in timings.items()}}
 
 
-# digit width of the library's radix sort: a cell table of up to 2^(9 p) cells sorts in p
-# passes, and the step graph provisions the passes the context's max_cells needs
-RADIX_BITS = 9
-
-
-def radix_capacity(scene, cell_size: float, margin: float = 1.1) -> int:
-    """The smallest cell-table capacity 2^(9 p) that holds ``scene``'s grid at this cell edge
-    with ``margin`` to spare (estimated from the bounding box), so that the step graph
-    provisions no radix pass the grid does not need.  A grid that outgrows it later stays
-    exact: the library doubles the cell edge until the grid fits."""
-    p = np.asarray(scene.pos, np.float64).reshape(-1, 2)
-    if p.size == 0:
-        return 1 << RADIX_BITS
-    ext = p.max(0) - p.min(0)
-    cells = float(np.prod(np.floor(ext / cell_size) + 1.0)) * margin
-    passes = max(1, math.ceil(math.log2(max(cells, 2.0)) / RADIX_BITS))
-    return 1 << (RADIX_BITS * passes)
-
-
 def batch_cell_sizes(batch, factor: float):
     return [float(np.float32(factor * expected_kth_distance(sc.pos, sc.max_neighbors)))
             if sc.n > 1 else 0.0 for sc in batch.scenes]

@@ -24,9 +24,10 @@ struct Layout {
 };
 
 struct Plan {
-    int N, K, S, max_cells, max_passes, nsb, nmb;
+    int N, K, S, max_cells, nmb;
+    long long table_cells;  // largest grid (cells over all scenes) the cell table holds
     size_t o_msg, o_sslot, o_pv[2][2], o_goal[2], o_rad[2], o_vmax[2], o_pref[2], o_tau[2], o_id[2], o_hint[2];
-    size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_scenes, o_slot, o_part, o_misc, o_blk, o_rnbr, o_rcell, o_robst, o_seg, o_near, o_otiles,
+    size_t o_keys[2], o_vals[2], o_hist, o_tot, o_cells, o_cnt, o_tsum, o_scenes, o_slot, o_part, o_misc, o_blk, o_rnbr, o_rcell, o_robst, o_seg, o_near, o_otiles,
         o_stage[2];
     size_t total;
 };
@@ -46,11 +47,8 @@ static bool make_plan(const orca_params& p, Plan& pl) {
     pl.K = p.max_neighbors;
     pl.S = p.max_scenes > 1 ? p.max_scenes : 1;
     pl.max_cells = p.max_cells ? p.max_cells : default_max_cells(p.max_agents);
-    int bits = 0;
-    while (bits < 31 && (1LL << bits) < (long long)pl.max_cells) ++bits;
-    pl.max_passes = (bits + kRadixBits - 1) / kRadixBits;
-    if (pl.max_passes < 1) pl.max_passes = 1;
-    pl.nsb = sort_blocks(pl.N);
+    // a batch gives every scene at least one cell beyond its proportional share
+    pl.table_cells = (long long)pl.max_cells + pl.S;
     pl.nmb = main_blocks(pl.N);
     Layout L;
     size_t N = (size_t)pl.N;
@@ -70,10 +68,11 @@ static bool make_plan(const orca_params& p, Plan& pl) {
         pl.o_vals[b] = L.add(N * 4);
         pl.o_stage[b] = L.add(N * sizeof(float2));
     }
-    pl.o_hist = L.add((size_t)kRadixBuckets * pl.nsb * 4);
-    pl.o_tot = L.add((size_t)kRadixBuckets * 4);
-    // a batch gives every scene at least one cell beyond its proportional share
-    pl.o_cells = L.add(((size_t)pl.max_cells + pl.S + 1) * 4);
+    pl.o_hist = L.add((N / 2048 + 1) * 4);  // removal: tile sums of 2048 agents
+    pl.o_tot = L.add(4);
+    pl.o_cells = L.add(((size_t)pl.table_cells + 1) * 4);
+    pl.o_cnt = L.add((size_t)pl.table_cells * 4);
+    pl.o_tsum = L.add(((size_t)pl.table_cells / kCellTile + 1) * 4);
     pl.o_scenes = L.add((size_t)pl.S * sizeof(SceneDev));
     pl.o_slot = p.max_scenes > 1 ? L.add(N * 4) : (size_t)-1;
     pl.o_part = L.add(kBboxBlocks * sizeof(float4));
@@ -187,6 +186,9 @@ static void bind_buffers(orca_ctx* c) {
     c->bins.hist = (uint32_t*)(w + pl.o_hist);
     c->bins.digit_totals = (uint32_t*)(w + pl.o_tot);
     c->bins.cell_start = (uint32_t*)(w + pl.o_cells);
+    c->bins.cnt = (uint32_t*)(w + pl.o_cnt);
+    c->bins.tile_sums = (uint32_t*)(w + pl.o_tsum);
+    c->bins.table_cells = pl.table_cells;
     c->bins.bbox_partials = (float4*)(w + pl.o_part);
     c->bins.misc = (DeviceMisc*)(w + pl.o_misc);
     c->blk = (unsigned long long*)(w + pl.o_blk);
@@ -216,10 +218,9 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (c->prof && (e = cudaEventRecordWithFlags(c->pev[0], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (c->n_scenes > 0)
-        e = launch_binning_batch(c->n, c->n_scenes, c->scenes, c->slot_scene, pl.max_passes, c->PV[0],
-                                 c->bins, st);
+        e = launch_binning_batch(c->n, c->n_scenes, c->scenes, c->slot_scene, c->PV[0], c->bins, st);
     else
-        e = launch_binning(c->n, cs, pl.max_cells, pl.max_passes, c->PV[0], c->bins, st);
+        e = launch_binning(c->n, cs, pl.max_cells, c->PV[0], c->bins, st);
     if (e != cudaSuccess) return e;
     if (c->prof && (e = cudaEventRecordWithFlags(c->pev[1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     e = launch_reorder(c->n, c->bins, c->PV[0], c->sorted, c->PR[par], c->PR[par ^ 1], st);
@@ -260,12 +261,12 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     return e;
 }
 
-// kernels per step: bounding box (a batch: scene boxes and scene prefix), keys+histogram,
-// per radix pass (upsweep except pass 0, scan, downsweep), reorder + cell table, ORCA kernel
-// (with obstacles: tile flags, the plain ORCA launch and the obstacle launch)
+// kernels per step: bounding box (a batch: scene boxes and scene prefix), keys + counts,
+// cell table, reorder, ORCA kernel (with obstacles: tile flags, the plain ORCA launch and
+// the obstacle launch)
 static int launches_per_step(const orca_ctx* c) {
     const int obstacles = c->n_scenes == 0 && c->nseg > 0 ? 2 : 0;  // tile flags, obstacle launch
-    return (c->n_scenes > 0 ? 3 : 2) + 3 * c->plan.max_passes - 1 + 2 + obstacles;
+    return (c->n_scenes > 0 ? 2 : 1) + 4 + obstacles;
 }
 
 // One step launched directly with the neighbour lists and LP records written in agent
@@ -274,7 +275,7 @@ static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, ui
                                           cudaStream_t st) {
     const Plan& pl = c->plan;
     float cs = c->p.cell_size > 0.0f ? c->p.cell_size : c->p.neighbor_dist * 0.25f;
-    cudaError_t e = launch_binning(c->n, cs, pl.max_cells, pl.max_passes, c->PV[0], c->bins, st);
+    cudaError_t e = launch_binning(c->n, cs, pl.max_cells, c->PV[0], c->bins, st);
     if (e != cudaSuccess) return e;
     e = launch_reorder(c->n, c->bins, c->PV[0], c->sorted, c->PR[par], c->PR[par ^ 1], st);
     if (e != cudaSuccess) return e;
@@ -456,6 +457,10 @@ ORCA_API int orca_create(const orca_params* params, void* workspace, size_t work
     if (e == cudaSuccess) {
         bind_buffers(ctx);
         e = cudaMemset(ctx->bins.misc, 0, sizeof(DeviceMisc));
+        // the counting sort's cell and tile counts are zero between steps
+        if (e == cudaSuccess) e = cudaMemset(ctx->bins.cnt, 0, (size_t)pl.table_cells * 4);
+        if (e == cudaSuccess)
+            e = cudaMemset(ctx->bins.tile_sums, 0, ((size_t)pl.table_cells / kCellTile + 1) * 4);
     }
     if (e != cudaSuccess) {
         std::string m = std::string("context set-up: ") + cudaGetErrorString(e);

@@ -1,19 +1,22 @@
 // orca_bin.cu -- spatial binning of the crowd (Fig. 2: "messages organised into bins").
 //
-// Per step, on one stream, with no host round trip:
-//   bbox_grid       exact min/max of positions -> grid descriptor (cell edge, gx, gy).
-//   keys_hist       cell key of every agent + digit histogram of radix pass 0.
-//   radix_upsweep / radix_scan / radix_downsweep   stable LSD radix sort of
-//                   (cell key, slot) with 9-bit digits; only ceil(bits(num_cells)/9)
-//                   passes do work, the rest return at once.
-//   reorder         gathers state and parameters into the new cell order, writes the
-//                   id -> slot map, and the cell table: cell_start[c] = first sorted slot
-//                   of cell c for every c in [0, num_cells] (empty cells included, no
-//                   memset needed).
+// Per step, on one stream, with no host round trip, four kernels:
+//   bbox_grid    exact min/max of positions -> grid descriptor (cell edge, gx, gy).
+//   keys_count   cell key of every agent, and its rank among the agents of its cell: one
+//                atomic increment of the cell's count per group of warp lanes that share
+//                the cell; the count of every tile of kCellTile cells likewise.
+//   cell_scan    the cell table cell_start[c] = agents in cells before c, for every c in
+//                [0, num_cells] (empty cells included): an exclusive scan of the counts in
+//                tiles of kCellTile cells, each CTA starting from the sum of the earlier
+//                tiles' counts; it clears the counts for the next step.
+//   reorder      every agent goes to slot cell_start[key] + rank: state and parameters
+//                are read in the previous order (coalesced) and written to the new slot
+//                with the message record and the id -> slot map.
 //
-// The sort is stable with respect to the previous step's cell order, so the layout is
-// deterministic; nothing downstream depends on the order inside a cell (neighbours are
-// ranked by (distance, agent index)).
+// This is a counting sort by cell (one pass over the agents, one over the cells).  The
+// order inside a cell follows the atomic increments and so varies from run to run;
+// nothing computed depends on it: neighbours are ranked by (distance, agent index), and
+// every agent's result is a function of its own neighbour list alone.
 #include "orca_common.cuh"
 
 namespace orca {
@@ -21,8 +24,7 @@ namespace orca {
 // Grid over a bounding box r = (xmin, ymin, xmax, ymax), all in FP32:
 // inv = fl(1/s), g = floor(fl(fl(max - min) * inv)) + 1, doubling s while gx*gy exceeds
 // max_cells.  A non-finite or absurd extent puts everything in one cell and sets *err.
-__device__ GridDev derive_grid(float4 r, float cell_size, long long max_cells, int max_passes,
-                               int* err) {
+__device__ GridDev derive_grid(float4 r, float cell_size, long long max_cells, int* err) {
     GridDev g;
     g.xmin = r.x;
     g.ymin = r.y;
@@ -50,10 +52,6 @@ __device__ GridDev derive_grid(float4 r, float cell_size, long long max_cells, i
     g.gx = (int)fx + 1;
     g.gy = (int)fy + 1;
     g.num_cells = g.gx * g.gy;
-    int bits = 0;
-    while (bits < 31 && (1u << bits) < (unsigned)g.num_cells) ++bits;
-    int passes = (bits + kRadixBits - 1) / kRadixBits;
-    g.passes = passes < 1 ? 1 : (passes > max_passes ? max_passes : passes);
     // rounding of fl(fl(x - xmin) * inv) moves a cell boundary by at most a few ulps of
     // the extent; 1e-5 relative is a wide margin
     g.slop = 1e-5f * (fabsf(g.xmin) + fabsf(g.ymin) + ex + ey + 2.0f * s) + 1e-6f;
@@ -68,8 +66,7 @@ __device__ GridDev derive_grid(float4 r, float cell_size, long long max_cells, i
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) bbox_grid_kernel(int n, const float2* __restrict__ pos,
                                                         float cell_size, long long max_cells,
-                                                        int max_passes, float4* partials,
-                                                        DeviceMisc* misc) {
+                                                        float4* partials, DeviceMisc* misc) {
     pdl_wait();
     float xmin = INFINITY, ymin = INFINITY, xmax = -INFINITY, ymax = -INFINITY;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -138,7 +135,7 @@ __global__ void __launch_bounds__(256) bbox_grid_kernel(int n, const float2* __r
     misc->tile_counter = 0;
     misc->obs_tiles = 0;
     int err = 0;
-    misc->grid = derive_grid(r, cell_size, max_cells, max_passes, &err);
+    misc->grid = derive_grid(r, cell_size, max_cells, &err);
     if (err) atomicOr(&misc->error, err);
 }
 
@@ -148,242 +145,197 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Cell key of each agent and the digit-0 histogram of this block's tile.
+// Cell key of every agent and its rank among the agents of its cell.  Lanes of a warp
+// that share a cell (agents arrive in the previous step's cell order, so neighbouring
+// lanes mostly do) take one atomic on the cell's count: the leader adds the group's size
+// and every lane's rank is the leader's old count plus the group's lanes below it.  The
+// tile counts for the scan are gathered the same way.  Lanes past the crowd carry an
+// impossible key, so every lane of a warp takes part in the warp primitives.
 // Batch mode (scenes != null): the key is the scene's cell offset plus its local cell.
-__global__ void __launch_bounds__(kSortThreads) keys_hist_kernel(int n, const float2* __restrict__ pos,
-                                                                 const DeviceMisc* __restrict__ misc,
-                                                                 const SceneDev* __restrict__ scenes,
-                                                                 const int* __restrict__ slot_scene,
-                                                                 uint32_t* __restrict__ keys,
-                                                                 uint32_t* __restrict__ hist) {
+__global__ void __launch_bounds__(256) keys_count_kernel(int n, const float2* __restrict__ pos,
+                                                         const DeviceMisc* __restrict__ misc,
+                                                         const SceneDev* __restrict__ scenes,
+                                                         const int* __restrict__ slot_scene,
+                                                         uint32_t* __restrict__ keys,
+                                                         uint32_t* __restrict__ ranks,
+                                                         uint32_t* cnt, uint32_t* tile_sums) {
     pdl_wait();
-    __shared__ uint32_t s_hist[kRadixBuckets];
-    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) s_hist[d] = 0;
-    __syncthreads();
-    int base = blockIdx.x * kSortTile;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    uint32_t key = 0xffffffffu;
+    if (valid) {
+        const float2 p = pos[i];
+        uint32_t off = 0;
+        const GridDev* gp = &misc->grid;
+        if (scenes) {
+            const SceneDev* sc = scenes + slot_scene[i];
+            gp = &sc->grid;
+            off = (uint32_t)sc->cell_off;
+        }
+        const GridDev g = *gp;
+        const int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
+        const int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
+        key = off + (uint32_t)cy * (uint32_t)g.gx + (uint32_t)cx;
+        keys[i] = key;
+    }
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(cnt + key, (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) ranks[i] = base + (uint32_t)__popc(peers & lt);
+    const uint32_t tile = valid ? key / (uint32_t)kCellTile : 0xffffffffu;
+    const unsigned tp = __match_any_sync(0xffffffffu, tile);
+    if (valid && lane == __ffs(tp) - 1) atomicAdd(tile_sums + tile, (uint32_t)__popc(tp));
+}
+
+// Block-wide exclusive scan (kCellScanThreads threads) of one value per thread; also
+// returns the block total through `total`.
+__device__ __forceinline__ uint32_t cell_block_scan(uint32_t v, uint32_t& total) {
+    __shared__ uint32_t s_warp[kCellScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
 #pragma unroll
-    for (int c = 0; c < kSortItems; ++c) {
-        int i = base + c * kSortThreads + threadIdx.x;
-        if (i < n) {
-            float2 p = pos[i];
-            uint32_t off = 0;
-            const GridDev* gp = &misc->grid;
-            if (scenes) {
-                const SceneDev* sc = scenes + slot_scene[i];
-                gp = &sc->grid;
-                off = (uint32_t)sc->cell_off;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    uint32_t base = 0;
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < kCellScanThreads / 32; ++w) {
+        const uint32_t sw = s_warp[w];
+        if (w < warp) base += sw;
+        total += sw;
+    }
+    __syncthreads();
+    return base + inc - v;
+}
+
+// The cell table from the counts, one tile of kCellTile cells per CTA (kCellsPerThread
+// consecutive cells per thread, read and written as 16-byte vectors): the tile starts at
+// the sum of the earlier tiles' counts (keys_count gathered them), then an exclusive scan
+// inside the tile.  The counts are cleared on the way for the next step, and the thread
+// whose range holds num_cells closes the table with cell_start[num_cells] = n.  CTAs past
+// the grid's last tile return at once (the launch covers the table's capacity).
+__global__ void __launch_bounds__(kCellScanThreads) cell_scan_kernel(int n, const DeviceMisc* __restrict__ misc,
+                                                                     uint32_t* __restrict__ cnt,
+                                                                     const uint32_t* __restrict__ tile_sums,
+                                                                     uint32_t* __restrict__ cell_start) {
+    pdl_wait();
+    const long long nc = misc->grid.num_cells;
+    const int tile = blockIdx.x;
+    if ((long long)tile * kCellTile > nc) return;  // the whole CTA
+    uint32_t pre = 0, tot = 0;
+    for (int b = threadIdx.x; b < tile; b += kCellScanThreads) pre += tile_sums[b];
+    (void)cell_block_scan(pre, tot);  // every thread gets the sum of the earlier tiles
+    pre = tot;
+    const long long c0 = (long long)tile * kCellTile + (long long)threadIdx.x * kCellsPerThread;
+    const bool full = c0 + kCellsPerThread <= nc;
+    uint32_t v[kCellsPerThread];
+    if (full) {
+        const uint4* src = reinterpret_cast<const uint4*>(cnt + c0);
+#pragma unroll
+        for (int q = 0; q < kCellsPerThread / 4; ++q) {
+            const uint4 w = src[q];
+            v[4 * q] = w.x;
+            v[4 * q + 1] = w.y;
+            v[4 * q + 2] = w.z;
+            v[4 * q + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kCellsPerThread; ++q) v[q] = c0 + q < nc ? cnt[c0 + q] : 0u;
+    }
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < kCellsPerThread; ++q) sum += v[q];
+    uint32_t run = pre + cell_block_scan(sum, tot);
+#pragma unroll
+    for (int q = 0; q < kCellsPerThread; ++q) {
+        const uint32_t c = v[q];
+        v[q] = run;
+        run += c;
+    }
+    if (full) {
+        uint4* dst = reinterpret_cast<uint4*>(cell_start + c0);
+        uint4* clr = reinterpret_cast<uint4*>(cnt + c0);
+#pragma unroll
+        for (int q = 0; q < kCellsPerThread / 4; ++q) {
+            dst[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            clr[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kCellsPerThread; ++q)
+            if (c0 + q < nc) {
+                cell_start[c0 + q] = v[q];
+                cnt[c0 + q] = 0u;
             }
-            const GridDev g = *gp;
-            int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
-            int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
-            uint32_t key = off + (uint32_t)cy * (uint32_t)g.gx + (uint32_t)cx;
-            keys[i] = key;
-            atomicAdd(&s_hist[key & (kRadixBuckets - 1)], 1u);
-        }
     }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x)
-        hist[d * gridDim.x + blockIdx.x] = s_hist[d];
+    if (c0 <= nc && nc < c0 + kCellsPerThread) cell_start[nc] = (uint32_t)n;
 }
 
-__global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(int n, int pass,
-                                                                     const DeviceMisc* __restrict__ misc,
-                                                                     const uint32_t* __restrict__ keys,
-                                                                     uint32_t* __restrict__ hist) {
-    pdl_wait();
-    if (pass >= misc->grid.passes) return;
-    __shared__ uint32_t s_hist[kRadixBuckets];
-    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) s_hist[d] = 0;
-    __syncthreads();
-    int shift = pass * kRadixBits;
-    int base = blockIdx.x * kSortTile;
-#pragma unroll
-    for (int c = 0; c < kSortItems; ++c) {
-        int i = base + c * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&s_hist[(keys[i] >> shift) & (kRadixBuckets - 1)], 1u);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x)
-        hist[d * gridDim.x + blockIdx.x] = s_hist[d];
-}
-
-// Exclusive scan, in place, of each digit's row hist[d * nblocks + 0..nblocks-1] (one
-// warp per digit, kScanWarps digits per CTA), and the digit's total into totals[d].  The
-// scan across digits is done by every downsweep block from the 256 totals.
-constexpr int kScanWarps = 8;
-__global__ void __launch_bounds__(kScanWarps * 32) radix_scan_kernel(int nblocks, int pass,
-                                                                     const DeviceMisc* __restrict__ misc,
-                                                                     uint32_t* __restrict__ hist,
-                                                                     uint32_t* __restrict__ totals) {
-    pdl_wait();
-    if (pass >= misc->grid.passes) return;
-    int lane = threadIdx.x & 31;
-    int d = blockIdx.x * kScanWarps + (threadIdx.x >> 5);
-    uint32_t run = 0;
-    uint32_t* row = hist + (size_t)d * nblocks;
-    for (int b0 = 0; b0 < nblocks; b0 += 32) {
-        int b = b0 + lane;
-        uint32_t v = b < nblocks ? row[b] : 0u;
-        uint32_t inc = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (b < nblocks) row[b] = run + inc - v;
-        run += __shfl_sync(0xffffffffu, inc, 31);
-    }
-    if (lane == 0) totals[d] = run;
-}
-
-// Stable scatter of one radix pass.  The tile is walked in order in chunks of one item
-// per thread; inside a warp, lanes with equal digits rank themselves with match.any, and
-// per-warp digit counts in shared memory order the warps.  vals == nullptr means the
-// identity (slot index).
-__global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
-    int n, int pass, const DeviceMisc* __restrict__ misc, const uint32_t* __restrict__ keys_in,
-    const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ offsets,
-    const uint32_t* __restrict__ totals) {
-    pdl_wait();
-    if (pass >= misc->grid.passes) return;
-    constexpr int kWarps = kSortThreads / 32;
-    constexpr int kPer = kRadixBuckets / kSortThreads;  // digits per thread below
-    static_assert(kRadixBuckets % kSortThreads == 0, "whole digits per thread");
-    __shared__ uint32_t s_run[kRadixBuckets];
-    __shared__ uint32_t s_wcnt[kWarps][kRadixBuckets];
-    __shared__ uint32_t s_wsum[kWarps];
-    int warp = threadIdx.x >> 5;
-    {
-        // base of each digit: exclusive scan of the digit totals (kPer consecutive digits
-        // per thread)
-        int lane0 = threadIdx.x & 31;
-        uint32_t v[kPer], sum = 0;
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            v[q] = totals[threadIdx.x * kPer + q];
-            sum += v[q];
-        }
-        uint32_t inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane0 >= o) inc += y;
-        }
-        if (lane0 == 31) s_wsum[warp] = inc;
-        __syncthreads();
-        uint32_t base = inc - sum;
-        for (int w = 0; w < warp; ++w) base += s_wsum[w];
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            int d = threadIdx.x * kPer + q;
-            s_run[d] = base + offsets[d * gridDim.x + blockIdx.x];
-            base += v[q];
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) s_wcnt[w][d] = 0;
-        }
-    }
-    __syncthreads();
-    int shift = pass * kRadixBits;
-    int base = blockIdx.x * kSortTile;
-    unsigned lt = lanemask_lt();
-    for (int c = 0; c < kSortItems; ++c) {
-        int i = base + c * kSortThreads + threadIdx.x;
-        bool valid = i < n;
-        uint32_t key = valid ? keys_in[i] : 0u;
-        uint32_t val = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
-        uint32_t d = (key >> shift) & (kRadixBuckets - 1);
-        unsigned vmask = __ballot_sync(0xffffffffu, valid);
-        unsigned rank = 0;
-        if (valid) {
-            unsigned peers = __match_any_sync(vmask, d);
-            rank = __popc(peers & lt);
-            if ((peers & lt) == 0) s_wcnt[warp][d] = __popc(peers);
-        }
-        __syncthreads();
-        if (valid) {
-            uint32_t dst = s_run[d] + rank;
-            for (int w = 0; w < warp; ++w) dst += s_wcnt[w][d];
-            keys_out[dst] = key;
-            vals_out[dst] = val;
-        }
-        __syncthreads();
-        for (int dd = threadIdx.x; dd < kRadixBuckets; dd += blockDim.x) {
-            uint32_t tot = 0;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                tot += s_wcnt[w][dd];
-                s_wcnt[w][dd] = 0;
-            }
-            s_run[dd] += tot;
-        }
-        __syncthreads();
-    }
-}
-
-// Gather state and parameters into the sorted order; build the message records, the
-// id -> slot map and the cell table.  Each thread takes kReorderR slots (blockDim apart)
-// and issues all their loads before any store, so that more gathers are in flight.
+// Every agent to its slot cell_start[key] + rank: state and parameters read at the old
+// slot (coalesced), written to the new one with the message record and the id -> slot
+// map.  Each thread takes kReorderR agents (blockDim apart) and issues all their loads
+// before any store, so that more loads are in flight.  Block 0 first clears the tile
+// counts, which the cell scan (complete before this kernel starts) no longer needs.
 constexpr int kReorderR = 2;
-__global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __restrict__ vals_a,
-                                                      const uint32_t* __restrict__ vals_b,
-                                                      const uint32_t* __restrict__ keys_a,
-                                                      const uint32_t* __restrict__ keys_b,
-                                                      const DeviceMisc* __restrict__ misc,
-                                                      uint32_t* __restrict__ cell_start,
+__global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __restrict__ keys,
+                                                      const uint32_t* __restrict__ ranks,
+                                                      DeviceMisc* misc,
+                                                      const uint32_t* __restrict__ cell_start,
+                                                      uint32_t* __restrict__ tile_sums,
                                                       AgentState src_s, Sorted dst_s,
                                                       AgentParams src_p, AgentParams dst_p) {
     pdl_wait();
-    const GridDev& g = misc->grid;
-    const uint32_t* vals = (g.passes & 1) ? vals_b : vals_a;
-    const uint32_t* keys = (g.passes & 1) ? keys_b : keys_a;
-    const int t0 = blockIdx.x * blockDim.x * kReorderR + threadIdx.x;
-    uint32_t s[kReorderR];
-    int prev[kReorderR], cur[kReorderR];
-#pragma unroll
-    for (int r = 0; r < kReorderR; ++r) {
-        int t = t0 + r * blockDim.x;
-        bool ok = t < n;
-        s[r] = ok ? vals[t] : 0u;
-        cur[r] = ok ? (int)keys[t] : 0;
-        prev[r] = (ok && t > 0) ? (int)keys[t - 1] : -1;
+    if (blockIdx.x == 0) {
+        const int tiles = misc->grid.num_cells / kCellTile + 1;
+        for (int b = threadIdx.x; b < tiles; b += blockDim.x) tile_sums[b] = 0u;
     }
+    const int i0 = blockIdx.x * blockDim.x * kReorderR + threadIdx.x;
+    uint32_t t[kReorderR];
     float2 p[kReorderR], v[kReorderR], goal[kReorderR];
     float rad[kReorderR], vmax[kReorderR], pref[kReorderR], tau[kReorderR], hint[kReorderR];
     uint32_t id[kReorderR];
 #pragma unroll
     for (int r = 0; r < kReorderR; ++r) {
-        if (t0 + r * (int)blockDim.x >= n) continue;
-        uint32_t q = s[r];
-        p[r] = src_s.pos[q];
-        v[r] = src_s.vel[q];
-        goal[r] = src_p.goal[q];
-        rad[r] = src_p.radius[q];
-        vmax[r] = src_p.max_speed[q];
-        pref[r] = src_p.pref_speed[q];
-        tau[r] = src_p.tau[q];
-        id[r] = src_p.id[q];
-        hint[r] = dst_p.hint ? src_p.hint[q] : 0.0f;
+        const int i = i0 + r * blockDim.x;
+        if (i >= n) continue;
+        t[r] = cell_start[keys[i]] + ranks[i];
+        p[r] = src_s.pos[i];
+        v[r] = src_s.vel[i];
+        goal[r] = src_p.goal[i];
+        rad[r] = src_p.radius[i];
+        vmax[r] = src_p.max_speed[i];
+        pref[r] = src_p.pref_speed[i];
+        tau[r] = src_p.tau[i];
+        id[r] = src_p.id[i];
+        hint[r] = dst_p.hint ? src_p.hint[i] : 0.0f;
     }
 #pragma unroll
     for (int r = 0; r < kReorderR; ++r) {
-        int t = t0 + r * blockDim.x;
-        if (t >= n) continue;
-        dst_s.msg[t] = make_float4(p[r].x, p[r].y, rad[r], __uint_as_float(id[r]));
-        dst_s.slot[id[r]] = (uint32_t)t;
-        dst_s.vel[t] = v[r];
-        dst_p.goal[t] = goal[r];
-        dst_p.radius[t] = rad[r];
-        dst_p.max_speed[t] = vmax[r];
-        dst_p.pref_speed[t] = pref[r];
-        dst_p.tau[t] = tau[r];
-        dst_p.id[t] = id[r];
-        if (dst_p.hint) dst_p.hint[t] = hint[r];
-        // cell table: slot t starts every cell in (key[t-1], key[t]]; the last slot also
-        // closes the cells after its own with cell_start = n
-        for (int c = prev[r] + 1; c <= cur[r]; ++c) cell_start[c] = (uint32_t)t;
-        if (t == n - 1)
-            for (int c = cur[r] + 1; c <= g.num_cells; ++c) cell_start[c] = (uint32_t)n;
+        if (i0 + r * (int)blockDim.x >= n) continue;
+        const uint32_t q = t[r];
+        if (q >= (uint32_t)n) {  // counts that do not add up (never in a consistent step)
+            atomicOr(&misc->error, kErrCapacity);
+            continue;
+        }
+        dst_s.msg[q] = make_float4(p[r].x, p[r].y, rad[r], __uint_as_float(id[r]));
+        dst_s.slot[id[r]] = q;
+        dst_s.vel[q] = v[r];
+        dst_p.goal[q] = goal[r];
+        dst_p.radius[q] = rad[r];
+        dst_p.max_speed[q] = vmax[r];
+        dst_p.pref_speed[q] = pref[r];
+        dst_p.tau[q] = tau[r];
+        dst_p.id[q] = id[r];
+        if (dst_p.hint) dst_p.hint[q] = hint[r];
     }
 }
 
@@ -469,46 +421,29 @@ __global__ void __launch_bounds__(256) iota_kernel(int n, uint32_t* __restrict__
 // ---------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------
-int sort_blocks(int n) { return (n + kSortTile - 1) / kSortTile; }
+// CTAs of the cell scan: enough tiles for the largest grid the table holds.
+static int scan_blocks(long long table_cells) { return (int)(table_cells / kCellTile + 1); }
 
-cudaError_t launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cudaStream_t st);
-
-cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_passes,
-                           const AgentState& cur, const BinBuffers& b, cudaStream_t st) {
-    int nb_bbox = (n + 255) / 256;
-    if (nb_bbox > kBboxBlocks) nb_bbox = kBboxBlocks;
-    bbox_grid_kernel<<<nb_bbox, 256, 0, st>>>(n, cur.pos, cell_size, max_cells, max_passes,
-                                              b.bbox_partials, b.misc);
-    cudaError_t e = cudaGetLastError();
+// keys_count, cell_scan (the grid and the bounding box are already in misc).
+static cudaError_t launch_counting_sort(int n, const SceneDev* scenes, const int* slot_scene,
+                                       const AgentState& cur, const BinBuffers& b, cudaStream_t st) {
+    cudaError_t e = launch_pdl(keys_count_kernel, (n + 255) / 256, 256, 0, st, n, (const float2*)cur.pos,
+                               (const DeviceMisc*)b.misc, scenes, slot_scene, b.keys[0], b.vals[0],
+                               b.cnt, b.tile_sums);
     if (e != cudaSuccess) return e;
-    int nsb = sort_blocks(n);
-    e = launch_pdl(keys_hist_kernel, nsb, kSortThreads, 0, st, n, (const float2*)cur.pos,
-                   (const DeviceMisc*)b.misc, (const SceneDev*)nullptr, (const int*)nullptr,
-                   b.keys[0], b.hist);
-    if (e != cudaSuccess) return e;
-    return launch_radix_passes(n, nsb, max_passes, b, st);
+    return launch_pdl(cell_scan_kernel, scan_blocks(b.table_cells), kCellScanThreads, 0, st, n,
+                      (const DeviceMisc*)b.misc, b.cnt, (const uint32_t*)b.tile_sums, b.cell_start);
 }
 
-// Radix passes over the keys written by keys_hist (the reorder kernel builds the cell table).
-cudaError_t launch_radix_passes(int n, int nsb, int max_passes, const BinBuffers& b, cudaStream_t st) {
-    const DeviceMisc* misc = b.misc;
-    for (int pass = 0; pass < max_passes; ++pass) {
-        int src = pass & 1, dst = src ^ 1;
-        cudaError_t e = cudaSuccess;
-        if (pass > 0)
-            e = launch_pdl(radix_upsweep_kernel, nsb, kSortThreads, 0, st, n, pass, misc,
-                           (const uint32_t*)b.keys[src], b.hist);
-        if (e == cudaSuccess)
-            e = launch_pdl(radix_scan_kernel, kRadixBuckets / kScanWarps, kScanWarps * 32, 0, st, nsb,
-                           pass, misc, b.hist, b.digit_totals);
-        if (e == cudaSuccess)
-            e = launch_pdl(radix_downsweep_kernel, nsb, kSortThreads, 0, st, n, pass, misc,
-                           (const uint32_t*)b.keys[src],
-                           (const uint32_t*)(pass == 0 ? nullptr : b.vals[src]), b.keys[dst],
-                           b.vals[dst], (const uint32_t*)b.hist, (const uint32_t*)b.digit_totals);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+cudaError_t launch_binning(int n, float cell_size, long long max_cells, const AgentState& cur,
+                           const BinBuffers& b, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int nb_bbox = (n + 255) / 256;
+    if (nb_bbox > kBboxBlocks) nb_bbox = kBboxBlocks;
+    bbox_grid_kernel<<<nb_bbox, 256, 0, st>>>(n, cur.pos, cell_size, max_cells, b.bbox_partials, b.misc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_counting_sort(n, nullptr, nullptr, cur, b, st);
 }
 
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
@@ -516,9 +451,8 @@ cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,
                            const AgentParams& dst_p, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     return launch_pdl(reorder_kernel, (n + 256 * kReorderR - 1) / (256 * kReorderR), 256, 0, st, n,
-                      (const uint32_t*)b.vals[0], (const uint32_t*)b.vals[1],
-                      (const uint32_t*)b.keys[0], (const uint32_t*)b.keys[1],
-                      (const DeviceMisc*)b.misc, b.cell_start, src_s, dst_s, src_p, dst_p);
+                      (const uint32_t*)b.keys[0], (const uint32_t*)b.vals[0], b.misc,
+                      (const uint32_t*)b.cell_start, b.tile_sums, src_s, dst_s, src_p, dst_p);
 }
 
 cudaError_t launch_unpermute(int n, const AgentState& s, const uint32_t* id, float2* pos_out,
@@ -556,8 +490,7 @@ cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st) {
 // ---------------------------------------------------------------------------------
 // Bounding box and grid of each scene: one CTA per scene over its slot range.
 __global__ void __launch_bounds__(1024) scene_bbox_grid_kernel(const float2* __restrict__ pos,
-                                                               SceneDev* scenes, int max_passes,
-                                                               DeviceMisc* misc) {
+                                                               SceneDev* scenes, DeviceMisc* misc) {
     pdl_wait();
     SceneDev* sc = scenes + blockIdx.x;
     const int off = sc->off, cnt = sc->cnt;
@@ -590,14 +523,14 @@ __global__ void __launch_bounds__(1024) scene_bbox_grid_kernel(const float2* __r
     if (cnt == 0) r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float cs = sc->cell_size > 0.0f ? sc->cell_size : sc->nd * 0.25f;
     int err = 0;
-    sc->grid = derive_grid(r, cs, sc->cell_budget, max_passes, &err);
+    sc->grid = derive_grid(r, cs, sc->cell_budget, &err);
     if (err) atomicOr(&misc->error, err);
 }
 
-// Cell offsets of the scenes (exclusive scan of their cell counts), the total and the
-// radix passes it needs; resets the persistent kernel's tile counter.
+// Cell offsets of the scenes (exclusive scan of their cell counts) and the total; resets
+// the persistent kernel's tile counter.
 __global__ void __launch_bounds__(1024) scene_prefix_kernel(int n_scenes, SceneDev* scenes,
-                                                            int max_passes, DeviceMisc* misc) {
+                                                            DeviceMisc* misc) {
     pdl_wait();
     __shared__ long long s_sum[1024];
     int per = (n_scenes + blockDim.x - 1) / blockDim.x;
@@ -613,11 +546,7 @@ __global__ void __launch_bounds__(1024) scene_prefix_kernel(int n_scenes, SceneD
             s_sum[t] = run;
             run += v;
         }
-        int bits = 0;
-        while (bits < 31 && (1LL << bits) < run) ++bits;
-        int passes = (bits + kRadixBits - 1) / kRadixBits;
         misc->grid.num_cells = (int)run;
-        misc->grid.passes = passes < 1 ? 1 : (passes > max_passes ? max_passes : passes);
         misc->tile_counter = 0;
     }
     __syncthreads();
@@ -652,19 +581,13 @@ cudaError_t launch_slot_scene(int n, int n_scenes, const SceneDev* scenes, int* 
 }
 
 cudaError_t launch_binning_batch(int n, int n_scenes, SceneDev* scenes, const int* slot_scene,
-                                 int max_passes, const AgentState& cur, const BinBuffers& b,
-                                 cudaStream_t st) {
-    scene_bbox_grid_kernel<<<n_scenes, 1024, 0, st>>>(cur.pos, scenes, max_passes, b.misc);
+                                 const AgentState& cur, const BinBuffers& b, cudaStream_t st) {
+    scene_bbox_grid_kernel<<<n_scenes, 1024, 0, st>>>(cur.pos, scenes, b.misc);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = launch_pdl(scene_prefix_kernel, 1, 1024, 0, st, n_scenes, scenes, max_passes, b.misc);
-    int nsb = sort_blocks(n);
-    if (e == cudaSuccess)
-        e = launch_pdl(keys_hist_kernel, nsb, kSortThreads, 0, st, n, (const float2*)cur.pos,
-                       (const DeviceMisc*)b.misc, (const SceneDev*)scenes, slot_scene, b.keys[0],
-                       b.hist);
-    if (e != cudaSuccess) return e;
-    return launch_radix_passes(n, nsb, max_passes, b, st);
+        e = launch_pdl(scene_prefix_kernel, 1, 1024, 0, st, n_scenes, scenes, b.misc);
+    if (e != cudaSuccess || n <= 0) return e;
+    return launch_counting_sort(n, scenes, slot_scene, cur, b, st);
 }
 
 }  // namespace orca

@@ -7,8 +7,9 @@
 //   PR[0], PR[1]: per-agent parameters float2 goal, float radius, max_speed, pref_speed,
 //                 time_horizon and uint32 id (agent index of orca_set_agents).  They are
 //                 permuted together with the state; the current copy alternates each step.
-//   sort keys/values (uint32, ping-pong), per-block digit histograms, the cell table
-//   cell_start[num_cells + 1], the grid descriptor and counters.
+//   cell keys and in-cell ranks (uint32), per-cell counts and per-tile counts of the
+//   counting sort, the cell table cell_start[num_cells + 1], the grid descriptor and
+//   counters.
 #pragma once
 
 #include <cstdint>
@@ -17,7 +18,6 @@
 namespace orca {
 
 constexpr int kMaxNeighbors = 32;
-constexpr int kRadixBits = 9;
 // per-CTA counters of the ORCA kernel: agents, LP3 agents, candidates, half-planes, then
 // (operation-counting launches only) LP1 calls, LP1 bounds, violation checks, bisectors
 constexpr int kBlockCounters = 8;
@@ -25,10 +25,10 @@ constexpr int kBlockCounters = 8;
 // tile can reach) and obstacle half-planes per agent
 constexpr int kMaxObstacles = 256;
 constexpr int kMaxObstacleNeighbors = 4;
-constexpr int kRadixBuckets = 1 << kRadixBits;
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 4;  // items per thread per tile
-constexpr int kSortTile = kSortThreads * kSortItems;
+// the cell-table scan: tiles of kCellTile cells, kCellsPerThread per thread
+constexpr int kCellScanThreads = 256;
+constexpr int kCellsPerThread = 16;
+constexpr int kCellTile = kCellScanThreads * kCellsPerThread;
 constexpr int kBboxBlocks = 304;  // 2 x 152 SMs
 
 // device error bits (latched in DeviceMisc::error)
@@ -42,13 +42,12 @@ struct GridDev {
     float s, inv;      // cell edge and fl32(1/s)
     int gx, gy;        // cells per row / column
     int num_cells;     // gx * gy
-    int passes;        // radix passes needed for keys < num_cells
     float slop;        // conservative bound on cell-assignment rounding, metres
-    int pad[3];
+    int pad[4];
 };
 
 struct DeviceMisc {
-    GridDev grid;              // single scene: the grid; batch: num_cells / passes of all scenes
+    GridDev grid;              // single scene: the grid; batch: num_cells of all scenes
     unsigned int bbox_ticket;  // last-block-done counter of the bbox reduction
     int error;                 // kErr* bits
     unsigned int tile_counter; // next tile of the persistent ORCA kernel (reset every step)
@@ -95,11 +94,14 @@ struct Sorted {
 };
 
 struct BinBuffers {
-    uint32_t* keys[2];
-    uint32_t* vals[2];
-    uint32_t* hist;
-    uint32_t* digit_totals;  // kRadixBuckets per radix pass (reused)
-    uint32_t* cell_start;
+    uint32_t* keys[2];       // keys[0]: cell key of every slot; keys[1]: scratch
+    uint32_t* vals[2];       // vals[0]: rank of every slot in its cell; vals[1]: scratch
+    uint32_t* hist;          // scratch between steps (agent removal: tile sums)
+    uint32_t* digit_totals;  // scratch between steps (agent removal: the count)
+    uint32_t* cnt;           // agents per cell, zero between steps (table_cells entries)
+    uint32_t* tile_sums;     // agents per kCellTile cells, zero between steps
+    uint32_t* cell_start;    // table_cells + 1 entries
+    long long table_cells;   // largest num_cells the table holds
     float4* bbox_partials;
     DeviceMisc* misc;
 };
@@ -134,13 +136,13 @@ struct MainArgs {
 };
 
 // host launchers (orca_bin.cu, orca_main.cu)
-int sort_blocks(int n);
 int main_blocks(int n);
-cudaError_t launch_binning(int n, float cell_size, long long max_cells, int max_passes,
-                           const AgentState& cur, const BinBuffers& b, cudaStream_t st);
+// bounding box and grid, cell keys and counts, cell table (cnt and tile_sums must be zero
+// on entry; they are zero again once the step's reorder has run)
+cudaError_t launch_binning(int n, float cell_size, long long max_cells, const AgentState& cur,
+                           const BinBuffers& b, cudaStream_t st);
 cudaError_t launch_binning_batch(int n, int n_scenes, SceneDev* scenes, const int* slot_scene,
-                                 int max_passes, const AgentState& cur, const BinBuffers& b,
-                                 cudaStream_t st);
+                                 const AgentState& cur, const BinBuffers& b, cudaStream_t st);
 cudaError_t launch_slot_scene(int n, int n_scenes, const SceneDev* scenes, int* slot_scene,
                               cudaStream_t st);
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,

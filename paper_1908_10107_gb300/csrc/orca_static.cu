@@ -9,7 +9,7 @@
 // the process exits).  The caller passes only its inputs and outputs.
 //
 // The step itself is the library's ordinary one (same kernels, same arithmetic): bounding
-// box and grid, cell keys, radix sort, cell table, gather into cell order, the per-agent
+// box and grid, cell keys and counts, cell table, reorder into cell order, the per-agent
 // ORCA kernel, and a scatter back to the caller's agent order.
 #include <mutex>
 #include <string>
@@ -25,10 +25,11 @@ constexpr int kStaticMaxAgents = 65536;
 constexpr int kStaticMaxCells = 262144;
 constexpr int kStaticMaxDevices = 64;
 
-// Scratch layout (bytes), every piece 256-byte aligned.
+// Scratch layout (bytes), every piece 256-byte aligned.  The pieces from misc to the end
+// are cleared by every call (grid, counters, and the counting sort's cell and tile counts).
 struct StaticLayout {
-    size_t id, keys0, keys1, vals0, vals1, hist, tot, cells, part, misc, msg, sslot, svel, goal, radius,
-        vmax, pref, tau, sid, opos, ovel, blk, total;
+    size_t id, keys, ranks, cells, part, msg, sslot, svel, goal, radius, vmax, pref, tau, sid, opos,
+        ovel, misc, cnt, tsum, blk, total;
 };
 
 constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -36,18 +37,12 @@ constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr StaticLayout static_layout() {
     StaticLayout L{};
     size_t N = kStaticMaxAgents, o = 0;
-    int nsb = (kStaticMaxAgents + kSortTile - 1) / kSortTile;
     int nmb = (kStaticMaxAgents + 63) / 64;
     L.id = o; o += al256(N * 4);
-    L.keys0 = o; o += al256(N * 4);
-    L.keys1 = o; o += al256(N * 4);
-    L.vals0 = o; o += al256(N * 4);
-    L.vals1 = o; o += al256(N * 4);
-    L.hist = o; o += al256((size_t)kRadixBuckets * nsb * 4);
-    L.tot = o; o += al256((size_t)kRadixBuckets * 4);
+    L.keys = o; o += al256(N * 4);
+    L.ranks = o; o += al256(N * 4);
     L.cells = o; o += al256(((size_t)kStaticMaxCells + 1) * 4);
     L.part = o; o += al256(kBboxBlocks * 16);
-    L.misc = o; o += al256(sizeof(DeviceMisc));
     L.msg = o; o += al256(N * 16);
     L.sslot = o; o += al256(N * 4);
     L.svel = o; o += al256(N * 8);
@@ -59,6 +54,9 @@ constexpr StaticLayout static_layout() {
     L.sid = o; o += al256(N * 4);
     L.opos = o; o += al256(N * 8);
     L.ovel = o; o += al256(N * 8);
+    L.misc = o; o += al256(sizeof(DeviceMisc));
+    L.cnt = o; o += al256((size_t)kStaticMaxCells * 4);
+    L.tsum = o; o += al256(((size_t)kStaticMaxCells / kCellTile + 1) * 4);
     L.blk = o; o += al256((size_t)nmb * kBlockCounters * 8);
     L.total = o;
     return L;
@@ -133,26 +131,22 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
                       (float*)(base + L.pref), (float*)(base + L.tau), (uint32_t*)(base + L.sid),
                       nullptr};
     AgentState out{(float2*)(base + L.opos), (float2*)(base + L.ovel)};
-    BinBuffers bins;
-    bins.keys[0] = (uint32_t*)(base + L.keys0);
-    bins.keys[1] = (uint32_t*)(base + L.keys1);
-    bins.vals[0] = (uint32_t*)(base + L.vals0);
-    bins.vals[1] = (uint32_t*)(base + L.vals1);
-    bins.hist = (uint32_t*)(base + L.hist);
-    bins.digit_totals = (uint32_t*)(base + L.tot);
+    BinBuffers bins{};
+    bins.keys[0] = (uint32_t*)(base + L.keys);
+    bins.vals[0] = (uint32_t*)(base + L.ranks);
+    bins.cnt = (uint32_t*)(base + L.cnt);
+    bins.tile_sums = (uint32_t*)(base + L.tsum);
     bins.cell_start = (uint32_t*)(base + L.cells);
+    bins.table_cells = kStaticMaxCells;
     bins.bbox_partials = (float4*)(base + L.part);
     bins.misc = (DeviceMisc*)(base + L.misc);
 
-    int bits = 0;
-    while ((1LL << bits) < (long long)kStaticMaxCells) ++bits;
-    int max_passes = (bits + kRadixBits - 1) / kRadixBits;
     float cs = cell_size > 0.0f ? cell_size : neighbor_dist * 0.25f;
-    // the previous call leaves its grid, ticket and counters behind: start from zero
-    cudaError_t e = cudaMemsetAsync(bins.misc, 0, sizeof(DeviceMisc), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.blk, 0, kStatic.total - L.blk, st);
+    // start from zero: the grid, ticket and counters of the previous call, and the cell and
+    // tile counts (zero after every completed call, cleared anyway)
+    cudaError_t e = cudaMemsetAsync(base + L.misc, 0, kStatic.total - L.misc, st);
     if (e == cudaSuccess) e = launch_iota(n, src_p.id, st);
-    if (e == cudaSuccess) e = launch_binning(n, cs, kStaticMaxCells, max_passes, src, bins, st);
+    if (e == cudaSuccess) e = launch_binning(n, cs, kStaticMaxCells, src, bins, st);
     if (e == cudaSuccess) e = launch_reorder(n, bins, src, sorted, src_p, dst_p, st);
     if (e == cudaSuccess) {
         MainArgs a{};
