@@ -295,6 +295,33 @@ ORCA_API int orca_count_ops(orca_ctx* ctx, int32_t on);
 ORCA_API int orca_get_op_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
 
 /*
+ * FP64 validation rollout (validation only; the paper has no counterpart).  Runs T steps
+ * of the ORCA step in FP64 from (pos0, vel0) -- neighbours decided in FP32 on the
+ * FP32-rounded positions as the FP32 step decides them (k nearest by (fl32 d^2, index)
+ * strictly inside r_obs), half-planes (Fig. 1), preferred velocity and the LP of Section 3
+ * in double -- and, when dL_dpos is not NULL, the double instantiation of the library's
+ * adjoint back through it (the same kernels the FP32 rollouts use, with the same record of
+ * what fixed each selected velocity).  This separates adjoint errors from the FP32
+ * trajectory's drift: the FP64 trajectory follows an FP64 reference to rounding.
+ *
+ * All arrays are device memory in agent order, double: pos0, vel0, goal (2n), radius,
+ * max_speed, pref_speed, time_horizon (n); dL_dpos (T x n x 2, the loss gradient of
+ * positions p(1..T), may be NULL); traj_pos (T x n x 2) receives p(1..T); g_pref_speed,
+ * g_radius, g_time_horizon (n) and g_pos0, g_vel0 (2n) receive the gradients (each may be
+ * NULL).  n <= 65,536 (the neighbour search scans all agents).  Allocates its scratch
+ * with cudaMalloc and synchronises `stream` before returning.  Errors: ORCA_ERR_ARG,
+ * ORCA_ERR_NOMEM, ORCA_ERR_CUDA, with a message in orca_last_error(NULL).
+ */
+ORCA_API int orca_validate_rollout_fp64(int32_t n, int32_t max_neighbors, float neighbor_dist, double dt,
+                                        int32_t T, const double* pos0, const double* vel0,
+                                        const double* goal, const double* radius,
+                                        const double* max_speed, const double* pref_speed,
+                                        const double* time_horizon, const double* dL_dpos,
+                                        double* traj_pos, double* g_pref_speed, double* g_radius,
+                                        double* g_time_horizon, double* g_pos0, double* g_vel0,
+                                        void* stream);
+
+/*
  * FP32 FMA throughput microbenchmark (measurement; the paper has no counterpart): the peak
  * against which the ORCA kernel's arithmetic roofline is quoted.  Enqueues one kernel on
  * `stream` of `blocks` CTAs of 256 threads (blocks <= 0: 8 per SM), each thread running

@@ -99,6 +99,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_step_static": ([i32] + [vp] * 7 + [c.c_float, i32, c.c_float, c.c_float, vp, vp, vp],
                              c.c_int),
         "orca_fma_bench": ([i32, i32, vp, c.POINTER(c.c_int64), vp], c.c_int),
+        "orca_validate_rollout_fp64": ([i32, i32, c.c_float, c.c_double, i32] + [vp] * 14, c.c_int),
         "orca_num_agents": ([vp, c.POINTER(i32)], c.c_int),
         "orca_last_error": ([vp], c.c_char_p),
         "orca_status_string": ([c.c_int], c.c_char_p),
@@ -397,6 +398,44 @@ def orca_fma_bench(blocks: int, iters: int, out, stream=None) -> int:
     _check(load_library().orca_fma_bench(int(blocks), int(iters), p, ctypes.byref(flops),
                                          _stream(stream)))
     return int(flops.value)
+
+
+def orca_validate_rollout_fp64(pos0, vel0, goal, radius, max_speed, pref_speed, time_horizon,
+                               neighbor_dist, max_neighbors, dt, T, dL_dpos=None, stream=None):
+    """FP64 rollout of T steps and, with ``dL_dpos`` ([T, n, 2]), the FP64 adjoint (validation
+    only).  Takes CUDA float64 tensors in agent order; returns a dict with ``traj`` [T, n, 2]
+    and, with dL_dpos, the gradients ``pref``, ``radius``, ``tau`` [n], ``pos0``, ``vel0``
+    [n, 2] (CUDA float64 tensors)."""
+    import torch
+    arrays = [pos0, vel0, goal, radius, max_speed, pref_speed, time_horizon]
+    n = int(radius.numel())
+    dev = pos0.device
+    for a, m in zip(arrays, (2, 2, 2, 1, 1, 1, 1)):
+        if not isinstance(a, torch.Tensor) or not a.is_cuda or a.dtype != torch.float64 \
+                or not a.is_contiguous() or a.numel() != m * n or a.device != dev:
+            raise TypeError("orca_validate_rollout_fp64 takes contiguous CUDA float64 tensors "
+                            "of n or 2n elements on one device")
+    T = int(T)
+    traj = torch.empty((T, n, 2), dtype=torch.float64, device=dev)
+    out = {"traj": traj}
+    gp = []
+    if dL_dpos is not None:
+        if dL_dpos.dtype != torch.float64 or dL_dpos.numel() != T * n * 2 or dL_dpos.device != dev:
+            raise TypeError("dL_dpos: CUDA float64 [T, n, 2]")
+        dL_dpos = dL_dpos.contiguous()
+        out.update(pref=torch.empty(n, dtype=torch.float64, device=dev),
+                   radius=torch.empty(n, dtype=torch.float64, device=dev),
+                   tau=torch.empty(n, dtype=torch.float64, device=dev),
+                   pos0=torch.empty((n, 2), dtype=torch.float64, device=dev),
+                   vel0=torch.empty((n, 2), dtype=torch.float64, device=dev))
+        gp = [out[k] for k in ("pref", "radius", "tau", "pos0", "vel0")]
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    with torch.cuda.device(dev):
+        _check(load_library().orca_validate_rollout_fp64(
+            n, int(max_neighbors), float(neighbor_dist), float(dt), T, *[ptr(a) for a in arrays],
+            ptr(dL_dpos), ptr(traj), *(ptr(g) for g in gp) if gp else (None,) * 5,
+            _stream(stream)))
+    return out
 
 
 def orca_num_agents(ctx) -> int:

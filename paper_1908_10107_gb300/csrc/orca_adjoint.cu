@@ -6,53 +6,77 @@
 // constraints fix x (recorded on the forward pass as the "tape"), which branch built each
 // half-plane, which branch built the preferred velocity -- x is a smooth function of the
 // half-planes (n_l, c_l) and of the preferred velocity o, and those are smooth functions of
-// the state and parameters.  This kernel pushes the adjoints (dL/dp', dL/dv') of one agent
-// back through that chain:
+// the state and parameters.  The adjoint of one agent pushes (dL/dp', dL/dv') back
+// through that chain:
 //   x -> (n, c) of at most three half-planes (the line or bisector x lies on, the one that
 //        bounds it, and line i of a least-penetration solve) and o;
 //   (n, c) -> p, v, r of the agent and of the neighbour, tau of the agent;
 //   o -> p and s of the agent.
-// Contributions to neighbours are added with atomics.
-#include "orca_geom.cuh"
+//
+// Deterministic accumulation.  What an agent's half-planes contribute to its neighbours
+// is not added with atomics (whose order, and so whose rounding, varies between runs):
+//   adj_agent   one thread per agent a writes its own adjoints and, for every neighbour
+//               slot l, the contribution to that neighbour into contrib[a k + l]; it
+//               also counts every agent's in-degree (how many lists it appears in);
+//   csr_scan    the in-degrees become the offsets of a transposed neighbour list;
+//   csr_fill    every (a, l) is entered in its neighbour's list;
+//   adj_gather  one thread per agent b sorts its list by (a, l) and adds the entries'
+//               contributions in that order (and the loss gradient of its position).
+// Every sum is then taken in a fixed order and the gradients are bitwise reproducible.
+//
+// The kernels are templates on the scalar type: float for rollouts of the FP32 step, and
+// double for the validation rollout (orca_validate.cu), which runs the same adjoint code
+// along an FP64 trajectory so that the adjoint can be checked against FP64 finite
+// differences without FP32 trajectory drift in the way.
+#include "orca_adjoint.cuh"
 
 namespace orca {
 
-constexpr int kTapePref = 0, kTapePrefClip = 1, kTapeLine = 2, kTapeLp3Dir = 3, kTapeLp3Line = 4;
-constexpr int kBoundFree = 0, kBoundDisc = 1;
-
-__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ float dot2(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
-__device__ __forceinline__ void add2(float2* p, float2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
-}
+// ---- scalar-generic helpers --------------------------------------------------------
+template <class T>
+struct V2 {
+    T x, y;
+};
+template <class T>
+__device__ __forceinline__ V2<T> mk2(T x, T y) { return V2<T>{x, y}; }
+template <class T>
+__device__ __forceinline__ T dot2(V2<T> a, V2<T> b) { return a.x * b.x + a.y * b.y; }
+template <class T>
+__device__ __forceinline__ T det2(V2<T> a, V2<T> b) { return a.x * b.y - a.y * b.x; }
+__device__ __forceinline__ V2<float> v2of(float2 a) { return V2<float>{a.x, a.y}; }
+__device__ __forceinline__ V2<double> v2of(double2 a) { return V2<double>{a.x, a.y}; }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 
 // Adjoint of x = e*m + t*d(m), d(m) = (m.y, -m.x), given xbar: returns tbar and adds to
 // ebar, mbar.
-__device__ __forceinline__ float point_on_line_bar(float2 m, float e, float t, float2 xbar,
-                                                   float& ebar, float2& mbar) {
+template <class T>
+__device__ __forceinline__ T point_on_line_bar(V2<T> m, T e, T t, V2<T> xbar, T& ebar, V2<T>& mbar) {
     ebar += dot2(m, xbar);
     // dx/dm = e I + t Q with Q m = d(m); Q^T xbar = (-xbar.y, xbar.x)
     mbar.x += e * xbar.x - t * xbar.y;
     mbar.y += e * xbar.y + t * xbar.x;
-    return dot2(f2(m.y, -m.x), xbar);
+    return dot2(mk2<T>(m.y, -m.x), xbar);
 }
 
 // t from a bounding line j on line i: t = -rhs/den, rhs = e_j - e_i (m_i.m_j),
-// den = det(m_i, m_j).  Adds the adjoints of (m_i, e_i, m_j, e_j) for tbar.
-__device__ __forceinline__ float bound_t(float2 mi, float ei, float2 mj, float ej) {
-    float den = det2f(mi.x, mi.y, mj.x, mj.y);
-    float rhs = ej - ei * dot2(mi, mj);
+// den = det(m_i, m_j).
+template <class T>
+__device__ __forceinline__ T bound_t(V2<T> mi, T ei, V2<T> mj, T ej) {
+    T den = det2(mi, mj);
+    T rhs = ej - ei * dot2(mi, mj);
     return -rhs / den;
 }
 
-__device__ __forceinline__ void bound_bar(float2 mi, float ei, float2 mj, float ej, float tbar,
-                                          float2& mibar, float& eibar, float2& mjbar, float& ejbar) {
-    float den = det2f(mi.x, mi.y, mj.x, mj.y);
-    float rhs = ej - ei * dot2(mi, mj);
-    float t = -rhs / den;
-    float rbar = -tbar / den;
-    float dbar = -tbar * t / den;
+// Adds the adjoints of (m_i, e_i, m_j, e_j) for tbar.
+template <class T>
+__device__ __forceinline__ void bound_bar(V2<T> mi, T ei, V2<T> mj, T ej, T tbar, V2<T>& mibar, T& eibar,
+                                          V2<T>& mjbar, T& ejbar) {
+    T den = det2(mi, mj);
+    T rhs = ej - ei * dot2(mi, mj);
+    T t = -rhs / den;
+    T rbar = -tbar / den;
+    T dbar = -tbar * t / den;
     ejbar += rbar;
     eibar -= rbar * dot2(mi, mj);
     mibar.x -= rbar * ei * mj.x;
@@ -66,21 +90,23 @@ __device__ __forceinline__ void bound_bar(float2 mi, float ei, float2 mj, float 
 }
 
 // Bisector of lines i and f: m = (n_f - n_i)/|n_f - n_i|, e = (c_f - c_i)/|n_f - n_i|.
-__device__ __forceinline__ void bisector(float4 li, float4 lf, float2& m, float& e) {
-    float ux = lf.x - li.x, uy = lf.y - li.y;
-    float inv = rsqrtf(ux * ux + uy * uy);
-    m = f2(ux * inv, uy * inv);
-    e = (lf.z - li.z) * inv;
+template <class T>
+__device__ __forceinline__ void bisector(Line<T> li, Line<T> lf, V2<T>& m, T& e) {
+    T ux = lf.nx - li.nx, uy = lf.ny - li.ny;
+    T ul = sqrt_t(ux * ux + uy * uy);
+    m = mk2<T>(ux / ul, uy / ul);
+    e = (lf.c - li.c) / ul;
 }
 
-__device__ __forceinline__ void bisector_bar(float4 li, float4 lf, float2 mbar, float ebar,
-                                             float2& nibar, float& cibar, float2& nfbar, float& cfbar) {
-    float ux = lf.x - li.x, uy = lf.y - li.y;
-    float ul = sqrtf(ux * ux + uy * uy);
-    float2 m = f2(ux / ul, uy / ul);
-    float e = (lf.z - li.z) / ul;
-    float mm = dot2(m, mbar);
-    float2 ubar = f2((mbar.x - m.x * mm - e * ebar * m.x) / ul, (mbar.y - m.y * mm - e * ebar * m.y) / ul);
+template <class T>
+__device__ __forceinline__ void bisector_bar(Line<T> li, Line<T> lf, V2<T> mbar, T ebar, V2<T>& nibar,
+                                             T& cibar, V2<T>& nfbar, T& cfbar) {
+    T ux = lf.nx - li.nx, uy = lf.ny - li.ny;
+    T ul = sqrt_t(ux * ux + uy * uy);
+    V2<T> m = mk2<T>(ux / ul, uy / ul);
+    T e = (lf.c - li.c) / ul;
+    T mm = dot2(m, mbar);
+    V2<T> ubar = mk2<T>((mbar.x - m.x * mm - e * ebar * m.x) / ul, (mbar.y - m.y * mm - e * ebar * m.y) / ul);
     nfbar.x += ubar.x;
     nfbar.y += ubar.y;
     nibar.x -= ubar.x;
@@ -90,62 +116,63 @@ __device__ __forceinline__ void bisector_bar(float4 li, float4 lf, float2 mbar, 
 }
 
 // Adjoint of the half-plane of agent a (p, v, r, 1/tau) induced by neighbour b (pb, vb, rb)
-// for (nbar, cbar), branch as in the forward step.  Outputs the adjoints of the agent's
-// and the neighbour's position, velocity, radius, and of 1/tau.
-__device__ __forceinline__ void line_bar(float2 pa, float2 va, float ra, float itau, float dt,
-                                         float half_idt, float2 pb, float2 vb, float rb, int branch,
-                                         float4 L, float2 nbar, float cbar, float2& pabar,
-                                         float2& vabar, float& rbar_ab, float& itaubar,
-                                         float2& pbbar, float2& vbbar) {
-    float2 p = f2(pb.x - pa.x, pb.y - pa.y);
-    float2 v = f2(va.x - vb.x, va.y - vb.y);
-    float R = ra + rb;
-    float2 n = f2(L.x, L.y);
-    float2 pbar = f2(0.f, 0.f), vbar = f2(0.f, 0.f);
-    float Rbar = 0.f;
+// for (nbar, cbar), branch as in the forward step.  Adds the adjoints of the agent's and
+// the neighbour's position, velocity, radius sum, and of 1/tau.
+template <class T>
+__device__ __forceinline__ void line_bar(V2<T> pa, V2<T> va, T ra, T itau, T dt, T half_idt, V2<T> pb,
+                                         V2<T> vb, T rb, int branch, Line<T> L, V2<T> nbar, T cbar,
+                                         V2<T>& pabar, V2<T>& vabar, T& rbar_ab, T& itaubar,
+                                         V2<T>& pbbar, V2<T>& vbbar) {
+    V2<T> p = mk2<T>(pb.x - pa.x, pb.y - pa.y);
+    V2<T> v = mk2<T>(va.x - vb.x, va.y - vb.y);
+    T R = ra + rb;
+    V2<T> n = mk2<T>(L.nx, L.ny);
+    V2<T> pbar = mk2<T>(0, 0), vbar = mk2<T>(0, 0);
+    T Rbar = 0;
     if (branch == kLineCutoff) {
-        float2 w = f2(v.x - p.x * itau, v.y - p.y * itau);
-        float wl = sqrtf(dot2(w, w));
+        V2<T> w = mk2<T>(v.x - p.x * itau, v.y - p.y * itau);
+        T wl = sqrt_t(dot2(w, w));
         vabar.x += cbar * n.x;
         vabar.y += cbar * n.y;
-        float2 nt = f2(nbar.x + cbar * va.x, nbar.y + cbar * va.y);
-        float nn = dot2(n, nt);
-        float2 wbar = f2((nt.x - n.x * nn) / wl - 0.5f * cbar * n.x, (nt.y - n.y * nn) / wl - 0.5f * cbar * n.y);
-        Rbar += 0.5f * cbar * itau;
-        itaubar += 0.5f * cbar * R - dot2(p, wbar);
+        V2<T> nt = mk2<T>(nbar.x + cbar * va.x, nbar.y + cbar * va.y);
+        T nn = dot2(n, nt);
+        V2<T> wbar = mk2<T>((nt.x - n.x * nn) / wl - T(0.5) * cbar * n.x,
+                            (nt.y - n.y * nn) / wl - T(0.5) * cbar * n.y);
+        Rbar += T(0.5) * cbar * itau;
+        itaubar += T(0.5) * cbar * R - dot2(p, wbar);
         vbar.x += wbar.x;
         vbar.y += wbar.y;
         pbar.x -= itau * wbar.x;
         pbar.y -= itau * wbar.y;
     } else if (branch == kLineLeftLeg || branch == kLineRightLeg) {
-        float s = branch == kLineLeftLeg ? 1.0f : -1.0f;
-        float p2 = dot2(p, p);
-        float l = sqrtf(p2 - R * R);
-        float2 vs = f2(va.x + vb.x, va.y + vb.y);
-        vabar.x += 0.5f * cbar * n.x;
-        vabar.y += 0.5f * cbar * n.y;
-        vbbar.x += 0.5f * cbar * n.x;
-        vbbar.y += 0.5f * cbar * n.y;
-        float2 nt = f2(nbar.x + 0.5f * cbar * vs.x, nbar.y + 0.5f * cbar * vs.y);
-        float2 Jp = f2(-p.y, p.x);  // J = rotation by +90 degrees
-        float ntJp = dot2(nt, Jp);
+        T s = branch == kLineLeftLeg ? T(1) : T(-1);
+        T p2 = dot2(p, p);
+        T l = sqrt_t(p2 - R * R);
+        V2<T> vs = mk2<T>(va.x + vb.x, va.y + vb.y);
+        vabar.x += T(0.5) * cbar * n.x;
+        vabar.y += T(0.5) * cbar * n.y;
+        vbbar.x += T(0.5) * cbar * n.x;
+        vbbar.y += T(0.5) * cbar * n.y;
+        V2<T> nt = mk2<T>(nbar.x + T(0.5) * cbar * vs.x, nbar.y + T(0.5) * cbar * vs.y);
+        V2<T> Jp = mk2<T>(-p.y, p.x);  // J = rotation by +90 degrees
+        T ntJp = dot2(nt, Jp);
         // n = (-R p + s l J p) / p2;  M^T nt = -R nt + s l J^T nt, J^T nt = (nt.y, -nt.x)
-        float2 MTn = f2(-R * nt.x + s * l * nt.y, -R * nt.y - s * l * nt.x);
-        float nnt = dot2(n, nt);
-        pbar.x += MTn.x / p2 + s * ntJp * p.x / (l * p2) - 2.0f * nnt * p.x / p2;
-        pbar.y += MTn.y / p2 + s * ntJp * p.y / (l * p2) - 2.0f * nnt * p.y / p2;
+        V2<T> MTn = mk2<T>(-R * nt.x + s * l * nt.y, -R * nt.y - s * l * nt.x);
+        T nnt = dot2(n, nt);
+        pbar.x += MTn.x / p2 + s * ntJp * p.x / (l * p2) - T(2) * nnt * p.x / p2;
+        pbar.y += MTn.y / p2 + s * ntJp * p.y / (l * p2) - T(2) * nnt * p.y / p2;
         Rbar += (-dot2(nt, p) - s * ntJp * R / l) / p2;
     } else {  // overlap: q = p - v dt, n = -q/|q|, c = n.v_a + (R - |q|)/(2 dt)
         vabar.x += cbar * n.x;
         vabar.y += cbar * n.y;
         Rbar += cbar * half_idt;
         if (branch == kLineOverlap) {
-            float2 q = f2(p.x - v.x * dt, p.y - v.y * dt);
-            float ql = sqrtf(dot2(q, q));
-            float2 nt = f2(nbar.x + cbar * va.x, nbar.y + cbar * va.y);
-            float nn = dot2(n, nt);
-            float2 qbar = f2(-(nt.x - n.x * nn) / ql + cbar * half_idt * n.x,
-                             -(nt.y - n.y * nn) / ql + cbar * half_idt * n.y);
+            V2<T> q = mk2<T>(p.x - v.x * dt, p.y - v.y * dt);
+            T ql = sqrt_t(dot2(q, q));
+            V2<T> nt = mk2<T>(nbar.x + cbar * va.x, nbar.y + cbar * va.y);
+            T nn = dot2(n, nt);
+            V2<T> qbar = mk2<T>(-(nt.x - n.x * nn) / ql + cbar * half_idt * n.x,
+                                -(nt.y - n.y * nn) / ql + cbar * half_idt * n.y);
             pbar.x += qbar.x;
             pbar.y += qbar.y;
             vbar.x -= dt * qbar.x;
@@ -164,77 +191,123 @@ __device__ __forceinline__ void line_bar(float2 pa, float2 va, float ra, float i
     rbar_ab += Rbar;
 }
 
-template <int KMAX>
-__global__ void __launch_bounds__(128) orca_adjoint_kernel(AdjointArgs A) {
+// The half-plane and preferred velocity exactly as the forward step built them: the FP32
+// step's own functions for float, their FP64 counterparts for double.
+__device__ __forceinline__ Line<float> forward_line(const AdjArgs<float>& A, int a, int b, float2 pa,
+                                                    float2 va, float ra, float itau, float dt,
+                                                    float half_idt, int* br) {
+    const float2 pb = A.pos[b];
+    const float4 L = orca_line_dev(pa, va, ra, itau, dt, half_idt, (uint32_t)a,
+                                   make_float4(pb.x, pb.y, A.radius[b], __uint_as_float((uint32_t)b)),
+                                   A.vel[b], br);
+    return Line<float>{L.x, L.y, L.z};
+}
+__device__ __forceinline__ Line<double> forward_line(const AdjArgs<double>& A, int a, int b, double2 pa,
+                                                     double2 va, double ra, double itau, double dt,
+                                                     double half_idt, int* br) {
+    return orca_line_fp64(pa, va, ra, itau, dt, half_idt, (uint32_t)a, A.pos[b], A.radius[b],
+                          (uint32_t)b, A.vel[b], br);
+}
+__device__ __forceinline__ float2 forward_pref(float2 p, float2 goal, float s, float dt, float idt, int* far) {
+    return pref_velocity_dev(p, goal, s, dt, idt, far);
+}
+__device__ __forceinline__ double2 forward_pref(double2 p, double2 goal, double s, double dt, double idt,
+                                                int* far) {
+    return pref_velocity_fp64(p, goal, s, dt, idt, far);
+}
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// ---- per-agent adjoint ---------------------------------------------------------------
+// Own adjoints of agent a: pbar[a] = dL/dp'(a) + what its half-planes and preferred
+// velocity give its position, vbar[a] likewise for its velocity; its parameter gradients
+// accumulate (one thread per agent, so without atomics).  What its half-planes give
+// neighbour b in slot l goes to contrib[(a k + l) 5 + 0..4] (pbar x, y, vbar x, y, rbar),
+// zeros when nothing flows; every slot's neighbour gets its in-degree counted.
+template <class T, int KMAX>
+__global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
+    using T2 = typename AdjArgs<T>::T2;
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A.n) return;
-    const float2 pbn = A.pbar_next[a], vbn = A.vbar_next[a];
-    // p' = p + x dt, v' = x
-    add2(&A.pbar[a], pbn);
-    float2 xbar = f2(vbn.x + A.dt * pbn.x, vbn.y + A.dt * pbn.y);
-    if (xbar.x == 0.0f && xbar.y == 0.0f) return;
-
-    const float dt = A.dt;
-    const float2 pa = A.pos[a], va = A.vel[a];
-    const float ra = A.radius[a], V = A.max_speed[a];
-    const float itau = __fdividef(1.0f, A.tau[a]);
-    const float idt = __fdividef(1.0f, dt);
-    const float half_idt = 0.5f * idt;
-    // half-planes and preferred velocity exactly as the forward step built them
-    float4 L[KMAX];
-    int br[KMAX], nb[KMAX];
+    const int K = A.kstride;
+    int nb[KMAX];
     int cnt = 0;
-    for (int l = 0; l < KMAX && l < A.kstride; ++l) {
-        int j = A.nbr[(size_t)a * A.kstride + l];
+    for (int l = 0; l < KMAX && l < K; ++l) {
+        const int j = A.nbr[(size_t)a * K + l];
         if (j < 0) break;
-        nb[cnt] = j;
-        L[cnt] = orca_line_dev(pa, va, ra, itau, dt, half_idt, (uint32_t)a,
-                               make_float4(A.pos[j].x, A.pos[j].y, A.radius[j], __uint_as_float((uint32_t)j)),
-                               A.vel[j], &br[cnt]);
-        ++cnt;
+        nb[cnt++] = j;
+        atomicAdd(A.incnt + j, 1u);  // integer: the count is exact in any order
     }
+    T* my_contrib = A.contrib + (size_t)a * K * 5;
+    const T2 pbn = A.pbar_next[a], vbn = A.vbar_next[a];
+    // p' = p + x dt, v' = x
+    const V2<T> xbar = mk2<T>(vbn.x + A.dt * pbn.x, vbn.y + A.dt * pbn.y);
+    if (xbar.x == T(0) && xbar.y == T(0)) {
+        A.pbar[a] = pbn;
+        T2 z;
+        z.x = T(0);
+        z.y = T(0);
+        A.vbar[a] = z;
+        for (int q = 0; q < cnt * 5; ++q) my_contrib[q] = T(0);
+        return;
+    }
+
+    const T dt = A.dt;
+    const T2 pa2 = A.pos[a], va2 = A.vel[a];
+    const V2<T> pa = v2of(pa2), va = v2of(va2);
+    const T ra = A.radius[a], V = A.max_speed[a];
+    const T itau = recip(A.tau[a]);
+    const T idt = recip(dt);
+    const T half_idt = T(0.5) * idt;
+    // half-planes and preferred velocity exactly as the forward step built them
+    Line<T> L[KMAX];
+    int br[KMAX];
+    for (int l = 0; l < cnt; ++l) L[l] = forward_line(A, a, nb[l], pa2, va2, ra, itau, dt, half_idt, &br[l]);
     int far = 0;
-    const float2 o = pref_velocity_dev(pa, A.goal[a], A.pref_speed[a], dt, idt, &far);
+    const T2 o2 = forward_pref(pa2, A.goal[a], A.pref_speed[a], dt, idt, &far);
+    const V2<T> o = v2of(o2);
 
     const uint32_t tp = A.tape[a];
     const int mode = tp & 7, i = (tp >> 3) & 63, f = (tp >> 9) & 63, bound = (tp >> 15) & 3,
               j = (tp >> 17) & 63, side = (tp >> 23) & 1;
-    float2 nbar[KMAX];
-    float cbar[KMAX];
+    V2<T> nbar[KMAX];
+    T cbar[KMAX];
     for (int l = 0; l < cnt; ++l) {
-        nbar[l] = f2(0.f, 0.f);
-        cbar[l] = 0.f;
+        nbar[l] = mk2<T>(0, 0);
+        cbar[l] = T(0);
     }
-    float2 obar = f2(0.f, 0.f);
+    V2<T> obar = mk2<T>(0, 0);
 
     if (mode == kTapePref) {
         obar = xbar;
     } else if (mode == kTapePrefClip) {
-        float ol = sqrtf(dot2(o, o));
-        float2 oh = f2(o.x / ol, o.y / ol);
-        float k = dot2(oh, xbar);
-        obar = f2(V / ol * (xbar.x - oh.x * k), V / ol * (xbar.y - oh.y * k));
+        T ol = sqrt_t(dot2(o, o));
+        V2<T> oh = mk2<T>(o.x / ol, o.y / ol);
+        T k = dot2(oh, xbar);
+        obar = mk2<T>(V / ol * (xbar.x - oh.x * k), V / ol * (xbar.y - oh.y * k));
     } else if (mode == kTapeLine) {
-        const float4 li = L[i];
-        const float2 mi = f2(li.x, li.y);
-        const float2 di = f2(li.y, -li.x);
-        float t;
+        const Line<T> li = L[i];
+        const V2<T> mi = mk2<T>(li.nx, li.ny);
+        const V2<T> di = mk2<T>(li.ny, -li.nx);
+        T t;
         if (bound == kBoundFree) t = dot2(di, o);
-        else if (bound == kBoundDisc) t = (side ? 1.f : -1.f) * sqrtf(fmaxf(V * V - li.z * li.z, 0.f));
-        else t = bound_t(mi, li.z, f2(L[j].x, L[j].y), L[j].z);
-        float2 mibar = f2(0.f, 0.f);
-        float eibar = 0.f;
-        float tbar = point_on_line_bar(mi, li.z, t, xbar, eibar, mibar);
+        else if (bound == kBoundDisc) {
+            T D = V * V - li.c * li.c;
+            t = (side ? T(1) : T(-1)) * sqrt_t(D > T(0) ? D : T(0));
+        } else t = bound_t(mi, li.c, mk2<T>(L[j].nx, L[j].ny), L[j].c);
+        V2<T> mibar = mk2<T>(0, 0);
+        T eibar = 0;
+        T tbar = point_on_line_bar(mi, li.c, t, xbar, eibar, mibar);
         if (bound == kBoundFree) {  // t = d(n_i).o
             mibar.x += -tbar * o.y;
             mibar.y += tbar * o.x;
-            obar = f2(tbar * di.x, tbar * di.y);
+            obar = mk2<T>(tbar * di.x, tbar * di.y);
         } else if (bound == kBoundDisc) {
-            if (t != 0.f) eibar += -tbar * li.z / t;
+            if (t != T(0)) eibar += -tbar * li.c / t;
         } else {
-            float2 mjbar = f2(0.f, 0.f);
-            float ejbar = 0.f;
-            bound_bar(mi, li.z, f2(L[j].x, L[j].y), L[j].z, tbar, mibar, eibar, mjbar, ejbar);
+            V2<T> mjbar = mk2<T>(0, 0);
+            T ejbar = 0;
+            bound_bar(mi, li.c, mk2<T>(L[j].nx, L[j].ny), L[j].c, tbar, mibar, eibar, mjbar, ejbar);
             nbar[j].x += mjbar.x;
             nbar[j].y += mjbar.y;
             cbar[j] += ejbar;
@@ -246,27 +319,28 @@ __global__ void __launch_bounds__(128) orca_adjoint_kernel(AdjointArgs A) {
         nbar[i].x += V * xbar.x;
         nbar[i].y += V * xbar.y;
     } else {  // kTapeLp3Line: LP1 on the bisector of lines i and f
-        const float4 li = L[i];
-        float2 m;
-        float e;
+        const Line<T> li = L[i];
+        V2<T> m;
+        T e;
         bisector(li, L[f], m, e);
-        float t;
-        float2 mj;
-        float ej = 0.f;
+        T t;
+        V2<T> mj = mk2<T>(0, 0);
+        T ej = 0;
         if (bound == kBoundDisc) {
-            t = (side ? 1.f : -1.f) * sqrtf(fmaxf(V * V - e * e, 0.f));
+            T D = V * V - e * e;
+            t = (side ? T(1) : T(-1)) * sqrt_t(D > T(0) ? D : T(0));
         } else {
             bisector(li, L[j], mj, ej);
             t = bound_t(m, e, mj, ej);
         }
-        float2 mbar = f2(0.f, 0.f);
-        float ebar = 0.f;
-        float tbar = point_on_line_bar(m, e, t, xbar, ebar, mbar);
+        V2<T> mbar = mk2<T>(0, 0);
+        T ebar = 0;
+        T tbar = point_on_line_bar(m, e, t, xbar, ebar, mbar);
         if (bound == kBoundDisc) {
-            if (t != 0.f) ebar += -tbar * e / t;
+            if (t != T(0)) ebar += -tbar * e / t;
         } else {
-            float2 mjbar = f2(0.f, 0.f);
-            float ejbar = 0.f;
+            V2<T> mjbar = mk2<T>(0, 0);
+            T ejbar = 0;
             bound_bar(m, e, mj, ej, tbar, mbar, ebar, mjbar, ejbar);
             bisector_bar(li, L[j], mjbar, ejbar, nbar[i], cbar[i], nbar[j], cbar[j]);
         }
@@ -274,29 +348,35 @@ __global__ void __launch_bounds__(128) orca_adjoint_kernel(AdjointArgs A) {
     }
 
     // half-planes -> state and parameters of the agent and its neighbours
-    float2 pabar = f2(0.f, 0.f), vabar = f2(0.f, 0.f);
-    float rabar = 0.f, itaubar = 0.f;
+    V2<T> pabar = v2of(pbn), vabar = mk2<T>(0, 0);
+    T rabar = 0, itaubar = 0;
     for (int l = 0; l < cnt; ++l) {
-        if (nbar[l].x == 0.f && nbar[l].y == 0.f && cbar[l] == 0.f) continue;
+        T* c = my_contrib + 5 * l;
+        if (nbar[l].x == T(0) && nbar[l].y == T(0) && cbar[l] == T(0)) {
+            c[0] = c[1] = c[2] = c[3] = c[4] = T(0);
+            continue;
+        }
         const int b = nb[l];
-        float2 pbbar = f2(0.f, 0.f), vbbar = f2(0.f, 0.f);
-        float Rbar = 0.f;
-        line_bar(pa, va, ra, itau, dt, half_idt, A.pos[b], A.vel[b], A.radius[b], br[l], L[l], nbar[l],
-                 cbar[l], pabar, vabar, Rbar, itaubar, pbbar, vbbar);
+        V2<T> pbbar = mk2<T>(0, 0), vbbar = mk2<T>(0, 0);
+        T Rbar = 0;
+        line_bar(pa, va, ra, itau, dt, half_idt, v2of(A.pos[b]), v2of(A.vel[b]), A.radius[b], br[l], L[l],
+                 nbar[l], cbar[l], pabar, vabar, Rbar, itaubar, pbbar, vbbar);
         rabar += Rbar;
-        add2(&A.pbar[b], pbbar);
-        add2(&A.vbar[b], vbbar);
-        atomicAdd(&A.g_radius[b], Rbar);
+        c[0] = pbbar.x;
+        c[1] = pbbar.y;
+        c[2] = vbbar.x;
+        c[3] = vbbar.y;
+        c[4] = Rbar;
     }
     // preferred velocity -> position and preferred speed of the agent
-    if (obar.x != 0.f || obar.y != 0.f) {
-        float2 g = f2(A.goal[a].x - pa.x, A.goal[a].y - pa.y);
+    if (obar.x != T(0) || obar.y != T(0)) {
+        V2<T> g = mk2<T>(A.goal[a].x - pa.x, A.goal[a].y - pa.y);
         if (far) {
-            float gl = sqrtf(dot2(g, g));
-            float2 gh = f2(g.x / gl, g.y / gl);
-            float k = dot2(gh, obar);
-            float s = A.pref_speed[a];
-            atomicAdd(&A.g_pref[a], k);
+            T gl = sqrt_t(dot2(g, g));
+            V2<T> gh = mk2<T>(g.x / gl, g.y / gl);
+            T k = dot2(gh, obar);
+            T s = A.pref_speed[a];
+            A.g_pref[a] += k;
             pabar.x -= s / gl * (obar.x - gh.x * k);
             pabar.y -= s / gl * (obar.y - gh.y * k);
         } else {
@@ -304,22 +384,132 @@ __global__ void __launch_bounds__(128) orca_adjoint_kernel(AdjointArgs A) {
             pabar.y -= obar.y * idt;
         }
     }
-    add2(&A.pbar[a], pabar);
-    add2(&A.vbar[a], vabar);
-    atomicAdd(&A.g_radius[a], rabar);
+    T2 pw, vw;
+    pw.x = pabar.x;
+    pw.y = pabar.y;
+    vw.x = vabar.x;
+    vw.y = vabar.y;
+    A.pbar[a] = pw;
+    A.vbar[a] = vw;
+    A.g_radius[a] += rabar;
     // d(1/tau)/dtau = -1/tau^2
-    atomicAdd(&A.g_tau[a], -itaubar * itau * itau);
+    A.g_tau[a] += -itaubar * itau * itau;
 }
 
-cudaError_t launch_adjoint(const AdjointArgs& A, int kmax, cudaStream_t st) {
-    int nb = (A.n + 127) / 128;
+// ---- transposed neighbour lists ------------------------------------------------------
+// Exclusive scan of the in-degrees into instart[0..n] (one CTA; the counts are cleared
+// for csr_fill, which counts them again as it places the entries).
+constexpr int kCsrThreads = 1024;
+__global__ void __launch_bounds__(kCsrThreads) csr_scan_kernel(int n, uint32_t* __restrict__ incnt,
+                                                               uint32_t* __restrict__ instart) {
+    __shared__ uint32_t s_warp[kCsrThreads / 32];
+    const int per = (n + kCsrThreads - 1) / kCsrThreads;
+    const int b0 = threadIdx.x * per;
+    const int b1 = b0 + per < n ? b0 + per : n;
+    uint32_t sum = 0;
+    for (int b = b0; b < b1; ++b) sum += incnt[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    uint32_t base = 0, total = 0;
+    for (int w = 0; w < kCsrThreads / 32; ++w) {
+        if (w < warp) base += s_warp[w];
+        total += s_warp[w];
+    }
+    uint32_t run = base + inc - sum;
+    for (int b = b0; b < b1; ++b) {
+        const uint32_t c = incnt[b];
+        instart[b] = run;
+        incnt[b] = 0u;
+        run += c;
+    }
+    if (threadIdx.x == 0) instart[n] = total;
+}
+
+// Every (agent a, slot l) into the list of its neighbour b, in arrival order (adj_gather
+// sorts each list).
+__global__ void __launch_bounds__(256) csr_fill_kernel(int n, int K, const int32_t* __restrict__ nbr,
+                                                       uint32_t* __restrict__ incnt,
+                                                       const uint32_t* __restrict__ instart,
+                                                       uint32_t* __restrict__ inlist) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    for (int l = 0; l < K; ++l) {
+        const int b = nbr[(size_t)a * K + l];
+        if (b < 0) break;
+        inlist[instart[b] + atomicAdd(incnt + b, 1u)] = (uint32_t)a * (uint32_t)K + (uint32_t)l;
+    }
+}
+
+// Agent b: its list sorted by (a, l) (insertion sort in place: lists are short -- the
+// in-degree of a k-nearest-neighbour graph in the plane is at most a small multiple of
+// k), then the contributions summed in that order into its adjoints and radius gradient,
+// plus the loss gradient of its position at this step (dl_dp, may be null).  Clears its
+// in-degree for the next step.
+template <class T>
+__global__ void __launch_bounds__(256) adj_gather_kernel(AdjArgs<T> A) {
+    using T2 = typename AdjArgs<T>::T2;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= A.n) return;
+    const uint32_t s0 = A.instart[b], s1 = A.instart[b + 1];
+    uint32_t* lst = A.inlist;
+    for (uint32_t q = s0 + 1; q < s1; ++q) {
+        const uint32_t key = lst[q];
+        uint32_t r = q;
+        while (r > s0 && lst[r - 1] > key) {
+            lst[r] = lst[r - 1];
+            --r;
+        }
+        lst[r] = key;
+    }
+    T px = 0, py = 0, vx = 0, vy = 0, rr = 0;
+    for (uint32_t q = s0; q < s1; ++q) {
+        const T* c = A.contrib + (size_t)lst[q] * 5;
+        px += c[0];
+        py += c[1];
+        vx += c[2];
+        vy += c[3];
+        rr += c[4];
+    }
+    T2 p = A.pbar[b], v = A.vbar[b];
+    p.x += px;
+    p.y += py;
+    if (A.dl_dp) {
+        p.x += A.dl_dp[b].x;
+        p.y += A.dl_dp[b].y;
+    }
+    v.x += vx;
+    v.y += vy;
+    A.pbar[b] = p;
+    A.vbar[b] = v;
+    A.g_radius[b] += rr;
+    A.incnt[b] = 0u;
+}
+
+template <class T>
+cudaError_t launch_adjoint_step(const AdjArgs<T>& A, int kmax, cudaStream_t st) {
     if (A.n <= 0) return cudaSuccess;
-    if (kmax <= 10) orca_adjoint_kernel<10><<<nb, 128, 0, st>>>(A);
-    else if (kmax <= 16) orca_adjoint_kernel<16><<<nb, 128, 0, st>>>(A);
-    else if (kmax <= 20) orca_adjoint_kernel<20><<<nb, 128, 0, st>>>(A);
-    else orca_adjoint_kernel<32><<<nb, 128, 0, st>>>(A);
+    const int nb = (A.n + 127) / 128;
+    if (kmax <= 10) adj_agent_kernel<T, 10><<<nb, 128, 0, st>>>(A);
+    else if (kmax <= 16) adj_agent_kernel<T, 16><<<nb, 128, 0, st>>>(A);
+    else if (kmax <= 20) adj_agent_kernel<T, 20><<<nb, 128, 0, st>>>(A);
+    else adj_agent_kernel<T, 32><<<nb, 128, 0, st>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    csr_scan_kernel<<<1, kCsrThreads, 0, st>>>(A.n, A.incnt, A.instart);
+    csr_fill_kernel<<<(A.n + 255) / 256, 256, 0, st>>>(A.n, A.kstride, A.nbr, A.incnt, A.instart, A.inlist);
+    adj_gather_kernel<T><<<(A.n + 255) / 256, 256, 0, st>>>(A);
     return cudaGetLastError();
 }
+
+template cudaError_t launch_adjoint_step<float>(const AdjArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_adjoint_step<double>(const AdjArgs<double>&, int, cudaStream_t);
 
 // rollout helpers ------------------------------------------------------------------
 // Parameters back to agent order.
@@ -336,23 +526,10 @@ __global__ void __launch_bounds__(256) unpermute_params_kernel(int n, AgentParam
     tau[i] = src.tau[t];
 }
 
-__global__ void __launch_bounds__(256) axpy2_kernel(int n, float2* y, const float2* x) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    float2 a = y[t], b = x[t];
-    y[t] = make_float2(a.x + b.x, a.y + b.y);
-}
-
 cudaError_t launch_unpermute_params(int n, const AgentParams& src, float2* goal, float* radius,
                                     float* vmax, float* pref, float* tau, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     unpermute_params_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, src, goal, radius, vmax, pref, tau);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_axpy2(int n, float2* y, const float2* x, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    axpy2_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, y, x);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <string>
 
 #include "../../include/orca_gb300.h"
+#include "orca_adjoint.cuh"
 #include "orca_common.cuh"
 
 namespace orca {
@@ -890,10 +891,12 @@ ORCA_API int orca_get_op_counters(orca_ctx* ctx, int64_t* counters4, void* strea
 }
 
 // Rollout workspace: checkpoints, parameters in agent order, one segment's recomputed
-// states / neighbour lists / LP records, and two pairs of adjoint buffers.
+// states / neighbour lists / LP records, two pairs of adjoint buffers, and the scratch of
+// the deterministic neighbour accumulation (per-slot contributions, transposed lists).
 struct RolloutPlan {
     int T, C, nseg;
-    size_t ckpt, goal, radius, vmax, pref, tau, seg_state, seg_nbr, seg_tape, adj, gscratch, total;
+    size_t ckpt, goal, radius, vmax, pref, tau, seg_state, seg_nbr, seg_tape, adj, gscratch, contrib,
+        incnt, instart, inlist, total;
 };
 
 static RolloutPlan rollout_plan(const orca_ctx* c, int T, int C) {
@@ -914,6 +917,10 @@ static RolloutPlan rollout_plan(const orca_ctx* c, int T, int C) {
     r.seg_tape = L.add((size_t)C * N * 4);
     r.adj = L.add(4 * N * 8);
     r.gscratch = L.add(3 * N * 4);
+    r.contrib = L.add(N * K * 5 * 4);
+    r.incnt = L.add(N * 4);
+    r.instart = L.add((N + 1) * 4);
+    r.inlist = L.add(N * K * 4);
     r.total = L.total;
     return r;
 }
@@ -994,6 +1001,7 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
     CK(cudaMemsetAsync(gt, 0, N * 4, st), "zero");
     CK(cudaMemcpyAsync(pnext, dLdp + (size_t)(T - 1) * N, N * 8, cudaMemcpyDeviceToDevice, st), "seed");
     CK(cudaMemsetAsync(vnext, 0, N * 8, st), "zero");
+    CK(cudaMemsetAsync(w + r.incnt, 0, N * 4, st), "zero");
     for (int seg = r.nseg - 1; seg >= 0; --seg) {
         int t0 = seg * C, t1 = t0 + C < T ? t0 + C : T;
         int rr = orca_set_agents(ctx, n, (const float*)ck(seg), (const float*)(ck(seg) + N),
@@ -1011,9 +1019,7 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
         }
         for (int t = t1 - 1; t >= t0; --t) {
             const float2* sp = sstate(t - t0);
-            CK(cudaMemsetAsync(pcur, 0, N * 8, st), "zero");
-            CK(cudaMemsetAsync(vcur, 0, N * 8, st), "zero");
-            AdjointArgs A;
+            AdjArgs<float> A;
             A.n = n;
             A.kstride = (int)K;
             A.dt = ctx->p.dt;
@@ -1028,13 +1034,18 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
             A.tape = (const uint32_t*)(w + r.seg_tape) + (size_t)(t - t0) * N;
             A.pbar_next = pnext;
             A.vbar_next = vnext;
+            // p(t) for t >= 1 is a trajectory point of the loss: its own gradient joins
+            A.dl_dp = t >= 1 ? dLdp + (size_t)(t - 1) * N : nullptr;
             A.pbar = pcur;
             A.vbar = vcur;
             A.g_pref = gp;
             A.g_radius = gr;
             A.g_tau = gt;
-            CK(launch_adjoint(A, (int)K, st), "adjoint kernel");
-            if (t >= 1) CK(launch_axpy2(n, pcur, dLdp + (size_t)(t - 1) * N, st), "loss gradient");
+            A.contrib = (float*)(w + r.contrib);
+            A.incnt = (uint32_t*)(w + r.incnt);
+            A.instart = (uint32_t*)(w + r.instart);
+            A.inlist = (uint32_t*)(w + r.inlist);
+            CK(launch_adjoint_step(A, (int)K, st), "adjoint kernels");
             float2* tmp = pnext;
             pnext = pcur;
             pcur = tmp;

@@ -182,31 +182,8 @@ cudaError_t launch_remove_arrived(int n, const AgentState& cur, const AgentParam
                                   uint32_t* keep, uint32_t* new_id, uint32_t* old_id,
                                   uint32_t* tile_sums, uint32_t* total, cudaStream_t st);
 
-// Reverse step of a rollout (orca_adjoint.cu); everything in agent order.
-struct AdjointArgs {
-    int n, kstride;
-    float dt;
-    const float2* pos;        // state at step t
-    const float2* vel;
-    const float2* goal;       // parameters
-    const float* radius;
-    const float* max_speed;
-    const float* pref_speed;
-    const float* tau;
-    const int32_t* nbr;       // n * kstride, -1 padded
-    const uint32_t* tape;     // n LP records
-    const float2* pbar_next;  // dL/dp(t+1), dL/dv(t+1)
-    const float2* vbar_next;
-    float2* pbar;             // dL/dp(t), dL/dv(t) (accumulated)
-    float2* vbar;
-    float* g_pref;            // parameter gradients (accumulated)
-    float* g_radius;
-    float* g_tau;
-};
-cudaError_t launch_adjoint(const AdjointArgs& A, int kmax, cudaStream_t st);
 cudaError_t launch_unpermute_params(int n, const AgentParams& src, float2* goal, float* radius,
                                     float* vmax, float* pref, float* tau, cudaStream_t st);
-cudaError_t launch_axpy2(int n, float2* y, const float2* x, cudaStream_t st);
 
 // Cell coordinate along one axis in FP32, one rounding per operation:
 // floor(fl(fl(v - vmin) * inv)) clamped to [0, g - 1].

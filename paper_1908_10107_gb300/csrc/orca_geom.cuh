@@ -16,6 +16,17 @@ constexpr int kLineRightLeg = 2;
 constexpr int kLineOverlap = 3;       // agents overlap: one-step disc
 constexpr int kLineOverlapFixed = 4;  // overlap with q = 0: direction fixed by a rule
 
+// What fixes an agent's final velocity, recorded for the adjoint (rollouts only):
+//   kTapePref      x = preferred velocity o;          kTapePrefClip  x = V o / |o|;
+//   kTapeLine      x from LP1 on line i (LP2 phase);
+//   kTapeLp3Dir    x = V n_i (LP3, no bisector was violated);
+//   kTapeLp3Line   x from LP1 on the bisector of lines i and f (LP3).
+// For the LP1 cases: t was free (projection of o), or the disc's or line / bisector j's
+// bound on the tL (side 0) or tR (side 1) end.  Packed in 32 bits: mode | i << 3 | f << 9 |
+// bound << 15 | j << 17 | side << 23.
+constexpr int kTapePref = 0, kTapePrefClip = 1, kTapeLine = 2, kTapeLp3Dir = 3, kTapeLp3Line = 4;
+constexpr int kBoundFree = 0, kBoundDisc = 1, kBoundLine = 2;
+
 // Every formula below is written with explicit FP32 operations (fused where a product
 // feeds a sum), none left to the compiler's contraction: each kernel that builds a
 // half-plane -- the plain and the obstacle instantiations of the step, the adjoint --

@@ -26,16 +26,6 @@ namespace orca {
 // Stored as float4 (nx, ny, c, unused).
 
 
-// What fixes an agent's final velocity, recorded for the adjoint (rollouts only):
-//   kTapePref      x = preferred velocity o;          kTapePrefClip  x = V o / |o|;
-//   kTapeLine      x from LP1 on line i (LP2 phase);
-//   kTapeLp3Dir    x = V n_i (LP3, no bisector was violated);
-//   kTapeLp3Line   x from LP1 on the bisector of lines i and f (LP3).
-// For the LP1 cases: t was free (projection of o), or the disc's or line / bisector j's
-// bound on the tL (side 0) or tR (side 1) end.
-constexpr int kTapePref = 0, kTapePrefClip = 1, kTapeLine = 2, kTapeLp3Dir = 3, kTapeLp3Line = 4;
-constexpr int kBoundFree = 0, kBoundDisc = 1, kBoundLine = 2;
-
 // Algorithmic operation counts of the LP (operation-counting launches only): LP1 calls,
 // LP1 bounds evaluated, violation checks (LP2 and LP3 scans), LP3 bisectors formed -- the
 // quantities the oracle counts, for the kernel's arithmetic roofline.
@@ -858,6 +848,30 @@ __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint
     }
 }
 
+// Start radius (squared) of a search with no prediction, the first step after a load:
+// the radius that holds about k + 3 sqrt(k) + 3 other agents at the density of the 3 x 3
+// cells around the agent (counted from the cell table; near the crowd's edge the block's
+// empty part lowers the estimate, so the start only errs wider).  A start that misses
+// costs the warp a whole extra pass, so it errs on the wide side.  One cell edge when the
+// block holds nobody else.
+__device__ __forceinline__ float density_lim(const MainArgs& a, const GridDev& g, int cell_off,
+                                             float2 p, int k) {
+    const int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
+    const int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
+    const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < g.gx ? cx + 1 : g.gx - 1;
+    const int y0 = cy > 0 ? cy - 1 : 0, y1 = cy + 1 < g.gy ? cy + 1 : g.gy - 1;
+    uint32_t cnt = 0;
+#pragma unroll 1
+    for (int y = y0; y <= y1; ++y) {
+        const int c = cell_off + y * g.gx;
+        cnt += a.cell_start[c + x1 + 1] - a.cell_start[c + x0];
+    }
+    if (cnt <= 1) return g.s * g.s;
+    const float area = (float)((x1 - x0 + 1) * (y1 - y0 + 1)) * g.s * g.s;
+    const float want = (float)k + 3.0f * sqrtf((float)k) + 3.0f;
+    return want * area / (3.14159265f * (float)(cnt - 1));
+}
+
 // Exact k nearest neighbours of the agent at sorted slot t: keys (d2 bits << 32 | id)
 // kept ascending in kk; the first KMAX-k entries are permanent zero sentinels so that
 // the live window is the last k entries.
@@ -872,7 +886,7 @@ __device__ __forceinline__ void offer_range(const float4* __restrict__ msg, uint
 // outside it).  h is the row's distance minus the slop; the search stops when the next
 // row's h^2 exceeds lim.  lim shrinks as the list fills, narrowing later rows.
 //
-// lim starts at lim0 (a predicted radius capped below r_obs^2; NaN: one cell edge).
+// lim starts at lim0 (a predicted radius capped below r_obs^2; NaN: from the density).
 // Every candidate with d^2 <= lim0 is offered, and all others have larger d^2, so when at
 // least k candidates were offered the list is exact; when fewer were and lim0 was below
 // the r_obs bound, the search is repeated with 1.5 x the radius (capped at the r_obs
@@ -885,9 +899,8 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
     const int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
     float nd2 = __fmul_rn(nd, nd);
     const float lim_max = __int_as_float(__float_as_int(nd2) - 1);  // largest float below r_obs^2
-    // no prediction: one cell edge (the tuned edge is about the k-th neighbour distance; a
-    // start that misses costs a warp a whole extra pass, so it errs on the wide side)
-    if (lim0 != lim0) lim0 = g.s * g.s;
+    // no prediction: from the local density
+    if (lim0 != lim0) lim0 = density_lim(a, g, cell_off, p, k);
     lim0 = fminf(lim0, lim_max);
     unsigned cand = 0;
 #pragma unroll 1
@@ -1101,7 +1114,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             // search radius predicted from the previous step's k-th neighbour distance
             // (no distance grows by more than the two agents' displacements, about 2 V dt);
             // +inf (fewer than k inside r_obs last time) starts at the r_obs bound, NaN (no
-            // prediction) at one cell edge
+            // prediction) from the density of the cells around the agent
             V = a.prm.max_speed[t];
             float lim0 = __int_as_float(0x7fffffff);
             if (a.prm.hint) {
