@@ -38,6 +38,24 @@ def test_bidirectional_small(n, seed, jitter):
     parity.gpu_step_and_compare(sc)
 
 
+@pytest.mark.parametrize("steps_before", [0, 1500])
+def test_eight_way_crossing(steps_before):
+    """The paper's eight-way crossing (Section 4, Fig. 5) at its 10,000 agents: at the start
+    and after 1,500 steps (150 s), when the eight crowds meet in the vortex near the centre."""
+    sc = S.eight_way_crossing(10000)
+    rep = parity.gpu_step_and_compare(sc, steps_before=steps_before)
+    assert rep["rows"] == 10000
+
+
+@pytest.mark.parametrize("heterogeneous", [False, True])
+def test_two_way_crossing(heterogeneous):
+    """The paper's two-way crossing (Section 4, Figs. 3-4) at its 2,500 agents, equal and
+    varied agents, when the two crowds meet."""
+    sc = S.two_way_crossing(2500, heterogeneous=heterogeneous)
+    rep = parity.gpu_step_and_compare(sc, steps_before=400)
+    assert rep["rows"] == 2500
+
+
 def test_bidirectional_after_steps():
     sc = S.bidirectional(8190, seed=3)
     parity.gpu_step_and_compare(sc, steps_before=40)
