@@ -91,6 +91,9 @@ def _bind(lib):
     lib.oracle_obstacle_line.argtypes = [_F64P, c.c_double, _F64P, c.c_double, c.c_double, _F64P]
     lib.oracle_obstacle_line.restype = c.c_int
     lib.oracle_arrived.argtypes = [c.c_int, _F32P, _F32P, _F32P, _I32P]
+    lib.oracle_spawn.argtypes = [c.c_int, _F32P, _F32P, _F32P, c.c_int, _F32P, _F32P, _F32P,
+                                 c.c_float, _I32P]
+    lib.oracle_spawn.restype = c.c_int
     lib.oracle_arrived.restype = c.c_int
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = c.c_int
@@ -308,6 +311,24 @@ def arrived(pos, goal, radius) -> np.ndarray:
     out = np.zeros(max(n, 1), np.int32)
     _load().oracle_arrived(n, pos, goal, radius, out)
     return out[:n].astype(bool)
+
+
+def spawn(pos, vel, radius, cand_pos, cand_radius, cand_vmax, window: float) -> np.ndarray:
+    """Which candidates may enter (Section 4: spawned without overlap within a time window
+    set by size and speed): a candidate at rest conflicts with a present agent j when
+    |p_c - p_j| <= r_c + r_j + (V_c + |v_j|) T, and with an earlier accepted candidate c'
+    when |p_c - p_c'| <= r_c + r_c' + (V_c + V_c') T; decided in FP32 (bool[m])."""
+    f = lambda a: np.ascontiguousarray(np.asarray(a, np.float32).reshape(-1))  # noqa: E731
+    pos, vel, radius = f(pos), f(vel), f(radius)
+    cand_pos, cand_radius, cand_vmax = f(cand_pos), f(cand_radius), f(cand_vmax)
+    n, m = radius.size, cand_radius.size
+    out = np.zeros(max(m, 1), np.int32)
+    _load().oracle_spawn(n, pos if n else np.zeros(2, np.float32), vel if n else np.zeros(2, np.float32),
+                         radius if n else np.zeros(1, np.float32), m,
+                         cand_pos if m else np.zeros(2, np.float32),
+                         cand_radius if m else np.zeros(1, np.float32),
+                         cand_vmax if m else np.zeros(1, np.float32), float(np.float32(window)), out)
+    return out[:m].astype(bool)
 
 
 def remove_arrived(scene):

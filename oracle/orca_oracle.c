@@ -851,6 +851,63 @@ int oracle_arrived(int n, const float* pos, const float* goal, const float* radi
     return count;
 }
 
+/* ----------------------------------------------------------------------------------
+ * Spawning without overlap (Section 4, test set-up: spawn locations are chosen so that a
+ * new person overlaps nobody within a time period based on person size and speed).
+ * Reading: a candidate c (position p_c, radius r_c, maximum speed V_c) enters at rest.
+ * It conflicts with a present agent j (position p_j, velocity v_j, radius r_j) when the
+ * two could touch within the window T moving straight at each other:
+ *     |p_c - p_j| <= r_c + r_j + (V_c + |v_j|) T,
+ * and with a candidate c' accepted before it (candidates are taken in index order) when
+ *     |p_c - p_c'| <= r_c + r_c' + (V_c + V_c') T.
+ * A candidate is accepted when it has no conflict.  Decided in FP32, one rounding per
+ * operation: dx = fl(x_c - x_j), d2 = fl(fl(dx dx) + fl(dy dy)), s_j = fl(sqrt(fl(fl(vx vx)
+ * + fl(vy vy)))), reach = fl(fl(r_c + r_j) + fl(fl(V_c + s_j) T)), conflict iff
+ * d2 <= fl(reach reach).
+ * pos, vel: 2n floats; radius: n; cand_pos: 2m; cand_radius, cand_vmax: m; accepted: m
+ * int32 (1 or 0).  Returns the number accepted.  O(n m + m^2): plain loops.
+ * -------------------------------------------------------------------------------- */
+static int spawn_conflict(float xc, float yc, float rc, float vc, float xj, float yj, float rj,
+                          float sj, float window) {
+    float dx = xc - xj;
+    float dy = yc - yj;
+    float dx2 = dx * dx;
+    float dy2 = dy * dy;
+    float d2 = dx2 + dy2;
+    float rr = rc + rj;
+    float ss = vc + sj;
+    float travel = ss * window;
+    float reach = rr + travel;
+    float reach2 = reach * reach;
+    return d2 <= reach2;
+}
+
+int oracle_spawn(int n, const float* pos, const float* vel, const float* radius, int m,
+                 const float* cand_pos, const float* cand_radius, const float* cand_vmax,
+                 float window, int32_t* accepted) {
+    int count = 0;
+    for (int c = 0; c < m; ++c) {
+        const float xc = cand_pos[2 * c], yc = cand_pos[2 * c + 1];
+        int ok = 1;
+        for (int j = 0; j < n && ok; ++j) {
+            float vx2 = vel[2 * j] * vel[2 * j];
+            float vy2 = vel[2 * j + 1] * vel[2 * j + 1];
+            float v2 = vx2 + vy2;
+            float sj = sqrtf(v2);
+            if (spawn_conflict(xc, yc, cand_radius[c], cand_vmax[c], pos[2 * j], pos[2 * j + 1],
+                               radius[j], sj, window))
+                ok = 0;
+        }
+        for (int e = 0; e < c && ok; ++e)
+            if (accepted[e] && spawn_conflict(xc, yc, cand_radius[c], cand_vmax[c], cand_pos[2 * e],
+                                              cand_pos[2 * e + 1], cand_radius[e], cand_vmax[e], window))
+                ok = 0;
+        accepted[c] = ok;
+        count += ok;
+    }
+    return count;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -18,6 +18,7 @@ import test_oracle_knn as K
 import test_oracle_lp as LP
 import test_oracle_obstacles as OB
 import test_oracle_population as POP
+import test_oracle_spawn as SP
 import test_oracle_step as ST
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "orca_oracle.c")
@@ -62,6 +63,15 @@ MUTANTS = {
     "sens_offset_from_wrong_point": ("double c = dot(nq, L[q].P);", "double c = dot(nq, L[q].d);"),
     "margin_overlap_scale": ("note(tg, p2, R2, R2);", "note(tg, p2, R2, 1.0);"),
     "margin_leg_scale": ("note(tg, side, 0.0, sqrt(p2 * w2));", "note(tg, side, 0.0, p2);"),
+    # spawning without overlap
+    "spawn_strict": ("    return d2 <= reach2;", "    return d2 < reach2;"),
+    "spawn_speed_of_neighbour_dropped": ("    float ss = vc + sj;", "    float ss = vc;"),
+    "spawn_radius_sum_wrong": ("    float rr = rc + rj;", "    float rr = rc + rc;"),
+    "spawn_window_dropped": ("    float travel = ss * window;", "    float travel = ss;"),
+    "spawn_ignores_earlier_candidates": ("            if (accepted[e] && spawn_conflict(",
+                                         "            if (0 && spawn_conflict("),
+    "spawn_blocked_by_rejected": ("            if (accepted[e] && spawn_conflict(",
+                                  "            if (1 && spawn_conflict("),
     "obstacle_lines_not_hard_in_lp3": ("for (int j = 0; j < nobst && j < OR_MAXK; ++j) proj[m++] = L[j];",
                                        "for (int j = 0; j < 0; ++j) proj[m++] = L[j];"),
 }
@@ -102,6 +112,10 @@ def _pins():
         ("obstacle_lp3", OB.test_lp3_keeps_obstacle_lines_hard_and_minimises_the_rest),
         ("obstacle_lone_agent", OB.test_lone_agent_into_a_wall_closed_form),
         ("arrival_exact", POP.test_matches_exact_arithmetic_away_from_the_boundary),
+        ("spawn_boundary", SP.test_touching_exactly_at_the_reach_is_a_conflict),
+        ("spawn_earlier", SP.test_earlier_accepted_candidates_block_later_ones),
+        ("spawn_reasons", SP.test_accepted_set_is_clear_and_every_rejection_has_a_reason),
+        ("spawn_physics", SP.test_accepted_candidates_cannot_touch_anyone_within_the_window),
     ]
 
 
