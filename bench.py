@@ -796,6 +796,7 @@ def post_load_step(torch, abi, sim, sc, stream, flush, warmup, reps=5) -> dict:
             else:
                 abi.orca_update_state(sim.ctx, pos, vel, stream=stream)
             c0 = sim.counters()
+            s0 = sim.search_counters()
             flush.fill_(0x5a)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -805,11 +806,16 @@ def post_load_step(torch, abi, sim, sc, stream, flush, warmup, reps=5) -> dict:
             times[kind].append(a.elapsed_time(b))
             phases[kind].append(abi.orca_profile_read(sim.ctx))
             c1 = sim.counters()
-            cands[kind].append((c1["candidates"] - c0["candidates"]) /
-                               max(c1["agent_steps"] - c0["agent_steps"], 1))
+            s1 = sim.search_counters()
+            na = max(c1["agent_steps"] - c0["agent_steps"], 1)
+            cands[kind].append(((c1["candidates"] - c0["candidates"]) / na,
+                                (s1["rows"] - s0["rows"]) / na,
+                                (s1["extra_passes"] - s0["extra_passes"]) / na))
     abi.orca_profile(sim.ctx, False)
     out = {k: float(np.median(v)) for k, v in times.items()}
-    out["candidates_per_agent"] = {k: round(float(np.median(v)), 2) for k, v in cands.items()}
+    out["search_per_agent"] = {k: dict(zip(("candidates", "rows", "extra_passes"),
+                                           [round(float(x), 3) for x in np.median(np.array(v), axis=0)]))
+                               for k, v in cands.items()}
     out["ratio"] = out["after_set_agents"] / out["after_update_state"]
     out["phases_ms"] = {k: [round(float(x), 4) for x in np.median(np.array(v), axis=0)]
                         for k, v in phases.items()}

@@ -59,6 +59,7 @@ extern "C" {
 #define ORCA_ERR_NUMERIC (-5)  /* a non-finite velocity or position was produced */
 #define ORCA_ERR_TIMEOUT (-6)  /* a bounded device-side wait gave up */
 #define ORCA_ERR_CAPACITY (-7) /* more agents / scenes / cells than the context was sized for */
+#define ORCA_ERR_BOUNDS (-8)   /* a device-side index check failed (library built with ORCA_CHECKS) */
 
 /* pointer location */
 #define ORCA_HOST 0
@@ -234,6 +235,18 @@ ORCA_API int orca_get_cells(orca_ctx* ctx, uint32_t* cell, float* grid_f, int32_
 ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
 
 /*
+ * Cost of the neighbour searches (Fig. 2: the r_obs filter, here the k nearest inside
+ * r_obs), accumulated since orca_set_agents (synchronises `stream`): counters[0] search
+ * passes beyond the first (the start radius held fewer than k agents inside r_obs and
+ * grew 1.5x), [1] searches that started without a radius prediction (the first step after
+ * a load: the start comes from the density of the cells around the agent), [2] grid rows
+ * scanned (a search stops at a row once its bound has tightened past it, which depends on
+ * the order of the agents inside a cell, so this count varies slightly between runs),
+ * [3] reserved (0).  Counted by every step.
+ */
+ORCA_API int orca_get_search_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
+
+/*
  * Static obstacles: n_seg line segments (0 <= n_seg <= 256; 0 clears them), seg_xyxy 4*n_seg
  * floats (x1, y1, x2, y2 per segment, host or device per `where`).  Not in the paper's
  * experiments; the ORCA obstacle rule the paper defers to (van den Berg et al.): the
@@ -276,6 +289,27 @@ ORCA_API int orca_get_obstacle_neighbors(orca_ctx* ctx, int32_t* obst, int where
  */
 ORCA_API int orca_remove_arrived(orca_ctx* ctx, int32_t* n_remaining, int32_t* kept_ids, int where,
                                  void* stream);
+
+/*
+ * Spawning during a run (Section 4, test set-up: people are spawned at random locations
+ * chosen so that they overlap nobody within a time period based on their size and speed).
+ * Candidates c = 0..m-1 -- cand_pos, goal_xy (2m floats), radius, max_speed, pref_speed,
+ * time_horizon (m floats), host or device memory per `where` -- enter at rest.  Candidate c
+ * is refused when it could touch a present agent j within `window` seconds, both moving
+ * straight at each other, |p_c - p_j| <= r_c + r_j + (V_c + |v_j|) window, or likewise a
+ * candidate accepted before it (candidates are taken in index order, with that
+ * candidate's maximum speed in place of |v_j|).  Decided in FP32, one rounding per
+ * operation.  The accepted ones are appended with agent indices n, n+1, ... in candidate
+ * order and no search-radius prediction; accepted (m int32 per `where`, may be NULL)
+ * receives 1 or 0 per candidate and *n_after the new agent count.  O(n m) work (every
+ * candidate against every present agent).  Synchronises `stream` (the host needs the
+ * count); the next orca_step re-captures its graphs.  Errors: ORCA_ERR_ARG, ORCA_ERR_STATE
+ * (a batch), ORCA_ERR_CAPACITY (n + m above max_agents), ORCA_ERR_CUDA.
+ */
+ORCA_API int orca_spawn_agents(orca_ctx* ctx, int32_t m, const float* cand_pos, const float* goal_xy,
+                               const float* radius, const float* max_speed, const float* pref_speed,
+                               const float* time_horizon, float window, int where, int32_t* accepted,
+                               int32_t* n_after, void* stream);
 
 /*
  * Operation counting (measurement; the paper has no counterpart).  With on != 0, later

@@ -869,11 +869,11 @@ int oracle_arrived(int n, const float* pos, const float* goal, const float* radi
  * -------------------------------------------------------------------------------- */
 static int spawn_conflict(float xc, float yc, float rc, float vc, float xj, float yj, float rj,
                           float sj, float window) {
-    float dx = xc - xj;
-    float dy = yc - yj;
-    float dx2 = dx * dx;
-    float dy2 = dy * dy;
-    float d2 = dx2 + dy2;
+    float ex = xc - xj;
+    float ey = yc - yj;
+    float ex2 = ex * ex;
+    float ey2 = ey * ey;
+    float d2 = ex2 + ey2;
     float rr = rc + rj;
     float ss = vc + sj;
     float travel = ss * window;

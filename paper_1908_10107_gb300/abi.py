@@ -10,6 +10,7 @@ instead of falling back to anything.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 
@@ -25,6 +26,7 @@ ORCA_ERR_STATE = -4
 ORCA_ERR_NUMERIC = -5
 ORCA_ERR_TIMEOUT = -6
 ORCA_ERR_CAPACITY = -7
+ORCA_ERR_BOUNDS = -8
 ORCA_HOST = 0
 ORCA_DEVICE = 1
 ORCA_FLAG_RECORD = 1
@@ -84,9 +86,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "orca_get_counters": ([vp, vp, vp], c.c_int),
         "orca_count_ops": ([vp, i32], c.c_int),
         "orca_remove_arrived": ([vp, c.POINTER(i32), vp, c.c_int, vp], c.c_int),
+        "orca_spawn_agents": ([vp, i32] + [vp] * 6 + [c.c_float, c.c_int, vp, c.POINTER(i32), vp], c.c_int),
         "orca_set_obstacles": ([vp, i32, vp, c.c_float, i32, c.c_int, vp], c.c_int),
         "orca_get_obstacle_neighbors": ([vp, vp, c.c_int, vp], c.c_int),
         "orca_get_op_counters": ([vp, vp, vp], c.c_int),
+        "orca_get_search_counters": ([vp, vp, vp], c.c_int),
         "orca_sync": ([vp, vp], c.c_int),
         "orca_profile": ([vp, c.c_int], c.c_int),
         "orca_profile_read": ([vp, vp], c.c_int),
@@ -111,6 +115,19 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     if path is None:
         _lib = lib
     return lib
+
+
+@contextlib.contextmanager
+def use_library(path: str):
+    """Route every binding call through another build of the library -- the ORCA_CHECKS
+    build, say -- inside the with-block.  Contexts created inside must be closed inside."""
+    global _lib
+    saved = _lib
+    _lib = load_library(path)
+    try:
+        yield _lib
+    finally:
+        _lib = saved
 
 
 def _check(status: int, ctx=None):
@@ -292,6 +309,34 @@ def orca_get_obstacle_neighbors(ctx, out, where=None, stream=None):
                                                       _stream(stream)), ctx)
 
 
+def orca_spawn_agents(ctx, cand_pos, goal_xy, radius, max_speed, pref_speed, time_horizon,
+                      window: float, accepted=None, stream=None) -> int:
+    """Spawn candidates (arrays of m or 2m float32, host or CUDA) that overlap nobody within
+    ``window`` seconds; returns the new agent count; ``accepted`` (int32[m], same memory
+    kind) receives 1/0 per candidate."""
+    arrays = (cand_pos, goal_xy, radius, max_speed, pref_speed, time_horizon)
+    m = int(np.asarray(radius.shape)[0]) if hasattr(radius, "shape") else len(radius)
+    ptrs, where = [], None
+    for a, k in zip(arrays, (2, 2, 1, 1, 1, 1)):
+        p, w = _ptr(a, np.float32)
+        if where is not None and w != where:
+            raise TypeError("orca_spawn_agents: all arrays host or all device")
+        size = a.size if isinstance(a, np.ndarray) else a.numel()
+        if size != k * m:
+            raise ValueError("orca_spawn_agents: arrays of m or 2m elements")
+        where = w
+        ptrs.append(p)
+    acc = None
+    if accepted is not None:
+        acc, w = _ptr(accepted, np.int32)
+        if w != where:
+            raise TypeError("accepted must live where the candidates do")
+    n_after = ctypes.c_int32(0)
+    _check(load_library().orca_spawn_agents(ctx, m, *ptrs, float(window), where, acc,
+                                            ctypes.byref(n_after), _stream(stream)), ctx)
+    return int(n_after.value)
+
+
 def orca_count_ops(ctx, on: bool):
     _check(load_library().orca_count_ops(ctx, int(bool(on))), ctx)
 
@@ -300,6 +345,13 @@ def orca_get_op_counters(ctx, stream=None) -> np.ndarray:
     out = np.zeros(4, np.int64)
     _check(load_library().orca_get_op_counters(ctx, ctypes.c_void_p(out.ctypes.data),
                                                _stream(stream)), ctx)
+    return out
+
+
+def orca_get_search_counters(ctx, stream=None) -> np.ndarray:
+    out = np.zeros(4, np.int64)
+    _check(load_library().orca_get_search_counters(ctx, ctypes.c_void_p(out.ctypes.data),
+                                                   _stream(stream)), ctx)
     return out
 
 
@@ -574,6 +626,19 @@ class OrcaSim:
         kept = np.zeros(max(self.n, 1), np.int32)
         m = orca_remove_arrived(self.ctx, kept, stream)
         return m, kept[:m].copy()
+
+    def search_counters(self, stream=None) -> dict:
+        c = orca_get_search_counters(self.ctx, stream)
+        return dict(zip(("extra_passes", "unpredicted", "rows"), map(int, c[:3])))
+
+    def spawn(self, cand_pos, goal, radius, max_speed, pref_speed, time_horizon, window, stream=None):
+        """Spawn the candidates that overlap nobody within ``window`` s; returns accepted
+        flags (bool[m]).  The entrants get agent indices n, n+1, ... in candidate order."""
+        f = lambda a: np.ascontiguousarray(np.asarray(a, np.float32))  # noqa: E731
+        acc = np.zeros(max(len(radius), 1), np.int32)
+        orca_spawn_agents(self.ctx, f(cand_pos).reshape(-1, 2), f(goal).reshape(-1, 2), f(radius),
+                          f(max_speed), f(pref_speed), f(time_horizon), window, acc[:len(radius)], stream)
+        return acc[:len(radius)].astype(bool)
 
     def op_counters(self, stream=None) -> dict:
         c = orca_get_op_counters(self.ctx, stream)

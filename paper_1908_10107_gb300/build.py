@@ -2,6 +2,8 @@
 
 Every .cu file under csrc/ is compiled in parallel to an object file under _build/,
 then linked into paper_1908_10107_gb300/liborca_gb300.so (static CUDA runtime).
+build(checks=True) builds the same sources with -DORCA_CHECKS (device index checks that
+latch an error instead of accessing out of range) into liborca_gb300_checks.so.
 """
 from __future__ import annotations
 
@@ -37,23 +39,30 @@ def _deps():
         os.path.join(ROOT, "include", "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+LIB_CHECKS = os.path.join(HERE, "liborca_gb300_checks.so")
+
+
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if stale) and return the path of liborca_gb300.so."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checks: bool = False) -> str:
+    """Compile (if stale) and return the path of liborca_gb300.so (checks=True: of
+    liborca_gb300_checks.so, built with -DORCA_CHECKS)."""
+    lib = LIB_CHECKS if checks else LIB
+    if not force and up_to_date(lib):
+        return lib
+    bdir = os.path.join(BUILD, "checks") if checks else BUILD
+    flags = list(extra_flags) + (["-DORCA_CHECKS"] if checks else [])
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -66,13 +75,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             if log.strip():
                 print(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

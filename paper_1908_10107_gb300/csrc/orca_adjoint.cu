@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
     for (int l = 0; l < KMAX && l < K; ++l) {
         const int j = A.nbr[(size_t)a * K + l];
         if (j < 0) break;
+        if (!idx_ok(j < A.n, A.err)) break;
         nb[cnt++] = j;
         atomicAdd(A.incnt + j, 1u);  // integer: the count is exact in any order
     }
@@ -437,12 +438,13 @@ __global__ void __launch_bounds__(kCsrThreads) csr_scan_kernel(int n, uint32_t* 
 __global__ void __launch_bounds__(256) csr_fill_kernel(int n, int K, const int32_t* __restrict__ nbr,
                                                        uint32_t* __restrict__ incnt,
                                                        const uint32_t* __restrict__ instart,
-                                                       uint32_t* __restrict__ inlist) {
+                                                       uint32_t* __restrict__ inlist, int* err) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
     for (int l = 0; l < K; ++l) {
         const int b = nbr[(size_t)a * K + l];
         if (b < 0) break;
+        if (!idx_ok(b < n, err)) break;
         inlist[instart[b] + atomicAdd(incnt + b, 1u)] = (uint32_t)a * (uint32_t)K + (uint32_t)l;
     }
 }
@@ -503,7 +505,8 @@ cudaError_t launch_adjoint_step(const AdjArgs<T>& A, int kmax, cudaStream_t st) 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     csr_scan_kernel<<<1, kCsrThreads, 0, st>>>(A.n, A.incnt, A.instart);
-    csr_fill_kernel<<<(A.n + 255) / 256, 256, 0, st>>>(A.n, A.kstride, A.nbr, A.incnt, A.instart, A.inlist);
+    csr_fill_kernel<<<(A.n + 255) / 256, 256, 0, st>>>(A.n, A.kstride, A.nbr, A.incnt, A.instart, A.inlist,
+                                                       A.err);
     adj_gather_kernel<T><<<(A.n + 255) / 256, 256, 0, st>>>(A);
     return cudaGetLastError();
 }

@@ -51,6 +51,7 @@ struct AdjArgs {
     uint32_t* incnt;        // n, zero on entry and on exit
     uint32_t* instart;      // n + 1
     uint32_t* inlist;       // n * kstride
+    int* err;               // the device error word (index checks of the ORCA_CHECKS build)
 };
 
 // adj_agent, csr_scan, csr_fill, adj_gather on st (T = float or double).

@@ -5,11 +5,22 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/orca_gb300.h"
 #include "orca_adjoint.cuh"
 #include "orca_common.cuh"
 
 namespace orca {
+
+// An NVTX range over one entry point that enqueues GPU work, so that a profiler's timeline
+// shows which library call launched what (header-only NVTX: a no-op without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Sub-allocation plan of the workspace (256-byte aligned pieces).
 struct Layout {
@@ -73,14 +84,14 @@ static bool make_plan(const orca_params& p, Plan& pl) {
     pl.o_tot = L.add(4);
     pl.o_cells = L.add(((size_t)pl.table_cells + 1) * 4);
     pl.o_cnt = L.add((size_t)pl.table_cells * 4);
-    pl.o_tsum = L.add(((size_t)pl.table_cells / kCellTile + 1) * 4);
+    pl.o_tsum = L.add(((size_t)pl.table_cells / kCellTile + 1) * kTileSumStride * 4);
     pl.o_scenes = L.add((size_t)pl.S * sizeof(SceneDev));
     pl.o_slot = p.max_scenes > 1 ? L.add(N * 4) : (size_t)-1;
     pl.o_part = L.add(kBboxBlocks * sizeof(float4));
     pl.o_misc = L.add(sizeof(DeviceMisc));
     pl.o_blk = L.add((size_t)pl.nmb * kBlockCounters * sizeof(unsigned long long));
     pl.o_seg = L.add((size_t)kMaxObstacles * sizeof(float4));
-    pl.o_near = L.add((size_t)pl.nmb);       // a flag per 64-agent tile (obstacle steps)
+    pl.o_near = L.add((size_t)pl.nmb);       // a flag per tile (obstacle steps)
     pl.o_otiles = L.add((size_t)pl.nmb * 4);  // the flagged tiles
     if (p.flags & ORCA_FLAG_RECORD) {
         pl.o_rnbr = L.add(N * pl.K * 4);
@@ -366,6 +377,8 @@ static int check_device_error(orca_ctx* ctx, cudaStream_t st) {
     if (herr & kErrTimeout) return fail(ctx, ORCA_ERR_TIMEOUT, "a bounded device-side wait gave up");
     if (herr & kErrCapacity)
         return fail(ctx, ORCA_ERR_CAPACITY, "crowd extent does not fit the cell table (non-finite positions?)");
+    if (herr & kErrBounds)
+        return fail(ctx, ORCA_ERR_BOUNDS, "a device-side index check failed (ORCA_CHECKS build)");
     return ORCA_OK;
 }
 
@@ -461,7 +474,8 @@ ORCA_API int orca_create(const orca_params* params, void* workspace, size_t work
         // the counting sort's cell and tile counts are zero between steps
         if (e == cudaSuccess) e = cudaMemset(ctx->bins.cnt, 0, (size_t)pl.table_cells * 4);
         if (e == cudaSuccess)
-            e = cudaMemset(ctx->bins.tile_sums, 0, ((size_t)pl.table_cells / kCellTile + 1) * 4);
+            e = cudaMemset(ctx->bins.tile_sums, 0,
+                           ((size_t)pl.table_cells / kCellTile + 1) * kTileSumStride * 4);
     }
     if (e != cudaSuccess) {
         std::string m = std::string("context set-up: ") + cudaGetErrorString(e);
@@ -543,6 +557,7 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy, cons
                              const float* goal_xy, const float* radius, const float* max_speed,
                              const float* pref_speed, const float* time_horizon, int where,
                              void* stream) {
+    NvtxRange nvtx_range("orca_set_agents");
     if (!ctx) return ORCA_ERR_ARG;
     if (n < 0) return fail(ctx, ORCA_ERR_ARG, "n < 0");
     if (n > ctx->plan.N) return fail(ctx, ORCA_ERR_CAPACITY, "n exceeds max_agents");
@@ -583,6 +598,7 @@ ORCA_API int orca_set_agents(orca_ctx* ctx, int32_t n, const float* pos_xy, cons
 
 ORCA_API int orca_update_state(orca_ctx* ctx, const float* pos_xy, const float* vel_xy, int where,
                                void* stream) {
+    NvtxRange nvtx_range("orca_update_state");
     if (!ctx) return ORCA_ERR_ARG;
     if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
     if (ctx->n == 0 || (!pos_xy && !vel_xy)) return ORCA_OK;
@@ -597,6 +613,7 @@ ORCA_API int orca_set_scenes(orca_ctx* ctx, int32_t n_scenes, const orca_scene* 
                              const float* pos_xy, const float* vel_xy, const float* goal_xy,
                              const float* radius, const float* max_speed, const float* pref_speed,
                              const float* time_horizon, int where, void* stream) {
+    NvtxRange nvtx_range("orca_set_scenes");
     if (!ctx) return ORCA_ERR_ARG;
     if (ctx->nseg > 0) return fail(ctx, ORCA_ERR_STATE, "clear the static obstacles before a batch");
     if (!ctx->slot_scene) return fail(ctx, ORCA_ERR_STATE, "context created with max_scenes <= 1");
@@ -674,6 +691,7 @@ ORCA_API int orca_get_scene_grids(orca_ctx* ctx, float* grid_f, int32_t* grid_i,
 }
 
 ORCA_API int orca_step(orca_ctx* ctx, int32_t nsteps, void* stream) {
+    NvtxRange nvtx_range("orca_step");
     if (!ctx) return ORCA_ERR_ARG;
     if (nsteps < 0) return fail(ctx, ORCA_ERR_ARG, "nsteps < 0");
     if (ctx->n == 0 || nsteps == 0) return ORCA_OK;
@@ -694,6 +712,7 @@ ORCA_API int orca_step(orca_ctx* ctx, int32_t nsteps, void* stream) {
 }
 
 ORCA_API int orca_get_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int where, void* stream) {
+    NvtxRange nvtx_range("orca_get_state");
     if (!ctx) return ORCA_ERR_ARG;
     if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
     cudaStream_t st = (cudaStream_t)stream;
@@ -707,6 +726,7 @@ ORCA_API int orca_get_state(orca_ctx* ctx, float* pos_xy, float* vel_xy, int whe
 
 ORCA_API int orca_step_host(orca_ctx* ctx, const float* pos_in, const float* vel_in, int32_t nsteps,
                             float* pos_out, float* vel_out, void* stream) {
+    NvtxRange nvtx_range("orca_step_host");
     if (!ctx) return ORCA_ERR_ARG;
     if (nsteps < 0) return fail(ctx, ORCA_ERR_ARG, "nsteps < 0");
     cudaStream_t st = (cudaStream_t)stream;
@@ -835,6 +855,7 @@ ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream) 
 
 ORCA_API int orca_remove_arrived(orca_ctx* ctx, int32_t* n_remaining, int32_t* kept_ids, int where,
                                  void* stream) {
+    NvtxRange nvtx_range("orca_remove_arrived");
     if (!ctx || !n_remaining) return ORCA_ERR_ARG;
     if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
     if (ctx->n_scenes > 0) return fail(ctx, ORCA_ERR_STATE, "removal needs a single-scene context");
@@ -874,6 +895,55 @@ ORCA_API int orca_remove_arrived(orca_ctx* ctx, int32_t* n_remaining, int32_t* k
     return ORCA_OK;
 }
 
+ORCA_API int orca_spawn_agents(orca_ctx* ctx, int32_t m, const float* cand_pos, const float* goal_xy,
+                               const float* radius, const float* max_speed, const float* pref_speed,
+                               const float* time_horizon, float window, int where, int32_t* accepted,
+                               int32_t* n_after, void* stream) {
+    NvtxRange nvtx_range("orca_spawn_agents");
+    if (!ctx || !n_after) return ORCA_ERR_ARG;
+    if (where != ORCA_HOST && where != ORCA_DEVICE) return fail(ctx, ORCA_ERR_ARG, "bad `where`");
+    if (ctx->n_scenes > 0) return fail(ctx, ORCA_ERR_STATE, "spawning needs a single-scene context");
+    if (m < 0 || !(window >= 0.0f)) return fail(ctx, ORCA_ERR_ARG, "m < 0 or window not >= 0");
+    if (m > 0 && (!cand_pos || !goal_xy || !radius || !max_speed || !pref_speed || !time_horizon))
+        return fail(ctx, ORCA_ERR_ARG, "null array");
+    if ((long long)ctx->n + m > (long long)ctx->plan.N)
+        return fail(ctx, ORCA_ERR_CAPACITY, "n + m exceeds max_agents");
+    const int n = ctx->n, par = ctx->cur;
+    *n_after = n;
+    if (m == 0) return ORCA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t M = (size_t)m;
+    SpawnIn in;
+    if (where == ORCA_HOST) {
+        // candidates staged in scratch that holds nothing between steps: the readout staging
+        // buffers and the other parameter copy
+        const AgentParams& sp = ctx->PR[par ^ 1];
+        CK(cudaMemcpyAsync(ctx->stage[0], cand_pos, M * 8, cudaMemcpyHostToDevice, st), "copy candidates");
+        CK(cudaMemcpyAsync(ctx->stage[1], goal_xy, M * 8, cudaMemcpyHostToDevice, st), "copy candidates");
+        CK(cudaMemcpyAsync(sp.radius, radius, M * 4, cudaMemcpyHostToDevice, st), "copy candidates");
+        CK(cudaMemcpyAsync(sp.max_speed, max_speed, M * 4, cudaMemcpyHostToDevice, st), "copy candidates");
+        CK(cudaMemcpyAsync(sp.pref_speed, pref_speed, M * 4, cudaMemcpyHostToDevice, st), "copy candidates");
+        CK(cudaMemcpyAsync(sp.tau, time_horizon, M * 4, cudaMemcpyHostToDevice, st), "copy candidates");
+        in = SpawnIn{ctx->stage[0], ctx->stage[1], sp.radius, sp.max_speed, sp.pref_speed, sp.tau};
+    } else {
+        in = SpawnIn{(const float2*)cand_pos, (const float2*)goal_xy, radius, max_speed, pref_speed,
+                     time_horizon};
+    }
+    int32_t* acc_dev = where == ORCA_DEVICE && accepted ? accepted : (int32_t*)ctx->bins.vals[0];
+    CK(launch_spawn(n, ctx->PV[0], ctx->PR[par], m, in, window, ctx->bins.keys[1], ctx->bins.vals[1],
+                    ctx->bins.keys[0], acc_dev, ctx->bins.digit_totals, st),
+       "spawn kernels");
+    uint32_t count = 0;
+    CK(cudaMemcpyAsync(&count, ctx->bins.digit_totals, 4, cudaMemcpyDeviceToHost, st), "copy count");
+    if (where == ORCA_HOST && accepted)
+        CK(cudaMemcpyAsync(accepted, acc_dev, M * 4, cudaMemcpyDeviceToHost, st), "copy accepted");
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    ctx->n = n + (int)count;
+    ctx->slot_ok = false;  // the entrants have no slot in the map yet
+    *n_after = ctx->n;
+    return ORCA_OK;
+}
+
 ORCA_API int orca_count_ops(orca_ctx* ctx, int32_t on) {
     if (!ctx) return ORCA_ERR_ARG;
     bool want = on != 0;
@@ -888,6 +958,11 @@ ORCA_API int orca_count_ops(orca_ctx* ctx, int32_t on) {
 ORCA_API int orca_get_op_counters(orca_ctx* ctx, int64_t* counters4, void* stream) {
     if (!ctx || !counters4) return ORCA_ERR_ARG;
     return sum_counters(ctx, 4, counters4, stream);
+}
+
+ORCA_API int orca_get_search_counters(orca_ctx* ctx, int64_t* counters4, void* stream) {
+    if (!ctx || !counters4) return ORCA_ERR_ARG;
+    return sum_counters(ctx, 8, counters4, stream);
 }
 
 // Rollout workspace: checkpoints, parameters in agent order, one segment's recomputed
@@ -934,6 +1009,7 @@ ORCA_API int orca_rollout_workspace_size(const orca_ctx* ctx, int32_t T, int32_t
 
 ORCA_API int orca_rollout_forward(orca_ctx* ctx, int32_t T, int32_t ckpt_every, float* traj_pos,
                                   void* workspace, size_t workspace_bytes, void* stream) {
+    NvtxRange nvtx_range("orca_rollout_forward");
     if (!ctx) return ORCA_ERR_ARG;
     ctx->slot_ok = false;  // rollouts reload and step the state on their own
     if (T < 1 || ckpt_every < 1) return fail(ctx, ORCA_ERR_ARG, "T and ckpt_every must be >= 1");
@@ -972,6 +1048,7 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
                                    float* g_radius, float* g_time_horizon, float* g_pos0,
                                    float* g_vel0, void* workspace, size_t workspace_bytes,
                                    void* stream) {
+    NvtxRange nvtx_range("orca_rollout_backward");
     if (!ctx) return ORCA_ERR_ARG;
     ctx->slot_ok = false;  // rollouts reload and step the state on their own
     if (!dL_dpos) return fail(ctx, ORCA_ERR_ARG, "dL_dpos is required");
@@ -1045,6 +1122,7 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
             A.incnt = (uint32_t*)(w + r.incnt);
             A.instart = (uint32_t*)(w + r.instart);
             A.inlist = (uint32_t*)(w + r.inlist);
+            A.err = &ctx->bins.misc->error;
             CK(launch_adjoint_step(A, (int)K, st), "adjoint kernels");
             float2* tmp = pnext;
             pnext = pcur;
@@ -1085,6 +1163,7 @@ ORCA_API const char* orca_status_string(int status) {
         case ORCA_ERR_NUMERIC: return "non-finite result";
         case ORCA_ERR_TIMEOUT: return "device wait timed out";
         case ORCA_ERR_CAPACITY: return "capacity exceeded";
+        case ORCA_ERR_BOUNDS: return "device index check failed";
         default: return "unknown status";
     }
 }

@@ -158,7 +158,8 @@ __global__ void __launch_bounds__(256) keys_count_kernel(int n, const float2* __
                                                          const int* __restrict__ slot_scene,
                                                          uint32_t* __restrict__ keys,
                                                          uint32_t* __restrict__ ranks,
-                                                         uint32_t* cnt, uint32_t* tile_sums) {
+                                                         uint32_t* cnt, uint32_t* tile_sums,
+                                                         long long table_cells) {
     pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(256) keys_count_kernel(int n, const float2* __
         const int cx = cell_coord(p.x, g.xmin, g.inv, g.gx);
         const int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
         key = off + (uint32_t)cy * (uint32_t)g.gx + (uint32_t)cx;
+        if (!idx_ok((long long)key < table_cells, const_cast<int*>(&misc->error))) key = 0u;
         keys[i] = key;
     }
     const int lane = threadIdx.x & 31;
@@ -186,9 +188,25 @@ __global__ void __launch_bounds__(256) keys_count_kernel(int n, const float2* __
     if (valid && lane == leader) base = atomicAdd(cnt + key, (uint32_t)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (valid) ranks[i] = base + (uint32_t)__popc(peers & lt);
+    // tile counts: the block's agents come in the previous step's cell order, so their
+    // keys mostly fall in a few consecutive tiles from the tile of the block's first agent;
+    // those are counted in shared memory and added with one atomic each, the rest directly
+    constexpr int kSlots = 4;
+    __shared__ uint32_t s_tc[kSlots];
+    __shared__ uint32_t s_t0;
+    if (threadIdx.x < kSlots) s_tc[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) s_t0 = valid ? key / (uint32_t)kCellTile : 0u;
+    __syncthreads();
     const uint32_t tile = valid ? key / (uint32_t)kCellTile : 0xffffffffu;
     const unsigned tp = __match_any_sync(0xffffffffu, tile);
-    if (valid && lane == __ffs(tp) - 1) atomicAdd(tile_sums + tile, (uint32_t)__popc(tp));
+    if (valid && lane == __ffs(tp) - 1) {
+        const uint32_t slot = tile - s_t0;  // wraps to a large value below the first tile
+        if (slot < (uint32_t)kSlots) atomicAdd(s_tc + slot, (uint32_t)__popc(tp));
+        else atomicAdd(tile_sums + (size_t)tile * kTileSumStride, (uint32_t)__popc(tp));
+    }
+    __syncthreads();
+    if (threadIdx.x < kSlots && s_tc[threadIdx.x])
+        atomicAdd(tile_sums + (size_t)(s_t0 + threadIdx.x) * kTileSumStride, s_tc[threadIdx.x]);
 }
 
 // Block-wide exclusive scan (kCellScanThreads threads) of one value per thread; also
@@ -231,7 +249,7 @@ __global__ void __launch_bounds__(kCellScanThreads) cell_scan_kernel(int n, cons
     const int tile = blockIdx.x;
     if ((long long)tile * kCellTile > nc) return;  // the whole CTA
     uint32_t pre = 0, tot = 0;
-    for (int b = threadIdx.x; b < tile; b += kCellScanThreads) pre += tile_sums[b];
+    for (int b = threadIdx.x; b < tile; b += kCellScanThreads) pre += tile_sums[(size_t)b * kTileSumStride];
     (void)cell_block_scan(pre, tot);  // every thread gets the sum of the earlier tiles
     pre = tot;
     const long long c0 = (long long)tile * kCellTile + (long long)threadIdx.x * kCellsPerThread;
@@ -296,7 +314,7 @@ __global__ void __launch_bounds__(256) reorder_kernel(int n, const uint32_t* __r
     pdl_wait();
     if (blockIdx.x == 0) {
         const int tiles = misc->grid.num_cells / kCellTile + 1;
-        for (int b = threadIdx.x; b < tiles; b += blockDim.x) tile_sums[b] = 0u;
+        for (int b = threadIdx.x; b < tiles; b += blockDim.x) tile_sums[(size_t)b * kTileSumStride] = 0u;
     }
     const int i0 = blockIdx.x * blockDim.x * kReorderR + threadIdx.x;
     uint32_t t[kReorderR];
@@ -429,7 +447,7 @@ static cudaError_t launch_counting_sort(int n, const SceneDev* scenes, const int
                                        const AgentState& cur, const BinBuffers& b, cudaStream_t st) {
     cudaError_t e = launch_pdl(keys_count_kernel, (n + 255) / 256, 256, 0, st, n, (const float2*)cur.pos,
                                (const DeviceMisc*)b.misc, scenes, slot_scene, b.keys[0], b.vals[0],
-                               b.cnt, b.tile_sums);
+                               b.cnt, b.tile_sums, b.table_cells);
     if (e != cudaSuccess) return e;
     return launch_pdl(cell_scan_kernel, scan_blocks(b.table_cells), kCellScanThreads, 0, st, n,
                       (const DeviceMisc*)b.misc, b.cnt, (const uint32_t*)b.tile_sums, b.cell_start);

@@ -18,9 +18,10 @@
 namespace orca {
 
 constexpr int kMaxNeighbors = 32;
-// per-CTA counters of the ORCA kernel: agents, LP3 agents, candidates, half-planes, then
-// (operation-counting launches only) LP1 calls, LP1 bounds, violation checks, bisectors
-constexpr int kBlockCounters = 8;
+// per-CTA counters of the ORCA kernel: agents, LP3 agents, candidates, half-planes; then
+// (operation-counting launches only) LP1 calls, LP1 bounds, violation checks, bisectors;
+// then the neighbour search's extra passes, unpredicted starts, rows scanned, and a spare
+constexpr int kBlockCounters = 12;
 // static obstacles: segments per context (read through L1; each CTA lists the ones its
 // tile can reach) and obstacle half-planes per agent
 constexpr int kMaxObstacles = 256;
@@ -29,12 +30,34 @@ constexpr int kMaxObstacleNeighbors = 4;
 constexpr int kCellScanThreads = 256;
 constexpr int kCellsPerThread = 16;
 constexpr int kCellTile = kCellScanThreads * kCellsPerThread;
+// the tile counts sit one per 128-byte line, so that their atomics spread over the L2
+// slices instead of queueing in one
+constexpr int kTileSumStride = 32;
 constexpr int kBboxBlocks = 304;  // 2 x 152 SMs
 
 // device error bits (latched in DeviceMisc::error)
 constexpr int kErrNumeric = 1;
 constexpr int kErrTimeout = 2;
 constexpr int kErrCapacity = 4;
+constexpr int kErrBounds = 8;  // an index check of the ORCA_CHECKS build failed
+
+// Index checks.  A build with -DORCA_CHECKS (build.build(checks=True)) tests the indices
+// that the kernels compute from data -- cell-table positions, candidate and neighbour
+// slots, agent ids, cell keys -- before using them; a failed check latches kErrBounds in
+// the device error word (reported by the next synchronising call as ORCA_ERR_BOUNDS) and
+// the access is skipped.  The ordinary build compiles the checks away.
+__device__ __forceinline__ bool idx_ok(bool ok, int* err) {
+#ifdef ORCA_CHECKS
+    if (!ok) {
+        if (err) atomicOr(err, kErrBounds);
+        return false;
+    }
+#else
+    (void)ok;
+    (void)err;
+#endif
+    return true;
+}
 
 // Grid of square cells over the crowd's bounding box, computed on the device each step.
 struct GridDev {
@@ -99,7 +122,7 @@ struct BinBuffers {
     uint32_t* hist;          // scratch between steps (agent removal: tile sums)
     uint32_t* digit_totals;  // scratch between steps (agent removal: the count)
     uint32_t* cnt;           // agents per cell, zero between steps (table_cells entries)
-    uint32_t* tile_sums;     // agents per kCellTile cells, zero between steps
+    uint32_t* tile_sums;     // agents per kCellTile cells (stride kTileSumStride), zero between steps
     uint32_t* cell_start;    // table_cells + 1 entries
     long long table_cells;   // largest num_cells the table holds
     float4* bbox_partials;
@@ -176,6 +199,19 @@ cudaError_t launch_main(const MainArgs& a, int kmax, const LaunchShape& sh, int 
                         cudaStream_t st,
                         const SideStream* side = nullptr);
 int main_resident_blocks(int kmax, const LaunchShape& sh);
+// orca_population.cu: spawn candidates into the crowd (see there); device arrays, m each
+// (pos and goal float2)
+struct SpawnIn {
+    const float2* pos;
+    const float2* goal;
+    const float* radius;
+    const float* max_speed;
+    const float* pref_speed;
+    const float* tau;
+};
+cudaError_t launch_spawn(int n, const AgentState& cur, const AgentParams& cur_p, int m, const SpawnIn& in,
+                         float window, uint32_t* blocked, uint32_t* entrants, uint32_t* rank,
+                         int32_t* accepted, uint32_t* count, cudaStream_t st);
 // orca_population.cu: remove the agents that have reached their goal (see there)
 cudaError_t launch_remove_arrived(int n, const AgentState& cur, const AgentParams& cur_p,
                                   const AgentParams& dst_p, float2* pos_tmp, float2* vel_tmp,

@@ -1,6 +1,6 @@
 // orca_main.cu -- per-agent ORCA velocity selection and integration (Sections 2-3).
 //
-// One CTA of 128 threads takes 128 consecutive agents of the cell order, so its agents
+// One CTA of TPB threads (64 to 256) takes TPB consecutive agents of the cell order, so its agents
 // are spatial neighbours and their candidate reads overlap in L1/L2.  Phases:
 //   1. (thread per agent) exact k nearest neighbours by (fl32 d^2, agent index) among
 //      agents strictly inside r_obs (Fig. 2), by a ring search over grid cells with
@@ -31,6 +31,13 @@ namespace orca {
 // quantities the oracle counts, for the kernel's arithmetic roofline.
 struct OpCount {
     unsigned lp1, bounds, checks, bis;
+};
+
+// What the neighbour searches cost (every launch): passes beyond the first (a start radius
+// that held fewer than k agents inside r_obs, grown 1.5x), searches that started without a
+// prediction, grid rows scanned.
+struct SearchCount {
+    unsigned retries, cold, rows;
 };
 
 struct LpTape {
@@ -864,6 +871,7 @@ __device__ __forceinline__ float density_lim(const MainArgs& a, const GridDev& g
 #pragma unroll 1
     for (int y = y0; y <= y1; ++y) {
         const int c = cell_off + y * g.gx;
+        if (!idx_ok(c + x0 >= 0 && c + x1 + 1 <= a.misc->grid.num_cells, &a.misc_rw->error)) continue;
         cnt += a.cell_start[c + x1 + 1] - a.cell_start[c + x0];
     }
     if (cnt <= 1) return g.s * g.s;
@@ -895,12 +903,15 @@ template <int KMAX, int CAP>
 __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g, int cell_off,
                                             float nd, int t, float2 p, int k, float lim0,
                                             unsigned long long* buf,
-                                            unsigned long long (&kk)[KMAX]) {
+                                            unsigned long long (&kk)[KMAX], SearchCount& sc) {
     const int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
     float nd2 = __fmul_rn(nd, nd);
     const float lim_max = __int_as_float(__float_as_int(nd2) - 1);  // largest float below r_obs^2
     // no prediction: from the local density
-    if (lim0 != lim0) lim0 = density_lim(a, g, cell_off, p, k);
+    if (lim0 != lim0) {
+        lim0 = density_lim(a, g, cell_off, p, k);
+        ++sc.cold;
+    }
     lim0 = fminf(lim0, lim_max);
     unsigned cand = 0;
 #pragma unroll 1
@@ -916,8 +927,14 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
             int x0 = cell_coord(p.x - w, g.xmin, g.inv, g.gx);
             int x1 = cell_coord(p.x + w, g.xmin, g.inv, g.gx);
             int c = cell_off + y * g.gx;
-            uint32_t q0 = a.cell_start[c + x0], q1 = a.cell_start[c + x1 + 1];
+            uint32_t q0 = 0u, q1 = 0u;
+            if (idx_ok(c + x0 >= 0 && c + x1 + 1 <= a.misc->grid.num_cells, &a.misc_rw->error)) {
+                q0 = a.cell_start[c + x0];
+                q1 = a.cell_start[c + x1 + 1];
+                if (!idx_ok(q0 <= q1 && q1 <= (uint32_t)a.n, &a.misc_rw->error)) q1 = q0;
+            }
             cand += q1 - q0;
+            ++sc.rows;
             offer_range<KMAX, CAP>(a.in.msg, q0, q1, t, p, kk, buf, nb, lim);
             // the nearer of the next rows above and below (none left: infinite gaps)
             float hu = up < g.gy ? (g.ymin + (float)up * g.s) - p.y : INFINITY;
@@ -938,6 +955,7 @@ __device__ __forceinline__ unsigned knn_dev(const MainArgs& a, const GridDev& g,
         // fewer than k inside: 1.5 x the radius (from at least 1e-3 r_obs, so the bound
         // reaches r_obs within 18 passes whatever the prediction was)
         lim0 = fminf(fmaxf(2.25f * lim0, 1e-6f * lim_max), lim_max);
+        ++sc.retries;
     }
     return cand;
 }
@@ -1050,6 +1068,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     __shared__ LpTape s_tape[TAPE ? TPB : 1];
     __shared__ int s_qn, s_tile;
     __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3;
+    __shared__ unsigned long long s_search[3];
     __shared__ unsigned long long s_ops[COUNT ? 4 : 1];
     constexpr bool WU = G == 32;  // work-unit LP (warp-cooperative) instead of per-lane LP
     __shared__ WarpLpShared s_wlp[WU ? TPB / 32 : 1];
@@ -1063,9 +1082,11 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         s_lines_n = 0;
         s_act = 0;
         s_lp3 = 0;
+        s_search[0] = s_search[1] = s_search[2] = 0;
         for (int q = 0; q < (COUNT ? 4 : 1); ++q) s_ops[q] = 0;
     }
     OpCount oc{0u, 0u, 0u, 0u};
+    SearchCount sc{0u, 0u, 0u};
     const int ntiles = (a.n + TPB - 1) / TPB;
     float4* row = s_lines + tid * kp;
     // the obstacle launch steps the listed tiles li = blockIdx.x, + gridDim.x, ...
@@ -1123,7 +1144,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             }
             unsigned long long kk[KMAX];
             cand = knn_dev<KMAX, 2 * KP>(a, sv.g, sv.cell_off, sv.nd, t, p, sv.k, lim0,
-                                         reinterpret_cast<unsigned long long*>(row), kk);
+                                         reinterpret_cast<unsigned long long*>(row), kk, sc);
             if (a.prm.hint)
                 a.prm.hint[t] = kk[KMAX - 1] != ~0ull
                                     ? __uint_as_float((unsigned)(kk[KMAX - 1] >> 32))
@@ -1142,8 +1163,13 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             // small enough for the instruction cache
 #pragma unroll
             for (int l = 0; l < KMAX; ++l) {
-                if (l >= KMAX - sv.k && kk[l] != ~0ull)
-                    row[nob + cnt++].w = __uint_as_float(a.in.slot[(uint32_t)kk[l]]);
+                if (l >= KMAX - sv.k && kk[l] != ~0ull) {
+                    const uint32_t nid = (uint32_t)kk[l];
+                    if (!idx_ok(nid < (uint32_t)a.n, &a.misc_rw->error)) continue;
+                    const uint32_t q = a.in.slot[nid];
+                    if (!idx_ok(q < (uint32_t)a.n, &a.misc_rw->error)) continue;
+                    row[nob + cnt++].w = __uint_as_float(q);
+                }
             }
             float2 v = a.in.vel[t];
             float itau = __fdividef(1.0f, a.prm.tau[t]);
@@ -1246,6 +1272,15 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             atomicAdd(&s_act, (unsigned long long)wa);
         }
         if (tid == 0) s_lp3 += (unsigned long long)nq;
+        {
+            const unsigned v3[3] = {sc.retries, sc.cold, sc.rows};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const unsigned w = __reduce_add_sync(0xffffffffu, v3[q]);
+                if ((tid & 31) == 0 && w) atomicAdd(&s_search[q], (unsigned long long)w);
+            }
+            sc = SearchCount{0u, 0u, 0u};
+        }
         if (COUNT) {
             unsigned v[4] = {oc.lp1, oc.bounds, oc.checks, oc.bis};
 #pragma unroll
@@ -1275,6 +1310,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         atomicAdd(c + 1, s_lp3);
         atomicAdd(c + 2, s_cand);
         atomicAdd(c + 3, s_lines_n);
+        for (int q = 0; q < 3; ++q) atomicAdd(c + 8 + q, s_search[q]);
         if (COUNT)
             for (int q = 0; q < 4; ++q) atomicAdd(c + 4 + q, s_ops[COUNT ? q : 0]);
     }

@@ -130,6 +130,114 @@ __global__ void __launch_bounds__(256) compact_kernel(int n, AgentState src, Age
     if (dp.hint) dp.hint[j] = sp.hint[t];
 }
 
+// ---------------------------------------------------------------------------------
+// Spawning during a run (Section 4: new people are placed where they overlap nobody
+// within a time period based on their size and speed).  A candidate enters at rest; it
+// conflicts with a present agent j when the two could touch within the window T moving
+// straight at each other, |p_c - p_j| <= r_c + r_j + (V_c + |v_j|) T, and with a
+// candidate accepted before it (index order) likewise with that candidate's V in place of
+// |v_j|.  Decided in FP32, one rounding per operation (the oracle decides it the same way).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ bool spawn_conflict(float xc, float yc, float rc, float vc, float xj, float yj,
+                                               float rj, float sj, float window) {
+    const float dx = __fsub_rn(xc, xj), dy = __fsub_rn(yc, yj);
+    const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    const float reach = __fadd_rn(__fadd_rn(rc, rj), __fmul_rn(__fadd_rn(vc, sj), window));
+    return d2 <= __fmul_rn(reach, reach);
+}
+
+// Candidate c (one CTA each) against every present agent: blocked[c] = 1 on a conflict.
+__global__ void __launch_bounds__(256) spawn_crowd_kernel(int n, AgentState cur, const float* __restrict__ radius,
+                                                          int m, const float2* __restrict__ cpos,
+                                                          const float* __restrict__ crad,
+                                                          const float* __restrict__ cvmax, float window,
+                                                          uint32_t* __restrict__ blocked) {
+    const int c = blockIdx.x;
+    if (c >= m) return;
+    const float2 pc = cpos[c];
+    const float rc = crad[c], vc = cvmax[c];
+    bool hit = false;
+    for (int j = threadIdx.x; j < n && !hit; j += blockDim.x) {
+        const float2 pj = cur.pos[j], vj = cur.vel[j];
+        const float sj = __fsqrt_rn(__fadd_rn(__fmul_rn(vj.x, vj.x), __fmul_rn(vj.y, vj.y)));
+        hit = spawn_conflict(pc.x, pc.y, rc, vc, pj.x, pj.y, radius[j], sj, window);
+    }
+    hit = __syncthreads_or(hit);
+    if (threadIdx.x == 0) blocked[c] = hit ? 1u : 0u;
+}
+
+// In candidate order (one CTA): a candidate not blocked by the crowd enters unless it
+// conflicts with one that entered before it.  rank[c] receives its place among the
+// entrants (or ~0), accepted[c] 1 or 0; *count the number of entrants.
+__global__ void __launch_bounds__(256) spawn_accept_kernel(int m, const float2* __restrict__ cpos,
+                                                           const float* __restrict__ crad,
+                                                           const float* __restrict__ cvmax, float window,
+                                                           const uint32_t* __restrict__ blocked,
+                                                           uint32_t* __restrict__ entrants,
+                                                           uint32_t* __restrict__ rank,
+                                                           int32_t* __restrict__ accepted,
+                                                           uint32_t* __restrict__ count) {
+    int na = 0;  // entrants so far (their candidate indices in entrants[0..na))
+    for (int c = 0; c < m; ++c) {
+        bool hit = blocked[c] != 0u;
+        if (!hit) {
+            const float2 pc = cpos[c];
+            const float rc = crad[c], vc = cvmax[c];
+            for (int q = threadIdx.x; q < na && !hit; q += blockDim.x) {
+                const uint32_t e = entrants[q];
+                const float2 pe = cpos[e];
+                hit = spawn_conflict(pc.x, pc.y, rc, vc, pe.x, pe.y, crad[e], cvmax[e], window);
+            }
+        }
+        hit = __syncthreads_or(hit);
+        if (threadIdx.x == 0) {
+            accepted[c] = hit ? 0 : 1;
+            rank[c] = hit ? 0xffffffffu : (uint32_t)na;
+            if (!hit) entrants[na] = (uint32_t)c;
+        }
+        if (!hit) ++na;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = (uint32_t)na;
+}
+
+// The entrants appended at rest after the n present agents, with agent indices n, n+1, ...
+// in candidate order and no search-radius prediction.
+__global__ void __launch_bounds__(256) spawn_append_kernel(int n, int m, const float2* __restrict__ cpos,
+                                                           const float2* __restrict__ cgoal,
+                                                           const float* __restrict__ crad,
+                                                           const float* __restrict__ cvmax,
+                                                           const float* __restrict__ cpref,
+                                                           const float* __restrict__ ctau,
+                                                           const uint32_t* __restrict__ rank,
+                                                           AgentState cur, AgentParams cp) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m || rank[c] == 0xffffffffu) return;
+    const uint32_t j = (uint32_t)n + rank[c];
+    cur.pos[j] = cpos[c];
+    cur.vel[j] = make_float2(0.0f, 0.0f);
+    cp.goal[j] = cgoal[c];
+    cp.radius[j] = crad[c];
+    cp.max_speed[j] = cvmax[c];
+    cp.pref_speed[j] = cpref[c];
+    cp.tau[j] = ctau[c];
+    cp.id[j] = j;
+    if (cp.hint) cp.hint[j] = __int_as_float(0x7fffffff);
+}
+
+cudaError_t launch_spawn(int n, const AgentState& cur, const AgentParams& cur_p, int m, const SpawnIn& in,
+                         float window, uint32_t* blocked, uint32_t* entrants, uint32_t* rank,
+                         int32_t* accepted, uint32_t* count, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    spawn_crowd_kernel<<<m, 256, 0, st>>>(n, cur, cur_p.radius, m, in.pos, in.radius, in.max_speed, window,
+                                          blocked);
+    spawn_accept_kernel<<<1, 256, 0, st>>>(m, in.pos, in.radius, in.max_speed, window, blocked, entrants,
+                                           rank, accepted, count);
+    spawn_append_kernel<<<(m + 255) / 256, 256, 0, st>>>(n, m, in.pos, in.goal, in.radius, in.max_speed,
+                                                         in.pref_speed, in.tau, rank, cur, cur_p);
+    return cudaGetLastError();
+}
+
 int scan_tiles(int n) { return (n + kScanTile - 1) / kScanTile; }
 
 cudaError_t launch_remove_arrived(int n, const AgentState& cur, const AgentParams& cur_p,

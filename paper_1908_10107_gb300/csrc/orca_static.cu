@@ -56,7 +56,7 @@ constexpr StaticLayout static_layout() {
     L.ovel = o; o += al256(N * 8);
     L.misc = o; o += al256(sizeof(DeviceMisc));
     L.cnt = o; o += al256((size_t)kStaticMaxCells * 4);
-    L.tsum = o; o += al256(((size_t)kStaticMaxCells / kCellTile + 1) * 4);
+    L.tsum = o; o += al256(((size_t)kStaticMaxCells / kCellTile + 1) * kTileSumStride * 4);
     L.blk = o; o += al256((size_t)nmb * kBlockCounters * 8);
     L.total = o;
     return L;

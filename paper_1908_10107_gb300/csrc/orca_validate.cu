@@ -364,6 +364,7 @@ extern "C" ORCA_API int orca_validate_rollout_fp64(
             A.incnt = (uint32_t*)(w + off[6]);
             A.instart = (uint32_t*)(w + off[7]);
             A.inlist = (uint32_t*)(w + off[8]);
+            A.err = nullptr;  // the validation rollout is built without index checks
             e = launch_adjoint_step(A, max_neighbors, st);
             double2* tmp = pnext;
             pnext = pcur;

@@ -97,8 +97,9 @@ def test_cell_size_does_not_change_results(cell_size):
 @pytest.mark.parametrize("spacing,steps_before", [(3.0, 0), (3.0, 3), (6.0, 0), (6.0, 3)])
 def test_sparse_lattice_with_tiny_cells(spacing, steps_before):
     # cells far smaller than the neighbour distances: with no radius prediction the search
-    # starts at 1.5 cell edges and doubles the radius many times; at spacing 6 most agents
-    # have fewer than k = 10 neighbours inside r_obs = 10 (the prediction then says so)
+    # starts from the local density (few agents in the 3 x 3 tiny cells) and grows the
+    # radius 1.5x many times; at spacing 6 most agents have fewer than k = 10 neighbours
+    # inside r_obs = 10 (the prediction then says so)
     rng = np.random.default_rng(int(spacing * 10) + steps_before)
     g = np.stack(np.meshgrid(np.arange(24.0), np.arange(24.0)), -1).reshape(-1, 2) * spacing
     g = g + rng.uniform(-0.2, 0.2, g.shape)
@@ -238,6 +239,30 @@ def test_device_pointers_match_host_pointers():
     ph, vh = sim.get_state()
     np.testing.assert_array_equal(pd.cpu().numpy(), ph)
     np.testing.assert_array_equal(vd.cpu().numpy(), vh)
+
+
+def test_search_counters():
+    """The first step after a load starts every search without a prediction; later steps
+    start from the previous k-th neighbour distance.  On a sparse lattice with tiny cells
+    the start radius must grow: extra passes are counted."""
+    sc = S.bidirectional(8190, seed=41)
+    sim = parity.make_sim(sc, flags=0)
+    sim.set_scene(sc)
+    sim.step(1)
+    c1 = sim.search_counters()
+    assert c1["unpredicted"] == sc.n and c1["rows"] >= 2 * sc.n
+    sim.step(3)
+    c4 = sim.search_counters()
+    assert c4["unpredicted"] == sc.n  # no new unpredicted searches
+    assert c4["rows"] > c1["rows"]
+    sim.close()
+    g = np.stack(np.meshgrid(np.arange(24.0), np.arange(24.0)), -1).reshape(-1, 2) * 6.0
+    lat = _tiny(g, r=0.4, nd=10.0, dt=0.1)
+    sim = parity.make_sim(lat, flags=0, cell_size=0.05)
+    sim.set_scene(lat)
+    sim.step(1)
+    assert sim.search_counters()["extra_passes"] > 0
+    sim.close()
 
 
 def test_counters():

@@ -110,3 +110,67 @@ def test_removal_needs_a_single_scene():
     with pytest.raises(abi.OrcaError):
         sim.remove_arrived()
     sim.close()
+
+
+def test_spawn_matches_the_oracle_and_steps_continue():
+    """Spawning during a run (Section 4): the candidates the GPU admits are exactly the
+    oracle's on the GPU's own state, the entrants are appended at rest with the next agent
+    indices, and the step after the spawn matches the oracle."""
+    sc = S.two_way_crossing(2500, seed=26)
+    sim = parity.make_sim(sc, max_agents=4000)
+    sim.set_scene(sc)
+    sim.step(60)
+    pos, vel = sim.get_state()
+    rng = np.random.default_rng(26)
+    m = 900
+    lo, hi = sc.pos.min(0), sc.pos.max(0)
+    cpos = (lo + rng.random((m, 2)) * (hi - lo)).astype(np.float32)
+    cgoal = (lo + rng.random((m, 2)) * (hi - lo)).astype(np.float32)
+    crad = np.full(m, 0.5, np.float32)
+    cpref = np.full(m, 1.0, np.float32)
+    cvmax = np.full(m, 1.33, np.float32)
+    ctau = np.full(m, 5.0, np.float32)
+    window = 1.0
+    want = oracle.spawn(pos, vel, sc.radius, cpos, crad, cvmax, window)
+    got = sim.spawn(cpos, cgoal, crad, cvmax, cpref, ctau, window)
+    np.testing.assert_array_equal(got, want)
+    a = int(want.sum())
+    assert 0 < a < m and sim.n == sc.n + a
+    p2, v2 = sim.get_state()
+    np.testing.assert_array_equal(p2[:sc.n], pos)
+    np.testing.assert_array_equal(v2[:sc.n], vel)
+    np.testing.assert_array_equal(p2[sc.n:], cpos[want])
+    assert not v2[sc.n:].any()
+    # the crowd with its entrants (oracle view), one recorded step, against the oracle
+    st = sc.copy()
+    st.pos = np.concatenate([pos, cpos[want]])
+    st.vel = np.concatenate([vel, np.zeros((a, 2), np.float32)])
+    st.goal = np.concatenate([sc.goal, cgoal[want]])
+    st.radius = np.concatenate([sc.radius, crad[want]])
+    st.max_speed = np.concatenate([sc.max_speed, cvmax[want]])
+    st.pref_speed = np.concatenate([sc.pref_speed, cpref[want]])
+    st.time_horizon = np.concatenate([sc.time_horizon, ctau[want]])
+    sim.step(1)
+    p3, v3 = sim.get_state()
+    cells, gf, gi = sim.get_cells()
+    parity.compare_step(st, p3, v3, sim.get_neighbors(), cells, (gf, gi))
+    sim.close()
+
+
+def test_spawn_refusals():
+    sc = S.two_way_crossing(500, seed=27)
+    sim = parity.make_sim(sc, max_agents=600)
+    sim.set_scene(sc)
+    c = np.zeros((200, 2), np.float32)
+    one = np.ones(200, np.float32)
+    with pytest.raises(abi.OrcaError) as e:
+        sim.spawn(c, c, one, one, one, one, 1.0)
+    assert e.value.status == abi.ORCA_ERR_CAPACITY
+    sim.close()
+    batch = S.Batch([S.two_way_crossing(200, seed=28), S.two_way_crossing(300, seed=29)])
+    sim = abi.OrcaSim.for_batch(batch)
+    sim.set_batch(batch)
+    with pytest.raises(abi.OrcaError) as e:
+        sim.spawn(c[:5], c[:5], one[:5], one[:5], one[:5], one[:5], 1.0)
+    assert e.value.status == abi.ORCA_ERR_STATE
+    sim.close()
