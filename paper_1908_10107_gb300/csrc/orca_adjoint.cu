@@ -15,13 +15,14 @@
 //
 // Deterministic accumulation.  What an agent's half-planes contribute to its neighbours
 // is not added with atomics (whose order, and so whose rounding, varies between runs):
-//   adj_agent   one thread per agent a writes its own adjoints and, for every neighbour
-//               slot l, the contribution to that neighbour into contrib[a k + l]; it
-//               also counts every agent's in-degree (how many lists it appears in);
-//   csr_scan    the in-degrees become the offsets of a transposed neighbour list;
-//   csr_fill    every (a, l) is entered in its neighbour's list;
-//   adj_gather  one thread per agent b sorts its list by (a, l) and adds the entries'
-//               contributions in that order (and the loss gradient of its position).
+//   adj_agent   one thread per agent a writes its own adjoints and, for each of the (at
+//               most three) half-planes that fix its velocity, the contribution to that
+//               half-plane's neighbour in an entry of its own; it counts the entries
+//               every agent receives (its in-degree);
+//   csr_scan    the in-degrees become the offsets of a transposed list;
+//   csr_fill    every entry is placed in its neighbour's list;
+//   adj_gather  one thread per agent b sorts its list by entry (agent, then line) and adds
+//               the contributions in that order (and the loss gradient of its position).
 // Every sum is then taken in a fixed order and the gradients are bitwise reproducible.
 //
 // The kernels are templates on the scalar type: float for rollouts of the FP32 step, and
@@ -221,25 +222,36 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // ---- per-agent adjoint ---------------------------------------------------------------
 // Own adjoints of agent a: pbar[a] = dL/dp'(a) + what its half-planes and preferred
 // velocity give its position, vbar[a] likewise for its velocity; its parameter gradients
-// accumulate (one thread per agent, so without atomics).  What its half-planes give
-// neighbour b in slot l goes to contrib[(a k + l) 5 + 0..4] (pbar x, y, vbar x, y, rbar),
-// zeros when nothing flows; every slot's neighbour gets its in-degree counted.
+// accumulate (one thread per agent, so without atomics).  Only the half-planes that fix
+// the selected velocity -- at most three, named by the LP record -- carry an adjoint; they
+// alone are rebuilt, and what each gives its neighbour goes to the agent's entry q
+// (entries in increasing line order), whose neighbour's in-degree is counted.
 template <class T, int KMAX>
 __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
     using T2 = typename AdjArgs<T>::T2;
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A.n) return;
     const int K = A.kstride;
-    int nb[KMAX];
-    int cnt = 0;
-    for (int l = 0; l < KMAX && l < K; ++l) {
-        const int j = A.nbr[(size_t)a * K + l];
-        if (j < 0) break;
-        if (!idx_ok(j < A.n, A.err)) break;
-        nb[cnt++] = j;
-        atomicAdd(A.incnt + j, 1u);  // integer: the count is exact in any order
+    const uint32_t tp = A.tape[a];
+    const int mode = tp & 7, i = (tp >> 3) & 63, f = (tp >> 9) & 63, bound = (tp >> 15) & 3,
+              j = (tp >> 17) & 63, side = (tp >> 23) & 1;
+    // the lines that fix x, in increasing order (j and f lie below i; in a least-penetration
+    // solve the bounding bisector j lies below f)
+    int used[kAdjEntries];
+    int nu = 0;
+    if (mode == kTapeLine) {
+        if (bound == kBoundLine) used[nu++] = j;
+        used[nu++] = i;
+    } else if (mode == kTapeLp3Dir) {
+        used[nu++] = i;
+    } else if (mode == kTapeLp3Line) {
+        if (bound != kBoundDisc) used[nu++] = j;
+        used[nu++] = f;
+        used[nu++] = i;
     }
-    T* my_contrib = A.contrib + (size_t)a * K * 5;
+    int32_t* my_ent = A.ent + (size_t)a * kAdjEntries;
+#pragma unroll
+    for (int q = 0; q < kAdjEntries; ++q) my_ent[q] = -1;
     const T2 pbn = A.pbar_next[a], vbn = A.vbar_next[a];
     // p' = p + x dt, v' = x
     const V2<T> xbar = mk2<T>(vbn.x + A.dt * pbn.x, vbn.y + A.dt * pbn.y);
@@ -249,7 +261,6 @@ __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
         z.x = T(0);
         z.y = T(0);
         A.vbar[a] = z;
-        for (int q = 0; q < cnt * 5; ++q) my_contrib[q] = T(0);
         return;
     }
 
@@ -260,23 +271,25 @@ __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
     const T itau = recip(A.tau[a]);
     const T idt = recip(dt);
     const T half_idt = T(0.5) * idt;
-    // half-planes and preferred velocity exactly as the forward step built them
+    // the used half-planes exactly as the forward step built them
     Line<T> L[KMAX];
-    int br[KMAX];
-    for (int l = 0; l < cnt; ++l) L[l] = forward_line(A, a, nb[l], pa2, va2, ra, itau, dt, half_idt, &br[l]);
-    int far = 0;
-    const T2 o2 = forward_pref(pa2, A.goal[a], A.pref_speed[a], dt, idt, &far);
-    const V2<T> o = v2of(o2);
-
-    const uint32_t tp = A.tape[a];
-    const int mode = tp & 7, i = (tp >> 3) & 63, f = (tp >> 9) & 63, bound = (tp >> 15) & 3,
-              j = (tp >> 17) & 63, side = (tp >> 23) & 1;
+    int br[KMAX], nb[KMAX];
     V2<T> nbar[KMAX];
     T cbar[KMAX];
-    for (int l = 0; l < cnt; ++l) {
+    for (int l = 0; l < KMAX; ++l) {
         nbar[l] = mk2<T>(0, 0);
         cbar[l] = T(0);
     }
+    for (int q = 0; q < nu; ++q) {
+        const int l = used[q];
+        int b = l < K ? A.nbr[(size_t)a * K + l] : -1;
+        if (!idx_ok(b >= 0 && b < A.n, A.err)) b = a;
+        nb[l] = b;
+        L[l] = forward_line(A, a, b, pa2, va2, ra, itau, dt, half_idt, &br[l]);
+    }
+    int far = 0;
+    const T2 o2 = forward_pref(pa2, A.goal[a], A.pref_speed[a], dt, idt, &far);
+    const V2<T> o = v2of(o2);
     V2<T> obar = mk2<T>(0, 0);
 
     if (mode == kTapePref) {
@@ -351,23 +364,24 @@ __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
     // half-planes -> state and parameters of the agent and its neighbours
     V2<T> pabar = v2of(pbn), vabar = mk2<T>(0, 0);
     T rabar = 0, itaubar = 0;
-    for (int l = 0; l < cnt; ++l) {
-        T* c = my_contrib + 5 * l;
-        if (nbar[l].x == T(0) && nbar[l].y == T(0) && cbar[l] == T(0)) {
-            c[0] = c[1] = c[2] = c[3] = c[4] = T(0);
-            continue;
-        }
+    for (int q = 0; q < nu; ++q) {
+        const int l = used[q];
+        if (nbar[l].x == T(0) && nbar[l].y == T(0) && cbar[l] == T(0)) continue;
         const int b = nb[l];
         V2<T> pbbar = mk2<T>(0, 0), vbbar = mk2<T>(0, 0);
         T Rbar = 0;
         line_bar(pa, va, ra, itau, dt, half_idt, v2of(A.pos[b]), v2of(A.vel[b]), A.radius[b], br[l], L[l],
                  nbar[l], cbar[l], pabar, vabar, Rbar, itaubar, pbbar, vbbar);
         rabar += Rbar;
+        const size_t e = (size_t)a * kAdjEntries + q;
+        T* c = A.contrib + 4 * e;
         c[0] = pbbar.x;
         c[1] = pbbar.y;
         c[2] = vbbar.x;
         c[3] = vbbar.y;
-        c[4] = Rbar;
+        A.contrib_r[e] = Rbar;
+        my_ent[q] = b;
+        atomicAdd(A.incnt + b, 1u);  // integer: the count is exact in any order
     }
     // preferred velocity -> position and preferred speed of the agent
     if (obar.x != T(0) || obar.y != T(0)) {
@@ -399,16 +413,22 @@ __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
 
 // ---- transposed neighbour lists ------------------------------------------------------
 // Exclusive scan of the in-degrees into instart[0..n] (one CTA; the counts are cleared
-// for csr_fill, which counts them again as it places the entries).
+// for csr_fill, which counts them again as it places the entries).  Each thread takes a
+// run of consecutive agents, read and written four at a time.
 constexpr int kCsrThreads = 1024;
 __global__ void __launch_bounds__(kCsrThreads) csr_scan_kernel(int n, uint32_t* __restrict__ incnt,
                                                                uint32_t* __restrict__ instart) {
     __shared__ uint32_t s_warp[kCsrThreads / 32];
-    const int per = (n + kCsrThreads - 1) / kCsrThreads;
+    const int per = ((n + kCsrThreads - 1) / kCsrThreads + 3) & ~3;
     const int b0 = threadIdx.x * per;
     const int b1 = b0 + per < n ? b0 + per : n;
     uint32_t sum = 0;
-    for (int b = b0; b < b1; ++b) sum += incnt[b];
+    int b = b0;
+    for (; b + 4 <= b1; b += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(incnt + b);
+        sum += v.x + v.y + v.z + v.w;
+    }
+    for (; b < b1; ++b) sum += incnt[b];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t inc = sum;
 #pragma unroll
@@ -424,7 +444,19 @@ __global__ void __launch_bounds__(kCsrThreads) csr_scan_kernel(int n, uint32_t* 
         total += s_warp[w];
     }
     uint32_t run = base + inc - sum;
-    for (int b = b0; b < b1; ++b) {
+    b = b0;
+    for (; b + 4 <= b1; b += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(incnt + b);
+        uint4 o;
+        o.x = run;
+        o.y = o.x + v.x;
+        o.z = o.y + v.y;
+        o.w = o.z + v.z;
+        run = o.w + v.w;
+        *reinterpret_cast<uint4*>(instart + b) = o;
+        *reinterpret_cast<uint4*>(incnt + b) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (; b < b1; ++b) {
         const uint32_t c = incnt[b];
         instart[b] = run;
         incnt[b] = 0u;
@@ -433,51 +465,63 @@ __global__ void __launch_bounds__(kCsrThreads) csr_scan_kernel(int n, uint32_t* 
     if (threadIdx.x == 0) instart[n] = total;
 }
 
-// Every (agent a, slot l) into the list of its neighbour b, in arrival order (adj_gather
-// sorts each list).
-__global__ void __launch_bounds__(256) csr_fill_kernel(int n, int K, const int32_t* __restrict__ nbr,
+// Every entry (agent a, q) with a neighbour into that neighbour's list, in arrival order
+// (adj_gather sorts each list).
+__global__ void __launch_bounds__(256) csr_fill_kernel(int n, const int32_t* __restrict__ ent,
                                                        uint32_t* __restrict__ incnt,
                                                        const uint32_t* __restrict__ instart,
                                                        uint32_t* __restrict__ inlist, int* err) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
-    for (int l = 0; l < K; ++l) {
-        const int b = nbr[(size_t)a * K + l];
-        if (b < 0) break;
-        if (!idx_ok(b < n, err)) break;
-        inlist[instart[b] + atomicAdd(incnt + b, 1u)] = (uint32_t)a * (uint32_t)K + (uint32_t)l;
+#pragma unroll
+    for (int q = 0; q < kAdjEntries; ++q) {
+        const int b = ent[(size_t)a * kAdjEntries + q];
+        if (b < 0) continue;
+        if (!idx_ok(b < n, err)) continue;
+        inlist[instart[b] + atomicAdd(incnt + b, 1u)] = (uint32_t)a * kAdjEntries + (uint32_t)q;
     }
 }
 
-// Agent b: its list sorted by (a, l) (insertion sort in place: lists are short -- the
-// in-degree of a k-nearest-neighbour graph in the plane is at most a small multiple of
-// k), then the contributions summed in that order into its adjoints and radius gradient,
-// plus the loss gradient of its position at this step (dl_dp, may be null).  Clears its
-// in-degree for the next step.
+// Agent b: its list sorted by entry index (agent, then line order) -- in shared memory when
+// it holds at most kGatherCap entries, in place otherwise -- then the contributions summed
+// in that order into its adjoints and radius gradient, plus the loss gradient of its
+// position at this step (dl_dp, may be null).  Clears its in-degree for the next step.
+constexpr int kGatherThreads = 128;
+constexpr int kGatherCap = 24;
 template <class T>
-__global__ void __launch_bounds__(256) adj_gather_kernel(AdjArgs<T> A) {
+__global__ void __launch_bounds__(kGatherThreads) adj_gather_kernel(AdjArgs<T> A) {
     using T2 = typename AdjArgs<T>::T2;
+    __shared__ uint32_t s_l[kGatherCap * kGatherThreads];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= A.n) return;
     const uint32_t s0 = A.instart[b], s1 = A.instart[b + 1];
-    uint32_t* lst = A.inlist;
-    for (uint32_t q = s0 + 1; q < s1; ++q) {
-        const uint32_t key = lst[q];
+    const uint32_t deg = s1 - s0;
+    uint32_t* lst = A.inlist + s0;
+    uint32_t stride = 1;
+    if (deg <= (uint32_t)kGatherCap) {
+        uint32_t* sl = s_l + threadIdx.x;  // element k at sl[k * kGatherThreads]
+        for (uint32_t q = 0; q < deg; ++q) sl[q * kGatherThreads] = lst[q];
+        lst = sl;
+        stride = kGatherThreads;
+    }
+    for (uint32_t q = 1; q < deg; ++q) {
+        const uint32_t key = lst[q * stride];
         uint32_t r = q;
-        while (r > s0 && lst[r - 1] > key) {
-            lst[r] = lst[r - 1];
+        while (r > 0 && lst[(r - 1) * stride] > key) {
+            lst[r * stride] = lst[(r - 1) * stride];
             --r;
         }
-        lst[r] = key;
+        lst[r * stride] = key;
     }
     T px = 0, py = 0, vx = 0, vy = 0, rr = 0;
-    for (uint32_t q = s0; q < s1; ++q) {
-        const T* c = A.contrib + (size_t)lst[q] * 5;
+    for (uint32_t q = 0; q < deg; ++q) {
+        const uint32_t e = lst[q * stride];
+        const T* c = A.contrib + 4 * (size_t)e;
         px += c[0];
         py += c[1];
         vx += c[2];
         vy += c[3];
-        rr += c[4];
+        rr += A.contrib_r[e];
     }
     T2 p = A.pbar[b], v = A.vbar[b];
     p.x += px;
@@ -505,9 +549,8 @@ cudaError_t launch_adjoint_step(const AdjArgs<T>& A, int kmax, cudaStream_t st) 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     csr_scan_kernel<<<1, kCsrThreads, 0, st>>>(A.n, A.incnt, A.instart);
-    csr_fill_kernel<<<(A.n + 255) / 256, 256, 0, st>>>(A.n, A.kstride, A.nbr, A.incnt, A.instart, A.inlist,
-                                                       A.err);
-    adj_gather_kernel<T><<<(A.n + 255) / 256, 256, 0, st>>>(A);
+    csr_fill_kernel<<<(A.n + 255) / 256, 256, 0, st>>>(A.n, A.ent, A.incnt, A.instart, A.inlist, A.err);
+    adj_gather_kernel<T><<<(A.n + kGatherThreads - 1) / kGatherThreads, kGatherThreads, 0, st>>>(A);
     return cudaGetLastError();
 }
 

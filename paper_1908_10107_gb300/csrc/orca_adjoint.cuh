@@ -24,6 +24,8 @@ struct Vec2Of<double> {
     using type = double2;
 };
 
+constexpr int kAdjEntries = 3;
+
 // One reverse step; everything in agent order.
 template <class T>
 struct AdjArgs {
@@ -47,10 +49,17 @@ struct AdjArgs {
     T* g_pref;              // parameter gradients (accumulated over the steps)
     T* g_radius;
     T* g_tau;
-    T* contrib;             // n * kstride * 5 scratch
+    // At most kAdjEntries half-planes of an agent carry an adjoint (the line or bisector
+    // its velocity lies on, the one that bounds it, line i of a least-penetration solve):
+    // entry a * kAdjEntries + q is one of them, with the neighbour it came from (ent, -1:
+    // none) and its contribution to that neighbour (contrib: pbar x, y, vbar x, y;
+    // contrib_r: radius)
+    int32_t* ent;           // n * kAdjEntries
+    T* contrib;             // n * kAdjEntries * 4
+    T* contrib_r;           // n * kAdjEntries
     uint32_t* incnt;        // n, zero on entry and on exit
     uint32_t* instart;      // n + 1
-    uint32_t* inlist;       // n * kstride
+    uint32_t* inlist;       // n * kAdjEntries
     int* err;               // the device error word (index checks of the ORCA_CHECKS build)
 };
 

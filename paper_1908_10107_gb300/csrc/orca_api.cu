@@ -232,7 +232,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     if (c->n_scenes > 0)
         e = launch_binning_batch(c->n, c->n_scenes, c->scenes, c->slot_scene, c->PV[0], c->bins, st);
     else
-        e = launch_binning(c->n, cs, pl.max_cells, c->PV[0], c->bins, st);
+        e = launch_binning(c->n, cs, pl.max_cells, c->PV[0], c->bins, par, st);
     if (e != cudaSuccess) return e;
     if (c->prof && (e = cudaEventRecordWithFlags(c->pev[1], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     e = launch_reorder(c->n, c->bins, c->PV[0], c->sorted, c->PR[par], c->PR[par ^ 1], st);
@@ -266,6 +266,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     a.slot_scene = c->n_scenes > 0 ? c->slot_scene : nullptr;
     a.rec_stride = pl.K;
     a.tape = nullptr;
+    if (c->n_scenes == 0) a.bbox_acc = c->bins.misc->bbox_acc[par ^ 1];
     e = launch_main(a, pl.K, c->shape, c->n_scenes > 0 ? c->resident : 0, st,
                     a.nseg > 0 && c->side.st ? &c->side : nullptr);
     if (e != cudaSuccess) return e;
@@ -287,7 +288,7 @@ static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, ui
                                           cudaStream_t st) {
     const Plan& pl = c->plan;
     float cs = c->p.cell_size > 0.0f ? c->p.cell_size : c->p.neighbor_dist * 0.25f;
-    cudaError_t e = launch_binning(c->n, cs, pl.max_cells, c->PV[0], c->bins, st);
+    cudaError_t e = launch_binning(c->n, cs, pl.max_cells, c->PV[0], c->bins, par, st);
     if (e != cudaSuccess) return e;
     e = launch_reorder(c->n, c->bins, c->PV[0], c->sorted, c->PR[par], c->PR[par ^ 1], st);
     if (e != cudaSuccess) return e;
@@ -315,6 +316,7 @@ static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, ui
     a.slot_scene = nullptr;
     a.rec_stride = pl.K;
     a.tape = tape;
+    a.bbox_acc = c->bins.misc->bbox_acc[par ^ 1];
     return launch_main(a, pl.K, c->shape, 0, st);
 }
 
@@ -382,12 +384,20 @@ static int check_device_error(orca_ctx* ctx, cudaStream_t st) {
     return ORCA_OK;
 }
 
+// Positions changed outside a step: the box the last step's ORCA kernel reduced no longer
+// holds, so the next step's bounding-box kernel scans.
+static cudaError_t clear_box(orca_ctx* ctx, cudaStream_t st) {
+    return cudaMemsetAsync(ctx->bins.misc->bbox_ok, 0, sizeof ctx->bins.misc->bbox_ok, st);
+}
+
 // Enqueue the write of agent-order positions / velocities (either may be null) into the
 // current slots, on st, without synchronising.  Pinned host arrays are read by one kernel
 // over the CPU-GPU link; other host arrays go through the staging buffers.
 static int enqueue_write_state(orca_ctx* ctx, const float* pos_xy, const float* vel_xy, int where,
                                cudaStream_t st) {
     const size_t N = (size_t)ctx->n;
+    // new positions: the next step scans for its bounding box
+    if (pos_xy) CK(clear_box(ctx, st), "clear box flags");
     const float2* pin = (const float2*)pos_xy;
     const float2* vin = (const float2*)vel_xy;
     if (where == ORCA_HOST) {
@@ -869,6 +879,7 @@ ORCA_API int orca_remove_arrived(orca_ctx* ctx, int32_t* n_remaining, int32_t* k
     // indices), digit histograms (tile sums), digit totals (the count); the survivors'
     // state goes through the readout staging buffers, their parameters to the other
     // parameter copy, which becomes the current one
+    CK(clear_box(ctx, st), "clear box flags");
     CK(launch_remove_arrived(n, ctx->PV[0], ctx->PR[par], ctx->PR[par ^ 1], ctx->stage[0],
                              ctx->stage[1], ctx->bins.keys[0], ctx->bins.keys[1],
                              ctx->bins.vals[0], ctx->bins.hist, ctx->bins.digit_totals, st),
@@ -930,6 +941,7 @@ ORCA_API int orca_spawn_agents(orca_ctx* ctx, int32_t m, const float* cand_pos, 
                      time_horizon};
     }
     int32_t* acc_dev = where == ORCA_DEVICE && accepted ? accepted : (int32_t*)ctx->bins.vals[0];
+    CK(clear_box(ctx, st), "clear box flags");
     CK(launch_spawn(n, ctx->PV[0], ctx->PR[par], m, in, window, ctx->bins.keys[1], ctx->bins.vals[1],
                     ctx->bins.keys[0], acc_dev, ctx->bins.digit_totals, st),
        "spawn kernels");
@@ -970,8 +982,8 @@ ORCA_API int orca_get_search_counters(orca_ctx* ctx, int64_t* counters4, void* s
 // the deterministic neighbour accumulation (per-slot contributions, transposed lists).
 struct RolloutPlan {
     int T, C, nseg;
-    size_t ckpt, goal, radius, vmax, pref, tau, seg_state, seg_nbr, seg_tape, adj, gscratch, contrib,
-        incnt, instart, inlist, total;
+    size_t ckpt, goal, radius, vmax, pref, tau, seg_state, seg_nbr, seg_tape, adj, gscratch, ent, contrib,
+        contrib_r, incnt, instart, inlist, total;
 };
 
 static RolloutPlan rollout_plan(const orca_ctx* c, int T, int C) {
@@ -992,10 +1004,12 @@ static RolloutPlan rollout_plan(const orca_ctx* c, int T, int C) {
     r.seg_tape = L.add((size_t)C * N * 4);
     r.adj = L.add(4 * N * 8);
     r.gscratch = L.add(3 * N * 4);
-    r.contrib = L.add(N * K * 5 * 4);
+    r.ent = L.add(N * kAdjEntries * 4);
+    r.contrib = L.add(N * kAdjEntries * 4 * 4);
+    r.contrib_r = L.add(N * kAdjEntries * 4);
     r.incnt = L.add(N * 4);
     r.instart = L.add((N + 1) * 4);
-    r.inlist = L.add(N * K * 4);
+    r.inlist = L.add(N * kAdjEntries * 4);
     r.total = L.total;
     return r;
 }
@@ -1118,7 +1132,9 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
             A.g_pref = gp;
             A.g_radius = gr;
             A.g_tau = gt;
+            A.ent = (int32_t*)(w + r.ent);
             A.contrib = (float*)(w + r.contrib);
+            A.contrib_r = (float*)(w + r.contrib_r);
             A.incnt = (uint32_t*)(w + r.incnt);
             A.instart = (uint32_t*)(w + r.instart);
             A.inlist = (uint32_t*)(w + r.inlist);

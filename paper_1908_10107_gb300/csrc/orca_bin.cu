@@ -64,10 +64,56 @@ __device__ GridDev derive_grid(float4 r, float cell_size, long long max_cells, i
 // inv = fl(1/s), g = floor(fl(fl(max - min) * inv)) + 1, doubling s while gx*gy exceeds
 // the table capacity.
 // ---------------------------------------------------------------------------------
+// Reset the box slot the step's ORCA kernel will fill and mark it as coming; called by
+// the first warp of one block (lane q resets copy q).
+__device__ __forceinline__ void open_next_box(DeviceMisc* misc, int slot, int lane) {
+    for (int q = lane; q < kBoxCopies; q += 32) {
+        int* acc = misc->bbox_acc[slot ^ 1] + q * kBoxStride;
+        acc[0] = acc[1] = float_order_code(INFINITY);
+        acc[2] = acc[3] = float_order_code(-INFINITY);
+    }
+    if (lane == 0) misc->bbox_ok[slot ^ 1] = 1u;
+}
+
 __global__ void __launch_bounds__(256) bbox_grid_kernel(int n, const float2* __restrict__ pos,
                                                         float cell_size, long long max_cells,
-                                                        float4* partials, DeviceMisc* misc) {
+                                                        float4* partials, DeviceMisc* misc,
+                                                        int slot) {
     pdl_wait();
+    // The previous step's ORCA kernel reduced the box of the positions it wrote: use it
+    // (the min / max are exact, so the grid is the one a scan would give).
+    if (slot >= 0 && misc->bbox_ok[slot]) {
+        if (blockIdx.x == 0 && threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int c0 = float_order_code(INFINITY), c1 = c0, c2 = float_order_code(-INFINITY), c3 = c2;
+            for (int q = lane; q < kBoxCopies; q += 32) {
+                const int* acc = misc->bbox_acc[slot] + q * kBoxStride;
+                c0 = min(c0, acc[0]);
+                c1 = min(c1, acc[1]);
+                c2 = max(c2, acc[2]);
+                c3 = max(c3, acc[3]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                c0 = min(c0, __shfl_xor_sync(0xffffffffu, c0, o));
+                c1 = min(c1, __shfl_xor_sync(0xffffffffu, c1, o));
+                c2 = max(c2, __shfl_xor_sync(0xffffffffu, c2, o));
+                c3 = max(c3, __shfl_xor_sync(0xffffffffu, c3, o));
+            }
+            open_next_box(misc, slot, lane);
+            if (lane == 0) {
+                const float4 r = make_float4(float_from_order_code(c0), float_from_order_code(c1),
+                                             float_from_order_code(c2), float_from_order_code(c3));
+                misc->bbox_ticket = 0;
+                misc->tile_counter = 0;
+                misc->obs_tiles = 0;
+                int err = 0;
+                misc->grid = derive_grid(r, cell_size, max_cells, &err);
+                if (err) atomicOr(&misc->error, err);
+            }
+        }
+        return;
+    }
     float xmin = INFINITY, ymin = INFINITY, xmax = -INFINITY, ymax = -INFINITY;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float2 p = pos[i];
@@ -123,6 +169,7 @@ __global__ void __launch_bounds__(256) bbox_grid_kernel(int n, const float2* __r
     __syncthreads();
     if (lane == 0) s_part[warp] = r;
     __syncthreads();
+    if (slot >= 0 && threadIdx.x < 32) open_next_box(misc, slot, threadIdx.x);
     if (threadIdx.x != 0) return;
     r = s_part[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
@@ -234,68 +281,70 @@ __device__ __forceinline__ uint32_t cell_block_scan(uint32_t v, uint32_t& total)
     return base + inc - v;
 }
 
-// The cell table from the counts, one tile of kCellTile cells per CTA (kCellsPerThread
-// consecutive cells per thread, read and written as 16-byte vectors): the tile starts at
-// the sum of the earlier tiles' counts (keys_count gathered them), then an exclusive scan
-// inside the tile.  The counts are cleared on the way for the next step, and the thread
-// whose range holds num_cells closes the table with cell_start[num_cells] = n.  CTAs past
-// the grid's last tile return at once (the launch covers the table's capacity).
+// The cell table from the counts, tiles of kCellTile cells (kCellsPerThread consecutive
+// cells per thread, read and written as 16-byte vectors): a tile starts at the sum of the
+// earlier tiles' counts (keys_count gathered them), then an exclusive scan inside the
+// tile.  The counts are cleared on the way for the next step, and the thread whose range
+// holds num_cells closes the table with cell_start[num_cells] = n.  CTA b takes tiles b,
+// b + gridDim.x, ... up to the grid's last one (the launch is sized for the table's
+// capacity, capped at two CTAs per SM, so a small grid costs few idle CTAs).
 __global__ void __launch_bounds__(kCellScanThreads) cell_scan_kernel(int n, const DeviceMisc* __restrict__ misc,
                                                                      uint32_t* __restrict__ cnt,
                                                                      const uint32_t* __restrict__ tile_sums,
                                                                      uint32_t* __restrict__ cell_start) {
     pdl_wait();
     const long long nc = misc->grid.num_cells;
-    const int tile = blockIdx.x;
-    if ((long long)tile * kCellTile > nc) return;  // the whole CTA
-    uint32_t pre = 0, tot = 0;
-    for (int b = threadIdx.x; b < tile; b += kCellScanThreads) pre += tile_sums[(size_t)b * kTileSumStride];
-    (void)cell_block_scan(pre, tot);  // every thread gets the sum of the earlier tiles
-    pre = tot;
-    const long long c0 = (long long)tile * kCellTile + (long long)threadIdx.x * kCellsPerThread;
-    const bool full = c0 + kCellsPerThread <= nc;
-    uint32_t v[kCellsPerThread];
-    if (full) {
-        const uint4* src = reinterpret_cast<const uint4*>(cnt + c0);
+#pragma unroll 1
+    for (int tile = blockIdx.x; (long long)tile * kCellTile <= nc; tile += gridDim.x) {
+        uint32_t pre = 0, tot = 0;
+        for (int b = threadIdx.x; b < tile; b += kCellScanThreads) pre += tile_sums[(size_t)b * kTileSumStride];
+        (void)cell_block_scan(pre, tot);  // every thread gets the sum of the earlier tiles
+        pre = tot;
+        const long long c0 = (long long)tile * kCellTile + (long long)threadIdx.x * kCellsPerThread;
+        const bool full = c0 + kCellsPerThread <= nc;
+        uint32_t v[kCellsPerThread];
+        if (full) {
+            const uint4* src = reinterpret_cast<const uint4*>(cnt + c0);
 #pragma unroll
-        for (int q = 0; q < kCellsPerThread / 4; ++q) {
-            const uint4 w = src[q];
-            v[4 * q] = w.x;
-            v[4 * q + 1] = w.y;
-            v[4 * q + 2] = w.z;
-            v[4 * q + 3] = w.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < kCellsPerThread; ++q) v[q] = c0 + q < nc ? cnt[c0 + q] : 0u;
-    }
-    uint32_t sum = 0;
-#pragma unroll
-    for (int q = 0; q < kCellsPerThread; ++q) sum += v[q];
-    uint32_t run = pre + cell_block_scan(sum, tot);
-#pragma unroll
-    for (int q = 0; q < kCellsPerThread; ++q) {
-        const uint32_t c = v[q];
-        v[q] = run;
-        run += c;
-    }
-    if (full) {
-        uint4* dst = reinterpret_cast<uint4*>(cell_start + c0);
-        uint4* clr = reinterpret_cast<uint4*>(cnt + c0);
-#pragma unroll
-        for (int q = 0; q < kCellsPerThread / 4; ++q) {
-            dst[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            clr[q] = make_uint4(0u, 0u, 0u, 0u);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < kCellsPerThread; ++q)
-            if (c0 + q < nc) {
-                cell_start[c0 + q] = v[q];
-                cnt[c0 + q] = 0u;
+            for (int q = 0; q < kCellsPerThread / 4; ++q) {
+                const uint4 w = src[q];
+                v[4 * q] = w.x;
+                v[4 * q + 1] = w.y;
+                v[4 * q + 2] = w.z;
+                v[4 * q + 3] = w.w;
             }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kCellsPerThread; ++q) v[q] = c0 + q < nc ? cnt[c0 + q] : 0u;
+        }
+        uint32_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < kCellsPerThread; ++q) sum += v[q];
+        uint32_t run = pre + cell_block_scan(sum, tot);
+#pragma unroll
+        for (int q = 0; q < kCellsPerThread; ++q) {
+            const uint32_t c = v[q];
+            v[q] = run;
+            run += c;
+        }
+        if (full) {
+            uint4* dst = reinterpret_cast<uint4*>(cell_start + c0);
+            uint4* clr = reinterpret_cast<uint4*>(cnt + c0);
+#pragma unroll
+            for (int q = 0; q < kCellsPerThread / 4; ++q) {
+                dst[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                clr[q] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kCellsPerThread; ++q)
+                if (c0 + q < nc) {
+                    cell_start[c0 + q] = v[q];
+                    cnt[c0 + q] = 0u;
+                }
+        }
+        if (c0 <= nc && nc < c0 + kCellsPerThread) cell_start[nc] = (uint32_t)n;
     }
-    if (c0 <= nc && nc < c0 + kCellsPerThread) cell_start[nc] = (uint32_t)n;
 }
 
 // Every agent to its slot cell_start[key] + rank: state and parameters read at the old
@@ -439,8 +488,12 @@ __global__ void __launch_bounds__(256) iota_kernel(int n, uint32_t* __restrict__
 // ---------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------
-// CTAs of the cell scan: enough tiles for the largest grid the table holds.
-static int scan_blocks(long long table_cells) { return (int)(table_cells / kCellTile + 1); }
+// CTAs of the cell scan: one per tile of the largest grid the table holds, at most two per
+// SM (152 SMs; each CTA loops over its tiles).
+static int scan_blocks(long long table_cells) {
+    const long long tiles = table_cells / kCellTile + 1;
+    return (int)(tiles < 304 ? tiles : 304);
+}
 
 // keys_count, cell_scan (the grid and the bounding box are already in misc).
 static cudaError_t launch_counting_sort(int n, const SceneDev* scenes, const int* slot_scene,
@@ -454,11 +507,12 @@ static cudaError_t launch_counting_sort(int n, const SceneDev* scenes, const int
 }
 
 cudaError_t launch_binning(int n, float cell_size, long long max_cells, const AgentState& cur,
-                           const BinBuffers& b, cudaStream_t st) {
+                           const BinBuffers& b, int slot, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int nb_bbox = (n + 255) / 256;
     if (nb_bbox > kBboxBlocks) nb_bbox = kBboxBlocks;
-    bbox_grid_kernel<<<nb_bbox, 256, 0, st>>>(n, cur.pos, cell_size, max_cells, b.bbox_partials, b.misc);
+    bbox_grid_kernel<<<nb_bbox, 256, 0, st>>>(n, cur.pos, cell_size, max_cells, b.bbox_partials, b.misc,
+                                              slot);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_counting_sort(n, nullptr, nullptr, cur, b, st);

@@ -59,6 +59,9 @@ __device__ __forceinline__ bool idx_ok(bool ok, int* err) {
     return true;
 }
 
+constexpr int kBoxCopies = 32;
+constexpr int kBoxStride = 32;  // ints: one 128-byte line per copy
+
 // Grid of square cells over the crowd's bounding box, computed on the device each step.
 struct GridDev {
     float xmin, ymin;  // exact minima over agents
@@ -76,7 +79,25 @@ struct DeviceMisc {
     unsigned int tile_counter; // next tile of the persistent ORCA kernel (reset every step)
     unsigned int obs_tiles;    // tiles listed for the obstacle launch (reset every step)
     unsigned long long counters[4];  // agent-steps, LP3 agent-steps, candidates, lines
+    // Single scene: the bounding box of the positions a step's ORCA kernel writes, reduced
+    // by that kernel (order-preserving integer codes of min x, min y, max x, max y), in
+    // the slot of the next step's parity; bbox_ok[s] says slot s holds the complete box
+    // of the current positions (cleared whenever positions change outside a step).  Each
+    // slot has kBoxCopies copies, one per 128-byte line, which the kernel's warps share
+    // out so that their atomics do not queue on one L2 line.
+    int bbox_acc[2][kBoxCopies * kBoxStride];
+    unsigned int bbox_ok[2];
 };
+
+// Order-preserving integer code of a float (a < b iff code(a) < code(b), NaN aside), for
+// min / max reductions with integer atomics.
+__device__ __forceinline__ int float_order_code(float f) {
+    const int k = __float_as_int(f);
+    return k >= 0 ? k : k ^ 0x7fffffff;
+}
+__device__ __forceinline__ float float_from_order_code(int k) {
+    return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff);
+}
 
 // One scene of a batch: its slot range (fixed: the sort keeps scenes contiguous), its
 // parameters and, recomputed every step, its grid and the offset of its cells in the
@@ -156,14 +177,16 @@ struct MainArgs {
     int* obs_tiles = nullptr;
     int32_t* rec_nbr;                    // n*k in agent order, or null
     uint32_t* rec_cell;                  // n in agent order, or null
+    int* bbox_acc = nullptr;             // single scene: the next step's box slot (copies), or null
 };
 
 // host launchers (orca_bin.cu, orca_main.cu)
 int main_blocks(int n);
 // bounding box and grid, cell keys and counts, cell table (cnt and tile_sums must be zero
 // on entry; they are zero again once the step's reorder has run)
+// slot: the step's parity (the box slot it reads; its ORCA kernel fills the other one)
 cudaError_t launch_binning(int n, float cell_size, long long max_cells, const AgentState& cur,
-                           const BinBuffers& b, cudaStream_t st);
+                           const BinBuffers& b, int slot, cudaStream_t st);
 cudaError_t launch_binning_batch(int n, int n_scenes, SceneDev* scenes, const int* slot_scene,
                                  const AgentState& cur, const BinBuffers& b, cudaStream_t st);
 cudaError_t launch_slot_scene(int n, int n_scenes, const SceneDev* scenes, int* slot_scene,

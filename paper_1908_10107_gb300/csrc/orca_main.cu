@@ -1249,6 +1249,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         }
         __syncthreads();
         // ---- phase 4: integrate
+        float bx0 = INFINITY, by0 = INFINITY, bx1 = -INFINITY, by1 = -INFINITY;
         if (active) {
             if (s_queued[tid]) {
                 float2 x = s_x[tid];
@@ -1261,6 +1262,27 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             a.out.vel[t] = make_float2(xx, xy);
             a.out.pos[t] = make_float2(nx, ny);
             if (TAPE) a.tape[me] = s_tape[TAPE ? tid : 0].pack();
+            bx0 = bx1 = nx;
+            by0 = by1 = ny;
+        }
+        // the box of the positions written, for the next step's grid (single scene): a
+        // warp reduction (fminf / fmaxf skip NaN, as the bounding-box scan does), then one
+        // atomic per bound on the warp's copy of the accumulator
+        if (a.bbox_acc) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+                by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+                bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+                by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+            }
+            if ((tid & 31) == 0 && bx0 <= bx1) {
+                int* acc = a.bbox_acc + ((blockIdx.x * (TPB / 32) + (tid >> 5)) % kBoxCopies) * kBoxStride;
+                atomicMin(acc + 0, float_order_code(bx0));
+                atomicMin(acc + 1, float_order_code(by0));
+                atomicMax(acc + 2, float_order_code(bx1));
+                atomicMax(acc + 3, float_order_code(by1));
+            }
         }
         // ---- counters: one shared-memory atomic per warp
         unsigned wc = __reduce_add_sync(0xffffffffu, cand);

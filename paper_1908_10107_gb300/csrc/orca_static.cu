@@ -146,7 +146,7 @@ extern "C" ORCA_API int orca_step_static(int32_t n, const float* pos_xy, const f
     // tile counts (zero after every completed call, cleared anyway)
     cudaError_t e = cudaMemsetAsync(base + L.misc, 0, kStatic.total - L.misc, st);
     if (e == cudaSuccess) e = launch_iota(n, src_p.id, st);
-    if (e == cudaSuccess) e = launch_binning(n, cs, kStaticMaxCells, src, bins, st);
+    if (e == cudaSuccess) e = launch_binning(n, cs, kStaticMaxCells, src, bins, -1, st);
     if (e == cudaSuccess) e = launch_reorder(n, bins, src, sorted, src_p, dst_p, st);
     if (e == cudaSuccess) {
         MainArgs a{};
