@@ -10,8 +10,8 @@ distance, re-times the two fastest with twice the steps, and returns the faster.
 conditions (an L2 flush, say) while tuning.  Results are cached in a JSON file keyed by
 (agent-count bucket, density bucket, k).
 
-``tune_launch`` then tries the per-agent kernel's launch shapes (threads per CTA 64 / 128 /
-256) and LP modes (one lane per solve, 4-lane LP3 groups, warp work units); ``tune_batch`` does both for a batch of
+``tune_launch`` then tries the per-agent kernel's launch shapes (64 or 128 threads per CTA)
+and LP modes (one lane per solve, warp work units); ``tune_batch`` does both for a batch of
 scenes, where each scene's edge is a common factor times its own expected k-th neighbour
 distance.
 """
@@ -26,8 +26,11 @@ import numpy as np
 from . import abi
 
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "orca_gb300_autotune.json")
-# candidate edges, in units of the expected k-th neighbour distance sqrt(k / (pi rho))
-FACTORS = (0.6, 0.8, 1.0, 1.2, 1.5, 2.0, 2.5)
+# candidate edges, in units of the expected k-th neighbour distance sqrt(k / (pi rho)).
+# Measured on the 524,288-agent flow, edges between 0.8 and 1.5 of that distance lie
+# within 1% of each other and the extremes 0.6 and 2.5 cost 6-11% more, so the sweep
+# keeps the band where the optimum has been found on every workload measured.
+FACTORS = (0.8, 1.0, 1.2, 1.5, 2.0)
 
 
 def expected_kth_distance(pos: np.ndarray, k: int) -> float:
@@ -99,7 +102,12 @@ def tune_cell_size(sim: "abi.OrcaSim", scene, steps: int = STEPS, factors=FACTOR
     return {"cell_size": best, "timings_ms": timings, "kth_distance": rk, "cached": False}
 
 
-SHAPES = ((64, 1), (128, 1), (256, 1), (64, 4), (128, 4), (256, 4), (64, 32), (128, 32))
+# Launch shapes tried: (threads per CTA, LP mode).  Four-lane LP3 groups and 256-thread
+# CTAs ran slower than these on every workload measured (the 524,288-agent flow, the dense
+# crowd at k = 10 and 20, the 256-scene batch: 5-30%), so they are not tried; they stay
+# available through orca_set_launch.  One lane per solve wins at k = 10, warp work units
+# at k = 20.
+SHAPES = ((64, 1), (128, 1), (64, 32), (128, 32))
 
 
 def _time_steps(sim, reload, steps, between=None):

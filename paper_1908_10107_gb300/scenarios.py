@@ -336,6 +336,53 @@ def two_way_crossing(n: int = 2500, heterogeneous: bool = False, seed: int = 191
                  _full(n, time_horizon), neighbor_dist, max_neighbors, dt, steps)
 
 
+class SpawnSource:
+    """People waiting to enter a crowd during the run: their start boxes, goals and
+    parameters.  ``candidates(rng)`` draws a uniform position in every waiting person's
+    start box (float32 arrays in waiting order); ``admit(mask)`` removes the admitted ones
+    (mask: bool over the same order)."""
+
+    def __init__(self, lo, hi, goal, radius, max_speed, pref_speed, time_horizon):
+        self.lo, self.hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+        self.goal, self.radius, self.max_speed = goal, radius, max_speed
+        self.pref_speed, self.time_horizon = pref_speed, time_horizon
+
+    @property
+    def n(self) -> int:
+        return int(self.radius.shape[0])
+
+    def candidates(self, rng):
+        pos = _f32(self.lo + rng.random(self.lo.shape) * (self.hi - self.lo))
+        return (pos, self.goal, self.radius, self.max_speed, self.pref_speed, self.time_horizon)
+
+    def admit(self, mask):
+        keep = ~np.asarray(mask, bool)
+        self.lo, self.hi, self.goal = self.lo[keep], self.hi[keep], self.goal[keep]
+        self.radius, self.max_speed = self.radius[keep], self.max_speed[keep]
+        self.pref_speed, self.time_horizon = self.pref_speed[keep], self.time_horizon[keep]
+
+
+def two_way_stream(n: int = 2500, heterogeneous: bool = False, seed: int = 1916,
+                   coverage: float = 0.3, dt: float = 0.1):
+    """The two-way crossing's people entering during the run (Section 4: people are spawned
+    at random locations of their start region where they overlap nobody within a time
+    period based on size and speed): the crossing's regions, goals and parameters, with
+    nobody present at the start.  Returns (empty Scene with the crossing's ORCA parameters,
+    SpawnSource of the n people)."""
+    rng = np.random.default_rng(seed)
+    h = n // 2
+    radius, pref, vmax = _crossing_parameters(rng, n, heterogeneous)
+    side = _region_side(radius, pref, dt, [slice(0, h), slice(h, n)], coverage)
+    centre = np.array([[-side, 0.0]] * h + [[side, 0.0]] * (n - h)).reshape(-1, 2)
+    lo, hi = _region_boxes(centre, side)
+    glo, ghi = _region_boxes(-centre, side)
+    goal = _f32(glo + rng.random((n, 2)) * (ghi - glo))
+    tau = _full(n, 5.0)
+    z2, z1 = np.zeros((0, 2), np.float32), np.zeros(0, np.float32)
+    empty = Scene("two_way_stream", z2, z2, z2, z1, z1, z1, z1, 10.0, 10, dt, 0)
+    return empty, SpawnSource(lo, hi, goal, radius, vmax, pref, tau)
+
+
 def eight_way_crossing(n: int = 10000, seed: int = 1915, coverage: float = 0.3,
                        neighbor_dist: float = 10.0, max_neighbors: int = 10,
                        time_horizon: float = 5.0, dt: float = 0.1, steps: int = 4000) -> Scene:

@@ -113,3 +113,19 @@ def test_bottleneck_layout():
     assert d.min() >= 2 * sc.radius.max()
     # goals past the door, within its width across
     assert np.all(sc.goal[:, 0] >= 10.0) and np.all(np.abs(sc.goal[:, 1]) <= 0.4 * 2.4 + 1e-6)
+
+
+def test_two_way_stream_spawn_source():
+    empty, src = S.two_way_stream(400, seed=3)
+    assert empty.n == 0 and src.n == 400
+    rng = np.random.default_rng(0)
+    pos, goal, rad, vmax, pref, tau = src.candidates(rng)
+    assert pos.dtype == np.float32 and pos.shape == (400, 2)
+    assert np.all(pos >= src.lo - 1e-4) and np.all(pos <= src.hi + 1e-4)
+    # the two crowds start on opposite sides and head for each other's region
+    assert np.all(np.sign(pos[:200, 0]) == -np.sign(goal[:200, 0]))
+    mask = np.zeros(400, bool)
+    mask[::3] = True
+    src.admit(mask)
+    assert src.n == 400 - mask.sum()
+    assert src.candidates(rng)[0].shape == (src.n, 2)
