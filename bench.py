@@ -538,6 +538,40 @@ def run_crossing(args):
                       "agent_steps": agent_steps, "agent_steps_per_s": agent_steps / wall,
                       "ms_per_step": 1e3 * wall / max(steps, 1), "removals": removals}
         sim.close()
+    # the same crossing with the people entering during the run (Section 4's spawning):
+    # every `every` steps each waiting person gets a random spot in its start region and is
+    # admitted unless it could touch someone within the next `every` steps
+    empty, _ = scenarios.two_way_stream(2500)
+    for timed in (False, True):
+        _, source = scenarios.two_way_stream(2500)
+        sim = abi.OrcaSim(max_agents=2500, max_neighbors=empty.max_neighbors,
+                          neighbor_dist=empty.neighbor_dist, dt=empty.dt)
+        sim.set_scene(empty)
+        rng = np.random.default_rng(1917)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, agent_steps, n, waves, last_entry = 0, 0, 0, 0, 0
+        while (source.n > 0 or n > 0) and steps < args.crossing_max_steps:
+            if source.n > 0:
+                admitted = sim.spawn(*source.candidates(rng), window=every * float(empty.dt))
+                source.admit(admitted)
+                waves += 1
+                n = sim.n
+                if admitted.any():
+                    last_entry = steps
+            sim.step(every)
+            steps += every
+            agent_steps += n * every
+            n = abi.orca_remove_arrived(sim.ctx)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        sim.close()
+    runs["two_way_2500_spawned_during_the_run"] = {
+        "agents": 2500, "steps_until_all_arrived": steps if n == 0 and source.n == 0 else None,
+        "agents_left": n + source.n, "simulated_s": steps * float(empty.dt), "wall_s": wall,
+        "agent_steps": agent_steps, "agent_steps_per_s": agent_steps / wall,
+        "ms_per_step": 1e3 * wall / max(steps, 1), "spawn_waves": waves,
+        "last_entry_step": last_entry}
     sweep = []
     for n in (2500, 10000, 50000, 100000, 500000):
         sc = scenarios.two_way_crossing(n)
@@ -623,6 +657,45 @@ def run_lp_ab(args):
             "config": {"workload": "LP-mode A/B on the 524,288-agent flow (early and later steps), "
                                    "the 2,097,152-agent dense crowd (k 20) and the eight-way crossing"},
             "cases": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_table(args):
+    """The five configurations side by side (GPU and, where it runs in seconds, the FP64
+    oracle on the host cores): the 1,024-agent circle swap (100 steps both), the
+    524,288-agent flow (20 steps both), the 2,097,152-agent dense crowd at k = 20 (GPU 100
+    steps, oracle 3 steps); the batch and the forward + adjoint rollout come from their own
+    workloads.  GPU: default cell edge r_obs / 4 autotuned, CUDA events, L2 flushed
+    between steps."""
+    import torch
+    from paper_1908_10107_gb300 import abi, autotune, scenarios
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rows = {}
+    for name, sc, gpu_steps, cpu_steps in (("circle_swap_1024", scenarios.circle_swap(), 100, 100),
+                                           ("bidirectional_524288", scenarios.bidirectional(), 20, 20),
+                                           ("dense_2097152_k20", scenarios.dense(), 100, 3)):
+        sim = abi.OrcaSim.for_scene(sc)
+        sim.set_scene(sc)
+        tune = autotune.tune_cell_size(sim, sc, use_cache=False, cache_path=None,
+                                       between=lambda: flush.fill_(0x5a))
+        shape = autotune.tune_launch(sim, lambda: sim.set_scene(sc), between=lambda: flush.fill_(0x5a))
+        sim.set_scene(sc)
+        ms = timed_steps(torch, lambda: sim.step(1), gpu_steps, args.warmup, flush, stream) / gpu_steps
+        sim.close()
+        cpu = cpu_baseline(sc, budget_s=1e9, max_steps=cpu_steps)
+        rows[name] = {"agents": sc.n, "gpu_ms_per_step": ms, "gpu_agent_steps_per_s": sc.n / (ms * 1e-3),
+                      "hbm_frac_128B": STEP_BYTES_PER_AGENT * sc.n / (ms * 1e-3) / 1e9 / peaks()[0],
+                      "gpu_steps": gpu_steps, "cell_m": tune["cell_size"], "shape": list(shape["shape"]),
+                      "cpu_ms_per_step": sc.n / cpu["value"] * 1e3, "cpu_agent_steps_per_s": cpu["value"],
+                      "cpu_sample": cpu["sample"], "cpu_cores": cpu["cores"], "cpu_model": cpu["cpu_model"]}
+    line = {"metric": "configurations table: GPU and FP64-oracle agent-steps/sec", "value":
+            rows["bidirectional_524288"]["gpu_agent_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": 20, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": "circle swap 1,024; bidirectional flow 524,288; dense 2,097,152 "
+                                   "(k 20)", "l2": "flushed between steps"}, "rows": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -868,7 +941,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--clocks-out", default=None)
     ap.add_argument("--workload", choices=["plain", "batched", "adjoint", "crossing", "lp_ab", "obstacles",
-                                           "dense"], default="plain")
+                                           "dense", "table"], default="plain")
     ap.add_argument("--dense-steps", type=int, default=100, help="dense workload: timed steps")
     ap.add_argument("--obst-steps", type=int, default=50, help="obstacles workload: timed steps")
     ap.add_argument("--no-evacuation", dest="evacuation", action="store_false",
@@ -898,6 +971,9 @@ def main():
         return
     if args.workload == "dense" and args.impl == "ours":
         run_dense(args)
+        return
+    if args.workload == "table" and args.impl == "ours":
+        run_table(args)
         return
     if args.workload == "obstacles" and args.impl == "ours":
         run_obstacles(args)
