@@ -1163,7 +1163,8 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                     a.rec_obst ? a.rec_obst + (size_t)me * kMaxObstacleNeighbors : nullptr);
             // park the neighbours' slots in the row (one unrolled store each), then build
             // the half-planes in a rolled loop: one copy of the line code keeps the kernel
-            // small enough for the instruction cache
+            // small enough for the instruction cache.  The next neighbour's record and
+            // velocity are loaded while the current half-plane is built.
 #pragma unroll
             for (int l = 0; l < KMAX; ++l) {
                 if (l >= KMAX - sv.k && kk[l] != ~0ull) {
@@ -1178,10 +1179,26 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             float itau = __fdividef(1.0f, a.prm.tau[t]);
             float idt = __fdividef(1.0f, dt);
             float half_idt = 0.5f * idt;
+            {
+                const int lend = nob + cnt;
+                float4 nm = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                float2 nv = make_float2(0.0f, 0.0f);
+                if (nob < lend) {
+                    const int q = __float_as_int(row[nob].w);
+                    nm = a.in.msg[q];
+                    nv = a.in.vel[q];
+                }
 #pragma unroll 1
-            for (int l = nob; l < nob + cnt; ++l) {
-                int q = __float_as_int(row[l].w);
-                row[l] = orca_line_dev(p, v, me4.z, itau, dt, half_idt, me, a.in.msg[q], a.in.vel[q]);
+                for (int l = nob; l < lend; ++l) {
+                    const float4 cm = nm;
+                    const float2 cv = nv;
+                    if (l + 1 < lend) {
+                        const int q = __float_as_int(row[l + 1].w);
+                        nm = a.in.msg[q];
+                        nv = a.in.vel[q];
+                    }
+                    row[l] = orca_line_dev(p, v, me4.z, itau, dt, half_idt, me, cm, cv);
+                }
             }
             if (a.rec_nbr) {
                 int w = 0;
