@@ -439,8 +439,10 @@ def fd_check_patch(sc, T, C, rel=1e-3, m=64, seed=0):
 
 def run_adjoint(args):
     """Forward + adjoint rollout of the differentiable workload (16,384-agent flow, 64 steps
-    at dt 0.1 s, checkpoints every 8 steps, loss = mean squared position error against a
-    rollout with perturbed parameters) against the plain step on the same crowd."""
+    at dt 0.1 s, loss = mean squared position error against a rollout with perturbed
+    parameters) against the plain step on the same crowd, in both rollout modes: every step
+    recorded by the forward pass (ckpt_every = 0, the headline) and checkpoints every 8
+    steps with the segments re-run by the backward pass."""
     import torch
     from paper_1908_10107_gb300 import abi, adjoint, scenarios
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -456,23 +458,27 @@ def run_adjoint(args):
         tgt = adjoint.rollout(sim, pos0, vel0, goal, tr, vmax, tp, tt, T, C)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    fwd_ms, bwd_ms = [], []
-    for rep in range(args.warmup + max(args.steps // 100, 5)):
-        for t in (radius, pref, tau):
-            t.grad = None
-            t.requires_grad_(True)
-        flush.fill_(rep & 0xff)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        traj = adjoint.rollout(sim, pos0, vel0, goal, radius, vmax, pref, tau, T, C)
-        loss = adjoint.mse_trajectory_loss(traj, tgt)
-        e1.record(stream)
-        loss.backward()
-        e2.record(stream)
-        torch.cuda.synchronize()
-        if rep >= args.warmup:
-            fwd_ms.append(e0.elapsed_time(e1))
-            bwd_ms.append(e1.elapsed_time(e2))
+    modes = {}
+    for mode in (0, C):
+        fwd_ms, bwd_ms = [], []
+        for rep in range(args.warmup + max(args.steps // 100, 5)):
+            for t in (radius, pref, tau):
+                t.grad = None
+                t.requires_grad_(True)
+            flush.fill_(rep & 0xff)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            traj = adjoint.rollout(sim, pos0, vel0, goal, radius, vmax, pref, tau, T, mode)
+            loss = adjoint.mse_trajectory_loss(traj, tgt)
+            e1.record(stream)
+            loss.backward()
+            e2.record(stream)
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                fwd_ms.append(e0.elapsed_time(e1))
+                bwd_ms.append(e1.elapsed_time(e2))
+        modes[mode] = (float(np.median(fwd_ms)), float(np.median(bwd_ms)),
+                       abi.orca_rollout_workspace_size(sim.ctx, T, mode))
     # the plain step on the same crowd: T steps through the graph
     sim.set_scene(sc)
     plain = []
@@ -487,19 +493,25 @@ def run_adjoint(args):
         if rep >= args.warmup:
             plain.append(e0.elapsed_time(e1))
     sim.close()
-    f, b, pl = float(np.median(fwd_ms)), float(np.median(bwd_ms)), float(np.median(plain))
+    pl = float(np.median(plain))
+    f, b, ws = modes[0]
+    fc, bc, wsc = modes[C]
     check = None if args.no_fd_check else {f"T{h}": fd_check_patch(sc, h, C) for h in (8, 16, T)}
     line = {
         "metric": "forward+adjoint ORCA rollout agent-steps/sec (16,384 agents, 64 steps)",
         "value": n * T / ((f + b) * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": T,
         "warmup": args.warmup, "ms_per_step": (f + b) / T, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-        "config": {"workload": "bidirectional flow, 16,384 agents, dt 0.1 s, 64 steps, checkpoint "
-                               "every 8; loss = mean squared position error against a rollout with "
-                               "perturbed pref speed / radius / tau", "n_agents": n},
+        "config": {"workload": "bidirectional flow, 16,384 agents, dt 0.1 s, 64 steps, every step "
+                               "recorded by the forward pass; loss = mean squared position error "
+                               "against a rollout with perturbed pref speed / radius / tau",
+                   "n_agents": n, "workspace_bytes": ws},
         "forward_ms": f, "backward_ms": b, "plain_ms_for_T_steps": pl,
         "plain_value": n * T / (pl * 1e-3),
         "forward_adjoint_over_plain": (f + b) / pl,
+        "checkpointed_every_8": {"value": n * T / ((fc + bc) * 1e-3), "forward_ms": fc,
+                                 "backward_ms": bc, "forward_adjoint_over_plain": (fc + bc) / pl,
+                                 "workspace_bytes": wsc},
         "fd_check_64_agent_patch_by_horizon": check,
     }
     print(json.dumps(line), flush=True)

@@ -446,9 +446,13 @@ ORCA_API int orca_set_launch(orca_ctx* ctx, int32_t threads_per_block, int32_t l
  * with respect to every agent's preferred speed, radius and time horizon (and initial
  * position and velocity).  The adjoint is hand-written: it differentiates each step
  * through the constraints that fixed the selected velocity, with neighbour sets and every
- * branch held fixed (the step is piecewise smooth).  The forward pass keeps a checkpoint
- * of the state every ckpt_every steps; the backward pass re-runs each segment from its
- * checkpoint, recording, and sweeps it in reverse.
+ * branch held fixed (the step is piecewise smooth).  With ckpt_every >= 1 the forward pass
+ * keeps a checkpoint of the state every ckpt_every steps and the backward pass re-runs each
+ * segment from its checkpoint, recording, and sweeps it in reverse (memory for ckpt_every
+ * steps' records).  With ckpt_every = 0 the forward pass records every step (state,
+ * neighbour lists, LP records: (20 + 4 max_neighbors) bytes per agent-step) and the
+ * backward pass only sweeps them in reverse, with no recomputation.  Both modes give
+ * bitwise the same trajectory and gradients.
  *
  * orca_rollout_workspace_size: device bytes for (T, ckpt_every) on this context.
  */
@@ -456,7 +460,8 @@ ORCA_API int orca_rollout_workspace_size(const orca_ctx* ctx, int32_t T, int32_t
                                          size_t* bytes);
 
 /*
- * Run T >= 1 steps from the loaded state, checkpointing every ckpt_every >= 1 steps.
+ * Run T >= 1 steps from the loaded state, checkpointing every ckpt_every >= 1 steps, or
+ * recording every step (ckpt_every = 0).
  *   traj_pos  device, T*n*2 floats: p(t) for t = 1..T in agent order (may be NULL).
  *   workspace device buffer of orca_rollout_workspace_size bytes, 256-byte aligned, kept by
  *             the caller until orca_rollout_backward.

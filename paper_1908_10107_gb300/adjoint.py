@@ -6,8 +6,9 @@ library, as a differentiable function of pos0, vel0, radius, pref_speed and time
 The backward pass is the library's hand-written adjoint (orca_rollout_backward): each step
 is differentiated through the constraints that fixed the selected velocity, with the
 neighbour sets and all branches held fixed, re-running each checkpoint segment
-(``ckpt_every`` steps) to recover the records it needs.  goal and max_speed get no
-gradient.
+(``ckpt_every`` steps) to recover the records it needs, or, with ``ckpt_every = 0``,
+sweeping the records the forward pass kept of every step ((20 + 4 k) bytes per
+agent-step of device memory, no recomputation).  goal and max_speed get no gradient.
 
 Any loss built from the trajectory in PyTorch can then be back-propagated, e.g. the mean
 squared position error against a target rollout.

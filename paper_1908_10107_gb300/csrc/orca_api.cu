@@ -986,11 +986,13 @@ struct RolloutPlan {
         contrib_r, incnt, instart, inlist, total;
 };
 
+// C = 0: one segment of T steps, recorded by the forward pass itself.
 static RolloutPlan rollout_plan(const orca_ctx* c, int T, int C) {
     RolloutPlan r;
     r.T = T;
     r.C = C;
-    r.nseg = (T + C - 1) / C;
+    r.nseg = C > 0 ? (T + C - 1) / C : 1;
+    const size_t S = (size_t)(C > 0 ? C : T);  // steps recorded at once
     size_t N = (size_t)(c->n > 0 ? c->n : 1), K = (size_t)c->plan.K;
     Layout L;
     r.ckpt = L.add((size_t)(r.nseg + 1) * N * 16);
@@ -999,9 +1001,9 @@ static RolloutPlan rollout_plan(const orca_ctx* c, int T, int C) {
     r.vmax = L.add(N * 4);
     r.pref = L.add(N * 4);
     r.tau = L.add(N * 4);
-    r.seg_state = L.add((size_t)(C + 1) * N * 16);
-    r.seg_nbr = L.add((size_t)C * N * K * 4);
-    r.seg_tape = L.add((size_t)C * N * 4);
+    r.seg_state = L.add((S + 1) * N * 16);
+    r.seg_nbr = L.add(S * N * K * 4);
+    r.seg_tape = L.add(S * N * 4);
     r.adj = L.add(4 * N * 8);
     r.gscratch = L.add(3 * N * 4);
     r.ent = L.add(N * kAdjEntries * 4);
@@ -1016,7 +1018,7 @@ static RolloutPlan rollout_plan(const orca_ctx* c, int T, int C) {
 
 ORCA_API int orca_rollout_workspace_size(const orca_ctx* ctx, int32_t T, int32_t ckpt_every,
                                          size_t* bytes) {
-    if (!ctx || !bytes || T < 1 || ckpt_every < 1) return ORCA_ERR_ARG;
+    if (!ctx || !bytes || T < 1 || ckpt_every < 0) return ORCA_ERR_ARG;
     *bytes = rollout_plan(ctx, T, ckpt_every).total;
     return ORCA_OK;
 }
@@ -1026,7 +1028,7 @@ ORCA_API int orca_rollout_forward(orca_ctx* ctx, int32_t T, int32_t ckpt_every, 
     NvtxRange nvtx_range("orca_rollout_forward");
     if (!ctx) return ORCA_ERR_ARG;
     ctx->slot_ok = false;  // rollouts reload and step the state on their own
-    if (T < 1 || ckpt_every < 1) return fail(ctx, ORCA_ERR_ARG, "T and ckpt_every must be >= 1");
+    if (T < 1 || ckpt_every < 0) return fail(ctx, ORCA_ERR_ARG, "T must be >= 1 and ckpt_every >= 0");
     if (ctx->n_scenes > 0) return fail(ctx, ORCA_ERR_STATE, "rollouts need a single scene");
     if (ctx->nseg > 0) return fail(ctx, ORCA_ERR_STATE, "the adjoint has no static obstacles");
     if (ctx->n < 1) return fail(ctx, ORCA_ERR_STATE, "no agents loaded");
@@ -1040,6 +1042,25 @@ ORCA_API int orca_rollout_forward(orca_ctx* ctx, int32_t T, int32_t ckpt_every, 
     CK(launch_unpermute_params(ctx->n, ctx->PR[ctx->cur], (float2*)(w + r.goal), (float*)(w + r.radius),
                                (float*)(w + r.vmax), (float*)(w + r.pref), (float*)(w + r.tau), st),
        "unpermute parameters");
+    if (ckpt_every == 0) {
+        // every step recorded as the backward pass needs it: the state it starts from, the
+        // neighbour lists and the LP records
+        for (int t = 0; t < T; ++t) {
+            float2* sp = (float2*)(w + r.seg_state + (size_t)t * N * 16);
+            CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, sp, sp + N, st), "step state");
+            CK(enqueue_recording_step(ctx, ctx->cur, (int32_t*)(w + r.seg_nbr) + (size_t)t * N * ctx->plan.K,
+                                      (uint32_t*)(w + r.seg_tape) + (size_t)t * N, st),
+               "recording step");
+            ctx->cur ^= 1;
+            if (traj_pos)
+                CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (float2*)traj_pos + (size_t)t * N,
+                                    nullptr, st), "trajectory");
+        }
+        ctx->roll_T = T;
+        ctx->roll_C = 0;
+        ctx->roll_ws = workspace;
+        return ORCA_OK;
+    }
     CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, ck(0), ck(0) + N, st), "checkpoint");
     for (int t = 0; t < T; ++t) {
         int rr = orca_step(ctx, 1, stream);
@@ -1094,13 +1115,16 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
     CK(cudaMemsetAsync(vnext, 0, N * 8, st), "zero");
     CK(cudaMemsetAsync(w + r.incnt, 0, N * 4, st), "zero");
     for (int seg = r.nseg - 1; seg >= 0; --seg) {
-        int t0 = seg * C, t1 = t0 + C < T ? t0 + C : T;
-        int rr = orca_set_agents(ctx, n, (const float*)ck(seg), (const float*)(ck(seg) + N),
-                                 (const float*)(w + r.goal), (const float*)(w + r.radius),
-                                 (const float*)(w + r.vmax), (const float*)(w + r.pref),
-                                 (const float*)(w + r.tau), ORCA_DEVICE, stream);
-        if (rr != ORCA_OK) return rr;
-        for (int t = t0; t < t1; ++t) {
+        // C = 0: the forward pass recorded all T steps (one segment, nothing to re-run)
+        const int t0 = seg * C, t1 = C > 0 && t0 + C < T ? t0 + C : T;
+        if (C > 0) {
+            int rr = orca_set_agents(ctx, n, (const float*)ck(seg), (const float*)(ck(seg) + N),
+                                     (const float*)(w + r.goal), (const float*)(w + r.radius),
+                                     (const float*)(w + r.vmax), (const float*)(w + r.pref),
+                                     (const float*)(w + r.tau), ORCA_DEVICE, stream);
+            if (rr != ORCA_OK) return rr;
+        }
+        for (int t = t0; C > 0 && t < t1; ++t) {
             float2* sp = sstate(t - t0);
             CK(launch_unpermute(n, ctx->PV[0], ctx->PR[ctx->cur].id, sp, sp + N, st), "segment state");
             CK(enqueue_recording_step(ctx, ctx->cur, (int32_t*)(w + r.seg_nbr) + (size_t)(t - t0) * N * K,

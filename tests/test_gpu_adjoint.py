@@ -167,6 +167,20 @@ def test_checkpoint_spacing_does_not_change_gradients(torch):
         np.testing.assert_allclose(a[key], c[key], atol=1e-5 * scale)
 
 
+def test_recording_forward_pass_gives_the_same_gradients(torch):
+    """ckpt_every = 0: the forward pass records every step and the backward pass re-runs
+    nothing; the recorded steps are the same arithmetic as the re-run ones, so trajectory
+    and gradients are bitwise those of the checkpointed modes."""
+    sc = S.jitter_velocities(S.bidirectional(3000, seed=36), 36)
+    W = np.random.default_rng(4).standard_normal((11, sc.n, 2))
+    rec = gpu_grads(torch, sc, W, 11, 0)
+    for C in (1, 4):
+        ck = gpu_grads(torch, sc, W, 11, C)
+        for key in ("traj", "pref", "radius", "tau", "pos0", "vel0"):
+            np.testing.assert_array_equal(rec[key], ck[key])
+    assert np.abs(rec["radius"]).max() > 0
+
+
 def test_autograd_function(torch):
     from paper_1908_10107_gb300 import adjoint
     sc = S.bidirectional(1500, seed=35)
