@@ -17,12 +17,13 @@
 // is not added with atomics (whose order, and so whose rounding, varies between runs):
 //   adj_agent   one thread per agent a writes its own adjoints and, for each of the (at
 //               most three) half-planes that fix its velocity, the contribution to that
-//               half-plane's neighbour in an entry of its own; it counts the entries
-//               every agent receives (its in-degree);
-//   csr_scan    the in-degrees become the offsets of a transposed list;
-//   csr_fill    every entry is placed in its neighbour's list;
+//               half-plane's neighbour in an entry of its own, whose index it appends to
+//               the neighbour's list (an atomic counter gives the place; up to kInCap
+//               places per agent);
 //   adj_gather  one thread per agent b sorts its list by entry (agent, then line) and adds
-//               the contributions in that order (and the loss gradient of its position).
+//               the contributions in that order (and the loss gradient of its position);
+//               an agent that received more than kInCap entries finds them all by a scan
+//               of every agent's entries, which meets them in the same order.
 // Every sum is then taken in a fixed order and the gradients are bitwise reproducible.
 //
 // The kernels are templates on the scalar type: float for rollouts of the FP32 step, and
@@ -381,7 +382,8 @@ __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
         c[3] = vbbar.y;
         A.contrib_r[e] = Rbar;
         my_ent[q] = b;
-        atomicAdd(A.incnt + b, 1u);  // integer: the count is exact in any order
+        const uint32_t at = atomicAdd(A.incnt + b, 1u);  // integer: exact in any order
+        if (at < (uint32_t)kInCap) A.inlist[(size_t)b * kInCap + at] = (uint32_t)e;
     }
     // preferred velocity -> position and preferred speed of the agent
     if (obar.x != T(0) || obar.y != T(0)) {
@@ -411,117 +413,47 @@ __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
     A.g_tau[a] += -itaubar * itau * itau;
 }
 
-// ---- transposed neighbour lists ------------------------------------------------------
-// Exclusive scan of the in-degrees into instart[0..n] (one CTA; the counts are cleared
-// for csr_fill, which counts them again as it places the entries).  Each thread takes a
-// run of consecutive agents, read and written four at a time.
-constexpr int kCsrThreads = 1024;
-__global__ void __launch_bounds__(kCsrThreads) csr_scan_kernel(int n, uint32_t* __restrict__ incnt,
-                                                               uint32_t* __restrict__ instart) {
-    __shared__ uint32_t s_warp[kCsrThreads / 32];
-    const int per = ((n + kCsrThreads - 1) / kCsrThreads + 3) & ~3;
-    const int b0 = threadIdx.x * per;
-    const int b1 = b0 + per < n ? b0 + per : n;
-    uint32_t sum = 0;
-    int b = b0;
-    for (; b + 4 <= b1; b += 4) {
-        const uint4 v = *reinterpret_cast<const uint4*>(incnt + b);
-        sum += v.x + v.y + v.z + v.w;
-    }
-    for (; b < b1; ++b) sum += incnt[b];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    uint32_t base = 0, total = 0;
-    for (int w = 0; w < kCsrThreads / 32; ++w) {
-        if (w < warp) base += s_warp[w];
-        total += s_warp[w];
-    }
-    uint32_t run = base + inc - sum;
-    b = b0;
-    for (; b + 4 <= b1; b += 4) {
-        const uint4 v = *reinterpret_cast<const uint4*>(incnt + b);
-        uint4 o;
-        o.x = run;
-        o.y = o.x + v.x;
-        o.z = o.y + v.y;
-        o.w = o.z + v.z;
-        run = o.w + v.w;
-        *reinterpret_cast<uint4*>(instart + b) = o;
-        *reinterpret_cast<uint4*>(incnt + b) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    for (; b < b1; ++b) {
-        const uint32_t c = incnt[b];
-        instart[b] = run;
-        incnt[b] = 0u;
-        run += c;
-    }
-    if (threadIdx.x == 0) instart[n] = total;
-}
-
-// Every entry (agent a, q) with a neighbour into that neighbour's list, in arrival order
-// (adj_gather sorts each list).
-__global__ void __launch_bounds__(256) csr_fill_kernel(int n, const int32_t* __restrict__ ent,
-                                                       uint32_t* __restrict__ incnt,
-                                                       const uint32_t* __restrict__ instart,
-                                                       uint32_t* __restrict__ inlist, int* err) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n) return;
-#pragma unroll
-    for (int q = 0; q < kAdjEntries; ++q) {
-        const int b = ent[(size_t)a * kAdjEntries + q];
-        if (b < 0) continue;
-        if (!idx_ok(b < n, err)) continue;
-        inlist[instart[b] + atomicAdd(incnt + b, 1u)] = (uint32_t)a * kAdjEntries + (uint32_t)q;
-    }
-}
-
-// Agent b: its list sorted by entry index (agent, then line order) -- in shared memory when
-// it holds at most kGatherCap entries, in place otherwise -- then the contributions summed
-// in that order into its adjoints and radius gradient, plus the loss gradient of its
-// position at this step (dl_dp, may be null).  Clears its in-degree for the next step.
+// Agent b: its list sorted by entry index (agent, then line order) in shared memory, then
+// the contributions summed in that order into its adjoints and radius gradient, plus the
+// loss gradient of its position at this step (dl_dp, may be null).  An agent that
+// received more than kInCap entries takes them from a scan of all agents' entries in
+// index order instead (the same order, so the same sums).  Clears its count for the next
+// step.
 constexpr int kGatherThreads = 128;
-constexpr int kGatherCap = 24;
 template <class T>
 __global__ void __launch_bounds__(kGatherThreads) adj_gather_kernel(AdjArgs<T> A) {
     using T2 = typename AdjArgs<T>::T2;
-    __shared__ uint32_t s_l[kGatherCap * kGatherThreads];
+    __shared__ uint32_t s_l[kInCap * kGatherThreads];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= A.n) return;
-    const uint32_t s0 = A.instart[b], s1 = A.instart[b + 1];
-    const uint32_t deg = s1 - s0;
-    uint32_t* lst = A.inlist + s0;
-    uint32_t stride = 1;
-    if (deg <= (uint32_t)kGatherCap) {
-        uint32_t* sl = s_l + threadIdx.x;  // element k at sl[k * kGatherThreads]
-        for (uint32_t q = 0; q < deg; ++q) sl[q * kGatherThreads] = lst[q];
-        lst = sl;
-        stride = kGatherThreads;
-    }
-    for (uint32_t q = 1; q < deg; ++q) {
-        const uint32_t key = lst[q * stride];
-        uint32_t r = q;
-        while (r > 0 && lst[(r - 1) * stride] > key) {
-            lst[r * stride] = lst[(r - 1) * stride];
-            --r;
-        }
-        lst[r * stride] = key;
-    }
+    const uint32_t deg = A.incnt[b];
     T px = 0, py = 0, vx = 0, vy = 0, rr = 0;
-    for (uint32_t q = 0; q < deg; ++q) {
-        const uint32_t e = lst[q * stride];
+    auto add = [&](uint32_t e) {
         const T* c = A.contrib + 4 * (size_t)e;
         px += c[0];
         py += c[1];
         vx += c[2];
         vy += c[3];
         rr += A.contrib_r[e];
+    };
+    if (deg <= (uint32_t)kInCap) {
+        uint32_t* sl = s_l + threadIdx.x;  // element k at sl[k * kGatherThreads]
+        const uint32_t* lst = A.inlist + (size_t)b * kInCap;
+        for (uint32_t q = 0; q < deg; ++q) sl[q * kGatherThreads] = lst[q];
+        for (uint32_t q = 1; q < deg; ++q) {
+            const uint32_t key = sl[q * kGatherThreads];
+            uint32_t r = q;
+            while (r > 0 && sl[(r - 1) * kGatherThreads] > key) {
+                sl[r * kGatherThreads] = sl[(r - 1) * kGatherThreads];
+                --r;
+            }
+            sl[r * kGatherThreads] = key;
+        }
+        for (uint32_t q = 0; q < deg; ++q) add(sl[q * kGatherThreads]);
+    } else {
+        const uint32_t ne = (uint32_t)A.n * kAdjEntries;
+        for (uint32_t e = 0; e < ne; ++e)
+            if (A.ent[e] == b) add(e);
     }
     T2 p = A.pbar[b], v = A.vbar[b];
     p.x += px;
@@ -548,8 +480,6 @@ cudaError_t launch_adjoint_step(const AdjArgs<T>& A, int kmax, cudaStream_t st) 
     else adj_agent_kernel<T, 32><<<nb, 128, 0, st>>>(A);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    csr_scan_kernel<<<1, kCsrThreads, 0, st>>>(A.n, A.incnt, A.instart);
-    csr_fill_kernel<<<(A.n + 255) / 256, 256, 0, st>>>(A.n, A.ent, A.incnt, A.instart, A.inlist, A.err);
     adj_gather_kernel<T><<<(A.n + kGatherThreads - 1) / kGatherThreads, kGatherThreads, 0, st>>>(A);
     return cudaGetLastError();
 }

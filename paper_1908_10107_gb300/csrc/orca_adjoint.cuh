@@ -25,6 +25,14 @@ struct Vec2Of<double> {
 };
 
 constexpr int kAdjEntries = 3;
+// Entries one agent's list holds; an agent that receives more is summed by a scan of all
+// agents' entries (exact, same order, slow).  The index-checked build keeps two, so that
+// its tests run the scan on ordinary crowds.
+#ifdef ORCA_CHECKS
+constexpr int kInCap = 2;
+#else
+constexpr int kInCap = 24;
+#endif
 
 // One reverse step; everything in agent order.
 template <class T>
@@ -57,13 +65,12 @@ struct AdjArgs {
     int32_t* ent;           // n * kAdjEntries
     T* contrib;             // n * kAdjEntries * 4
     T* contrib_r;           // n * kAdjEntries
-    uint32_t* incnt;        // n, zero on entry and on exit
-    uint32_t* instart;      // n + 1
-    uint32_t* inlist;       // n * kAdjEntries
+    uint32_t* incnt;        // n: entries each agent receives; zero on entry and on exit
+    uint32_t* inlist;       // n * kInCap: the entries agent b receives, in arrival order
     int* err;               // the device error word (index checks of the ORCA_CHECKS build)
 };
 
-// adj_agent, csr_scan, csr_fill, adj_gather on st (T = float or double).
+// adj_agent, adj_gather on st (T = float or double).
 template <class T>
 cudaError_t launch_adjoint_step(const AdjArgs<T>& A, int kmax, cudaStream_t st);
 

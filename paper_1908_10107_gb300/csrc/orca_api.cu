@@ -283,9 +283,9 @@ static int launches_per_step(const orca_ctx* c) {
 }
 
 // One step launched directly with the neighbour lists and LP records written in agent
-// order (recomputation inside orca_rollout_backward).
+// order, and (each may be null) the state it starts from and the positions it ends at.
 static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, uint32_t* tape,
-                                          cudaStream_t st) {
+                                          float2* state, float2* next, cudaStream_t st) {
     const Plan& pl = c->plan;
     float cs = c->p.cell_size > 0.0f ? c->p.cell_size : c->p.neighbor_dist * 0.25f;
     cudaError_t e = launch_binning(c->n, cs, pl.max_cells, c->PV[0], c->bins, par, st);
@@ -317,6 +317,9 @@ static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, ui
     a.rec_stride = pl.K;
     a.tape = tape;
     a.bbox_acc = c->bins.misc->bbox_acc[par ^ 1];
+    a.rec_pos = state;
+    a.rec_vel = state ? state + c->n : nullptr;
+    a.rec_next = next;
     return launch_main(a, pl.K, c->shape, 0, st);
 }
 
@@ -983,7 +986,7 @@ ORCA_API int orca_get_search_counters(orca_ctx* ctx, int64_t* counters4, void* s
 struct RolloutPlan {
     int T, C, nseg;
     size_t ckpt, goal, radius, vmax, pref, tau, seg_state, seg_nbr, seg_tape, adj, gscratch, ent, contrib,
-        contrib_r, incnt, instart, inlist, total;
+        contrib_r, incnt, inlist, total;
 };
 
 // C = 0: one segment of T steps, recorded by the forward pass itself.
@@ -1010,8 +1013,7 @@ static RolloutPlan rollout_plan(const orca_ctx* c, int T, int C) {
     r.contrib = L.add(N * kAdjEntries * 4 * 4);
     r.contrib_r = L.add(N * kAdjEntries * 4);
     r.incnt = L.add(N * 4);
-    r.instart = L.add((N + 1) * 4);
-    r.inlist = L.add(N * kAdjEntries * 4);
+    r.inlist = L.add(N * kInCap * 4);
     r.total = L.total;
     return r;
 }
@@ -1047,14 +1049,11 @@ ORCA_API int orca_rollout_forward(orca_ctx* ctx, int32_t T, int32_t ckpt_every, 
         // neighbour lists and the LP records
         for (int t = 0; t < T; ++t) {
             float2* sp = (float2*)(w + r.seg_state + (size_t)t * N * 16);
-            CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, sp, sp + N, st), "step state");
             CK(enqueue_recording_step(ctx, ctx->cur, (int32_t*)(w + r.seg_nbr) + (size_t)t * N * ctx->plan.K,
-                                      (uint32_t*)(w + r.seg_tape) + (size_t)t * N, st),
+                                      (uint32_t*)(w + r.seg_tape) + (size_t)t * N, sp,
+                                      traj_pos ? (float2*)traj_pos + (size_t)t * N : nullptr, st),
                "recording step");
             ctx->cur ^= 1;
-            if (traj_pos)
-                CK(launch_unpermute(ctx->n, ctx->PV[0], ctx->PR[ctx->cur].id, (float2*)traj_pos + (size_t)t * N,
-                                    nullptr, st), "trajectory");
         }
         ctx->roll_T = T;
         ctx->roll_C = 0;
@@ -1125,10 +1124,9 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
             if (rr != ORCA_OK) return rr;
         }
         for (int t = t0; C > 0 && t < t1; ++t) {
-            float2* sp = sstate(t - t0);
-            CK(launch_unpermute(n, ctx->PV[0], ctx->PR[ctx->cur].id, sp, sp + N, st), "segment state");
             CK(enqueue_recording_step(ctx, ctx->cur, (int32_t*)(w + r.seg_nbr) + (size_t)(t - t0) * N * K,
-                                      (uint32_t*)(w + r.seg_tape) + (size_t)(t - t0) * N, st),
+                                      (uint32_t*)(w + r.seg_tape) + (size_t)(t - t0) * N, sstate(t - t0),
+                                      nullptr, st),
                "recording step");
             ctx->cur ^= 1;
         }
@@ -1160,7 +1158,6 @@ ORCA_API int orca_rollout_backward(orca_ctx* ctx, const float* dL_dpos, float* g
             A.contrib = (float*)(w + r.contrib);
             A.contrib_r = (float*)(w + r.contrib_r);
             A.incnt = (uint32_t*)(w + r.incnt);
-            A.instart = (uint32_t*)(w + r.instart);
             A.inlist = (uint32_t*)(w + r.inlist);
             A.err = &ctx->bins.misc->error;
             CK(launch_adjoint_step(A, (int)K, st), "adjoint kernels");

@@ -178,6 +178,11 @@ struct MainArgs {
     int32_t* rec_nbr;                    // n*k in agent order, or null
     uint32_t* rec_cell;                  // n in agent order, or null
     int* bbox_acc = nullptr;             // single scene: the next step's box slot (copies), or null
+    // rollouts (TAPE instantiation only), agent order, each may be null: the state the step
+    // starts from and the position it ends at
+    float2* rec_pos = nullptr;
+    float2* rec_vel = nullptr;
+    float2* rec_next = nullptr;
 };
 
 // host launchers (orca_bin.cu, orca_main.cu)

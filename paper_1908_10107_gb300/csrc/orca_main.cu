@@ -1281,7 +1281,12 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 atomicOr(&a.misc_rw->error, kErrNumeric);
             a.out.vel[t] = make_float2(xx, xy);
             a.out.pos[t] = make_float2(nx, ny);
-            if (TAPE) a.tape[me] = s_tape[TAPE ? tid : 0].pack();
+            if (TAPE) {
+                a.tape[me] = s_tape[TAPE ? tid : 0].pack();
+                if (a.rec_pos) a.rec_pos[me] = p;
+                if (a.rec_vel) a.rec_vel[me] = a.in.vel[t];
+                if (a.rec_next) a.rec_next[me] = make_float2(nx, ny);
+            }
             bx0 = bx1 = nx;
             by0 = by1 = ny;
         }

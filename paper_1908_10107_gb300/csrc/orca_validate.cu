@@ -281,12 +281,12 @@ extern "C" ORCA_API int orca_validate_rollout_fp64(
     const size_t N = (size_t)n, K = (size_t)max_neighbors;
     // every state of the rollout, its neighbour lists and LP records, the adjoint buffers
     const size_t b_state = 2 * N * sizeof(double2), b_nbr = N * K * 4, b_tape = N * 4;
-    size_t off[11], total = 0;
+    size_t off[10], total = 0;
     const size_t E = N * kAdjEntries;
-    const size_t sizes[11] = {(size_t)(T + 1) * b_state, (size_t)T * b_nbr, (size_t)T * b_tape,
+    const size_t sizes[10] = {(size_t)(T + 1) * b_state, (size_t)T * b_nbr, (size_t)T * b_tape,
                               4 * N * sizeof(double2), 3 * N * sizeof(double), E * 4 * sizeof(double),
-                              N * 4, (N + 1) * 4, E * 4, E * 4, E * sizeof(double)};
-    for (int q = 0; q < 11; ++q) {
+                              N * 4, N * kInCap * 4, E * 4, E * sizeof(double)};
+    for (int q = 0; q < 10; ++q) {
         off[q] = total;
         total += (sizes[q] + 255) & ~size_t(255);
     }
@@ -362,11 +362,10 @@ extern "C" ORCA_API int orca_validate_rollout_fp64(
             A.g_radius = gr;
             A.g_tau = gt;
             A.contrib = (double*)(w + off[5]);
-            A.ent = (int32_t*)(w + off[9]);
-            A.contrib_r = (double*)(w + off[10]);
+            A.ent = (int32_t*)(w + off[8]);
+            A.contrib_r = (double*)(w + off[9]);
             A.incnt = (uint32_t*)(w + off[6]);
-            A.instart = (uint32_t*)(w + off[7]);
-            A.inlist = (uint32_t*)(w + off[8]);
+            A.inlist = (uint32_t*)(w + off[7]);
             A.err = nullptr;  // the validation rollout is built without index checks
             e = launch_adjoint_step(A, max_neighbors, st);
             double2* tmp = pnext;

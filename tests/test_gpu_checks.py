@@ -62,3 +62,39 @@ def test_checked_build_passes_the_parity_bar(checks_lib):
     with abi.use_library(checks_lib):
         rep = parity.gpu_step_and_compare(sc, steps_before=5)
     assert rep["rows"] == sc.n
+
+
+def _grads(torch, sc, W, T, C):
+    sim = abi.OrcaSim.for_scene(sc)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in sc.arrays()]
+    sim.set_agents(*dev)
+    nbytes = abi.orca_rollout_workspace_size(sim.ctx, T, C)
+    raw = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    off = (-raw.data_ptr()) % 256
+    ws = raw[off: off + nbytes]
+    traj = torch.empty((T, sc.n, 2), device="cuda")
+    abi.orca_rollout_forward(sim.ctx, T, C, traj, ws)
+    g = [torch.empty(sc.n, device="cuda") for _ in range(3)]
+    gp0 = torch.empty((sc.n, 2), device="cuda")
+    gv0 = torch.empty((sc.n, 2), device="cuda")
+    abi.orca_rollout_backward(sim.ctx, torch.from_numpy(W).float().cuda(), g[0], g[1], g[2], gp0, gv0, ws)
+    abi.orca_sync(sim.ctx)
+    out = [x.cpu().numpy() for x in (traj, *g, gp0, gv0)]
+    sim.close()
+    return out
+
+
+@pytest.mark.parametrize("C", [0, 4])
+def test_checked_build_adjoint_overflow_scan_matches_bitwise(checks_lib, C):
+    """The checked build gives each agent two places for the entries it receives, so most
+    agents of a crowd take their entries from the scan of all agents' entries: the sums
+    meet the entries in the same order and must agree bit for bit with the lists."""
+    import torch
+    sc = S.jitter_velocities(S.bidirectional(2500, seed=64), 64)
+    W = np.random.default_rng(5).standard_normal((9, sc.n, 2))
+    want = _grads(torch, sc, W, 9, C)
+    with abi.use_library(checks_lib):
+        got = _grads(torch, sc, W, 9, C)
+    for a, b in zip(got, want):
+        np.testing.assert_array_equal(a, b)
+    assert np.abs(want[2]).max() > 0
