@@ -403,8 +403,10 @@ ORCA_API int orca_launches_per_step(const orca_ctx* ctx, int32_t* count);
  * All scratch space lives in a fixed device array inside the library, sized for at most
  * 65,536 agents and 262,144 grid cells (about 7 MiB, held on every GPU that loads the
  * library until the process exits); n above 65,536 returns ORCA_ERR_CAPACITY.  More cells
- * than that only coarsen the grid (results do not change).  The first call on a device
- * looks up the array's device address; make that first call before any stream capture.
+ * than that only coarsen the grid (results do not change).  Every call looks up the
+ * array's device address in the current context (so a reset of the primary context is
+ * safe); the first call on a device may load the library's device code, so make it
+ * before any stream capture.
  * The call is asynchronous on `stream` and never synchronises, so errors that arise on
  * the GPU are not reported here: non-finite inputs give non-finite outputs, and a crowd
  * whose extent fits no grid of the scratch's cell table (which, with the cell edge

@@ -11,7 +11,6 @@
 // The step itself is the library's ordinary one (same kernels, same arithmetic): bounding
 // box and grid, cell keys and counts, cell table, reorder into cell order, the per-agent
 // ORCA kernel, and a scatter back to the caller's agent order.
-#include <mutex>
 #include <string>
 
 #include "../../include/orca_gb300.h"
@@ -23,7 +22,6 @@ void set_context_free_error(const std::string& msg);
 
 constexpr int kStaticMaxAgents = 65536;
 constexpr int kStaticMaxCells = 262144;
-constexpr int kStaticMaxDevices = 64;
 
 // Scratch layout (bytes), every piece 256-byte aligned.  The pieces from misc to the end
 // are cleared by every call (grid, counters, and the counting sort's cell and tile counts).
@@ -65,33 +63,23 @@ constexpr StaticLayout static_layout() {
 constexpr StaticLayout kStatic = static_layout();
 
 // The scratch space.  Host code must not use this name as an address: it obtains the
-// device address with cudaGetSymbolAddress (once per device) and passes pointers on.
+// device address with cudaGetSymbolAddress and passes pointers on.
 static __device__ __align__(256) unsigned char g_orca_static_scratch[kStatic.total];
-
-static std::mutex g_static_mu;
-static char* g_static_ptr[kStaticMaxDevices] = {nullptr};
 
 static int static_fail(int code, const std::string& msg) {
     set_context_free_error(msg);
     return code;
 }
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array in the current context, looked up on every call (a
+// host-side table lookup once the module is loaded): a cached address would outlive a
+// reset of the device's primary context, after which the array lives elsewhere.
 static int static_scratch(char** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return static_fail(ORCA_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kStaticMaxDevices) return static_fail(ORCA_ERR_CAPACITY, "device ordinal too large");
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_orca_static_scratch);
-        if (e != cudaSuccess || !p)
-            return static_fail(ORCA_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") +
-                                                  cudaGetErrorString(e));
-        g_static_ptr[dev] = (char*)p;
-    }
-    *out = g_static_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_orca_static_scratch);
+    if (e != cudaSuccess || !p)
+        return static_fail(ORCA_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    *out = (char*)p;
     return ORCA_OK;
 }
 
