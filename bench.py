@@ -51,7 +51,7 @@ FLOPS = {"candidates": 6, "lines": 45, "lp1_calls": 25, "lp1_bounds": 14, "lp_ch
          "bisectors": 24}
 FP32_LANES_PER_SM = 128
 
-# Algorithmic HBM bytes of one whole step per agent, the survey's model (Section 8(d)):
+# Algorithmic HBM bytes of one whole step per agent (the minimal traffic model of a step):
 # state read 40 (pos, vel, goal 8 each; radius, max speed, pref speed, tau 4 each), state
 # write 16, cell key and index written and read once 16, one sort scatter (read + write)
 # 16, the cell-ordered message record written and read once 2 x 20.  It counts no re-read
@@ -1193,7 +1193,7 @@ def main():
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                          if peak_kind == "measured" else "fallback 6800 GB/s"},
         "step_roofline": {"bound": "hbm", "alg_bytes_per_agent": STEP_BYTES_PER_AGENT,
-                          "bytes_model": "survey 8(d): state read 40, write 16, key+index 16, "
+                          "bytes_model": "minimal step: state read 40, write 16, key+index 16, "
                                          "sort scatter 16, message record 2 x 20",
                           "achieved": STEP_BYTES_PER_AGENT * n / (ms_per_step * 1e-3) / 1e9,
                           "peak": hbm_peak, "unit": "GB/s",
