@@ -128,6 +128,20 @@ def test_full_size_bidirectional_sampled():
     parity.gpu_step_and_compare(sc, steps_before=5, subset=subset)
 
 
+@pytest.mark.parametrize("cell,tpb,lanes", [(1.4105, 64, 1), (1.7631, 64, 1), (1.4105, 128, 32)])
+def test_full_size_bidirectional_in_the_benchmarked_launch_shapes(cell, tpb, lanes):
+    """The 524,288-agent flow in the settings the benchmark's tuner picks among (cell edges
+    1.41 / 1.76 m, 64 threads with one lane per solve, 128 threads with warp work units),
+    after 20 steps (the benchmark's warm-up), sampled."""
+    sc = S.bidirectional()
+    sim = parity.make_sim(sc, cell_size=cell)
+    abi.orca_set_launch(sim.ctx, tpb, lanes)
+    subset = np.sort(np.random.default_rng(int(cell * 1000) + tpb).choice(sc.n, 3000, replace=False))
+    rep = parity.gpu_step_and_compare(sc, steps_before=20, cell_size=cell, sim=sim, subset=subset)
+    sim.close()
+    assert rep["rows"] == len(subset)
+
+
 def test_full_size_dense_sampled():
     sc = S.dense()  # 2,097,152 agents, k = 20
     rng = np.random.default_rng(1)
