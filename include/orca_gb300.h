@@ -381,10 +381,9 @@ ORCA_API int orca_profile(orca_ctx* ctx, int enable);
  */
 ORCA_API int orca_profile_read(orca_ctx* ctx, float* ms3);
 
-/* Number of kernels one orca_step enqueues per step: five for one scene (bounding box,
- * cell keys and counts, cell table, reorder, ORCA kernel), six for a batch (scene boxes
- * and scene offsets in place of the bounding box); static obstacles add two: the tile
- * flags and the obstacle launch. */
+/* Number of kernels one orca_step enqueues per step: five (bounding box -- for a batch,
+ * the scenes' boxes and cell ranges --, cell keys and counts, cell table, reorder, ORCA
+ * kernel); static obstacles add two: the tile flags and the obstacle launch. */
 ORCA_API int orca_launches_per_step(const orca_ctx* ctx, int32_t* count);
 
 /*

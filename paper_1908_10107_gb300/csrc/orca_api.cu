@@ -230,7 +230,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (c->prof && (e = cudaEventRecordWithFlags(c->pev[0], st, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (c->n_scenes > 0)
-        e = launch_binning_batch(c->n, c->n_scenes, c->scenes, c->slot_scene, c->PV[0], c->bins, st);
+        e = launch_binning_batch(c->n, c->n_scenes, c->scenes, c->slot_scene, c->PV[0], c->bins, par, st);
     else
         e = launch_binning(c->n, cs, pl.max_cells, c->PV[0], c->bins, par, st);
     if (e != cudaSuccess) return e;
@@ -267,6 +267,10 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     a.rec_stride = pl.K;
     a.tape = nullptr;
     if (c->n_scenes == 0) a.bbox_acc = c->bins.misc->bbox_acc[par ^ 1];
+    else {
+        a.scene_box = c->scenes;
+        a.scene_box_slot = par ^ 1;
+    }
     e = launch_main(a, pl.K, c->shape, c->n_scenes > 0 ? c->resident : 0, st,
                     a.nseg > 0 && c->side.st ? &c->side : nullptr);
     if (e != cudaSuccess) return e;
@@ -274,12 +278,12 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     return e;
 }
 
-// kernels per step: bounding box (a batch: scene boxes and scene prefix), keys + counts,
-// cell table, reorder, ORCA kernel (with obstacles: tile flags, the plain ORCA launch and
-// the obstacle launch)
+// kernels per step: bounding box (a batch: the scenes' boxes and cell ranges), keys +
+// counts, cell table, reorder, ORCA kernel (with obstacles: tile flags, the plain ORCA
+// launch and the obstacle launch)
 static int launches_per_step(const orca_ctx* c) {
     const int obstacles = c->n_scenes == 0 && c->nseg > 0 ? 2 : 0;  // tile flags, obstacle launch
-    return (c->n_scenes > 0 ? 2 : 1) + 4 + obstacles;
+    return 5 + obstacles;
 }
 
 // One step launched directly with the neighbour lists and LP records written in agent
@@ -390,7 +394,9 @@ static int check_device_error(orca_ctx* ctx, cudaStream_t st) {
 // Positions changed outside a step: the box the last step's ORCA kernel reduced no longer
 // holds, so the next step's bounding-box kernel scans.
 static cudaError_t clear_box(orca_ctx* ctx, cudaStream_t st) {
-    return cudaMemsetAsync(ctx->bins.misc->bbox_ok, 0, sizeof ctx->bins.misc->bbox_ok, st);
+    cudaError_t e = cudaMemsetAsync(ctx->bins.misc->bbox_ok, 0, sizeof ctx->bins.misc->bbox_ok, st);
+    if (e == cudaSuccess && ctx->n_scenes > 0) e = launch_clear_scene_boxes(ctx->n_scenes, ctx->scenes, st);
+    return e;
 }
 
 // Enqueue the write of agent-order positions / velocities (either may be null) into the

@@ -561,72 +561,113 @@ cudaError_t launch_iota(int n, uint32_t* id, cudaStream_t st) {
 // Batch of independent scenes
 // ---------------------------------------------------------------------------------
 // Bounding box and grid of each scene: one CTA per scene over its slot range.
-__global__ void __launch_bounds__(1024) scene_bbox_grid_kernel(const float2* __restrict__ pos,
-                                                               SceneDev* scenes, DeviceMisc* misc) {
+// Bounding box and grid of each scene, one CTA per scene: from the box the previous
+// step's ORCA kernel reduced into the scene's slot `slot` when that slot is complete, else
+// a min / max scan of the scene's positions.  The CTA opens the other slot for this step's
+// ORCA kernel.  The last CTA to finish (ticket counter, no waiting) then lays the scenes'
+// cell ranges end to end: cell_off of every scene and the table's total.
+constexpr int kSceneThreads = 1024;
+__global__ void __launch_bounds__(kSceneThreads) scene_bbox_grid_kernel(const float2* __restrict__ pos,
+                                                                        int n_scenes, SceneDev* scenes,
+                                                                        DeviceMisc* misc, int slot) {
     pdl_wait();
     SceneDev* sc = scenes + blockIdx.x;
     const int off = sc->off, cnt = sc->cnt;
+    __shared__ float4 s_part[kSceneThreads / 32];
+    __shared__ bool s_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 r = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        float2 p = pos[off + i];
-        r.x = fminf(r.x, p.x);
-        r.y = fminf(r.y, p.y);
-        r.z = fmaxf(r.z, p.x);
-        r.w = fmaxf(r.w, p.y);
-    }
+    if (slot >= 0 && sc->box_ok[slot]) {
+        if (threadIdx.x == 0) {
+            const int* c = sc->box_acc[slot];
+            r = make_float4(float_from_order_code(c[0]), float_from_order_code(c[1]),
+                            float_from_order_code(c[2]), float_from_order_code(c[3]));
+        }
+    } else {
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            float2 p = pos[off + i];
+            r.x = fminf(r.x, p.x);
+            r.y = fminf(r.y, p.y);
+            r.z = fmaxf(r.z, p.x);
+            r.w = fmaxf(r.w, p.y);
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        r.x = fminf(r.x, __shfl_xor_sync(0xffffffffu, r.x, o));
-        r.y = fminf(r.y, __shfl_xor_sync(0xffffffffu, r.y, o));
-        r.z = fmaxf(r.z, __shfl_xor_sync(0xffffffffu, r.z, o));
-        r.w = fmaxf(r.w, __shfl_xor_sync(0xffffffffu, r.w, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            r.x = fminf(r.x, __shfl_xor_sync(0xffffffffu, r.x, o));
+            r.y = fminf(r.y, __shfl_xor_sync(0xffffffffu, r.y, o));
+            r.z = fmaxf(r.z, __shfl_xor_sync(0xffffffffu, r.z, o));
+            r.w = fmaxf(r.w, __shfl_xor_sync(0xffffffffu, r.w, o));
+        }
+        if (lane == 0) s_part[warp] = r;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                r.x = fminf(r.x, s_part[w].x);
+                r.y = fminf(r.y, s_part[w].y);
+                r.z = fmaxf(r.z, s_part[w].z);
+                r.w = fmaxf(r.w, s_part[w].w);
+            }
     }
-    __shared__ float4 s_part[32];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) s_part[warp] = r;
+    if (threadIdx.x == 0) {
+        if (cnt == 0) r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float cs = sc->cell_size > 0.0f ? sc->cell_size : sc->nd * 0.25f;
+        int err = 0;
+        sc->grid = derive_grid(r, cs, sc->cell_budget, &err);
+        if (err) atomicOr(&misc->error, err);
+        if (slot >= 0) {  // the slot this step's ORCA kernel fills
+            int* c = sc->box_acc[slot ^ 1];
+            c[0] = c[1] = float_order_code(INFINITY);
+            c[2] = c[3] = float_order_code(-INFINITY);
+            sc->box_ok[slot ^ 1] = 1u;
+        }
+        __threadfence();
+        s_last = atomicAdd(&misc->bbox_ticket, 1u) == (unsigned)gridDim.x - 1;
+    }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-        r.x = fminf(r.x, s_part[w].x);
-        r.y = fminf(r.y, s_part[w].y);
-        r.z = fmaxf(r.z, s_part[w].z);
-        r.w = fmaxf(r.w, s_part[w].w);
+    if (!s_last) return;
+    // last CTA: exclusive scan of the scenes' cell counts (kSceneThreads-wide, in rounds)
+    __threadfence();
+    __shared__ long long s_w[kSceneThreads / 32];
+    __shared__ long long s_base;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int q0 = 0; q0 < n_scenes; q0 += kSceneThreads) {
+        const int q = q0 + threadIdx.x;
+        const long long v = q < n_scenes ? (long long)__ldcg(&scenes[q].grid.num_cells) : 0;
+        long long inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        long long wb = 0, tot = 0;
+        for (int w = 0; w < kSceneThreads / 32; ++w) {
+            if (w < warp) wb += s_w[w];
+            tot += s_w[w];
+        }
+        if (q < n_scenes) scenes[q].cell_off = (int)(s_base + wb + inc - v);
+        __syncthreads();
+        if (threadIdx.x == 0) s_base += tot;
+        __syncthreads();
     }
-    if (cnt == 0) r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    float cs = sc->cell_size > 0.0f ? sc->cell_size : sc->nd * 0.25f;
-    int err = 0;
-    sc->grid = derive_grid(r, cs, sc->cell_budget, &err);
-    if (err) atomicOr(&misc->error, err);
+    if (threadIdx.x == 0) {
+        misc->grid.num_cells = (int)s_base;
+        misc->tile_counter = 0;
+        misc->bbox_ticket = 0;
+    }
 }
 
-// Cell offsets of the scenes (exclusive scan of their cell counts) and the total; resets
-// the persistent kernel's tile counter.
-__global__ void __launch_bounds__(1024) scene_prefix_kernel(int n_scenes, SceneDev* scenes,
-                                                            DeviceMisc* misc) {
-    pdl_wait();
-    __shared__ long long s_sum[1024];
-    int per = (n_scenes + blockDim.x - 1) / blockDim.x;
-    int s0 = threadIdx.x * per, s1 = min(s0 + per, n_scenes);
-    long long sum = 0;
-    for (int q = s0; q < s1; ++q) sum += scenes[q].grid.num_cells;
-    s_sum[threadIdx.x] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long run = 0;
-        for (int t = 0; t < (int)blockDim.x; ++t) {
-            long long v = s_sum[t];
-            s_sum[t] = run;
-            run += v;
-        }
-        misc->grid.num_cells = (int)run;
-        misc->tile_counter = 0;
-    }
-    __syncthreads();
-    long long run = s_sum[threadIdx.x];
-    for (int q = s0; q < s1; ++q) {
-        scenes[q].cell_off = (int)run;
-        run += scenes[q].grid.num_cells;
-    }
+__global__ void __launch_bounds__(256) clear_scene_boxes_kernel(int n_scenes, SceneDev* scenes) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n_scenes) scenes[q].box_ok[0] = scenes[q].box_ok[1] = 0u;
+}
+
+cudaError_t launch_clear_scene_boxes(int n_scenes, SceneDev* scenes, cudaStream_t st) {
+    if (n_scenes <= 0) return cudaSuccess;
+    clear_scene_boxes_kernel<<<(n_scenes + 255) / 256, 256, 0, st>>>(n_scenes, scenes);
+    return cudaGetLastError();
 }
 
 // Scene of every slot: the first scene whose slot range ends after it (binary search;
@@ -653,11 +694,9 @@ cudaError_t launch_slot_scene(int n, int n_scenes, const SceneDev* scenes, int* 
 }
 
 cudaError_t launch_binning_batch(int n, int n_scenes, SceneDev* scenes, const int* slot_scene,
-                                 const AgentState& cur, const BinBuffers& b, cudaStream_t st) {
-    scene_bbox_grid_kernel<<<n_scenes, 1024, 0, st>>>(cur.pos, scenes, b.misc);
+                                 const AgentState& cur, const BinBuffers& b, int slot, cudaStream_t st) {
+    scene_bbox_grid_kernel<<<n_scenes, kSceneThreads, 0, st>>>(cur.pos, n_scenes, scenes, b.misc, slot);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess)
-        e = launch_pdl(scene_prefix_kernel, 1, 1024, 0, st, n_scenes, scenes, b.misc);
     if (e != cudaSuccess || n <= 0) return e;
     return launch_counting_sort(n, scenes, slot_scene, cur, b, st);
 }

@@ -111,6 +111,12 @@ struct SceneDev {
     float cell_size;     // requested cell edge
     int pad_;
     long long cell_budget;  // cells this scene may use (capacity rule)
+    // The box of the positions a step's ORCA kernel writes, reduced by that kernel per
+    // scene (order codes of min x, min y, max x, max y) into the slot of the next step's
+    // parity; box_ok[s]: slot s holds the complete box of the scene's current positions
+    // (zero when positions change outside a step).
+    int box_acc[2][4];
+    unsigned int box_ok[2];
 };
 
 struct AgentParams {  // one of PR[0] / PR[1]
@@ -178,6 +184,8 @@ struct MainArgs {
     int32_t* rec_nbr;                    // n*k in agent order, or null
     uint32_t* rec_cell;                  // n in agent order, or null
     int* bbox_acc = nullptr;             // single scene: the next step's box slot (copies), or null
+    SceneDev* scene_box = nullptr;       // batch: the scenes whose box slot scene_box_slot is filled
+    int scene_box_slot = 0;
     // rollouts (TAPE instantiation only), agent order, each may be null: the state the step
     // starts from and the position it ends at
     float2* rec_pos = nullptr;
@@ -192,8 +200,13 @@ int main_blocks(int n);
 // slot: the step's parity (the box slot it reads; its ORCA kernel fills the other one)
 cudaError_t launch_binning(int n, float cell_size, long long max_cells, const AgentState& cur,
                            const BinBuffers& b, int slot, cudaStream_t st);
+// Positions changed outside a step: every scene's box slots are cleared (the next batched
+// step scans).
+cudaError_t launch_clear_scene_boxes(int n_scenes, SceneDev* scenes, cudaStream_t st);
+// slot: the parity of the step (its scenes' boxes come from box slot `slot` when the
+// previous step's ORCA kernel filled it; slot < 0: always scan).
 cudaError_t launch_binning_batch(int n, int n_scenes, SceneDev* scenes, const int* slot_scene,
-                                 const AgentState& cur, const BinBuffers& b, cudaStream_t st);
+                                 const AgentState& cur, const BinBuffers& b, int slot, cudaStream_t st);
 cudaError_t launch_slot_scene(int n, int n_scenes, const SceneDev* scenes, int* slot_scene,
                               cudaStream_t st);
 cudaError_t launch_reorder(int n, const BinBuffers& b, const AgentState& src_s,

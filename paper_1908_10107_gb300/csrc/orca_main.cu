@@ -1309,6 +1309,24 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 atomicMax(acc + 3, float_order_code(by1));
             }
         }
+        // batch: the box of each scene's written positions, for the scene's next grid -- the
+        // warp's lanes grouped by scene (a warp straddles at most a few), a min / max
+        // reduction per group, one atomic per bound per group
+        if (a.scene_box) {
+            const int sid = active ? a.slot_scene[t] : -1;
+            const unsigned grp = __match_any_sync(0xffffffffu, sid);
+            const int c0 = __reduce_min_sync(grp, float_order_code(bx0));
+            const int c1 = __reduce_min_sync(grp, float_order_code(by0));
+            const int c2 = __reduce_max_sync(grp, float_order_code(bx1));
+            const int c3 = __reduce_max_sync(grp, float_order_code(by1));
+            if (sid >= 0 && (tid & 31) == __ffs(grp) - 1) {
+                int* acc = a.scene_box[sid].box_acc[a.scene_box_slot];
+                atomicMin(acc + 0, c0);
+                atomicMin(acc + 1, c1);
+                atomicMax(acc + 2, c2);
+                atomicMax(acc + 3, c3);
+            }
+        }
         // ---- counters: one shared-memory atomic per warp
         unsigned wc = __reduce_add_sync(0xffffffffu, cand);
         unsigned wl = __reduce_add_sync(0xffffffffu, (unsigned)cnt);

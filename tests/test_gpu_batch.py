@@ -111,6 +111,34 @@ def test_scene_in_batch_equals_scene_alone_bitwise():
         np.testing.assert_array_equal(vel[off[s]:off[s + 1]], v1)
 
 
+def test_batch_state_update_rescans_the_boxes_bitwise():
+    """After steps, every scene's grid comes from the box the ORCA kernel reduced for it;
+    new positions written from outside (orca_update_state) invalidate those boxes, and the
+    next step must scan: stepping on equals a fresh batch loaded with the new state, bit
+    for bit (grids included)."""
+    batch = small_batch(seed=11)
+    sim = run_batch(batch, steps_before=6)
+    pos, vel = sim.get_state()
+    pos = (pos + np.float32(0.37)).astype(np.float32)
+    sim.update_state(pos, vel)
+    sim.step(3)
+    p1, v1 = sim.get_state()
+    g1 = sim.get_scene_grids()
+    off = batch.offsets
+    fresh = S.Batch([sc.copy() for sc in batch.scenes])
+    for s, sc in enumerate(fresh.scenes):
+        sc.pos, sc.vel = pos[off[s]:off[s + 1]].copy(), vel[off[s]:off[s + 1]].copy()
+    ref = run_batch(fresh, steps_before=3)
+    p2, v2 = ref.get_state()
+    g2 = ref.get_scene_grids()
+    np.testing.assert_array_equal(p1, p2)
+    np.testing.assert_array_equal(v1, v2)
+    for a, b in zip(g1, g2):
+        np.testing.assert_array_equal(a, b)
+    sim.close()
+    ref.close()
+
+
 def test_default_batch_sampled():
     batch = S.batched()  # 256 scenes, ~2.6M agents
     sim = run_batch(batch, steps_before=3)
