@@ -327,8 +327,13 @@ static cudaError_t enqueue_recording_step(orca_ctx* c, int par, int32_t* nbr, ui
     return launch_main(a, pl.K, c->shape, 0, st);
 }
 
+// Capture the two step graphs (one per parity).  When instantiated graphs exist and only
+// the number of agents changed since (removal, spawning: the calls that change n without
+// dropping the graphs), the new captures update them in place, which costs a fraction of
+// a fresh instantiation; a capture whose shape the update does not take is instantiated.
 static int build_graphs(orca_ctx* ctx) {
-    drop_graphs(ctx);
+    const bool update = ctx->exec[0] && ctx->exec[1];
+    if (!update) drop_graphs(ctx);
     for (int par = 0; par < 2; ++par) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
@@ -336,12 +341,29 @@ static int build_graphs(orca_ctx* ctx) {
         cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
         if (e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
+            drop_graphs(ctx);
             return cuda_fail(ctx, e, "kernel launch during capture");
         }
-        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+        if (e2 != cudaSuccess) {
+            drop_graphs(ctx);
+            return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+        }
+        if (update && ctx->exec[par]) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(ctx->exec[par], g, &info) == cudaSuccess) {
+                cudaGraphDestroy(g);
+                continue;
+            }
+            cudaGetLastError();  // not updatable: instantiate instead
+            cudaGraphExecDestroy(ctx->exec[par]);
+            ctx->exec[par] = nullptr;
+        }
         e = cudaGraphInstantiate(&ctx->exec[par], g, 0);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        if (e != cudaSuccess) {
+            drop_graphs(ctx);
+            return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
     }
     ctx->graph_n = ctx->n;
     return ORCA_OK;
