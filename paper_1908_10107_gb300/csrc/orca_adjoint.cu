@@ -229,6 +229,7 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // (entries in increasing line order), whose neighbour's in-degree is counted.
 template <class T, int KMAX>
 __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
+    pdl_wait();  // launched as a dependent of the previous reverse step's gather
     using T2 = typename AdjArgs<T>::T2;
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A.n) return;
@@ -422,6 +423,7 @@ __global__ void __launch_bounds__(128) adj_agent_kernel(AdjArgs<T> A) {
 constexpr int kGatherThreads = 128;
 template <class T>
 __global__ void __launch_bounds__(kGatherThreads) adj_gather_kernel(AdjArgs<T> A) {
+    pdl_wait();  // every entry of this step is placed before any list is read
     using T2 = typename AdjArgs<T>::T2;
     __shared__ uint32_t s_l[kInCap * kGatherThreads];
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -474,14 +476,15 @@ template <class T>
 cudaError_t launch_adjoint_step(const AdjArgs<T>& A, int kmax, cudaStream_t st) {
     if (A.n <= 0) return cudaSuccess;
     const int nb = (A.n + 127) / 128;
-    if (kmax <= 10) adj_agent_kernel<T, 10><<<nb, 128, 0, st>>>(A);
-    else if (kmax <= 16) adj_agent_kernel<T, 16><<<nb, 128, 0, st>>>(A);
-    else if (kmax <= 20) adj_agent_kernel<T, 20><<<nb, 128, 0, st>>>(A);
-    else adj_agent_kernel<T, 32><<<nb, 128, 0, st>>>(A);
-    cudaError_t e = cudaGetLastError();
+    // both kernels launched as programmatic dependents: each waits at entry (pdl_wait) for
+    // the kernel before it, and its launch overlaps that kernel's tail
+    cudaError_t e;
+    if (kmax <= 10) e = launch_pdl(adj_agent_kernel<T, 10>, nb, 128, 0, st, A);
+    else if (kmax <= 16) e = launch_pdl(adj_agent_kernel<T, 16>, nb, 128, 0, st, A);
+    else if (kmax <= 20) e = launch_pdl(adj_agent_kernel<T, 20>, nb, 128, 0, st, A);
+    else e = launch_pdl(adj_agent_kernel<T, 32>, nb, 128, 0, st, A);
     if (e != cudaSuccess) return e;
-    adj_gather_kernel<T><<<(A.n + kGatherThreads - 1) / kGatherThreads, kGatherThreads, 0, st>>>(A);
-    return cudaGetLastError();
+    return launch_pdl(adj_gather_kernel<T>, (A.n + kGatherThreads - 1) / kGatherThreads, kGatherThreads, 0, st, A);
 }
 
 template cudaError_t launch_adjoint_step<float>(const AdjArgs<float>&, int, cudaStream_t);
