@@ -622,8 +622,8 @@ def run_crossing(args):
 
 
 def run_lp_ab(args):
-    """A/B of the LP modes -- one lane per solve, four-lane groups for LP3, and warp work
-    units (the paper's load-balanced LP) -- on LP3-heavy and lighter crowds.  Each mode
+    """A/B of the LP modes -- one lane per solve, the agent split (four lanes per agent), and
+    warp work units (the paper's load-balanced LP) -- on LP3-heavy and lighter crowds.  Each mode
     replays the same steps from the same saved state (the modes give bitwise-equal
     trajectories); the ORCA kernel's mean time comes from the library's phase events."""
     import torch
@@ -663,7 +663,7 @@ def run_lp_ab(args):
                                      "lp3_fraction": c["lp3_agent_steps"] / max(c["agent_steps"], 1)}
         out[name] = row
         sim.close()
-    line = {"metric": "ORCA kernel ms per LP mode (one lane / 4-lane LP3 groups / warp work units)",
+    line = {"metric": "ORCA kernel ms per LP mode (one lane / agent split / warp work units)",
             "value": None, "unit": "ms", "n_gpus": 1, "steps": args.ab_steps, "warmup": 1,
             "higher_is_better": False, "dtype": "f32", "data": "synthetic (seeded)",
             "config": {"workload": "LP-mode A/B on the 524,288-agent flow (early and later steps), "

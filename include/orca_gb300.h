@@ -432,12 +432,16 @@ ORCA_API int orca_set_cell_size(orca_ctx* ctx, float cell_size);
 
 /*
  * Launch shape of the per-agent ORCA kernel: threads per CTA (64, 128 or 256; default 128)
- * and the LP mode, lp3_lanes: 1 -- each lane solves its agent's LPs alone; 4 -- groups of
- * four lanes share one agent's least-penetration solve; 32 -- work units: every lane keeps
- * its agent's LPs, but the bound evaluations of all the LP1 solves a warp needs at once are
- * dealt out over its 32 lanes (the paper's load-balanced LP, Section 3); 0 -> default: 1
- * for max_neighbors <= 16, else 32.  Results are bitwise the same in every mode; speed
- * differs.  Rebuilds the step graphs.
+ * and the mode, lp3_lanes: 1 -- one lane per agent, which solves its LPs alone; 4 -- agent
+ * split: a quad of lanes steps each agent (the neighbour search's candidates, the
+ * half-planes and the least-penetration solve shared out over the four lanes; for crowds
+ * too small to fill the GPU; a batch keeps one lane per agent); 32 -- work units: every
+ * lane keeps its agent's LPs, but the bound evaluations of all the LP1 solves a warp needs
+ * at once are dealt out over its 32 lanes (the paper's load-balanced LP, Section 3); 0 ->
+ * default: 1 for max_neighbors <= 16, else 32.  Results are bitwise the same in every mode;
+ * speed differs.  Until this is first called, a context steps a single scene of at most
+ * 12,000 agents with k <= 16 in the agent split (64 threads) and anything else with 128
+ * threads and the default mode.  Rebuilds the step graphs.
  */
 ORCA_API int orca_set_launch(orca_ctx* ctx, int32_t threads_per_block, int32_t lp3_lanes);
 

@@ -102,12 +102,14 @@ def tune_cell_size(sim: "abi.OrcaSim", scene, steps: int = STEPS, factors=FACTOR
     return {"cell_size": best, "timings_ms": timings, "kth_distance": rk, "cached": False}
 
 
-# Launch shapes tried: (threads per CTA, LP mode).  Four-lane LP3 groups and 256-thread
-# CTAs ran slower than these on every workload measured (the 524,288-agent flow, the dense
-# crowd at k = 10 and 20, the 256-scene batch: 5-30%), so they are not tried; they stay
-# available through orca_set_launch.  One lane per solve wins at k = 10, warp work units
-# at k = 20.
-SHAPES = ((64, 1), (128, 1), (64, 32), (128, 32))
+# Launch shapes tried: (threads per CTA, LP mode).  256-thread CTAs ran slower than these
+# on every workload measured (the 524,288-agent flow, the dense crowd at k = 10 and 20, the
+# 256-scene batch: 5-30%), so they are not tried; they stay available through
+# orca_set_launch.  One lane per solve wins at k = 10, warp work units at k = 20, and the
+# agent split (four lanes per agent) in crowds of a few thousand agents; a batch never
+# runs the split (its persistent kernel keeps one lane per agent).
+SHAPES = ((64, 1), (128, 1), (64, 32), (128, 32), (64, 4))
+BATCH_SHAPES = ((64, 1), (128, 1), (64, 32), (128, 32))
 
 
 def _time_steps(sim, reload, steps, between=None):
@@ -171,7 +173,7 @@ def set_batch_cells(sim, batch, cells):
     abi.orca_set_scenes(sim.ctx, params, *batch.arrays())
 
 
-def tune_batch(sim: "abi.OrcaSim", batch, steps: int = STEPS, factors=FACTORS, shapes=SHAPES,
+def tune_batch(sim: "abi.OrcaSim", batch, steps: int = STEPS, factors=FACTORS, shapes=BATCH_SHAPES,
                between=None) -> dict:
     """Cell-edge factor (common to all scenes, times each scene's expected k-th neighbour
     distance) and launch shape for a batch; leaves ``sim`` tuned with the batch loaded."""

@@ -143,6 +143,7 @@ struct orca_ctx {
     int* slot_scene = nullptr;
     int resident = 0;  // CTAs of the ORCA kernel resident at once (persistent launch)
     LaunchShape shape{128, 1};
+    bool shape_auto = true;  // no orca_set_launch yet: small crowds take the agent split
     int roll_T = 0, roll_C = 0;  // last orca_rollout_forward
     void* roll_ws = nullptr;
     cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -223,6 +224,16 @@ static void drop_graphs(orca_ctx* c) {
     c->graph_n = -1;
 }
 
+// Launch shape of a step: the context's, except that without an orca_set_launch a single
+// scene of at most kSplitMaxAgents agents with k <= 16 takes the agent split (four lanes
+// per agent; 2-12% faster there, slower above about 20,000 agents).
+constexpr int kSplitMaxAgents = 12000;
+static LaunchShape step_shape(const orca_ctx* c) {
+    if (c->shape_auto && c->n_scenes == 0 && c->nseg == 0 && c->n <= kSplitMaxAgents && c->plan.K <= 16)
+        return LaunchShape{64, 4};
+    return c->shape;
+}
+
 // Enqueue one step whose current parameters live in PR[par].
 static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
     const Plan& pl = c->plan;
@@ -271,7 +282,7 @@ static cudaError_t enqueue_step(orca_ctx* c, int par, cudaStream_t st) {
         a.scene_box = c->scenes;
         a.scene_box_slot = par ^ 1;
     }
-    e = launch_main(a, pl.K, c->shape, c->n_scenes > 0 ? c->resident : 0, st,
+    e = launch_main(a, pl.K, step_shape(c), c->n_scenes > 0 ? c->resident : 0, st,
                     a.nseg > 0 && c->side.st ? &c->side : nullptr);
     if (e != cudaSuccess) return e;
     if (c->prof) e = cudaEventRecordWithFlags(c->pev[3], st, cudaEventRecordExternal);
@@ -579,7 +590,8 @@ ORCA_API int orca_set_launch(orca_ctx* ctx, int32_t threads_per_block, int32_t l
     if (lp3_lanes != 0 && lp3_lanes != 1 && lp3_lanes != 4 && lp3_lanes != 32)
         return fail(ctx, ORCA_ERR_ARG, "lp3_lanes must be 0 (default), 1, 4 or 32");
     LaunchShape sh{threads_per_block, lp3_lanes ? lp3_lanes : default_lp3_group(ctx->plan.K)};
-    if (sh.tpb != ctx->shape.tpb || sh.lp3_group != ctx->shape.lp3_group) {
+    if (ctx->shape_auto || sh.tpb != ctx->shape.tpb || sh.lp3_group != ctx->shape.lp3_group) {
+        ctx->shape_auto = false;
         ctx->shape = sh;
         ctx->resident = 0;
         if (ctx->n_scenes > 0) ctx->resident = main_resident_blocks(ctx->plan.K, ctx->shape);

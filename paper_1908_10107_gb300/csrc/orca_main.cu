@@ -1381,7 +1381,276 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     }
 }
 
-// at most one CTA per 64 agents (the smallest CTA)
+// ---------------------------------------------------------------------------------
+// Agent split (lanes = 4): each agent is stepped by a quad of lanes (lanes 4j..4j+3 of a
+// warp), for crowds too small to fill the GPU, where a step is as long as one agent's
+// chain of dependent instructions.  The quad scans the candidate rows together (lane q
+// takes every fourth candidate and parks its entrants in its own shared-memory row; the
+// quad's leader inserts them all), builds the half-planes four at a time, and solves the
+// least-penetration LP with the 4-lane group LP3; LP2 stays on the leader.  Every decision
+// is the one-lane kernel's (the same exact neighbour list, the same half-plane arithmetic,
+// the same LP decisions), so the results are bitwise those of the other modes.  Single
+// scene, no obstacles, no record of the LP (those launches use one lane per agent).
+// ---------------------------------------------------------------------------------
+constexpr int kSplitU = 2;  // candidates per lane per round (eight per quad)
+
+template <int KMAX, int CAP>
+__device__ __forceinline__ unsigned knn_split_dev(const MainArgs& a, const GridDev& g, int cell_off, float nd,
+                                                  int t, float2 p, int k, float lim0,
+                                                  unsigned long long* quad_buf, int stride, int gq,
+                                                  unsigned qmask, int lead, unsigned long long (&kk)[KMAX],
+                                                  SearchCount& sc) {
+    static_assert(CAP > kSplitU, "parking space for one round");
+    const int cy = cell_coord(p.y, g.ymin, g.inv, g.gy);
+    const float nd2 = __fmul_rn(nd, nd);
+    const float lim_max = __int_as_float(__float_as_int(nd2) - 1);
+    if (lim0 != lim0) {
+        lim0 = density_lim(a, g, cell_off, p, k);
+        if (gq == 0) ++sc.cold;
+    }
+    lim0 = fminf(lim0, lim_max);
+    unsigned long long* buf = quad_buf + gq * stride;
+    unsigned cand = 0;
+    int nb = 0;
+    float lim = lim0;
+    // the leader inserts every lane's parked keys (the sorted list is the same in any
+    // insertion order); lim is then its list's k-th d^2 for the whole quad
+    auto drain_quad = [&]() {
+        int n4[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) n4[j] = __shfl_sync(qmask, nb, lead + j);
+        __syncwarp(qmask);  // the parked keys are visible to the leader
+        if (gq == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned long long* bj = quad_buf + j * stride;
+#pragma unroll 1
+                for (int i = 0; i < n4[j]; ++i) insert_key<KMAX>(bj[i], kk);
+            }
+            if (kk[KMAX - 1] != ~0ull) lim = fminf(lim, __uint_as_float((unsigned)(kk[KMAX - 1] >> 32)));
+        }
+        lim = __shfl_sync(qmask, lim, lead);
+        nb = 0;
+        __syncwarp(qmask);  // the leader has read the rows before they are refilled
+    };
+#pragma unroll 1
+    for (;;) {
+#pragma unroll
+        for (int l = 0; l < KMAX; ++l) kk[l] = (l < KMAX - k) ? 0ull : ~0ull;
+        lim = lim0;
+        nb = 0;
+        int y = cy, up = cy + 1, dn = cy - 1;
+        float h = 0.0f;
+#pragma unroll 1
+        for (;;) {
+            const float w = sqrtf(fmaxf(lim * (1.0f + 1e-5f) - h * h, 0.0f)) + 2.0f * g.slop;
+            const int x0 = cell_coord(p.x - w, g.xmin, g.inv, g.gx);
+            const int x1 = cell_coord(p.x + w, g.xmin, g.inv, g.gx);
+            const int c = cell_off + y * g.gx;
+            uint32_t q0 = 0u, q1 = 0u;
+            if (idx_ok(c + x0 >= 0 && c + x1 + 1 <= a.misc->grid.num_cells, &a.misc_rw->error)) {
+                q0 = a.cell_start[c + x0];
+                q1 = a.cell_start[c + x1 + 1];
+                if (!idx_ok(q0 <= q1 && q1 <= (uint32_t)a.n, &a.misc_rw->error)) q1 = q0;
+            }
+            if (gq == 0) {
+                cand += q1 - q0;
+                ++sc.rows;
+            }
+            // rounds of eight candidates, the same count in every lane of the quad
+#pragma unroll 1
+            for (uint32_t base = q0; base < q1; base += 4 * kSplitU) {
+                float d2[kSplitU];
+                unsigned id[kSplitU];
+#pragma unroll
+                for (int u = 0; u < kSplitU; ++u) {
+                    const uint32_t qu = base + (uint32_t)(gq + 4 * u);
+                    float4 mj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (qu < q1) mj = a.in.msg[qu];
+                    const float ddx = __fsub_rn(mj.x, p.x), ddy = __fsub_rn(mj.y, p.y);
+                    d2[u] = __fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy));
+                    id[u] = __float_as_uint(mj.w);
+                    if (qu >= q1 || (int)qu == t) d2[u] = INFINITY;
+                }
+#pragma unroll
+                for (int u = 0; u < kSplitU; ++u)
+                    if (d2[u] <= lim) buf[nb++] = ((unsigned long long)__float_as_uint(d2[u]) << 32) | id[u];
+                if (__any_sync(qmask, nb > CAP - kSplitU)) drain_quad();
+            }
+            const float hu = up < g.gy ? (g.ymin + (float)up * g.s) - p.y : INFINITY;
+            const float hd = dn >= 0 ? p.y - (g.ymin + (float)(dn + 1) * g.s) : INFINITY;
+            if (hu <= hd) {
+                y = up++;
+                h = hu;
+            } else {
+                y = dn--;
+                h = hd;
+            }
+            if (h == INFINITY) break;
+            h = fmaxf(0.0f, h - g.slop);
+            if (h * h * (1.0f - 1e-5f) > lim) break;
+        }
+        drain_quad();
+        const int full = __shfl_sync(qmask, kk[KMAX - 1] != ~0ull ? 1 : 0, lead);
+        if (full || !(lim0 < lim_max)) break;
+        lim0 = fminf(fmaxf(2.25f * lim0, 1e-6f * lim_max), lim_max);
+        if (gq == 0) ++sc.retries;
+    }
+    return cand;
+}
+
+template <int KMAX, int TPB>
+__global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_split_kernel(MainArgs a) {
+    pdl_wait();
+    constexpr int KP = row_len<KMAX>();
+    extern __shared__ float4 s_lines[];  // TPB rows: each lane's parking row; the leader's holds the lines
+    __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3;
+    __shared__ unsigned long long s_search[3];
+    const int tid = threadIdx.x, lane = tid & 31, gq = tid & 3;
+    const int lead = lane & ~3;
+    const unsigned qmask = 0xfu << lead;
+    if (tid == 0) {
+        s_cand = s_lines_n = s_act = s_lp3 = 0;
+        s_search[0] = s_search[1] = s_search[2] = 0;
+    }
+    __syncthreads();
+    SearchCount sc{0u, 0u, 0u};
+    const int t = blockIdx.x * (TPB / 4) + (tid >> 2);
+    const bool active = t < a.n;  // the same for the four lanes of a quad
+    float4* row = s_lines + (tid & ~3) * KP;  // the agent's half-planes (the leader's row)
+    unsigned cand = 0;
+    int cnt = 0, lp3 = 0;
+    float bx0 = INFINITY, by0 = INFINITY, bx1 = -INFINITY, by1 = -INFINITY;
+    if (active) {
+        SceneView sv;
+        scene_view(a, t, sv);
+        const float dt = sv.dt;
+        const float4 me4 = a.in.msg[t];
+        const float2 p = make_float2(me4.x, me4.y);
+        const uint32_t me = __float_as_uint(me4.w);
+        const float V = a.prm.max_speed[t];
+        float lim0 = __int_as_float(0x7fffffff);
+        if (a.prm.hint) {
+            const float hd = sqrtf(a.prm.hint[t]) * (1.0f + 1e-3f) + 3.0f * V * dt + 1e-3f;
+            lim0 = hd * hd;
+        }
+        unsigned long long kk[KMAX];
+        cand = knn_split_dev<KMAX, 2 * KP>(a, sv.g, sv.cell_off, sv.nd, t, p, sv.k, lim0,
+                                           reinterpret_cast<unsigned long long*>(row), 2 * KP, gq, qmask,
+                                           lead, kk, sc);
+        if (gq == 0) {
+            if (a.prm.hint)
+                a.prm.hint[t] = kk[KMAX - 1] != ~0ull ? __uint_as_float((unsigned)(kk[KMAX - 1] >> 32)) : INFINITY;
+            // the neighbours' slots, in rank order, parked in the row
+#pragma unroll
+            for (int l = 0; l < KMAX; ++l) {
+                if (l >= KMAX - sv.k && kk[l] != ~0ull) {
+                    const uint32_t nid = (uint32_t)kk[l];
+                    if (!idx_ok(nid < (uint32_t)a.n, &a.misc_rw->error)) continue;
+                    const uint32_t q = a.in.slot[nid];
+                    if (!idx_ok(q < (uint32_t)a.n, &a.misc_rw->error)) continue;
+                    row[cnt++].w = __uint_as_float(q);
+                }
+            }
+            if (a.rec_nbr) {
+                int w = 0;
+#pragma unroll
+                for (int l = 0; l < KMAX; ++l)
+                    if (l >= KMAX - sv.k)
+                        a.rec_nbr[(size_t)me * a.rec_stride + (w++)] =
+                            kk[l] != ~0ull ? (int32_t)(kk[l] & 0xffffffffu) : -1;
+                for (; w < a.rec_stride; ++w) a.rec_nbr[(size_t)me * a.rec_stride + w] = -1;
+            }
+            if (a.rec_cell) {
+                const int cx = cell_coord(p.x, sv.g.xmin, sv.g.inv, sv.g.gx);
+                const int cyy = cell_coord(p.y, sv.g.ymin, sv.g.inv, sv.g.gy);
+                a.rec_cell[me] = (uint32_t)sv.cell_off + (uint32_t)cyy * (uint32_t)sv.g.gx + (uint32_t)cx;
+            }
+        }
+        cnt = __shfl_sync(qmask, cnt, lead);
+        __syncwarp(qmask);
+        // half-planes l = gq, gq + 4, ... (each lane overwrites only its own entries' slots)
+        const float2 v = a.in.vel[t];
+        const float itau = __fdividef(1.0f, a.prm.tau[t]);
+        const float idt = __fdividef(1.0f, dt);
+        const float half_idt = 0.5f * idt;
+#pragma unroll 1
+        for (int l = gq; l < cnt; l += 4) {
+            const int q = __float_as_int(row[l].w);
+            row[l] = orca_line_dev(p, v, me4.z, itau, dt, half_idt, me, a.in.msg[q], a.in.vel[q]);
+        }
+        __syncwarp(qmask);
+        float xx = 0.0f, xy = 0.0f;
+        int b = cnt;
+        if (gq == 0) {
+            const float2 o = pref_velocity_dev(p, a.prm.goal[t], a.prm.pref_speed[t], dt, idt);
+            RowLines rl{row};
+            b = lp2_dev(rl, cnt, V, o.x, o.y, false, xx, xy);
+        }
+        b = __shfl_sync(qmask, b, lead);
+        xx = __shfl_sync(qmask, xx, lead);
+        xy = __shfl_sync(qmask, xy, lead);
+        if (b < cnt) {
+            lp3_group_dev<4>(row, cnt, b, V, xx, xy);
+            lp3 = 1;
+        }
+        if (gq == 0) {
+            const float nx = __fmaf_rn(xx, dt, p.x), ny = __fmaf_rn(xy, dt, p.y);
+            if (!isfinite(xx) || !isfinite(xy) || !isfinite(nx) || !isfinite(ny))
+                atomicOr(&a.misc_rw->error, kErrNumeric);
+            a.out.vel[t] = make_float2(xx, xy);
+            a.out.pos[t] = make_float2(nx, ny);
+            bx0 = bx1 = nx;
+            by0 = by1 = ny;
+        }
+    }
+    if (a.bbox_acc) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+            by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+            bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+            by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+        }
+        if (lane == 0 && bx0 <= bx1) {
+            int* acc = a.bbox_acc + ((blockIdx.x * (TPB / 32) + (tid >> 5)) % kBoxCopies) * kBoxStride;
+            atomicMin(acc + 0, float_order_code(bx0));
+            atomicMin(acc + 1, float_order_code(by0));
+            atomicMax(acc + 2, float_order_code(bx1));
+            atomicMax(acc + 3, float_order_code(by1));
+        }
+    }
+    // counters: the leaders' counts (one shared-memory atomic per warp)
+    const bool leader = active && gq == 0;
+    const unsigned wc = __reduce_add_sync(0xffffffffu, leader ? cand : 0u);
+    const unsigned wl = __reduce_add_sync(0xffffffffu, leader ? (unsigned)cnt : 0u);
+    const unsigned wa = __reduce_add_sync(0xffffffffu, leader ? 1u : 0u);
+    const unsigned w3 = __reduce_add_sync(0xffffffffu, leader ? (unsigned)lp3 : 0u);
+    const unsigned v3[3] = {sc.retries, sc.cold, sc.rows};
+    unsigned ws[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) ws[q] = __reduce_add_sync(0xffffffffu, v3[q]);
+    if (lane == 0) {
+        atomicAdd(&s_cand, (unsigned long long)wc);
+        atomicAdd(&s_lines_n, (unsigned long long)wl);
+        atomicAdd(&s_act, (unsigned long long)wa);
+        atomicAdd(&s_lp3, (unsigned long long)w3);
+        for (int q = 0; q < 3; ++q)
+            if (ws[q]) atomicAdd(&s_search[q], (unsigned long long)ws[q]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // four split CTAs (at least 64 agents) share one block's counters
+        unsigned long long* c = a.block_counters + kBlockCounters * (size_t)(blockIdx.x >> 2);
+        atomicAdd(c + 0, s_act);
+        atomicAdd(c + 1, s_lp3);
+        atomicAdd(c + 2, s_cand);
+        atomicAdd(c + 3, s_lines_n);
+        for (int q = 0; q < 3; ++q) atomicAdd(c + 8 + q, s_search[q]);
+    }
+}
+
+// at most one CTA per 64 agents (the smallest CTA; the agent split's CTAs share counters)
 int main_blocks(int n) { return (n + 63) / 64; }
 
 // CTAs of the ORCA kernel that fit on the GPU at once (for the persistent launch).
@@ -1419,9 +1688,14 @@ static cudaError_t dispatch_g(const MainArgs& a, int g, int grid_blocks, cudaStr
         if (resident) { *resident = resident_blocks_k<KMAX, TPB, 32>(); return cudaSuccess; }
         return launch_main_k<KMAX, TPB, 32>(a, grid_blocks, st);
     }
-    if (g == 4) {
-        if (resident) { *resident = resident_blocks_k<KMAX, TPB, 4>(); return cudaSuccess; }
-        return launch_main_k<KMAX, TPB, 4>(a, grid_blocks, st);
+    // agent split: a single scene without obstacles (the plain launch of an obstacle step
+    // skips the flagged tiles of TPB agents, which only the one-lane kernel knows)
+    if (g == 4 && !resident && !a.scenes && !a.tile_near && grid_blocks <= 0) {
+        constexpr size_t smem = main_smem_bytes<KMAX, TPB>();
+        cudaError_t e = cudaFuncSetAttribute(orca_split_kernel<KMAX, TPB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return launch_pdl(orca_split_kernel<KMAX, TPB>, (a.n + TPB / 4 - 1) / (TPB / 4), TPB, smem, st, a);
     }
     if (resident) { *resident = resident_blocks_k<KMAX, TPB, 1>(); return cudaSuccess; }
     return launch_main_k<KMAX, TPB, 1>(a, grid_blocks, st);

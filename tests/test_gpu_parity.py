@@ -293,7 +293,7 @@ def test_counters():
 
 @pytest.mark.parametrize("scene", ["flow", "dense20", "circle"])
 def test_lp_modes_agree_bitwise(scene):
-    # one lane per solve, four-lane groups and warp work units take the same decisions
+    # one lane per agent, the agent split and warp work units take the same decisions
     # with the same roundings: identical states after several steps
     if scene == "flow":
         sc = S.jitter_velocities(S.bidirectional(8190, seed=17), 17)
@@ -304,7 +304,7 @@ def test_lp_modes_agree_bitwise(scene):
     else:
         sc = S.circle_swap()
     states = {}
-    for tpb, lanes in ((64, 1), (128, 4), (64, 32), (256, 32)):
+    for tpb, lanes in ((64, 1), (64, 4), (128, 4), (64, 32), (256, 32)):
         sim = parity.make_sim(sc, flags=0)
         abi.orca_set_launch(sim.ctx, tpb, lanes)
         sim.set_scene(sc)
@@ -315,6 +315,25 @@ def test_lp_modes_agree_bitwise(scene):
     for key, (pos, vel) in states.items():
         np.testing.assert_array_equal(pos, ref[0], err_msg=str(key))
         np.testing.assert_array_equal(vel, ref[1], err_msg=str(key))
+
+
+@pytest.mark.parametrize("scene,tpb", [("two_way", 64), ("eight_way", 128), ("dense20", 64)])
+def test_agent_split_passes_parity(scene, tpb):
+    """Four lanes per agent (neighbour search, half-planes and least penetration shared by a
+    quad of lanes): exact neighbour lists and cells, velocities within the oracle's bar."""
+    if scene == "two_way":
+        sc = S.two_way_crossing(2500, heterogeneous=True)
+    elif scene == "eight_way":
+        sc = S.eight_way_crossing(10000)
+    else:
+        sc = S.dense(6007, seed=19)
+        sc.max_neighbors = 20
+        sc = S.jitter_velocities(sc, 19)
+    sim = parity.make_sim(sc)
+    abi.orca_set_launch(sim.ctx, tpb, 4)
+    rep = parity.gpu_step_and_compare(sc, steps_before=30, sim=sim)
+    sim.close()
+    assert rep["rows"] == sc.n
 
 
 def test_operation_counts_match_the_oracle():
