@@ -76,6 +76,9 @@ def _bind(lib):
     lib.oracle_lp2.restype = c.c_int
     lib.oracle_solve.argtypes = [_F64P, c.c_int, c.c_double, _F64P, _F64P]
     lib.oracle_solve.restype = c.c_int
+    lib.oracle_solve_counted.argtypes = [_F64P, c.c_int, c.c_double, _F64P, _F64P,
+                                         np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
+    lib.oracle_solve_counted.restype = c.c_int
     lib.oracle_step.argtypes = ([c.c_int] + [_F64P] * 7 + [c.c_double, c.c_int, c.c_double,
                                 c.c_int, c.c_int, c.c_void_p, c.c_void_p, c.c_void_p, c.c_int,
                                 c.c_int, _F64P, _F64P, c.c_void_p, c.c_void_p, c.c_void_p,
@@ -195,6 +198,20 @@ def solve(lines, V: float, o):
     return bool(r), x
 
 
+def solve_counted(lines, V: float, o):
+    """As solve, also returning the LP's operation counts as a dict (lp1_calls,
+    lp1_bounds, lp_checks, bisectors, lp3_problem_lines)."""
+    lines = np.ascontiguousarray(lines, np.float64).reshape(-1)
+    x = np.zeros(2)
+    counts = np.zeros(5, np.int64)
+    r = _load().oracle_solve_counted(lines, lines.size // 4, float(V), np.asarray(o, np.float64),
+                                     x, counts)
+    if r < 0:
+        raise ValueError("oracle_solve_counted: bad arguments")
+    names = ("lp1_calls", "lp1_bounds", "lp_checks", "bisectors", "lp3_problem_lines")
+    return bool(r), x, dict(zip(names, (int(c) for c in counts)))
+
+
 def lp_sensitivity(lines, V: float, o, nobst: int = 0):
     """Conditioning of the velocity selection (LP2, then LP3) for FP32 parity: the largest
     move of the selected velocity (max-norm) when one half-plane at a time is shifted
@@ -276,9 +293,10 @@ def step(pos, vel, goal, radius, max_speed, pref_speed, time_horizon, neighbor_d
 
 # operation counts of oracle_step, summed over the stepped agents: candidates scanned,
 # half-planes built, LP1 calls (LP2 and inside LP3), agents that needed LP3, LP1 bounds
-# evaluated, LP2/LP3 violation checks, LP3 bisectors formed
+# evaluated, LP2/LP3 violation checks, LP3 bisectors formed, and the lines of LP3's
+# projected problems (a problem for line i, 0-based, takes that line and the i before it)
 COUNTER_NAMES = ("scanned", "lines", "lp1_calls", "lp3_agents", "lp1_bounds", "lp_checks",
-                 "bisectors")
+                 "bisectors", "lp3_problem_lines")
 
 
 def obstacle_line(p, r, seg, time_horizon: float, dt: float):

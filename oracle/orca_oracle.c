@@ -327,9 +327,11 @@ static line2 orca_line(v2 pa, v2 va, double ra, v2 pb, v2 vb, double rb, double 
  * otherwise the projection of o onto the line, clamped to the interval.
  * Returns 1 and writes *x on success, 0 when the interval is empty.
  * -------------------------------------------------------------------------------- */
-/* Operation counts of the LP (for the flop model of a step; no effect on results). */
+/* Operation counts of the LP (for the flop model of a step; no effect on results).
+ * problem_lines: over LP3's projected problems, the lines each involves -- a problem for
+ * line i (0-based) takes that line and the i lines before it, i + 1 in all. */
 typedef struct {
-    long long lp1, bounds, checks, bisectors;
+    long long lp1, bounds, checks, bisectors, problem_lines;
 } lpcount;
 
 static int lp1(const line2* L, int i, double V, v2 o, int dir_opt, v2* x, tags* tg,
@@ -426,6 +428,7 @@ static void lp3(const line2* L, int n, int nobst, int begin, double V, v2* x, ta
             }
             v2 keep = *x;
             if (work) work->bisectors += i > nobst ? i - nobst : 0;
+            if (work) work->problem_lines += i + 1;
             if (lp2(proj, m, V, mk(-L[i].d.y, L[i].d.x), 1, x, tg, work) < m) *x = keep;
             dist = det2(L[i].d, sub(L[i].P, *x));
         }
@@ -477,6 +480,23 @@ int oracle_obstacle_line(const double* p, double r, const double* seg, double ta
 /* Full velocity selection: LP2, then LP3 from the failing line.  Returns 1 if LP3 ran. */
 int oracle_solve(const double* lines, int n, double V, const double* o, double* x2) {
     return oracle_solve_fixed(lines, n, 0, V, o, x2);
+}
+
+/* As oracle_solve, also returning the LP's operation counts: counts[5] = {LP1 calls, LP1
+ * bounds, violation checks, LP3 bisectors formed, LP3 problem lines} (see lpcount). */
+int oracle_solve_counted(const double* lines, int n, double V, const double* o, double* x2,
+                         long long* counts) {
+    line2 L[OR_MAXK];
+    if (n < 0 || n > OR_MAXK) return -1;
+    unpack(lines, n, L);
+    lpcount w = {0, 0, 0, 0, 0};
+    v2 x;
+    int b = lp2(L, n, V, mk(o[0], o[1]), 0, &x, NULL, &w);
+    if (b < n) lp3(L, n, 0, b, V, &x, NULL, &w);
+    x2[0] = x.x; x2[1] = x.y;
+    counts[0] = w.lp1; counts[1] = w.bounds; counts[2] = w.checks; counts[3] = w.bisectors;
+    counts[4] = w.problem_lines;
+    return b < n;
 }
 
 /* As oracle_solve, with the first nobst lines hard (static obstacles) in LP3. */
@@ -586,7 +606,8 @@ int oracle_obstacle_line(const double* p, double r, const double* seg, double ta
  * Outputs: pos_out, vel_out (2 per row), nbr (k per row, -1 padded, may be NULL), status
  * (1 per row: 1 if LP3 ran, may be NULL), margin (1 per row, may be NULL), counters[8] =
  * {candidates scanned, lines built, LP1 calls (incl. inside LP3), agents needing LP3,
- * LP1 bounds evaluated, LP2/LP3 violation checks, LP3 bisectors formed, 0} (may be NULL), sens (1 per row, may be NULL; filled when cond_check != 0, see the
+ * LP1 bounds evaluated, LP2/LP3 violation checks, LP3 bisectors formed, LP3 problem lines}
+ * (may be NULL), sens (1 per row, may be NULL; filled when cond_check != 0, see the
  * header).  Returns 0, or a negative value on bad arguments / allocation failure.
  * -------------------------------------------------------------------------------- */
 /* Velocity selection (LP2, then LP3 if needed) on given lines. */
@@ -705,7 +726,7 @@ static void step_agent(const step_in* S, int i, double* pos_out, double* vel_out
     *c_lines += cnt;
     v2 pv = pref_velocity(pa, mk(S->goal[2 * i], S->goal[2 * i + 1]), S->pref_speed[i], S->dt);
     v2 x;
-    lpcount w = {0, 0, 0, 0};
+    lpcount w = {0, 0, 0, 0, 0};
     int nl = nob + cnt;
     int bfail = lp2(L, nl, S->max_speed[i], pv, 0, &x, &tg, &w);
     int used3 = bfail < nl;
@@ -714,6 +735,7 @@ static void step_agent(const step_in* S, int i, double* pos_out, double* vel_out
     c_work->bounds += w.bounds;
     c_work->checks += w.checks;
     c_work->bisectors += w.bisectors;
+    c_work->problem_lines += w.problem_lines;
     if (sens) *sens = S->cond ? lp_sensitivity(L, nl, nob, S->max_speed[i], pv, x) : 0.0;
     vel_out[0] = x.x;
     vel_out[1] = x.y;
@@ -767,15 +789,16 @@ static int step_all(int n, const double* pos, const double* vel, const double* g
         if (bins_build(&b, pf, n, gf, gi) != 0) { free(pf); free(segf); return -2; }
         S.b = &b;
     }
-    long long c_scan = 0, c_lines = 0, c_lp3 = 0, c_lp1 = 0, c_bounds = 0, c_checks = 0, c_bis = 0;
+    long long c_scan = 0, c_lines = 0, c_lp3 = 0, c_lp1 = 0, c_bounds = 0, c_checks = 0, c_bis = 0,
+              c_plines = 0;
 #ifdef _OPENMP
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads) \
-    reduction(+ : c_scan, c_lines, c_lp3, c_lp1, c_bounds, c_checks, c_bis)
+    reduction(+ : c_scan, c_lines, c_lp3, c_lp1, c_bounds, c_checks, c_bis, c_plines)
 #endif
     for (int q = 0; q < rows; ++q) {
         int i = subset ? subset[q] : q;
-        lpcount w = {0, 0, 0, 0};
+        lpcount w = {0, 0, 0, 0, 0};
         step_agent(&S, i, pos_out + 2 * (size_t)q, vel_out + 2 * (size_t)q,
                    nbr ? nbr + (size_t)q * k : NULL,
                    obst ? obst + (size_t)q * (kobst > 0 ? kobst : 1) : NULL, status ? status + q : NULL,
@@ -785,6 +808,7 @@ static int step_all(int n, const double* pos, const double* vel, const double* g
         c_bounds += w.bounds;
         c_checks += w.checks;
         c_bis += w.bisectors;
+        c_plines += w.problem_lines;
     }
     if (S.b) bins_free(&b);
     free(pf);
@@ -792,6 +816,7 @@ static int step_all(int n, const double* pos, const double* vel, const double* g
     if (counters) {
         counters[0] = c_scan; counters[1] = c_lines; counters[2] = c_lp1; counters[3] = c_lp3;
         counters[4] = c_bounds; counters[5] = c_checks; counters[6] = c_bis;
+        counters[7] = c_plines;
     }
     return 0;
 }

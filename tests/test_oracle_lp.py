@@ -206,3 +206,29 @@ def test_lp_feasible_result_satisfies_all_constraints(oracle_mod):
             # least-penetration case: nearly parallel lines make the projected LP
             # ill-conditioned; the speed bound holds to rounding of that LP
             assert np.linalg.norm(x) <= V * (1 + 1e-7)
+
+
+def test_lp3_problem_lines_closed_forms(oracle_mod):
+    """The count of lines in LP3's projected problems (a problem for line i, 0-based,
+    takes that line and the i before it).  Closed forms: n parallel lines facing the same
+    way, each farther outside the disc than the last, open one problem each (every line is
+    violated by more than the penetration the previous problem reached, and same-direction
+    bisectors constrain nothing), so the count is 1 + 2 + ... + n; a feasible LP opens
+    none; two opposite parallel lines with a gap fail LP2 at the second and open one
+    problem of two lines, whose optimum is the midline."""
+    V = 1.0
+    for n in (1, 2, 3, 5, 10):
+        # valid side x >= 1.5 + 0.1 i: normal (1, 0), direction (0, -1)
+        lines = np.array([[1.5 + 0.1 * i, 0.0, 0.0, -1.0] for i in range(n)])
+        used, x, c = oracle_mod.solve_counted(lines, V, [0.0, 0.0])
+        assert used
+        assert c["lp3_problem_lines"] == n * (n + 1) // 2
+        np.testing.assert_allclose(x, [V, 0.0], atol=1e-15)
+    feasible_lines = np.array([[-0.5, 0.0, 0.0, -1.0], [0.0, -0.5, 1.0, 0.0]])  # x >= -0.5, y >= -0.5
+    used, x, c = oracle_mod.solve_counted(feasible_lines, V, [0.2, 0.1])
+    assert not used and c["lp3_problem_lines"] == 0
+    np.testing.assert_allclose(x, [0.2, 0.1], atol=1e-15)
+    gap = np.array([[0.5, 0.0, 0.0, -1.0], [-0.5, 0.0, 0.0, 1.0]])  # x >= 0.5, x <= -0.5
+    used, x, c = oracle_mod.solve_counted(gap, V, [0.0, 0.0])
+    assert used and c["lp3_problem_lines"] == 2
+    np.testing.assert_allclose(x[0], 0.0, atol=1e-15)

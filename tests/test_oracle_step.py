@@ -141,3 +141,20 @@ def test_fp64_neighbour_mode_on_exact_floats(oracle_mod):
     b = oracle_mod.step(**sc, fp64_knn=True, **kw)
     np.testing.assert_array_equal(a["nbr"], b["nbr"])
     np.testing.assert_array_equal(a["vel"], b["vel"])
+
+
+def test_step_counts_least_penetration_problem_lines(oracle_mod):
+    """Two agents overlapping deep inside each other's radius: each one's only half-plane
+    lies beyond its speed disc, so LP2 fails at line 0 and the least-penetration LP solves
+    one projected problem of one line -- 2 lines over the step.  A lone agent needs no
+    fallback (0)."""
+    pos = np.array([[0.0, 0.0], [0.3, 0.0]])
+    kw = dict(radius=np.full(2, 0.5), max_speed=np.full(2, 1.0), pref_speed=np.full(2, 1.0),
+              time_horizon=np.full(2, 2.0), neighbor_dist=5.0, max_neighbors=10, dt=0.1,
+              knn_mode=0)
+    r = oracle_mod.step(pos, np.zeros((2, 2)), goal=pos + [[10.0, 0.0], [-10.0, 0.0]], **kw)
+    assert r["lp3"].all()
+    assert r["counters"]["lp3_problem_lines"] == 2
+    far = np.array([[0.0, 0.0], [50.0, 0.0]])
+    r = oracle_mod.step(far, np.zeros((2, 2)), goal=far + [[10.0, 0.0], [-10.0, 0.0]], **kw)
+    assert not r["lp3"].any() and r["counters"]["lp3_problem_lines"] == 0
