@@ -236,13 +236,20 @@ ORCA_API int orca_get_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
 
 /*
  * Cost of the neighbour searches (Fig. 2: the r_obs filter, here the k nearest inside
- * r_obs), accumulated since orca_set_agents (synchronises `stream`): counters[0] search
- * passes beyond the first (the start radius held fewer than k agents inside r_obs and
- * grew 1.5x), [1] searches that started without a radius prediction (the first step after
- * a load: the start comes from the density of the cells around the agent), [2] grid rows
- * scanned (a search stops at a row once its bound has tightened past it, which depends on
- * the order of the agents inside a cell, so this count varies slightly between runs),
- * [3] reserved (0).  Counted by every step.
+ * r_obs) and of the least-penetration fallback, accumulated since orca_set_agents
+ * (synchronises `stream`):
+ *   counters[0] search passes beyond the first (the start radius held fewer than k agents
+ *               inside r_obs and grew 1.5x);
+ *   [1] searches that started without a radius prediction (the first step after a load:
+ *       the start comes from the density of the cells around the agent);
+ *   [2] grid rows scanned (a search stops at a row once its bound has tightened past it,
+ *       which depends on the order of the agents inside a cell, so this count varies
+ *       slightly between runs);
+ *   [3] the lines of the least-penetration LP's projected problems (Section 3: each line
+ *       violated by more than the penetration reached so far opens a problem over itself
+ *       and the bisectors with the lines before it; a problem for line i, 0-based,
+ *       counts i + 1).
+ * Counted by every step.
  */
 ORCA_API int orca_get_search_counters(orca_ctx* ctx, int64_t* counters4, void* stream);
 

@@ -629,7 +629,7 @@ class OrcaSim:
 
     def search_counters(self, stream=None) -> dict:
         c = orca_get_search_counters(self.ctx, stream)
-        return dict(zip(("extra_passes", "unpredicted", "rows"), map(int, c[:3])))
+        return dict(zip(("extra_passes", "unpredicted", "rows", "lp3_problem_lines"), map(int, c)))
 
     def spawn(self, cand_pos, goal, radius, max_speed, pref_speed, time_horizon, window, stream=None):
         """Spawn the candidates that overlap nobody within ``window`` s; returns accepted

@@ -244,11 +244,13 @@ struct Bisectors {
 // in direction mode maximises n_i.x over the bisectors of i with the earlier lines; a
 // numerically failed LP2 keeps x.
 // rec (may be null) keeps the record of the LP2 phase until an LP3 solve succeeds.
-__device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, float V, float& xx,
-                                        float& xy, LpTape* rec = nullptr, OpCount* oc = nullptr,
-                                        int nobst = 0) {
+// Returns the lines of the projected problems solved: a problem for line i takes that
+// line and the i lines before it, i + 1 in all (the search counters report the sum).
+__device__ __forceinline__ int lp3_dev(const float4* row, int n, int begin, float V, float& xx,
+                                       float& xy, LpTape* rec = nullptr, OpCount* oc = nullptr,
+                                       int nobst = 0) {
     float dist = 0.0f;
-    int i = begin;
+    int i = begin, problems = 0;
     // scan ahead to the next line violated by more than dist, then solve for it (the
     // lanes meet again after the scan, as in lp2_dev)
 #pragma unroll 1
@@ -264,7 +266,8 @@ __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, flo
                 break;
             }
         }
-        if (!hit) return;
+        if (!hit) return problems;
+        problems += i + 1;
         if (oc) oc->bis += i > nobst ? i - nobst : 0;
         Bisectors bis{row, li, nobst};
         // the projected problem: every obstacle line, then the bisectors with the lines
@@ -304,18 +307,22 @@ __device__ __forceinline__ void lp3_dev(const float4* row, int n, int begin, flo
 //     min / max shuffles (exact, order-free); the sequential early exits (tL > tR, an
 //     infeasible parallel bisector) become "any lane failed" / "final tL > tR", which
 //     fail exactly when some prefix fails because the bounds only tighten.
+// Returns the lines of the projected problems solved, as lp3_dev does (the same in every
+// lane of the group).
 template <int G>
-__device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begin, float V,
-                                              float& xx, float& xy) {
+__device__ __forceinline__ int lp3_group_dev(const float4* row, int n, int begin, float V,
+                                             float& xx, float& xy) {
     const int lane = threadIdx.x & 31;
     const int g = lane & (G - 1);
     const int base = lane & ~(G - 1);
     const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << base);
     float dist = 0.0f;
+    int problems = 0;
 #pragma unroll 1
     for (int i = begin; i < n; ++i) {
         const float4 li = row[i];
         if (!(lp_viol(li, xx, xy) > dist)) continue;
+        problems += i + 1;
         Bisectors bis{row, li};
         float nx = __fmul_rn(li.x, V), ny = __fmul_rn(li.y, V);  // direction mode starts at V n_i
         bool ok = true;
@@ -382,6 +389,7 @@ __device__ __forceinline__ void lp3_group_dev(const float4* row, int n, int begi
         }
         dist = lp_viol(li, xx, xy);
     }
+    return problems;
 }
 
 // ---------------------------------------------------------------------------------
@@ -530,13 +538,14 @@ __device__ __forceinline__ int warp_lp2_units(WarpLpShared& S, const float4* s_l
 // LP3 (least penetration) of the lane's queued agent, if it has one: the lp3_dev of one
 // lane (outer scan over the lines, inner direction-mode LP2 over the bisectors), with the
 // bounds of every bisector LP1 shared out.
-__device__ __forceinline__ void warp_lp3_units(WarpLpShared& S, const float4* s_lines, int row_off,
-                                               bool has, int n, int begin, float V, float& xx,
-                                               float& xy) {
+// Returns the lines of the projected problems of the lane's agent, as lp3_dev does.
+__device__ __forceinline__ int warp_lp3_units(WarpLpShared& S, const float4* s_lines, int row_off,
+                                              bool has, int n, int begin, float V, float& xx,
+                                              float& xy) {
     const int lane = threadIdx.x & 31;
     const float4* row = s_lines + row_off;
     float dist = 0.0f, sx = 0.0f, sy = 0.0f;
-    int i = begin, f = 0;
+    int i = begin, f = 0, problems = 0;
     bool done = !has, inner = false;
     float4 li = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 1
@@ -560,6 +569,7 @@ __device__ __forceinline__ void warp_lp3_units(WarpLpShared& S, const float4* s_
                     break;
                 }
                 inner = true;
+                problems += i + 1;
                 f = 0;
                 sx = xx;
                 sy = xy;
@@ -619,6 +629,7 @@ __device__ __forceinline__ void warp_lp3_units(WarpLpShared& S, const float4* s_
         }
         __syncwarp();
     }
+    return problems;
 }
 
 // Insert key into the ascending list kk; its largest entry drops out, and a key not below
@@ -1070,7 +1081,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
     __shared__ unsigned char s_queue[TPB];
     __shared__ LpTape s_tape[TAPE ? TPB : 1];
     __shared__ int s_qn, s_tile;
-    __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3;
+    __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3, s_proj;
     __shared__ unsigned long long s_search[3];
     __shared__ unsigned long long s_ops[COUNT ? 4 : 1];
     constexpr bool WU = G == 32;  // work-unit LP (warp-cooperative) instead of per-lane LP
@@ -1085,11 +1096,13 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         s_lines_n = 0;
         s_act = 0;
         s_lp3 = 0;
+        s_proj = 0;
         s_search[0] = s_search[1] = s_search[2] = 0;
         for (int q = 0; q < (COUNT ? 4 : 1); ++q) s_ops[q] = 0;
     }
     OpCount oc{0u, 0u, 0u, 0u};
     SearchCount sc{0u, 0u, 0u};
+    unsigned proj = 0;  // lines of the least-penetration projected problems this lane solved
     const int ntiles = (a.n + TPB - 1) / TPB;
     float4* row = s_lines + tid * kp;
     // the obstacle launch steps the listed tiles li = blockIdx.x, + gridDim.x, ...
@@ -1253,19 +1266,24 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 const bool has = q < nq;
                 const int ag = has ? s_queue[q] : 0;
                 float2 x = has ? s_x[ag] : make_float2(0.0f, 0.0f);
-                warp_lp3_units(s_wlp[WU ? tid >> 5 : 0], s_lines, ag * kp, has, has ? s_cnt[ag] : 0,
-                               has ? s_b[ag] : 0, has ? s_V[ag] : 0.0f, x.x, x.y);
+                proj += (unsigned)warp_lp3_units(s_wlp[WU ? tid >> 5 : 0], s_lines, ag * kp, has,
+                                                 has ? s_cnt[ag] : 0, has ? s_b[ag] : 0,
+                                                 has ? s_V[ag] : 0.0f, x.x, x.y);
                 if (has) s_x[ag] = x;
             }
         }
         for (int q = q0; !WU && q < nq; q += TPB / GL) {
             int ag = s_queue[q];
             float2 x = s_x[ag];
-            if (G == 1) lp3_dev(s_lines + ag * kp, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y,
-                                TAPE ? &s_tape[TAPE ? ag : 0] : nullptr, COUNT ? &oc : nullptr,
-                                OBS ? s_nob[OBS ? ag : 0] : 0);
-            else lp3_group_dev<WU ? 4 : G>(s_lines + ag * kp, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
-            if ((tid & (G - 1)) == 0) s_x[ag] = x;
+            int np;
+            if (G == 1) np = lp3_dev(s_lines + ag * kp, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y,
+                                     TAPE ? &s_tape[TAPE ? ag : 0] : nullptr, COUNT ? &oc : nullptr,
+                                     OBS ? s_nob[OBS ? ag : 0] : 0);
+            else np = lp3_group_dev<WU ? 4 : G>(s_lines + ag * kp, s_cnt[ag], s_b[ag], s_V[ag], x.x, x.y);
+            if ((tid & (G - 1)) == 0) {
+                s_x[ag] = x;
+                proj += (unsigned)np;
+            }
         }
         __syncthreads();
         // ---- phase 4: integrate
@@ -1345,6 +1363,9 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
                 if ((tid & 31) == 0 && w) atomicAdd(&s_search[q], (unsigned long long)w);
             }
             sc = SearchCount{0u, 0u, 0u};
+            const unsigned wp = __reduce_add_sync(0xffffffffu, proj);
+            if ((tid & 31) == 0 && wp) atomicAdd(&s_proj, (unsigned long long)wp);
+            proj = 0;
         }
         if (COUNT) {
             unsigned v[4] = {oc.lp1, oc.bounds, oc.checks, oc.bis};
@@ -1376,6 +1397,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
         atomicAdd(c + 2, s_cand);
         atomicAdd(c + 3, s_lines_n);
         for (int q = 0; q < 3; ++q) atomicAdd(c + 8 + q, s_search[q]);
+        atomicAdd(c + 11, s_proj);
         if (COUNT)
             for (int q = 0; q < 4; ++q) atomicAdd(c + 4 + q, s_ops[COUNT ? q : 0]);
     }
@@ -1504,13 +1526,13 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_split_
     pdl_wait();
     constexpr int KP = row_len<KMAX>();
     extern __shared__ float4 s_lines[];  // TPB rows: each lane's parking row; the leader's holds the lines
-    __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3;
+    __shared__ unsigned long long s_cand, s_lines_n, s_act, s_lp3, s_proj;
     __shared__ unsigned long long s_search[3];
     const int tid = threadIdx.x, lane = tid & 31, gq = tid & 3;
     const int lead = lane & ~3;
     const unsigned qmask = 0xfu << lead;
     if (tid == 0) {
-        s_cand = s_lines_n = s_act = s_lp3 = 0;
+        s_cand = s_lines_n = s_act = s_lp3 = s_proj = 0;
         s_search[0] = s_search[1] = s_search[2] = 0;
     }
     __syncthreads();
@@ -1519,7 +1541,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_split_
     const bool active = t < a.n;  // the same for the four lanes of a quad
     float4* row = s_lines + (tid & ~3) * KP;  // the agent's half-planes (the leader's row)
     unsigned cand = 0;
-    int cnt = 0, lp3 = 0;
+    int cnt = 0, lp3 = 0, proj = 0;
     float bx0 = INFINITY, by0 = INFINITY, bx1 = -INFINITY, by1 = -INFINITY;
     if (active) {
         SceneView sv;
@@ -1591,7 +1613,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_split_
         xx = __shfl_sync(qmask, xx, lead);
         xy = __shfl_sync(qmask, xy, lead);
         if (b < cnt) {
-            lp3_group_dev<4>(row, cnt, b, V, xx, xy);
+            proj = lp3_group_dev<4>(row, cnt, b, V, xx, xy);
             lp3 = 1;
         }
         if (gq == 0) {
@@ -1626,6 +1648,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_split_
     const unsigned wl = __reduce_add_sync(0xffffffffu, leader ? (unsigned)cnt : 0u);
     const unsigned wa = __reduce_add_sync(0xffffffffu, leader ? 1u : 0u);
     const unsigned w3 = __reduce_add_sync(0xffffffffu, leader ? (unsigned)lp3 : 0u);
+    const unsigned wp = __reduce_add_sync(0xffffffffu, leader ? (unsigned)proj : 0u);
     const unsigned v3[3] = {sc.retries, sc.cold, sc.rows};
     unsigned ws[3];
 #pragma unroll
@@ -1635,6 +1658,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_split_
         atomicAdd(&s_lines_n, (unsigned long long)wl);
         atomicAdd(&s_act, (unsigned long long)wa);
         atomicAdd(&s_lp3, (unsigned long long)w3);
+        if (wp) atomicAdd(&s_proj, (unsigned long long)wp);
         for (int q = 0; q < 3; ++q)
             if (ws[q]) atomicAdd(&s_search[q], (unsigned long long)ws[q]);
     }
@@ -1647,6 +1671,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_split_
         atomicAdd(c + 2, s_cand);
         atomicAdd(c + 3, s_lines_n);
         for (int q = 0; q < 3; ++q) atomicAdd(c + 8 + q, s_search[q]);
+        atomicAdd(c + 11, s_proj);
     }
 }
 

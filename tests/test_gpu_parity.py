@@ -294,7 +294,8 @@ def test_counters():
 @pytest.mark.parametrize("scene", ["flow", "dense20", "circle"])
 def test_lp_modes_agree_bitwise(scene):
     # one lane per agent, the agent split and warp work units take the same decisions
-    # with the same roundings: identical states after several steps
+    # with the same roundings: identical states after several steps, and the same
+    # least-penetration work (the lines of the projected problems each mode solved)
     if scene == "flow":
         sc = S.jitter_velocities(S.bidirectional(8190, seed=17), 17)
     elif scene == "dense20":
@@ -303,18 +304,21 @@ def test_lp_modes_agree_bitwise(scene):
         sc = S.jitter_velocities(sc, 18)
     else:
         sc = S.circle_swap()
-    states = {}
+    states, work = {}, {}
     for tpb, lanes in ((64, 1), (64, 4), (128, 4), (64, 32), (256, 32)):
         sim = parity.make_sim(sc, flags=0)
         abi.orca_set_launch(sim.ctx, tpb, lanes)
         sim.set_scene(sc)
         sim.step(12)
         states[(tpb, lanes)] = sim.get_state()
+        work[(tpb, lanes)] = sim.search_counters()["lp3_problem_lines"]
         sim.close()
     ref = states[(64, 1)]
     for key, (pos, vel) in states.items():
         np.testing.assert_array_equal(pos, ref[0], err_msg=str(key))
         np.testing.assert_array_equal(vel, ref[1], err_msg=str(key))
+        assert work[key] == work[(64, 1)], (key, work)
+    assert scene == "circle" or work[(64, 1)] > 0
 
 
 @pytest.mark.parametrize("scene,tpb", [("two_way", 64), ("eight_way", 128), ("dense20", 64)])
@@ -348,9 +352,14 @@ def test_operation_counts_match_the_oracle():
     abi.orca_count_ops(sim.ctx, True)
     sim.step(1)
     ops, c = sim.op_counters(), sim.counters()
+    plines = sim.search_counters()["lp3_problem_lines"]
     pos, vel = sim.get_state()
     sim.close()
     assert c["lines"] == ref["lines"]
+    # every step counts the lines of the least-penetration projected problems
+    assert ref["lp3_problem_lines"] > 0
+    assert abs(plines - ref["lp3_problem_lines"]) <= 0.01 * ref["lp3_problem_lines"], \
+        (plines, ref["lp3_problem_lines"])
     assert abs(c["lp3_agent_steps"] - ref["lp3_agents"]) <= 0.002 * sc.n
     for key in ("lp1_calls", "lp1_bounds", "lp_checks", "bisectors"):
         assert ref[key] > 0
