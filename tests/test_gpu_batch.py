@@ -94,11 +94,15 @@ def test_small_batch_after_steps():
 
 
 def test_scene_in_batch_equals_scene_alone_bitwise():
+    # the same states, and so the same least-penetration work: the batch's count of
+    # projected-problem lines is the sum of the scenes' counts stepped alone
     batch = small_batch(seed=9)
     sim = run_batch(batch, flags=0)
     sim.step(20)
     pos, vel = sim.get_state()
+    batch_work = sim.search_counters()["lp3_problem_lines"]
     off = batch.offsets
+    alone_work = 0
     for s, sc in enumerate(batch.scenes):
         if sc.n == 0:
             continue
@@ -106,9 +110,11 @@ def test_scene_in_batch_equals_scene_alone_bitwise():
         alone.set_scene(sc)
         alone.step(20)
         p1, v1 = alone.get_state()
+        alone_work += alone.search_counters()["lp3_problem_lines"]
         alone.close()
         np.testing.assert_array_equal(pos[off[s]:off[s + 1]], p1)
         np.testing.assert_array_equal(vel[off[s]:off[s + 1]], v1)
+    assert batch_work == alone_work > 0
 
 
 def test_batch_state_update_rescans_the_boxes_bitwise():
