@@ -1155,7 +1155,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_main_k
             V = a.prm.max_speed[t];
             float lim0 = __int_as_float(0x7fffffff);
             if (a.prm.hint) {
-                float hd = sqrtf(a.prm.hint[t]) * (1.0f + 1e-3f) + 3.0f * V * dt + 1e-3f;
+                float hd = sqrtf(a.prm.hint[t]) * (1.0f + 1e-3f) + 2.5f * V * dt + 1e-3f;
                 lim0 = hd * hd;
             }
             unsigned long long kk[KMAX];
@@ -1553,7 +1553,7 @@ __global__ void __launch_bounds__(TPB, main_min_blocks<KMAX, TPB>()) orca_split_
         const float V = a.prm.max_speed[t];
         float lim0 = __int_as_float(0x7fffffff);
         if (a.prm.hint) {
-            const float hd = sqrtf(a.prm.hint[t]) * (1.0f + 1e-3f) + 3.0f * V * dt + 1e-3f;
+            const float hd = sqrtf(a.prm.hint[t]) * (1.0f + 1e-3f) + 2.5f * V * dt + 1e-3f;
             lim0 = hd * hd;
         }
         unsigned long long kk[KMAX];
